@@ -1,0 +1,507 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself:
+printed tables of the paper, closed forms, invariants, brute force and dense algebra.
+
+Each test names the passage it checks.  None of these needs a GPU.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import hz_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------------------
+# helpers: an independent dense construction of the operator (Kronecker sums)
+# ---------------------------------------------------------------------------------------
+
+def lap1d(n, h):
+    return sp.diags([-np.ones(n - 1), 2.0 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]) / (h * h)
+
+
+def dense_laplacian(nx, ny, nz, h):
+    """7-point Dirichlet -Delta_h as a Kronecker sum, x fastest (index i + nx(j + ny k))."""
+    Ix, Iy, Iz = sp.identity(nx), sp.identity(ny), sp.identity(nz)
+    L = (sp.kron(Iz, sp.kron(Iy, lap1d(nx, h))) + sp.kron(Iz, sp.kron(lap1d(ny, h), Ix))
+         + sp.kron(lap1d(nz, h), sp.kron(Iy, Ix)))
+    return L.toarray()
+
+
+def dense_operator(op):
+    L = dense_laplacian(op.nx, op.ny, op.nz, op.h)
+    return op.s * L - np.diag(op.m.ravel()) - 1j * np.diag(op.a.ravel())
+
+
+def tiny_operator(seed=5, nx=5, ny=4, nz=6, layer=1, ppw=6.0, medium="bumps"):
+    wl = W.small_case(seed, nx, ny, nz, ppw=ppw, layer=layer, medium=medium)
+    return O.make_operator(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max), wl
+
+
+def sine_mode(nx, ny, nz, kx, ky, kz):
+    i = np.arange(1, nx + 1)
+    j = np.arange(1, ny + 1)
+    k = np.arange(1, nz + 1)
+    vx = np.sin(kx * math.pi * i / (nx + 1))
+    vy = np.sin(ky * math.pi * j / (ny + 1))
+    vz = np.sin(kz * math.pi * k / (nz + 1))
+    return (vz[:, None, None] * vy[None, :, None] * vx[None, None, :]).astype(np.complex128)
+
+
+def sine_eig(n, k, h):
+    return 4.0 / (h * h) * math.sin(k * math.pi / (2.0 * (n + 1))) ** 2
+
+
+def constant_operator(nx, ny, nz, h, omega):
+    c = np.ones((nz, ny, nx))
+    return O.make_operator(c, h, omega, 0, 0.0)
+
+
+def read_golden(name):
+    meta, rows = {}, []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            parts = line.split()
+            try:
+                rows.append([float(p) for p in parts])
+            except ValueError:
+                meta[parts[0]] = [float(p) for p in parts[1:]]
+    return meta, rows
+
+
+# ---------------------------------------------------------------------------------------
+# operator (§7.1)
+# ---------------------------------------------------------------------------------------
+
+def test_stencil_matches_kronecker_sum():
+    """(A - zI)x by the slicing stencil equals the dense Kronecker-sum matrix (§7.1)."""
+    op, _ = tiny_operator(nx=5, ny=4, nz=6, layer=2)
+    A = dense_operator(op)
+    g = np.random.default_rng(0)
+    x = g.standard_normal(op.n) + 1j * g.standard_normal(op.n)
+    z = 0.3 - 1.7j
+    ref = A @ x - z * x
+    got = op.apply(x.reshape(op.shape), z).ravel()
+    assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("shape,modes", [((7, 5, 6), [(1, 1, 1), (3, 2, 5), (7, 5, 6)]),
+                                         ((16, 16, 16), [(1, 2, 3), (16, 1, 9)])])
+def test_stencil_sine_modes(shape, modes):
+    """P1: c const and no layer: the sine modes are exact eigenvectors, A v = (s lam_k - 1) v."""
+    nx, ny, nz = shape
+    h = 1.0 / (max(shape) + 1)
+    omega = 2 * math.pi / (8 * h)
+    op = constant_operator(nx, ny, nz, h, omega)
+    for kx, ky, kz in modes:
+        v = sine_mode(nx, ny, nz, kx, ky, kz)
+        lam = sine_eig(nx, kx, h) + sine_eig(ny, ky, h) + sine_eig(nz, kz, h)
+        mu = op.s * lam - 1.0
+        got = op.apply(v)
+        assert np.linalg.norm(got - mu * v) <= 1e-13 * max(1.0, abs(mu)) * np.linalg.norm(v)
+
+
+def test_sponge_profile_values():
+    """Sponge depth: layer cells at the outermost point, 0 in the core, max over axes."""
+    d = O.sponge_depth(6, 1, 1, 2)
+    assert d[0, 0].tolist() == [2, 1, 0, 0, 1, 2] or d.shape == (1, 1, 6)
+    # with one point along y and z the y/z depth is the full layer everywhere
+    d = O.sponge_depth(6, 8, 8, 2)
+    assert d[3, 3].tolist() == [2, 1, 0, 0, 1, 2]
+    assert d[0, 3, 3] == 2 and d[1, 3, 3] == 1 and d[2, 3, 3] == 0
+    op, _ = tiny_operator(nx=8, ny=8, nz=8, layer=2, medium="const")
+    # corner: a = sigma_max * m; core: 0
+    assert op.a[0, 0, 0] == pytest.approx(1.0 * op.m[0, 0, 0])
+    assert op.a[4, 4, 4] == 0.0
+    assert op.a[1, 4, 4] == pytest.approx(0.25 * op.m[1, 4, 4])
+
+
+def test_scaling_matches_physical_operator():
+    """A = s(-Delta_h - omega^2/c^2) - i a with s = c_min^2/omega^2 (normalisation of §7.1)."""
+    op, wl = tiny_operator(nx=4, ny=5, nz=3, layer=0)
+    L = dense_laplacian(op.nx, op.ny, op.nz, op.h)
+    phys = L - np.diag((wl.omega ** 2 / wl.c ** 2).ravel())
+    A = dense_operator(op)
+    s = wl.c.min() ** 2 / wl.omega ** 2
+    assert np.allclose(A, s * phys, rtol=0, atol=1e-12 * np.abs(A).max())
+    assert op.m.max() == pytest.approx(1.0) and op.m.min() > 0
+
+
+# ---------------------------------------------------------------------------------------
+# spectrum (§3 Lemma 3.1) and contour (§6)
+# ---------------------------------------------------------------------------------------
+
+def test_laplacian_extremes_exact():
+    for shape in [(3, 4, 5), (6, 6, 6), (1, 2, 7)]:
+        h = 0.13
+        ev = np.linalg.eigvalsh(dense_laplacian(*shape, h))
+        lo, hi = O.laplacian_extremes(*shape, h)
+        assert lo == pytest.approx(ev[0], rel=1e-12)
+        assert hi == pytest.approx(ev[-1], rel=1e-12)
+
+
+@pytest.mark.parametrize("seed,shape,layer", [(1, (5, 4, 6), 1), (2, (6, 6, 6), 2), (3, (7, 3, 4), 1)])
+def test_spectrum_inside_box(seed, shape, layer):
+    """P10: every eigenvalue of A lies in B = [b1, b2] x [-rho2, 0] (Lemma 3.1), and B's
+    real interval sits inside the Lemma's [-1, rho1 - 1]."""
+    op, _ = tiny_operator(seed=seed, nx=shape[0], ny=shape[1], nz=shape[2], layer=layer)
+    ev = np.linalg.eigvals(dense_operator(op))
+    b1, b2, rho2 = O.spectrum_box(op)
+    tol = 1e-10 * max(abs(b1), abs(b2))
+    assert np.all(ev.real >= b1 - tol) and np.all(ev.real <= b2 + tol)
+    assert np.all(ev.imag <= tol) and np.all(ev.imag >= -rho2 - tol)
+    assert b1 >= -1.0 - 1e-12
+    assert rho2 > 0
+    # some eigenvalue is strictly damped
+    assert ev.imag.min() < -1e-6
+
+
+def test_contour_nodes_paper_sets():
+    """P5: the four node sets printed in §7.3 follow from eq:quad-points (J=6, t=0.1)."""
+    meta, rows = read_golden("quad_points_scaling.txt")
+    J, t, rho2 = int(meta["J"][0]), meta["t"][0], meta["rho2"][0]
+    for setno in sorted({int(r[0]) for r in rows}):
+        sel = [r for r in rows if int(r[0]) == setno]
+        eps = sel[0][1]
+        z, _ = O.contour_nodes(J, t, eps, rho2)
+        for r in sel:
+            j = int(r[2]) - 1
+            assert abs(z[j].real - r[3]) <= 0.015, (setno, j, z[j])
+            assert abs(z[j].imag - r[4]) <= 0.015, (setno, j, z[j])
+
+
+@pytest.mark.parametrize("J,t,eps,rho2", [(4, 1.0, 1.0, 1.0), (8, 1.0, 0.5, 0.7), (6, 0.3, 0.2, 1.3)])
+def test_contour_invariants(J, t, eps, rho2):
+    """§6.2: Re z_j <= 0 and Im z_j outside (-eps - rho2, eps); the weights integrate dz/z."""
+    z, sigma = O.contour_nodes(J, t, eps, rho2)
+    assert np.all(z.real <= 1e-14)
+    assert np.all((z.imag >= eps - 1e-12) | (z.imag <= -eps - rho2 + 1e-12))
+    # the nodes are the trapezoid rule on the ellipse through them: with many nodes on
+    # that fixed ellipse, (1/2 pi i) \oint dz/z -> 1 (origin inside), \oint dz = \oint z dz = 0
+    phi = math.pi / J
+    r = (rho2 / 2 + eps) / math.sin(phi)
+    centre = complex(-t * r * math.cos(phi), -rho2 / 2)
+    zz, ss = O.ellipse_quadrature(centre, r, t, 2048, phi)
+    assert abs(np.sum(ss / zz) - 1.0) < 1e-9
+    assert abs(np.sum(ss)) < 1e-12 and abs(np.sum(ss * zz)) < 1e-10
+    zj, sj = O.ellipse_quadrature(centre, r, t, J, phi)
+    assert np.allclose(zj, z, atol=1e-13) and np.allclose(sj, sigma, atol=1e-13)
+
+
+def test_quadrature_converges_to_projector():
+    """P4: sum sigma_j/z_j (A - z_j)^{-1} -> P A^{-1} (eq:rational), with P the spectral
+    projector on the eigenvalues outside the contour (eq:eigenprojector); P^2 = P,
+    AP = PA, and P_in + P_out = I."""
+    op, _ = tiny_operator(seed=2, nx=3, ny=4, nz=3, layer=1, ppw=4.0)
+    A = dense_operator(op)
+    b1, b2, rho2 = O.spectrum_box(op)
+    ev, X = np.linalg.eig(A)
+    Xi = np.linalg.inv(X)
+    # a fixed circle around the lower-left part of the spectrum (origin inside), its radius
+    # in the widest gap of |lambda - centre|, so the trapezoid rule converges fast
+    t = 1.0
+    centre = complex(-0.6, -rho2 / 2)
+    dd = np.sort(np.abs(ev - centre))
+    ok = (dd[:-1] > 0.6) & (dd[1:] < 4.0)
+    k = int(np.argmax(np.diff(dd) * ok))
+    r = 0.5 * (dd[k] + dd[k + 1])
+    assert dd[k + 1] - dd[k] > 0.2
+    z, sigma = O.ellipse_quadrature(centre, r, t, 256, 0.1)
+    inside = np.abs(ev - centre) < r
+    dist = np.min(np.abs(np.abs(ev - centre) - r))
+    assert dist > 0.05 and inside.any() and (~inside).any()
+    P = (X * (~inside)) @ Xi
+    PAinv = (X * np.where(inside, 0.0, 1.0 / ev)) @ Xi
+    Q = O.quadrature_resolvent_sum(A, z, sigma)
+    assert np.linalg.norm(Q - PAinv) <= 1e-9 * np.linalg.norm(PAinv)
+    n = A.shape[0]
+    eye = np.eye(n)
+    Pout = sum((sj / zj) * np.linalg.inv(eye - zj * np.linalg.inv(A)) for zj, sj in zip(z, sigma))
+    Pin = sum(sj * np.linalg.inv(zj * eye - A) for zj, sj in zip(z, sigma))
+    assert np.linalg.norm(Pout - P) <= 1e-9 * np.linalg.norm(P)
+    assert np.linalg.norm(Pin + Pout - eye) <= 1e-9 * math.sqrt(n)
+    assert np.linalg.norm(Pout @ Pout - Pout) <= 1e-8 * np.linalg.norm(Pout)
+    assert np.linalg.norm(A @ Pout - Pout @ A) <= 1e-8 * np.linalg.norm(A)
+    # few nodes: the quadrature is only an approximation, but still a convergent one
+    errs = []
+    for JJ in (8, 16, 32, 64):
+        zz, ss = O.ellipse_quadrature(centre, r, t, JJ, 0.1)
+        errs.append(np.linalg.norm(O.quadrature_resolvent_sum(A, zz, ss) - PAinv))
+    assert errs[-1] < errs[0]
+
+
+# ---------------------------------------------------------------------------------------
+# polynomial parameters (§4.1 Theorem 4.1, §4.2 tables)
+# ---------------------------------------------------------------------------------------
+
+def test_rate_table_at_printed_delta():
+    """P6a: nu at the printed delta* reproduces Table tab:exp-rate-order within 0.003."""
+    meta, rows = read_golden("exp_rate_order.txt")
+    b1, b2, rho2 = meta["b1"][0], meta["b2"][0], meta["rho2"][0]
+    z = complex(meta["z_re"][0], meta["z_im"][0])
+    z0 = complex(0.5 * (b1 + b2), z.imag)
+    bd = O.box_boundary(b1, b2, rho2)
+    for q, dstar, nu_p, nuq_p in rows:
+        nu = O.nu_of(int(q), dstar, z, z0, bd)
+        assert abs(nu - nu_p) <= 0.003, (q, nu, nu_p)
+        assert abs(nu ** (1.0 / q) - nuq_p) <= 0.003
+
+
+def test_rate_table_optimizer():
+    """P6b: the delta search finds nu no worse than the printed optimum (+0.002)."""
+    meta, rows = read_golden("exp_rate_order.txt")
+    b1, b2, rho2 = meta["b1"][0], meta["b2"][0], meta["rho2"][0]
+    z = complex(meta["z_re"][0], meta["z_im"][0])
+    z0 = complex(0.5 * (b1 + b2), z.imag)
+    bd = O.box_boundary(b1, b2, rho2)
+    for q, dstar, nu_p, _ in rows:
+        delta, nu = O.optimize_delta(int(q), z, z0, bd)
+        assert delta > 0
+        assert nu <= nu_p + 0.002, (q, delta, nu, nu_p)
+        assert abs(delta - dstar) < 0.1
+
+
+@pytest.mark.parametrize("zim", [1.0, 0.5, 0.25, 0.125])
+def test_richardson_closed_form(zim):
+    """Theorem 4.1: for q = 1 the optimal rate is |a1 - a2| / (|a1| + |a2|), a = (b1-z, b2-z)."""
+    b1, b2, rho2 = -1.0, 2.8, 0.65
+    z = complex(0.0, zim)
+    z0 = complex(0.5 * (b1 + b2), zim)
+    _, nu = O.optimize_delta(1, z, z0, O.box_boundary(b1, b2, rho2))
+    a1, a2 = b1 - z, b2 - z
+    closed = abs(a1 - a2) / (abs(a1) + abs(a2))
+    assert nu == pytest.approx(closed, abs=2e-6)
+
+
+def test_nmatvec_table():
+    """P6c: q*ceil(ln 100 / -ln nu) reproduces Table tab:exp-nmatvec: 16 of 20 entries
+    exactly, all within 10%, and never more than 2% above the printed count (where the
+    finer delta search finds a better optimum than the paper's, the count is lower)."""
+    meta, rows = read_golden("exp_nmatvec.txt")
+    b1, b2, rho2 = meta["b1"][0], meta["b2"][0], meta["rho2"][0]
+    zims = meta["zim"]
+    bd = O.box_boundary(b1, b2, rho2)
+    exact = 0
+    for row in rows:
+        q = int(row[0])
+        for zim, printed in zip(zims, row[1:]):
+            z = complex(0.0, zim)
+            z0 = complex(0.5 * (b1 + b2), zim)
+            _, nu = O.optimize_delta(q, z, z0, bd)
+            mvs = q * math.ceil(math.log(100.0) / -math.log(nu))
+            assert abs(mvs - printed) <= 0.1 * printed, (q, zim, mvs, printed)
+            assert mvs <= 1.02 * printed
+            exact += int(mvs == printed)
+    assert exact >= 16
+
+
+def test_node_parameters_rule():
+    """Sweeps = ceil(ln 5 / -ln nu); the chosen q has the fewest matvecs q*sweeps."""
+    b1, b2, rho2 = -0.93, 29.3, 1.0
+    for z in [1j, -3 + 1j, -3 - 2j, -2j]:
+        p = O.node_parameters(complex(z), 0.1, b1, b2, rho2)
+        assert p.sweeps == math.ceil(math.log(5.0) / -math.log(p.nu))
+        assert p.nu < 1 and (p.delta > 0) == (complex(z).imag > 0)
+        bd = O.box_boundary(b1, b2, rho2)
+        for q in range(1, 6):
+            _, nu = O.optimize_delta(q, complex(z), p.z0, bd)
+            if nu < 1:
+                assert q * math.ceil(math.log(5.0) / -math.log(nu)) >= p.q * p.sweeps
+
+
+# ---------------------------------------------------------------------------------------
+# polynomial fixed-point iteration (§4.2 eq:fix-pt-exp, Theorem 4.2)
+# ---------------------------------------------------------------------------------------
+
+def _node(z, b1, b2, rho2, q=None, sweeps=None):
+    p = O.node_parameters(complex(z), 0.0, b1, b2, rho2)
+    if q is not None:
+        z0 = p.z0
+        delta, nu = O.optimize_delta(q, complex(z), z0, O.box_boundary(b1, b2, rho2))
+        p = O.NodeParams(complex(z), 0.0, z0, delta, q, nu, sweeps or 3)
+    return p
+
+
+@pytest.mark.parametrize("q,sweeps", [(1, 4), (2, 3), (3, 5), (5, 2)])
+def test_poly_sine_mode_closed_form(q, sweeps):
+    """P2: on an eigenvector v (eigenvalue mu) from y0 = 0, m sweeps give
+    y = (1 - R^m) v / (mu - z) with R = ptilde(mu)/ptilde(z) (Theorem 4.2)."""
+    nx, ny, nz = 7, 6, 5
+    h = 1.0 / 8
+    op = constant_operator(nx, ny, nz, h, 2 * math.pi / (6 * h))
+    b1, b2, rho2 = O.spectrum_box(op)
+    rho2 = 0.5  # any box containing the (real) spectrum
+    for z in [0.7j, -1.5 - 2.0j]:
+        nd = _node(z, b1, b2, rho2, q=q, sweeps=sweeps)
+        v = sine_mode(nx, ny, nz, 2, 3, 1)
+        mu = op.s * (sine_eig(nx, 2, h) + sine_eig(ny, 3, h) + sine_eig(nz, 1, h)) - 1.0
+        y = O.poly_solve(op, v, nd)
+        R = complex(O.ptilde(mu, q, nd.delta, nd.z0) / O.ptilde(nd.z, q, nd.delta, nd.z0))
+        ref = (1.0 - R ** sweeps) / (mu - nd.z) * v
+        assert np.linalg.norm(y - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("q", [1, 2, 3, 4])
+def test_poly_error_propagation(q):
+    """P3: y^(m) - y = (ptilde(A)/ptilde(z))^m (y^(0) - y) for a general (damped,
+    variable-coefficient) A (Theorem 4.2), with y from dense LU."""
+    op, _ = tiny_operator(seed=21, nx=4, ny=5, nz=3, layer=1)
+    A = dense_operator(op)
+    n = op.n
+    b1, b2, rho2 = O.spectrum_box(op)
+    nd = _node(0.8j, b1, b2, rho2, q=q, sweeps=3)
+    g = np.random.default_rng(q)
+    f = g.standard_normal(n) + 1j * g.standard_normal(n)
+    y0 = g.standard_normal(n) + 1j * g.standard_normal(n)
+    ystar = np.linalg.solve(A - nd.z * np.eye(n), f)
+    got = O.poly_solve(op, f.reshape(op.shape), nd, y0=y0.reshape(op.shape)).ravel()
+    U = -1j * nd.delta * (A - nd.z0 * np.eye(n))
+    pA = np.eye(n, dtype=complex)
+    term = np.eye(n, dtype=complex)
+    for j in range(1, q + 1):
+        term = term @ U / j
+        pA = pA + term
+    pz = complex(O.ptilde(nd.z, q, nd.delta, nd.z0))
+    E = np.linalg.matrix_power(pA / pz, 3)
+    ref = ystar + E @ (y0 - ystar)
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+    # the exact solution is a fixed point
+    fixed = O.poly_solve(op, f.reshape(op.shape), nd, sweeps=1, y0=ystar.reshape(op.shape)).ravel()
+    assert np.linalg.norm(fixed - ystar) <= 1e-11 * np.linalg.norm(ystar)
+
+
+# ---------------------------------------------------------------------------------------
+# GMRES pieces, FCI (Algorithm 1), FGMRES
+# ---------------------------------------------------------------------------------------
+
+def test_gmres_is_krylov_least_squares():
+    """P8: one GMRES(k) cycle reaches min ||b - A x|| over the Krylov space K_k (brute
+    force by QR of the Krylov matrix), its Givens estimate equals the true residual, and
+    the CGS2 basis is orthonormal."""
+    op, _ = tiny_operator(seed=8, nx=4, ny=4, nz=4, layer=1)
+    A = dense_operator(op)
+    g = np.random.default_rng(3)
+    b = (g.standard_normal(op.n) + 1j * g.standard_normal(op.n)).reshape(op.shape)
+    for k in (1, 3, 6):
+        x, est = O.gmres_cycle(op.apply, b, k)
+        K = np.empty((op.n, k), dtype=complex)
+        v = b.ravel() / np.linalg.norm(b)
+        for j in range(k):
+            K[:, j] = v
+            v = A @ v
+            v /= np.linalg.norm(v)
+        Q, _ = np.linalg.qr(K)
+        c, *_ = np.linalg.lstsq(A @ Q, b.ravel(), rcond=None)
+        best = np.linalg.norm(b.ravel() - A @ (Q @ c))
+        true = np.linalg.norm(b.ravel() - A @ x.ravel())
+        assert true == pytest.approx(best, rel=1e-10)
+        assert est == pytest.approx(true, rel=1e-9)
+    V = [b / np.linalg.norm(b)]
+    for _ in range(5):
+        w, _h = O.cgs2(V, op.apply(V[-1]))
+        V.append(w / np.linalg.norm(w))
+    G = np.array([[np.vdot(a, c) for c in V] for a in V])
+    assert np.abs(G - np.eye(len(V))).max() < 1e-13
+
+
+def test_givens_rotation():
+    for a, b in [(1 + 2j, 3.0), (-0.5j, 0.25), (0j, 1.0), (2.0, 0.0)]:
+        c, s = O.givens(complex(a), b)
+        r = c * a + s * b
+        assert abs(-np.conj(s) * a + c * b) < 1e-15
+        assert abs(abs(r) - math.hypot(abs(a), b)) < 1e-14
+        assert abs(c * c + abs(s) ** 2 - 1.0) < 1e-14
+
+
+def test_fci_on_eigenvector_is_exact():
+    """P7: Algorithm 1 on an eigenvector v returns v/mu exactly: the step d absorbs every
+    quadrature and polynomial error and the inner residual is zero."""
+    nx, ny, nz = 6, 5, 7
+    h = 1.0 / 8
+    op = constant_operator(nx, ny, nz, h, 2 * math.pi / (6 * h))
+    b1, b2, _ = O.spectrum_box(op)
+    rho2 = 0.5
+    z, sigma = O.contour_nodes(4, 1.0, 0.5, rho2)
+    nodes = [O.node_parameters(zj, sj, b1, b2, rho2) for zj, sj in zip(z, sigma)]
+    v = sine_mode(nx, ny, nz, 3, 1, 2)
+    mu = op.s * (sine_eig(nx, 3, h) + sine_eig(ny, 1, h) + sine_eig(nz, 2, h)) - 1.0
+    out = O.fci(op, v, nodes, k_in=3)
+    assert np.linalg.norm(out - v / mu) <= 1e-12 * np.linalg.norm(v / mu)
+
+
+def test_fci_step_size_is_least_squares():
+    """Algorithm 1 step 3: d minimises ||r - d A w||; check against lstsq on one column and
+    that the inner GMRES starts from the orthogonal residual."""
+    op, _ = tiny_operator(seed=4, nx=4, ny=5, nz=4, layer=1)
+    (b1, b2, rho2), nodes = O.setup_nodes(op, 4, 1.0, 1.0)
+    g = np.random.default_rng(9)
+    r = (g.standard_normal(op.n) + 1j * g.standard_normal(op.n)).reshape(op.shape)
+    w = sum((nd.sigma / nd.z) * O.poly_solve(op, r, nd) for nd in nodes)
+    Aw = op.apply(w).ravel()
+    d_ls = np.linalg.lstsq(Aw[:, None], r.ravel(), rcond=None)[0][0]
+    d = np.vdot(Aw, r.ravel()) / np.vdot(Aw, Aw)
+    assert d == pytest.approx(d_ls, rel=1e-12)
+    # with k_in = 0 inner steps the FCI output is exactly d w
+    out0 = O.fci(op, r, nodes, k_in=0)
+    assert np.linalg.norm(out0 - d * w) <= 1e-13 * np.linalg.norm(d * w)
+
+
+def test_fci_with_exact_solves_and_many_nodes():
+    """With exact shifted solves and J large, w -> P A^{-1} r (eq:rational), so the FCI
+    residual lives on the eigenvalues inside the contour only."""
+    op, _ = tiny_operator(seed=2, nx=3, ny=4, nz=3, layer=1, ppw=4.0)
+    A = dense_operator(op)
+    b1, b2, rho2 = O.spectrum_box(op)
+    z, sigma = O.ellipse_quadrature(complex(-0.6, -rho2 / 2), 1.2512, 1.0, 128, 0.1)
+    nodes = [O.NodeParams(zj, sj, 0j, 0.0, 1, 0.5, 1) for zj, sj in zip(z, sigma)]
+    exact = lambda nd, r: np.linalg.solve(A - nd.z * np.eye(op.n), r.ravel()).reshape(op.shape)
+    g = np.random.default_rng(2)
+    r = (g.standard_normal(op.n) + 1j * g.standard_normal(op.n)).reshape(op.shape)
+    w = sum((nd.sigma / nd.z) * exact(nd, r) for nd in nodes)
+    Q = O.quadrature_resolvent_sum(A, z, sigma)
+    assert np.linalg.norm(w.ravel() - Q @ r.ravel()) <= 1e-12 * np.linalg.norm(w)
+    out = O.fci(op, r, nodes, k_in=op.n, shifted_solve=exact)
+    # k_in = n inner GMRES steps solve the rest exactly
+    assert np.linalg.norm(A @ out.ravel() - r.ravel()) <= 1e-8 * np.linalg.norm(r)
+
+
+@pytest.mark.parametrize("shape,layer,J", [((6, 6, 6), 2, 4), ((5, 7, 6), 1, 8)])
+def test_fgmres_matches_dense_lu(shape, layer, J):
+    """P9: FGMRES(m) with the FCI preconditioner reaches a true relative residual <= 1e-8
+    and agrees with the dense LU solution within kappa_2(A) * 1e-8."""
+    op, wl = tiny_operator(seed=31, nx=shape[0], ny=shape[1], nz=shape[2], layer=layer, ppw=5.0)
+    (b1, b2, rho2), nodes = O.setup_nodes(op, J, 1.0, 1.0)
+    A = dense_operator(op)
+    f = wl.f[0]
+    res = O.solve(op, f, nodes, m=10, k_in=3, rtol=1e-8, max_cycles=30)
+    assert res.converged and res.rel_res_true <= 1e-8
+    u = np.linalg.solve(A, f.ravel())
+    kappa = np.linalg.cond(A)
+    err = np.linalg.norm(res.u.ravel() - u) / np.linalg.norm(u)
+    assert err <= kappa * 1e-8
+    assert np.linalg.norm(A @ res.u.ravel() - f.ravel()) <= 1e-8 * np.linalg.norm(f)
+
+
+def test_fgmres_fixed_iterations_mode():
+    """fixed_its counts Arnoldi steps exactly, across restarts, ignoring rtol."""
+    op, wl = tiny_operator(seed=2, nx=5, ny=5, nz=5, layer=1)
+    (_, _, _), nodes = O.setup_nodes(op, 4, 1.0, 1.0)
+    res = O.solve(op, wl.f[0], nodes, m=3, k_in=2, rtol=1e-30, max_cycles=100, fixed_its=7)
+    assert res.its == 7 and res.cycles == 3
+
+
+def test_precond_identity_gives_gmres():
+    """With the identity as preconditioner FGMRES(m) is GMRES(m): compare one cycle with
+    the Krylov least-squares minimum."""
+    op, wl = tiny_operator(seed=6, nx=4, ny=4, nz=4, layer=1)
+    f = wl.f[0]
+    res = O.fgmres(op, f, lambda v: v, m=5, rtol=1e-30, max_cycles=1)
+    x, _ = O.gmres_cycle(op.apply, f, 5)
+    assert np.linalg.norm(res.u - x) <= 1e-12 * np.linalg.norm(x)
