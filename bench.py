@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 contour-integral Helmholtz solver.
+
+Metric: right-hand sides per second solved to a relative residual of 1e-8 (float64 true
+residual), for the 64^3 Gaussian-bump workload (8 bumps, c in [1, 2], 8 points per wavelength
+at c_min, 8-cell sponge, one Gaussian source, J = 8 contour nodes, FGMRES(30) with FCI and 4
+inner GMRES steps).  One step = one full solve of that right-hand side.  `value` is the chosen
+(mixed-precision) form; the plain all-float64 form is reported beside it.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank solves its own copy of the workload (replicas, weak
+scaling, no data-path collective); value = all ranks' right-hand sides / max rank time.
+--impl reference times the CPU oracle (complex128 numpy) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RHS/s to rel. residual 1e-8, plain vs chosen form; stencil HBM GB/s"
+WORKLOAD = ("gaussian_bumps_64: 64^3 grid (h=1/65), c = 1 + 8 seeded Gaussian bumps (width 0.1, "
+            "amplitudes U[0,0.4]) clipped to [1,2], 8 ppw at c_min, 8-cell sponge, Gaussian "
+            "source sigma=2h, J=8 contour nodes, FGMRES(30) + FCI with 4 inner GMRES steps, "
+            "rtol 1e-8 on the float64 true residual")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_counts():
+    with open(os.path.join(ROOT, "oracle", "reference_counts.json")) as fh:
+        return json.load(fh)
+
+
+def time_oracle_sample(wl, outer_steps: int):
+    """Seconds for `outer_steps` outer FGMRES steps of the oracle on this workload (plus the
+    time per step), with the thread count numpy's BLAS uses."""
+    from oracle import hz_oracle as O
+    op = O.make_operator(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max)
+    _, nodes = O.setup_nodes(op, wl.J, wl.t, wl.eps)
+    t0 = time.perf_counter()
+    O.solve(op, op.s * wl.f[0], nodes, wl.restart, wl.k_in, 1e-30, 1, fixed_its=outer_steps)
+    return time.perf_counter() - t0
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+        return int(n)
+    except Exception:
+        return 1
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import workloads as W
+    wl = W.gaussian_bumps_64()
+    its = oracle_counts()[wl.name]["its"]
+    per = 1  # outer FGMRES steps per timed sample
+    for _ in range(args.warmup):
+        time_oracle_sample(wl, per)
+    tt = [time_oracle_sample(wl, per) for _ in range(args.steps)]
+    step_s = sum(tt) / len(tt)
+    value = 1.0 / (step_s / per * its)
+    sample = (f"{per} outer FGMRES step (FCI with {oracle_counts()[wl.name]['poly_matvecs_per_fci']}"
+              f" polynomial-sweep matvecs + inner GMRES + CGS2) of the oracle per timed step, "
+              f"scaled by the oracle's {its} steps to 1e-8")
+    cores = cpu_threads()
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "form": "oracle complex128"},
+        "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def traffic_from_profile(kernel_src_hash: str):
+    """DRAM bytes per launch of the polynomial-stage kernel from the committed ncu summary,
+    or None if the summary is missing or was taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "poly_stage_gaussian_bumps_64.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for ln in open(path):
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256") != kernel_src_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1811_12378_gb300", "csrc", "hz_kernels.cu"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1811_12378_gb300 as hz
+    import workloads as W
+
+    rank, local, world = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = W.gaussian_bumps_64()
+    P = hz.Problem(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, wl.J, wl.t, wl.eps,
+                   nrhs_max=1, restart_max=wl.restart, inner_k_max=wl.k_in)
+    n = P.n
+    f_host = torch.from_numpy(wl.f.reshape(1, n).copy()).pin_memory()
+    f_dev = f_host.to(dev)
+    u_dev = torch.empty_like(f_dev)
+    u_host = torch.empty_like(f_host).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    kw = dict(restart=wl.restart, inner_k=wl.k_in, rtol=wl.rtol, max_cycles=20)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    def timed(form, k, e2e=False):
+        """Device time of k solves (events on the launching stream, L2 flushed between)."""
+        total = 0.0
+        stats = None
+        for _ in range(k):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if e2e:
+                f_dev.copy_(f_host, non_blocking=True)
+            _, stats = P.solve(f_dev, out=u_dev, precision=form, **kw)
+            if e2e:
+                u_host.copy_(u_dev, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1) / 1e3
+        return total, stats[0]
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # warm-up (both forms)
+    for _ in range(max(args.warmup, 3)):
+        P.solve(f_dev, out=u_dev, precision=hz.HZ_MIXED_C64, **kw)
+    P.solve(f_dev, out=u_dev, precision=hz.HZ_C128, **kw)
+    barrier()
+
+    # timed region: chosen form, with kernel-class timing for the roofline
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = hz.launch_count()
+    P.profile(True)
+    barrier()
+    t_mixed, st_mixed = timed(hz.HZ_MIXED_C64, args.steps)
+    barrier()
+    launches = hz.launch_count() - launches0
+    poly = P.profile_read(hz.PROF_POLY)
+    sten = P.profile_read(hz.PROF_STENCIL)
+    kryl = P.profile_read(hz.PROF_KRYLOV)
+    P.profile(False)
+    clk = clocks.stop()
+    t_mixed = max_over_ranks(t_mixed)
+
+    # plain float64 form, same steps
+    barrier()
+    t_plain, st_plain = timed(hz.HZ_C128, args.steps)
+    t_plain = max_over_ranks(t_plain)
+
+    # end to end through the public API: pinned host f -> device, solve, u -> pinned host
+    barrier()
+    t_e2e, _ = timed(hz.HZ_MIXED_C64, args.steps, e2e=True)
+    t_e2e = max_over_ranks(t_e2e)
+
+    # residual check of the last chosen-form solution with an independent float64 stencil
+    s = P.info["s"]
+    Au = P.apply_shifted(u_dev)
+    res = float(torch.linalg.vector_norm(s * f_dev - Au) / torch.linalg.vector_norm(s * f_dev))
+
+    rhs_total = args.steps * world
+    value = rhs_total / t_mixed
+    peak, peak_kind = measured_peak_hbm()
+    nl, ms, by = poly
+    achieved = (by / nl) / ((ms / nl) / 1e3) / 1e9 if nl else None
+    traffic = traffic_from_profile(kernel_hash())
+    line = {
+        "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_mixed / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": "mixed: complex64 polynomial sweeps, float64 "
+                   "quadrature sum, step d, inner/outer Arnoldi (CGS2), Givens, true residual",
+                   "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "parallelism": f"replicas x{world}"},
+        "its": st_mixed.its, "matvecs": st_mixed.matvecs,
+        "rel_res_true": st_mixed.rel_res_true, "rel_res_check": res,
+        "plain": {"value": rhs_total / t_plain, "unit": "RHS/s",
+                  "ms_per_step": t_plain / args.steps * 1e3, "dtype": "c128",
+                  "its": st_plain.its, "rel_res_true": st_plain.rel_res_true},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": traffic, "kernel": "k_poly_stage<float2> (batched sweeps)",
+                     "launches": nl, "avg_launch_us": (ms / nl * 1e3) if nl else None,
+                     "peak_kind": f"{peak_kind} copy bandwidth"},
+        "kernel_classes": {
+            "poly_stage": {"launches": poly[0], "ms": poly[1], "GB": poly[2] / 1e9},
+            "stencil_f64": {"launches": sten[0], "ms": sten[1], "GB": sten[2] / 1e9},
+            "krylov_f64": {"launches": kryl[0], "ms": kryl[1], "GB": kryl[2] / 1e9}},
+        "e2e": {"value": rhs_total / t_e2e, "unit": "RHS/s", "h2d_bytes_per_step": n * 16,
+                "d2h_bytes_per_step": n * 16},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        counts = oracle_counts()[wl.name]
+        per = 1
+        t_cpu = time_oracle_sample(wl, per)
+        line["cpu_baseline"] = {
+            "value": 1.0 / (t_cpu / per * counts["its"]), "unit": "RHS/s",
+            "cores": cpu_threads(), "kind": "oracle",
+            "sample": f"{per} outer FGMRES step of the complex128 oracle on this workload "
+                      f"({t_cpu:.2f} s), scaled by the oracle's {counts['its']} steps to 1e-8"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    P.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

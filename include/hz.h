@@ -1,0 +1,208 @@
+/*
+ * hz.h -- C ABI of the GB300 contour-integral Helmholtz solver.
+ *
+ * The library solves A u = f for the discretised 3D Helmholtz operator -Delta - omega^2/c^2(x)
+ * (Section 1, eq:helmholtz-op and eq:lin-sys) with a 7-point finite-difference Laplacian,
+ * zero Dirichlet ghosts and a diagonal absorbing sponge (Section 7.1, eq:stiff-mass).
+ * It uses the fast contour-integration preconditioner FCI of Algorithm 1 (Section 2) inside
+ * flexible GMRES: every shifted system (A - z_j I) y = f at the contour nodes z_j of
+ * eq:quad-points (Section 6.2) is solved by the polynomial fixed-point scheme eq:fix-pt-exp
+ * (Section 4.2), with parameters chosen by eq:fix-pt-conv.
+ *
+ * Units.  Internally the operator is normalised as in Section 7.1:
+ *     A = s * L_h - diag(m) - i * diag(a),   s = c_min^2 / omega^2,   m = c_min^2 / c^2,
+ * L_h = 7-point -Delta_h, a = sigma_max * (depth/layer)^2 * m in the sponge (0 in the core),
+ * so that the real part of the spectrum lies in [-1, rho1 - 1] and the imaginary part in
+ * [-rho2, 0] (Lemma 3.1).  hz_apply_shifted, hz_shifted_solve and hz_fci work in these
+ * normalised units.  hz_solve takes the physical right-hand side f of
+ * -Delta u - omega^2/c^2 u = f and scales it by s internally, so u is in physical units.
+ *
+ * Layout.  A field is nx*ny*nz complex values, x fastest: point (i, j, k) at linear index
+ * i + nx*(j + ny*k), interleaved (re, im).  HZ_C128 fields are double complex (16 bytes a
+ * point), HZ_MIXED_C64 fields of hz_apply_shifted / hz_shifted_solve are float complex
+ * (8 bytes a point).  A batch of nvec fields is stored one field after another.
+ *
+ * Memory.  Pointers named x, y, f, r, out, u are DEVICE pointers owned by the caller
+ * (cudaMalloc / torch).  hz_problem_create copies the wavespeed from host memory and
+ * allocates every workspace of the problem on the current device; no later call allocates.
+ * Calls taking a stream enqueue their work on it (0 = legacy default stream); hz_solve
+ * synchronises that stream to read convergence flags and returns when u is final.
+ *
+ * Errors.  Every call returns an hz_status and never aborts.  On HZ_ERR_CUDA the problem
+ * should be destroyed.  hz_last_error() gives a message for the last failure on the
+ * calling thread.
+ */
+#ifndef HZ_H
+#define HZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hz_problem hz_problem;
+
+typedef enum {
+  HZ_OK = 0,
+  HZ_ERR_INVALID = 1,        /* bad argument (null pointer, size, option) */
+  HZ_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  HZ_ERR_OOM = 3,            /* device or pinned allocation failed */
+  HZ_ERR_NOT_CONVERGED = 4,  /* hz_solve: max_cycles reached above rtol; u is the last iterate */
+  HZ_ERR_BREAKDOWN = 5,      /* reserved */
+  HZ_ERR_DIVERGED = 6,       /* hz_solve: a residual became NaN or Inf */
+  HZ_ERR_SETUP = 7           /* no polynomial order <= qmax converges at some node */
+} hz_status;
+
+typedef enum {
+  HZ_C128 = 0,      /* everything complex128 / float64 ("plain" form) */
+  HZ_MIXED_C64 = 1  /* polynomial sweeps in complex64; quadrature sum, step d, inner and
+                       outer Arnoldi, Givens and true residual in float64 */
+} hz_precision;
+
+/* Grid and medium.  Interior points nx*ny*nz with spacing h; omega the angular frequency;
+ * layer_cells the sponge thickness in cells (0 = none); sigma_max its peak strength in
+ * normalised units (Section 7.1: "positive diagonal entries for points near the boundary"). */
+typedef struct {
+  int nx, ny, nz;
+  double h;
+  double omega;
+  int layer_cells;
+  double sigma_max;
+} hz_grid;
+
+/* Contour and polynomial-scheme settings (Sections 4.2, 6.1, 6.2).  J nodes on the ellipse
+ * with axis ratio t and margin eps (eq:quad-points, eq:quad-radius); polynomial orders
+ * 1..qmax are tried and each shifted solve runs the sweeps that reduce its error bound by
+ * `reduction` (Table tab:param uses 5). */
+typedef struct {
+  int J;
+  double t;
+  double eps;
+  int qmax;
+  double reduction;
+} hz_contour_opts;
+
+/* Workspace limits fixed at creation: right-hand sides per call, outer restart length,
+ * inner GMRES steps. */
+typedef struct {
+  int nrhs_max;
+  int restart_max;
+  int inner_k_max;
+} hz_limits;
+
+/* hz_solve settings.  restart_m <= restart_max, inner_k <= inner_k_max.  precision is an
+ * hz_precision.  fixed_its > 0 takes exactly that many outer Arnoldi steps (cycles of
+ * restart_m) ignoring rtol, for run-to-run comparison of iterates. */
+typedef struct {
+  int restart_m;
+  int inner_k;
+  double rtol;
+  int max_cycles;
+  int precision;
+  int fixed_its;
+} hz_solve_opts;
+
+/* Per right-hand side results of hz_solve. */
+typedef struct {
+  int cycles;           /* FGMRES restarts begun */
+  int its;              /* outer Arnoldi steps */
+  long long matvecs;    /* stencil applications charged to this right-hand side */
+  int converged;        /* 1 if the true relative residual <= rtol */
+  double rel_res_true;  /* ||f - A u|| / ||f|| recomputed at the end, float64 */
+} hz_solve_stats;
+
+/* Scalars of a problem after set-up. */
+typedef struct {
+  double s;        /* c_min^2 / omega^2 */
+  double b1, b2;   /* real extent of the spectrum rectangle B (Lemma 3.1 with Weyl bounds) */
+  double rho2;     /* largest damping = height of B */
+  int J;           /* contour nodes */
+  int stages;      /* stencil sweeps of one FCI application (max over nodes of q*sweeps) */
+  long long n;     /* grid points */
+} hz_problem_info;
+
+/* Create a problem: copy the wavespeed c_host (nx*ny*nz doubles, x fastest, host memory),
+ * build m and the sponge, bound the spectrum (Lemma 3.1), place the J contour nodes
+ * (eq:quad-points), pick (z0, delta, q, sweeps) per node (eq:fix-pt-conv) and allocate all
+ * device workspace for `limits`.  Uses the current CUDA device.  *out receives the handle. */
+hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
+                            const hz_contour_opts* contour, const hz_limits* limits,
+                            hz_problem** out);
+
+/* Host-only planning: the scalars of hz_problem_get_info (info->n, s, b1, b2, rho2, J,
+ * stages) and the node tables of hz_problem_nodes that hz_problem_create would compute for
+ * this grid, wavespeed (host array as in hz_problem_create) and contour.  Touches no GPU and
+ * allocates no device memory.  Table pointers may be null; non-null ones take J entries. */
+hz_status hz_plan(const hz_grid* grid, const double* c_host, const hz_contour_opts* contour,
+                  hz_problem_info* info, double* z_ri, double* sigma_ri, double* z0_ri,
+                  double* delta, int* q, double* nu, int* sweeps);
+
+/* Free the problem and all its device memory.  Null is accepted. */
+hz_status hz_problem_destroy(hz_problem* p);
+
+hz_status hz_problem_get_info(const hz_problem* p, hz_problem_info* info);
+
+/* Copy the node tables out (host arrays, J entries each; complex values as (re, im) pairs):
+ * nodes z_j, weights sigma_j (Section 6.1), expansion centres z0_j, step delta_j, order q_j,
+ * rate nu_j (eq:fix-pt-conv) and sweeps_j.  Any pointer may be null. */
+hz_status hz_problem_nodes(const hz_problem* p, double* z_ri, double* sigma_ri, double* z0_ri,
+                           double* delta, int* q, double* nu, int* sweeps);
+
+/* Replace the node tables (J <= the J given at creation; host arrays as in
+ * hz_problem_nodes; nu is not needed).  Lets a caller run the method with externally
+ * chosen nodes and parameters. */
+hz_status hz_problem_set_nodes(hz_problem* p, int J, const double* z_ri, const double* sigma_ri,
+                               const double* z0_ri, const double* delta, const int* q,
+                               const int* sweeps);
+
+/* y = (A - z I) x for nvec fields (normalised operator; Section 7.1).  x and y must not
+ * overlap.  precision HZ_C128: double complex fields; HZ_MIXED_C64: float complex fields,
+ * computed in float32. */
+hz_status hz_apply_shifted(hz_problem* p, double zr, double zi, const void* x, void* y,
+                           int nvec, int precision, void* stream);
+
+/* y ~ (A - z_node I)^{-1} f for nvec fields by sweeps_node steps of eq:fix-pt-exp from
+ * y = 0 (Section 4.2).  Field type as in hz_apply_shifted.  nvec <= nrhs_max. */
+hz_status hz_shifted_solve(hz_problem* p, int node, const void* f, void* y, int nvec,
+                           int precision, void* stream);
+
+/* out = FCI(r) (Algorithm 1) for nvec double-complex fields: the J shifted solves, the
+ * quadrature w = sum_j sigma_j/z_j y_j, the step d = argmin ||r - d A w||, inner_k GMRES
+ * steps on A v = r - d A w, out = v + d w.  precision selects the field type of the
+ * shifted solves; r and out are always double complex.  nvec <= nrhs_max. */
+hz_status hz_fci(hz_problem* p, const void* r, void* out, int nvec, int inner_k, int precision,
+                 void* stream);
+
+/* Solve -Delta u - omega^2/c^2 u = f for nrhs double-complex right-hand sides (physical
+ * units) by FGMRES(restart_m) with FCI as the right preconditioner, x0 = 0.  Convergence is
+ * declared on the float64 true residual ||f - A u|| <= rtol ||f||.  stats: nrhs entries
+ * (may be null).  Returns HZ_ERR_NOT_CONVERGED if any right-hand side missed rtol. */
+hz_status hz_solve(hz_problem* p, const void* f, void* u, int nrhs, const hz_solve_opts* opts,
+                   hz_solve_stats* stats, void* stream);
+
+/* Kernel timing for roofline reports.  While enabled on a problem, each launch of a kernel
+ * class is bracketed by CUDA events on its stream, and the algorithmic bytes it must move
+ * (fields read and written once, neighbours not counted again) are added up.  Classes:
+ * 0 = batched polynomial stage (eq:fix-pt-exp sweeps + quadrature), 1 = shifted stencil,
+ * 2 = Krylov reductions (CGS2, norms, step d).  hz_profile_read synchronises the recorded
+ * events and returns, per class, launches, total milliseconds and total algorithmic bytes
+ * since the last enable; any output pointer may be null. */
+hz_status hz_profile_enable(hz_problem* p, int on);
+hz_status hz_profile_read(hz_problem* p, int cls, long long* launches, double* ms,
+                          double* bytes);
+
+/* Name of a status code. */
+const char* hz_status_string(hz_status s);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* hz_last_error(void);
+
+/* Kernels this library has launched since it was loaded (all problems, all threads). */
+unsigned long long hz_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HZ_H */

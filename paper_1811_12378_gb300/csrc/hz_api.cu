@@ -1,0 +1,897 @@
+// C ABI of libhz and the host orchestration of the solver:
+//   * the batched polynomial solve of all contour nodes (§4.2 eq:fix-pt-exp), right-aligned so
+//     that every node ends on the same stencil sweep, where the quadrature sum
+//     w = sum_j sigma_j/z_j y_j of Algorithm 1 is formed without storing the y_j;
+//   * FCI (§2 Algorithm 1): w, the step d, a few float64 GMRES steps on A v = r - d A w;
+//   * flexible GMRES(m) with FCI as the variable right preconditioner (§2, after Algorithm 1),
+//     float64 CGS2 Arnoldi and Givens on the device, restarts on the float64 true residual.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hz.h"
+#include "hz_internal.h"
+
+using hz::Buf;
+using hz::GmresDev;
+using hz::NodeParams;
+using hz::StageArgs;
+using hz::StageNode;
+
+namespace {
+
+thread_local std::string t_err;
+
+hz_status fail(hz_status s, const std::string& msg) {
+  t_err = msg;
+  return s;
+}
+
+hz_status cuda_fail(cudaError_t e, const char* where) {
+  t_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return HZ_ERR_CUDA;
+}
+
+#define HZ_CUDA(call)                                    \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+#define HZ_TRY(call)                  \
+  do {                                \
+    hz_status s_ = (call);            \
+    if (s_ != HZ_OK) return s_;       \
+  } while (0)
+
+constexpr double kBreakdown = 1e-14;
+constexpr int kProfPool = 1024;  // event pairs per kernel class before a flush
+
+// CUDA-event timing of one kernel class (see hz_profile_enable).
+struct ProfClass {
+  std::vector<cudaEvent_t> ev;  // 2 * kProfPool
+  int used = 0;
+  long long launches = 0;
+  double ms = 0.0, bytes = 0.0;
+};
+
+}  // namespace
+
+struct hz_problem {
+  int device = 0;
+  hz_grid grid{};
+  hz_contour_opts copt{};
+  hz_limits lim{};
+  hz::Geom g{};
+  hz::Setup su;
+  std::vector<NodeParams> nodes;
+  int J = 0;
+
+  // device memory
+  double* m64 = nullptr;
+  float* m32 = nullptr;
+  void* poly = nullptr;      // [nrhs][4 J][n] fields (double2 or float2)
+  float2* f32 = nullptr;     // [nrhs][n]
+  double2* w = nullptr;      // [nrhs][n] quadrature sum
+  double2* Aw = nullptr;     // [nrhs][n]
+  double2* Vin = nullptr;    // [nrhs][kin+1][n] inner basis
+  double2* V = nullptr;      // [nrhs][m+1][n] outer basis
+  double2* Z = nullptr;      // [nrhs][m][n] preconditioned directions
+  double2* partial = nullptr;
+  unsigned* counters = nullptr;
+  void* gmem = nullptr;      // all GmresDev arrays
+  GmresDev gin{}, gout{};
+
+  // pinned host mirrors
+  double* h_scal = nullptr;  // [nrhs][SC_COUNT]   device -> host
+  int* h_stopped = nullptr;  // [nrhs]             both directions, always after a sync
+  double* h_tol = nullptr;   // [nrhs]             host -> device
+
+  std::vector<void*> allocs;
+
+  bool prof_on = false;
+  ProfClass prof[3];
+
+  ~hz_problem() {
+    for (auto& c : prof)
+      for (cudaEvent_t e : c.ev) cudaEventDestroy(e);
+    for (void* p : allocs) cudaFree(p);
+    if (h_scal) cudaFreeHost(h_scal);
+    if (h_stopped) cudaFreeHost(h_stopped);
+    if (h_tol) cudaFreeHost(h_tol);
+  }
+};
+
+namespace {
+
+hz_status dalloc(hz_problem* p, void** out, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(out, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(HZ_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                cudaGetErrorString(e));
+  }
+  p->allocs.push_back(*out);
+  return HZ_OK;
+}
+
+char* carve(char*& cur, size_t bytes) {
+  char* r = cur;
+  cur += (bytes + 255) / 256 * 256;
+  return r;
+}
+
+// Device arrays of a GmresDev for nrhs right-hand sides and M columns, carved from `cur`.
+void gmres_layout(GmresDev& gs, char*& cur, int nrhs, int M) {
+  const int Mc = std::max(M, 1);
+  gs.mmax = M;
+  gs.R = (double2*)carve(cur, sizeof(double2) * nrhs * (size_t)(M + 1) * Mc);
+  gs.cc = (double*)carve(cur, sizeof(double) * nrhs * Mc);
+  gs.ss = (double2*)carve(cur, sizeof(double2) * nrhs * Mc);
+  gs.g = (double2*)carve(cur, sizeof(double2) * nrhs * (M + 1));
+  gs.y = (double2*)carve(cur, sizeof(double2) * nrhs * Mc);
+  gs.h1 = (double2*)carve(cur, sizeof(double2) * nrhs * (M + 2));
+  gs.h2 = (double2*)carve(cur, sizeof(double2) * nrhs * (M + 2));
+  gs.nrm = (double2*)carve(cur, sizeof(double2) * 2 * nrhs);
+  gs.scal = (double*)carve(cur, sizeof(double) * nrhs * hz::SC_COUNT);
+  gs.kend = (int*)carve(cur, sizeof(int) * nrhs);
+  gs.stopped = (int*)carve(cur, sizeof(int) * nrhs);
+}
+
+size_t gmres_carved_bytes(int nrhs, int M) {
+  const int Mc = std::max(M, 1);
+  auto r = [](size_t b) { return (b + 255) / 256 * 256; };
+  return r(sizeof(double2) * nrhs * (size_t)(M + 1) * Mc) + r(sizeof(double) * nrhs * Mc) +
+         r(sizeof(double2) * nrhs * Mc) + r(sizeof(double2) * nrhs * (M + 1)) +
+         r(sizeof(double2) * nrhs * Mc) + 2 * r(sizeof(double2) * nrhs * (M + 2)) +
+         r(sizeof(double2) * 2 * nrhs) + r(sizeof(double) * nrhs * hz::SC_COUNT) +
+         2 * r(sizeof(int) * nrhs);
+}
+
+bool valid_grid(const hz_grid* g) {
+  return g && g->nx >= 1 && g->ny >= 1 && g->nz >= 1 && g->h > 0 && std::isfinite(g->h) &&
+         g->omega > 0 && std::isfinite(g->omega) && g->layer_cells >= 0 && g->sigma_max >= 0 &&
+         std::isfinite(g->sigma_max) && g->nz <= 65535;
+}
+
+// ------------------------------------------------------------------ kernel timing
+
+hz_status prof_flush(ProfClass& c) {
+  for (int i = 0; i < c.used; ++i) {
+    HZ_CUDA(cudaEventSynchronize(c.ev[2 * i + 1]));
+    float ms = 0.f;
+    HZ_CUDA(cudaEventElapsedTime(&ms, c.ev[2 * i], c.ev[2 * i + 1]));
+    c.ms += ms;
+  }
+  c.used = 0;
+  return HZ_OK;
+}
+
+// Brackets one launch of class `cls` with events when timing is on.
+struct ProfScope {
+  hz_problem* p;
+  int cls, slot = -1;
+  cudaStream_t st;
+  double bytes;
+  hz_status begin() {
+    if (!p->prof_on) return HZ_OK;
+    ProfClass& c = p->prof[cls];
+    if (c.used == kProfPool) HZ_TRY(prof_flush(c));
+    slot = c.used++;
+    HZ_CUDA(cudaEventRecord(c.ev[2 * slot], st));
+    return HZ_OK;
+  }
+  hz_status end() {
+    if (slot < 0) return HZ_OK;
+    ProfClass& c = p->prof[cls];
+    HZ_CUDA(cudaEventRecord(c.ev[2 * slot + 1], st));
+    c.launches++;
+    c.bytes += bytes;
+    return HZ_OK;
+  }
+};
+
+#define HZ_TIMED(P, CLS, ST, BYTES, CALL)        \
+  do {                                           \
+    ProfScope ps_{(P), (CLS), -1, (ST), (BYTES)}; \
+    HZ_TRY(ps_.begin());                         \
+    HZ_CUDA(CALL);                               \
+    HZ_TRY(ps_.end());                           \
+  } while (0)
+
+// Algorithmic bytes of one stencil launch: x read and y written once per field, m once.
+template <typename T, typename R>
+double stencil_bytes(long long n, int nvec) {
+  return double(n) * (2.0 * sizeof(T) * nvec + sizeof(R));
+}
+
+// Algorithmic bytes of one Gram-Schmidt launch over nb basis fields (V read once, w read,
+// and written back in the update modes).
+double cgs_bytes(int mode, long long n, int nb, int nvec) {
+  const double fld = 16.0 * double(n) * nvec;
+  return mode == 0 ? fld * (nb + 1) : fld * (nb + 2);
+}
+
+// ------------------------------------------------------------------ polynomial solves
+
+// Buffer slots of node slot `s` in one rhs workspace of 4*nn fields.
+struct Slots {
+  long long Y, ACC, KA, KB;
+};
+
+Slots slots_of(int s, long long n) {
+  const long long b = 4LL * s * n;
+  return {b, b + n, b + 2 * n, b + 3 * n};
+}
+
+// Runs the batched scheme eq:fix-pt-exp for the nodes in `which` from y = 0.  With `quad`
+// the last stage writes w = sum sigma_j/z_j y_j (double2, wbuf); otherwise node slot s ends
+// with its y in the returned offset yfinal[s] of the workspace.
+template <typename T, typename R>
+hz_status run_poly(hz_problem* p, const R* m, Buf<const T> f, int nvec,
+                   const std::vector<int>& which, bool quad, Buf<double2> wbuf,
+                   std::vector<long long>* yfinal, cudaStream_t st) {
+  const long long n = p->g.n;
+  const int nn = (int)which.size();
+  T* ws = (T*)p->poly;
+  const long long wrs = 4LL * p->J * n;  // elements of T per rhs
+  int T_total = 0;
+  for (int node : which) T_total = std::max(T_total, p->nodes[node].q * p->nodes[node].sweeps);
+  std::vector<long long> ycur(nn);
+  for (int s = 0; s < nn; ++s) ycur[s] = slots_of(s, n).Y;
+  for (int t = 0; t < T_total; ++t) {
+    StageArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nnodes = nn;
+    a.final_quad = (quad && t == T_total - 1) ? 1 : 0;
+    for (int s = 0; s < nn; ++s) {
+      const NodeParams& np = p->nodes[which[s]];
+      StageNode& sn = a.nd[s];
+      const int Tj = np.q * np.sweeps;
+      const int start = T_total - Tj;
+      if (t < start) {
+        sn.kind = hz::SK_NONE;
+        continue;
+      }
+      const int tl = t - start;
+      const int sweep = tl / np.q;
+      const int jj = tl % np.q + 1;
+      const Slots sl = slots_of(s, n);
+      // c_{j} = (-i delta (z - z0))^j / j!,  ptilde(z) = sum_{j<=q} c_j
+      const std::complex<double> zz(np.zr, np.zi), z0(np.z0r, np.z0i);
+      const std::complex<double> u = std::complex<double>(0.0, -np.delta) * (zz - z0);
+      std::vector<std::complex<double>> c(np.q + 1);
+      c[0] = 1.0;
+      for (int k = 1; k <= np.q; ++k) c[k] = c[k - 1] * u / double(k);
+      std::complex<double> pz = 0.0;
+      for (int k = 0; k <= np.q; ++k) pz += c[k];
+      const std::complex<double> ip = 1.0 / pz;
+      const std::complex<double> md = std::complex<double>(0.0, -np.delta) / double(jj);
+      const std::complex<double> wq = std::complex<double>(np.sr, np.si) / zz;
+      sn.mdr = md.real();
+      sn.mdi = md.imag();
+      sn.cfr = c[jj - 1].real();
+      sn.cfi = c[jj - 1].imag();
+      sn.z0r = np.z0r;
+      sn.z0i = np.z0i;
+      sn.ipr = ip.real();
+      sn.ipi = ip.imag();
+      sn.wqr = wq.real();
+      sn.wqi = wq.imag();
+      sn.acc = sl.ACC;
+      auto kbuf = [&](int step) { return (step % 2 == 1) ? sl.KA : sl.KB; };
+      if (jj == 1) {
+        sn.yzero = sweep == 0 ? 1 : 0;
+        sn.in = ycur[s];
+        if (np.q == 1) {
+          sn.kind = hz::SK_FIRST_LAST;
+          sn.yout = (ycur[s] == sl.Y) ? sl.ACC : sl.Y;
+          ycur[s] = sn.yout;
+        } else {
+          sn.kind = hz::SK_FIRST;
+          sn.kout = kbuf(1);
+        }
+      } else if (jj < np.q) {
+        sn.kind = hz::SK_MID;
+        sn.in = kbuf(jj - 1);
+        sn.kout = kbuf(jj);
+      } else {
+        sn.kind = hz::SK_LAST;
+        sn.in = kbuf(jj - 1);
+        sn.yout = sl.Y;
+        ycur[s] = sl.Y;
+      }
+    }
+    // algorithmic bytes per point: f and m once; per node FIRST y?(r) k(w) acc(w), MID k(r)
+    // acc(r/w) k(w), LAST k(r) acc(r) y(w, or the float64 sum w once at the final stage)
+    double bpp = double(sizeof(T)) * 1 + double(sizeof(R)) / nvec;
+    for (int s = 0; s < nn; ++s) {
+      const StageNode& sn = a.nd[s];
+      const double e = sizeof(T);
+      if (sn.kind == hz::SK_FIRST) bpp += (sn.yzero ? 2 : 3) * e;
+      else if (sn.kind == hz::SK_MID) bpp += 4 * e;
+      else if (sn.kind == hz::SK_LAST) bpp += (a.final_quad ? 2 : 3) * e;
+      else if (sn.kind == hz::SK_FIRST_LAST) bpp += ((sn.yzero ? 0 : 1) + (a.final_quad ? 0 : 1)) * e;
+    }
+    if (a.final_quad) bpp += sizeof(double2);
+    HZ_TIMED(p, 0, st, bpp * double(n) * nvec,
+             (hz::launch_poly_stage<T, R>(p->g, m, f, ws, wrs, wbuf, nvec, a, st)));
+  }
+  if (yfinal) *yfinal = ycur;
+  return HZ_OK;
+}
+
+// FCI (Algorithm 1) on nvec double-complex fields r -> out.
+hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nvec, int kin,
+                  int precision, cudaStream_t st) {
+  const long long n = p->g.n;
+  std::vector<int> all(p->J);
+  for (int j = 0; j < p->J; ++j) all[j] = j;
+  Buf<double2> wb{p->w, n};
+  if (precision == HZ_MIXED_C64) {
+    HZ_CUDA(hz::launch_convert_c128_c64(r, Buf<float2>{p->f32, n}, n, nvec, st));
+    HZ_TRY((run_poly<float2, float>(p, p->m32, Buf<const float2>{p->f32, n}, nvec, all, true, wb,
+                                    nullptr, st)));
+  } else {
+    HZ_TRY((run_poly<double2, double>(p, p->m64, r, nvec, all, true, wb, nullptr, st)));
+  }
+  // Aw, step d, inner start v0 = (r - d Aw)/||r - d Aw||
+  HZ_TIMED(p, 1, st, (stencil_bytes<double2, double>(n, nvec)),
+           (hz::launch_stencil<double2, double>(p->g, p->m64, Buf<const double2>{p->w, n},
+                                                Buf<double2>{p->Aw, n}, nvec, 0.0, 0.0, st)));
+  const long long vrs = (long long)(p->lim.inner_k_max + 1) * n;
+  HZ_TIMED(p, 2, st, 16.0 * n * nvec * 5,
+           hz::launch_fci_step(Buf<const double2>{p->Aw, n}, r, Buf<double2>{p->Vin, vrs}, p->gin,
+                               p->partial, p->counters, n, nvec, st));
+  HZ_CUDA(hz::launch_scale(Buf<double2>{p->Vin, vrs}, Buf<const double2>{p->Vin, vrs}, n, p->gin,
+                           nvec, st));
+  for (int j = 0; j < kin; ++j) {
+    Buf<double2> wj{p->Vin + (long long)(j + 1) * n, vrs};
+    HZ_TIMED(p, 1, st, (stencil_bytes<double2, double>(n, nvec)),
+             (hz::launch_stencil<double2, double>(
+                 p->g, p->m64, Buf<const double2>{p->Vin + (long long)j * n, vrs}, wj, nvec, 0.0,
+                 0.0, st)));
+    for (int mode = 0; mode < 3; ++mode)
+      HZ_TIMED(p, 2, st, cgs_bytes(mode, n, j + 1, nvec),
+               hz::launch_cgs(mode, p->Vin, n, vrs, j + 1, wj, n, p->gin, p->partial, p->counters,
+                              nvec, kBreakdown, st));
+    HZ_CUDA(hz::launch_scale(wj, Buf<const double2>{wj.p, vrs}, n, p->gin, nvec, st));
+  }
+  HZ_CUDA(hz::launch_backsolve(p->gin, nvec, st));
+  HZ_CUDA(hz::launch_combine(out, p->Vin, n, vrs, p->gin, Buf<const double2>{p->w, n}, 0, 0, n,
+                             nvec, kin, st));
+  return HZ_OK;
+}
+
+hz_status check_problem(const hz_problem* p) {
+  if (!p) return fail(HZ_ERR_INVALID, "null problem");
+  return HZ_OK;
+}
+
+hz_status set_device(const hz_problem* p) {
+  int cur = -1;
+  HZ_CUDA(cudaGetDevice(&cur));
+  if (cur != p->device) HZ_CUDA(cudaSetDevice(p->device));
+  return HZ_OK;
+}
+
+// Early-stop tolerance of the outer cycle per rhs (scal[r][SC_TOL]; < 0: never).  The pinned
+// staging buffer is only rewritten after a stream synchronisation, so no copy from it is
+// still pending.
+hz_status fill_scal_tol(hz_problem* p, GmresDev& gs, const std::vector<double>& tol, int nvec,
+                        cudaStream_t st) {
+  for (int r = 0; r < nvec; ++r) p->h_tol[r] = tol[r];
+  HZ_CUDA(cudaMemcpy2DAsync(gs.scal + hz::SC_TOL, sizeof(double) * hz::SC_COUNT, p->h_tol,
+                            sizeof(double), sizeof(double), nvec, cudaMemcpyHostToDevice, st));
+  return HZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hz_status_string(hz_status s) {
+  switch (s) {
+    case HZ_OK: return "ok";
+    case HZ_ERR_INVALID: return "invalid argument";
+    case HZ_ERR_CUDA: return "CUDA error";
+    case HZ_ERR_OOM: return "out of memory";
+    case HZ_ERR_NOT_CONVERGED: return "not converged";
+    case HZ_ERR_BREAKDOWN: return "breakdown";
+    case HZ_ERR_DIVERGED: return "diverged";
+    case HZ_ERR_SETUP: return "set-up failed";
+  }
+  return "unknown status";
+}
+
+const char* hz_last_error(void) { return t_err.c_str(); }
+
+unsigned long long hz_launch_count(void) { return hz::g_launches.load(); }
+
+hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
+                            const hz_contour_opts* contour, const hz_limits* limits,
+                            hz_problem** out) {
+  if (!out) return fail(HZ_ERR_INVALID, "out is null");
+  *out = nullptr;
+  if (!valid_grid(grid)) return fail(HZ_ERR_INVALID, "invalid grid");
+  if (!c_host) return fail(HZ_ERR_INVALID, "c_host is null");
+  if (!contour || contour->J < 1 || contour->J > hz::MAXJ || !(contour->t > 0) ||
+      !(contour->eps > 0) || contour->qmax < 1 || contour->qmax > 12 ||
+      !(contour->reduction > 1.0))
+    return fail(HZ_ERR_INVALID, "invalid contour options (1 <= J <= 16, t > 0, eps > 0, "
+                                "1 <= qmax <= 12, reduction > 1)");
+  if (!limits || limits->nrhs_max < 1 || limits->restart_max < 1 || limits->inner_k_max < 0 ||
+      limits->restart_max > 1000 || limits->inner_k_max > 1000)
+    return fail(HZ_ERR_INVALID, "invalid limits");
+  const long long n = (long long)grid->nx * grid->ny * grid->nz;
+  for (long long i = 0; i < n; ++i)
+    if (!(c_host[i] > 0) || !std::isfinite(c_host[i]))
+      return fail(HZ_ERR_INVALID, "wavespeed must be positive and finite");
+  if ((long long)grid->nz * limits->nrhs_max > 65535)
+    return fail(HZ_ERR_INVALID, "nz * nrhs_max must not exceed 65535");
+
+  hz_problem* p = new hz_problem();
+  auto bail = [&](hz_status s) {
+    delete p;
+    return s;
+  };
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  p->grid = *grid;
+  p->copt = *contour;
+  p->lim = *limits;
+  p->J = contour->J;
+  hz::setup_operator(*grid, c_host, p->su);
+  p->g.nx = grid->nx;
+  p->g.ny = grid->ny;
+  p->g.nz = grid->nz;
+  p->g.n = n;
+  p->g.layer = grid->layer_cells;
+  p->g.cs = p->su.s / (grid->h * grid->h);
+  p->g.sig = grid->sigma_max;
+  std::string err;
+  if (!hz::setup_nodes(p->su, *contour, p->nodes, err)) {
+    delete p;
+    return fail(HZ_ERR_SETUP, err);
+  }
+
+  const int R = limits->nrhs_max, M = limits->restart_max, K = limits->inner_k_max;
+  hz_status s;
+  if ((s = dalloc(p, (void**)&p->m64, sizeof(double) * n)) != HZ_OK) return bail(s);
+  if ((s = dalloc(p, (void**)&p->m32, sizeof(float) * n)) != HZ_OK) return bail(s);
+  if ((s = dalloc(p, &p->poly, sizeof(double2) * 4 * (size_t)p->J * n * R)) != HZ_OK) return bail(s);
+  if ((s = dalloc(p, (void**)&p->f32, sizeof(float2) * (size_t)n * R)) != HZ_OK) return bail(s);
+  if ((s = dalloc(p, (void**)&p->w, sizeof(double2) * (size_t)n * R)) != HZ_OK) return bail(s);
+  if ((s = dalloc(p, (void**)&p->Aw, sizeof(double2) * (size_t)n * R)) != HZ_OK) return bail(s);
+  if ((s = dalloc(p, (void**)&p->Vin, sizeof(double2) * (size_t)n * (K + 1) * R)) != HZ_OK)
+    return bail(s);
+  if ((s = dalloc(p, (void**)&p->V, sizeof(double2) * (size_t)n * (M + 1) * R)) != HZ_OK)
+    return bail(s);
+  if ((s = dalloc(p, (void**)&p->Z, sizeof(double2) * (size_t)n * M * R)) != HZ_OK) return bail(s);
+  const long long nblk = (n + hz::RED_CHUNK - 1) / hz::RED_CHUNK;
+  const int slots = std::max(M, K) + 2;
+  if ((s = dalloc(p, (void**)&p->partial, sizeof(double2) * (size_t)nblk * slots * R)) != HZ_OK)
+    return bail(s);
+  if ((s = dalloc(p, (void**)&p->counters, sizeof(unsigned) * R)) != HZ_OK) return bail(s);
+  const size_t gb = gmres_carved_bytes(R, M) + gmres_carved_bytes(R, K) + 1024;
+  if ((s = dalloc(p, &p->gmem, gb)) != HZ_OK) return bail(s);
+  char* cur = (char*)p->gmem;
+  gmres_layout(p->gout, cur, R, M);
+  gmres_layout(p->gin, cur, R, K);
+  e = cudaMemset(p->gmem, 0, gb);
+  if (e == cudaSuccess) e = cudaMemset(p->counters, 0, sizeof(unsigned) * R);
+  if (e == cudaSuccess) e = cudaMemset(p->poly, 0, sizeof(double2) * 4 * (size_t)p->J * n * R);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "cudaMemset");
+  }
+  if (cudaMallocHost(&p->h_scal, sizeof(double) * hz::SC_COUNT * R) != cudaSuccess ||
+      cudaMallocHost(&p->h_stopped, sizeof(int) * R) != cudaSuccess ||
+      cudaMallocHost(&p->h_tol, sizeof(double) * R) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return fail(HZ_ERR_OOM, "pinned host allocation failed");
+  }
+  // the inner GMRES of FCI never stops on a tolerance (SC_TOL < 0), fixed once here
+  {
+    std::vector<double> sc(hz::SC_COUNT * (size_t)R, 0.0);
+    for (int r = 0; r < R; ++r) sc[r * hz::SC_COUNT + hz::SC_TOL] = -1.0;
+    e = cudaMemcpy(p->gin.scal, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      delete p;
+      return cuda_fail(e, "cudaMemcpy of inner tolerances");
+    }
+  }
+  std::vector<float> m32(n);
+  for (long long i = 0; i < n; ++i) m32[i] = float(p->su.m[i]);
+  e = cudaMemcpy(p->m64, p->su.m.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->m32, m32.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "cudaMemcpy of coefficients");
+  }
+  *out = p;
+  return HZ_OK;
+}
+
+hz_status hz_plan(const hz_grid* grid, const double* c_host, const hz_contour_opts* contour,
+                  hz_problem_info* info, double* z_ri, double* sigma_ri, double* z0_ri,
+                  double* delta, int* q, double* nu, int* sweeps) {
+  if (!valid_grid(grid)) return fail(HZ_ERR_INVALID, "invalid grid");
+  if (!c_host) return fail(HZ_ERR_INVALID, "c_host is null");
+  if (!contour || contour->J < 1 || contour->J > hz::MAXJ || !(contour->t > 0) ||
+      !(contour->eps > 0) || contour->qmax < 1 || contour->qmax > 12 ||
+      !(contour->reduction > 1.0))
+    return fail(HZ_ERR_INVALID, "invalid contour options");
+  const long long n = (long long)grid->nx * grid->ny * grid->nz;
+  for (long long i = 0; i < n; ++i)
+    if (!(c_host[i] > 0) || !std::isfinite(c_host[i]))
+      return fail(HZ_ERR_INVALID, "wavespeed must be positive and finite");
+  hz::Setup su;
+  hz::setup_operator(*grid, c_host, su);
+  std::vector<NodeParams> nodes;
+  std::string err;
+  if (!hz::setup_nodes(su, *contour, nodes, err)) return fail(HZ_ERR_SETUP, err);
+  if (info) {
+    info->s = su.s;
+    info->b1 = su.b1;
+    info->b2 = su.b2;
+    info->rho2 = su.rho2;
+    info->J = contour->J;
+    int T = 0;
+    for (const auto& nd : nodes) T = std::max(T, nd.q * nd.sweeps);
+    info->stages = T;
+    info->n = n;
+  }
+  for (int j = 0; j < contour->J; ++j) {
+    const NodeParams& nd = nodes[j];
+    if (z_ri) { z_ri[2 * j] = nd.zr; z_ri[2 * j + 1] = nd.zi; }
+    if (sigma_ri) { sigma_ri[2 * j] = nd.sr; sigma_ri[2 * j + 1] = nd.si; }
+    if (z0_ri) { z0_ri[2 * j] = nd.z0r; z0_ri[2 * j + 1] = nd.z0i; }
+    if (delta) delta[j] = nd.delta;
+    if (q) q[j] = nd.q;
+    if (nu) nu[j] = nd.nu;
+    if (sweeps) sweeps[j] = nd.sweeps;
+  }
+  return HZ_OK;
+}
+
+hz_status hz_profile_enable(hz_problem* p, int on) {
+  HZ_TRY(check_problem(p));
+  HZ_TRY(set_device(p));
+  for (ProfClass& c : p->prof) {
+    if (c.ev.empty()) {
+      c.ev.resize(2 * kProfPool);
+      for (cudaEvent_t& e : c.ev) HZ_CUDA(cudaEventCreate(&e));
+    }
+    HZ_TRY(prof_flush(c));
+    c.launches = 0;
+    c.ms = 0.0;
+    c.bytes = 0.0;
+  }
+  p->prof_on = on != 0;
+  return HZ_OK;
+}
+
+hz_status hz_profile_read(hz_problem* p, int cls, long long* launches, double* ms,
+                          double* bytes) {
+  HZ_TRY(check_problem(p));
+  if (cls < 0 || cls > 2) return fail(HZ_ERR_INVALID, "kernel class must be 0, 1 or 2");
+  ProfClass& c = p->prof[cls];
+  HZ_TRY(prof_flush(c));
+  if (launches) *launches = c.launches;
+  if (ms) *ms = c.ms;
+  if (bytes) *bytes = c.bytes;
+  return HZ_OK;
+}
+
+hz_status hz_problem_destroy(hz_problem* p) {
+  if (!p) return HZ_OK;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  const int dev = p->device;
+  if (cur != dev) cudaSetDevice(dev);
+  cudaDeviceSynchronize();
+  delete p;
+  if (cur >= 0 && cur != dev) cudaSetDevice(cur);
+  return HZ_OK;
+}
+
+hz_status hz_problem_get_info(const hz_problem* p, hz_problem_info* info) {
+  HZ_TRY(check_problem(p));
+  if (!info) return fail(HZ_ERR_INVALID, "info is null");
+  info->s = p->su.s;
+  info->b1 = p->su.b1;
+  info->b2 = p->su.b2;
+  info->rho2 = p->su.rho2;
+  info->J = p->J;
+  int T = 0;
+  for (const auto& nd : p->nodes) T = std::max(T, nd.q * nd.sweeps);
+  info->stages = T;
+  info->n = p->g.n;
+  return HZ_OK;
+}
+
+hz_status hz_problem_nodes(const hz_problem* p, double* z_ri, double* sigma_ri, double* z0_ri,
+                           double* delta, int* q, double* nu, int* sweeps) {
+  HZ_TRY(check_problem(p));
+  for (int j = 0; j < p->J; ++j) {
+    const NodeParams& nd = p->nodes[j];
+    if (z_ri) { z_ri[2 * j] = nd.zr; z_ri[2 * j + 1] = nd.zi; }
+    if (sigma_ri) { sigma_ri[2 * j] = nd.sr; sigma_ri[2 * j + 1] = nd.si; }
+    if (z0_ri) { z0_ri[2 * j] = nd.z0r; z0_ri[2 * j + 1] = nd.z0i; }
+    if (delta) delta[j] = nd.delta;
+    if (q) q[j] = nd.q;
+    if (nu) nu[j] = nd.nu;
+    if (sweeps) sweeps[j] = nd.sweeps;
+  }
+  return HZ_OK;
+}
+
+hz_status hz_problem_set_nodes(hz_problem* p, int J, const double* z_ri, const double* sigma_ri,
+                               const double* z0_ri, const double* delta, const int* q,
+                               const int* sweeps) {
+  HZ_TRY(check_problem(p));
+  if (J < 1 || J > p->copt.J) return fail(HZ_ERR_INVALID, "J must be in [1, J at creation]");
+  if (!z_ri || !sigma_ri || !z0_ri || !delta || !q || !sweeps)
+    return fail(HZ_ERR_INVALID, "null node table");
+  std::vector<NodeParams> nodes(J);
+  for (int j = 0; j < J; ++j) {
+    NodeParams& nd = nodes[j];
+    nd.zr = z_ri[2 * j];
+    nd.zi = z_ri[2 * j + 1];
+    nd.sr = sigma_ri[2 * j];
+    nd.si = sigma_ri[2 * j + 1];
+    nd.z0r = z0_ri[2 * j];
+    nd.z0i = z0_ri[2 * j + 1];
+    nd.delta = delta[j];
+    nd.q = q[j];
+    nd.sweeps = sweeps[j];
+    nd.nu = std::nan("");
+    if (nd.q < 1 || nd.q > 64 || nd.sweeps < 1 || nd.sweeps > 100000 || (nd.zr == 0 && nd.zi == 0))
+      return fail(HZ_ERR_INVALID, "node " + std::to_string(j) + ": need 1 <= q <= 64, "
+                                  "1 <= sweeps <= 100000, z != 0");
+  }
+  p->nodes = nodes;
+  p->J = J;
+  return HZ_OK;
+}
+
+hz_status hz_apply_shifted(hz_problem* p, double zr, double zi, const void* x, void* y, int nvec,
+                           int precision, void* stream) {
+  HZ_TRY(check_problem(p));
+  if (nvec < 0) return fail(HZ_ERR_INVALID, "nvec < 0");
+  if (nvec == 0) return HZ_OK;
+  if (!x || !y) return fail(HZ_ERR_INVALID, "null field");
+  if ((long long)p->g.nz * nvec > 65535) return fail(HZ_ERR_INVALID, "nz * nvec > 65535");
+  HZ_TRY(set_device(p));
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long n = p->g.n;
+  if (precision == HZ_C128) {
+    HZ_TIMED(p, 1, st, (stencil_bytes<double2, double>(n, nvec)),
+             (hz::launch_stencil<double2, double>(p->g, p->m64,
+                                                  Buf<const double2>{(const double2*)x, n},
+                                                  Buf<double2>{(double2*)y, n}, nvec, zr, zi, st)));
+  } else if (precision == HZ_MIXED_C64) {
+    HZ_TIMED(p, 1, st, (stencil_bytes<float2, float>(n, nvec)),
+             (hz::launch_stencil<float2, float>(p->g, p->m32,
+                                                Buf<const float2>{(const float2*)x, n},
+                                                Buf<float2>{(float2*)y, n}, nvec, zr, zi, st)));
+  } else {
+    return fail(HZ_ERR_INVALID, "unknown precision");
+  }
+  return HZ_OK;
+}
+
+hz_status hz_shifted_solve(hz_problem* p, int node, const void* f, void* y, int nvec,
+                           int precision, void* stream) {
+  HZ_TRY(check_problem(p));
+  if (node < 0 || node >= p->J) return fail(HZ_ERR_INVALID, "node out of range");
+  if (nvec < 0 || nvec > p->lim.nrhs_max) return fail(HZ_ERR_INVALID, "nvec out of range");
+  if (nvec == 0) return HZ_OK;
+  if (!f || !y) return fail(HZ_ERR_INVALID, "null field");
+  HZ_TRY(set_device(p));
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long n = p->g.n;
+  std::vector<int> which{node};
+  std::vector<long long> yfin;
+  Buf<double2> nob{nullptr, 0};
+  size_t es;
+  if (precision == HZ_C128) {
+    HZ_TRY((run_poly<double2, double>(p, p->m64, Buf<const double2>{(const double2*)f, n}, nvec,
+                                      which, false, nob, &yfin, st)));
+    es = sizeof(double2);
+  } else if (precision == HZ_MIXED_C64) {
+    HZ_TRY((run_poly<float2, float>(p, p->m32, Buf<const float2>{(const float2*)f, n}, nvec, which,
+                                    false, nob, &yfin, st)));
+    es = sizeof(float2);
+  } else {
+    return fail(HZ_ERR_INVALID, "unknown precision");
+  }
+  const long long wrs = 4LL * p->J * n;
+  HZ_CUDA(cudaMemcpy2DAsync(y, es * n, (const char*)p->poly + es * yfin[0], es * wrs, es * n, nvec,
+                            cudaMemcpyDeviceToDevice, st));
+  return HZ_OK;
+}
+
+hz_status hz_fci(hz_problem* p, const void* r, void* out, int nvec, int inner_k, int precision,
+                 void* stream) {
+  HZ_TRY(check_problem(p));
+  if (nvec < 0 || nvec > p->lim.nrhs_max) return fail(HZ_ERR_INVALID, "nvec out of range");
+  if (inner_k < 0 || inner_k > p->lim.inner_k_max)
+    return fail(HZ_ERR_INVALID, "inner_k out of range");
+  if (precision != HZ_C128 && precision != HZ_MIXED_C64)
+    return fail(HZ_ERR_INVALID, "unknown precision");
+  if (nvec == 0) return HZ_OK;
+  if (!r || !out) return fail(HZ_ERR_INVALID, "null field");
+  HZ_TRY(set_device(p));
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long n = p->g.n;
+  return run_fci(p, Buf<const double2>{(const double2*)r, n}, Buf<double2>{(double2*)out, n}, nvec,
+                 inner_k, precision, st);
+}
+
+hz_status hz_solve(hz_problem* p, const void* f, void* u, int nrhs, const hz_solve_opts* opts,
+                   hz_solve_stats* stats, void* stream) {
+  HZ_TRY(check_problem(p));
+  if (!opts) return fail(HZ_ERR_INVALID, "opts is null");
+  if (nrhs < 0 || nrhs > p->lim.nrhs_max) return fail(HZ_ERR_INVALID, "nrhs out of range");
+  const int M = opts->restart_m, K = opts->inner_k;
+  if (M < 1 || M > p->lim.restart_max) return fail(HZ_ERR_INVALID, "restart_m out of range");
+  if (K < 0 || K > p->lim.inner_k_max) return fail(HZ_ERR_INVALID, "inner_k out of range");
+  if (opts->max_cycles < 0 || opts->fixed_its < 0 || !(opts->rtol >= 0))
+    return fail(HZ_ERR_INVALID, "invalid max_cycles / fixed_its / rtol");
+  if (opts->precision != HZ_C128 && opts->precision != HZ_MIXED_C64)
+    return fail(HZ_ERR_INVALID, "unknown precision");
+  if (nrhs == 0) return HZ_OK;
+  if (!f || !u) return fail(HZ_ERR_INVALID, "null field");
+  HZ_TRY(set_device(p));
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long n = p->g.n;
+  const long long vrs = (long long)(p->lim.restart_max + 1) * n;
+  const long long zrs = (long long)p->lim.restart_max * n;
+  const bool fixed = opts->fixed_its > 0;
+  Buf<const double2> fb{(const double2*)f, n};
+  Buf<double2> ub{(double2*)u, n};
+  GmresDev& go = p->gout;
+
+  long long mv_fci = 1 + K;
+  for (const auto& nd : p->nodes) mv_fci += nd.q * nd.sweeps - 1;
+
+  std::vector<double> fnorm(nrhs, 0.0), rel(nrhs, 1.0);
+  std::vector<int> its(nrhs, 0), cycles(nrhs, 0), done(nrhs, 0);
+  std::vector<long long> mvs(nrhs, 0);
+  HZ_CUDA(cudaMemsetAsync(u, 0, sizeof(double2) * n * nrhs, st));
+
+  auto read_scal = [&](GmresDev& gs) -> hz_status {
+    HZ_CUDA(cudaMemcpyAsync(p->h_scal, gs.scal, sizeof(double) * hz::SC_COUNT * nrhs,
+                            cudaMemcpyDeviceToHost, st));
+    HZ_CUDA(cudaMemcpyAsync(p->h_stopped, gs.stopped, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+    HZ_CUDA(cudaStreamSynchronize(st));
+    return HZ_OK;
+  };
+
+  int cycle = 0;
+  bool diverged = false;
+  for (;;) {
+    // true residual r = s f - A u, v0 = r/||r||
+    HZ_CUDA(hz::launch_residual_start(p->g, p->m64, fb, p->su.s,
+                                      cycle == 0 ? Buf<const double2>{nullptr, 0}
+                                                 : Buf<const double2>{(const double2*)u, n},
+                                      Buf<double2>{p->V, vrs}, go, p->partial, p->counters, nrhs,
+                                      st));
+    for (int r = 0; r < nrhs; ++r) mvs[r] += cycle == 0 ? 0 : 1;
+    HZ_CUDA(hz::launch_scale(Buf<double2>{p->V, vrs}, Buf<const double2>{p->V, vrs}, n, go, nrhs, st));
+    HZ_TRY(read_scal(go));
+    bool all_done = true;
+    for (int r = 0; r < nrhs; ++r) {
+      const double beta = p->h_scal[r * hz::SC_COUNT + hz::SC_BETA];
+      if (cycle == 0) fnorm[r] = beta;
+      rel[r] = fnorm[r] > 0 ? beta / fnorm[r] : 0.0;
+      if (!std::isfinite(beta)) {
+        diverged = true;
+        done[r] = 1;
+      } else if (fnorm[r] == 0.0) {
+        done[r] = 1;
+      } else if (fixed) {
+        done[r] = its[r] >= opts->fixed_its ? 1 : 0;
+      } else {
+        done[r] = rel[r] <= opts->rtol ? 1 : 0;
+      }
+      all_done = all_done && done[r];
+    }
+    if (all_done || cycle >= opts->max_cycles) break;
+    ++cycle;
+    // per-rhs stop flags and tolerance of this cycle
+    std::vector<double> tol(nrhs);
+    for (int r = 0; r < nrhs; ++r) {
+      tol[r] = fixed ? -1.0 : opts->rtol * fnorm[r];
+      p->h_stopped[r] = done[r];
+      if (!done[r]) cycles[r]++;
+    }
+    HZ_TRY(fill_scal_tol(p, go, tol, nrhs, st));
+    HZ_CUDA(cudaMemcpyAsync(go.stopped, p->h_stopped, sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+    std::vector<int> active(nrhs);
+    for (int r = 0; r < nrhs; ++r) active[r] = !done[r];
+    for (int k = 0; k < M; ++k) {
+      Buf<const double2> vk{p->V + (long long)k * n, vrs};
+      Buf<double2> zk{p->Z + (long long)k * n, zrs};
+      HZ_TRY(run_fci(p, vk, zk, nrhs, K, opts->precision, st));
+      Buf<double2> wk{p->V + (long long)(k + 1) * n, vrs};
+      HZ_TIMED(p, 1, st, (stencil_bytes<double2, double>(n, nrhs)),
+               (hz::launch_stencil<double2, double>(p->g, p->m64, Buf<const double2>{zk.p, zrs},
+                                                    wk, nrhs, 0.0, 0.0, st)));
+      for (int mode = 0; mode < 3; ++mode)
+        HZ_TIMED(p, 2, st, cgs_bytes(mode, n, k + 1, nrhs),
+                 hz::launch_cgs(mode, p->V, n, vrs, k + 1, wk, n, go, p->partial, p->counters,
+                                nrhs, kBreakdown, st));
+      HZ_CUDA(hz::launch_scale(wk, Buf<const double2>{wk.p, vrs}, n, go, nrhs, st));
+      for (int r = 0; r < nrhs; ++r)
+        if (active[r]) {
+          its[r]++;
+          mvs[r] += mv_fci + 1;
+        }
+      HZ_TRY(read_scal(go));
+      bool any_active = false;
+      bool push = false;
+      for (int r = 0; r < nrhs; ++r) {
+        if (!active[r]) continue;
+        if (!std::isfinite(p->h_scal[r * hz::SC_COUNT + hz::SC_EST])) {
+          diverged = true;
+          p->h_stopped[r] = 1;
+          push = true;
+        }
+        if (p->h_stopped[r]) {
+          active[r] = 0;
+          continue;
+        }
+        if (fixed && its[r] >= opts->fixed_its) {
+          p->h_stopped[r] = 1;
+          active[r] = 0;
+          push = true;
+          continue;
+        }
+        any_active = true;
+      }
+      if (push)
+        HZ_CUDA(cudaMemcpyAsync(go.stopped, p->h_stopped, sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+      if (!any_active) break;
+    }
+    // u += Z y (rhs that were done at the cycle start have kend = 0)
+    HZ_CUDA(hz::launch_backsolve(go, nrhs, st));
+    HZ_CUDA(hz::launch_combine(ub, p->Z, n, zrs, go, Buf<const double2>{nullptr, 0}, -1, 1, n, nrhs,
+                               M, st));
+    if (diverged) break;
+  }
+  // the loop ends right after a residual evaluation, so rel[] is the final true residual
+  hz_status ret = HZ_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    const bool conv = std::isfinite(rel[r]) && rel[r] <= opts->rtol;
+    if (stats) {
+      stats[r].cycles = cycles[r];
+      stats[r].its = its[r];
+      stats[r].matvecs = mvs[r];
+      stats[r].converged = conv ? 1 : 0;
+      stats[r].rel_res_true = rel[r];
+    }
+    if (!conv && !fixed && ret == HZ_OK) ret = HZ_ERR_NOT_CONVERGED;
+  }
+  if (diverged) {
+    t_err = "a residual became NaN or Inf";
+    return HZ_ERR_DIVERGED;
+  }
+  if (ret == HZ_ERR_NOT_CONVERGED) t_err = "max_cycles reached above rtol";
+  return ret;
+}
+
+}  // extern "C"

@@ -1,0 +1,155 @@
+// Internal declarations shared by the translation units of libhz (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hz.h"
+
+namespace hz {
+
+constexpr int MAXJ = 16;          // contour nodes per problem
+constexpr int RED_THREADS = 256;  // threads of a reduction block
+constexpr int RED_PPT = 4;        // points per thread in a reduction block
+constexpr int RED_CHUNK = RED_THREADS * RED_PPT;
+
+// Grid geometry and the scalars of the normalised operator (A = s L_h - diag(m) - i diag(a)).
+struct Geom {
+  int nx, ny, nz;
+  int layer;       // sponge cells
+  long long n;     // nx*ny*nz
+  double cs;       // s / h^2: weight of the 7-point Laplacian
+  double sig;      // sigma_max of the sponge
+};
+
+// Per-node parameters of the polynomial scheme (eq:fix-pt-exp) and the quadrature (§6).
+struct NodeParams {
+  double zr, zi;     // node z_j
+  double sr, si;     // weight sigma_j
+  double z0r, z0i;   // Taylor centre z0 = (b1+b2)/2 + i Im z_j
+  double delta;      // real step
+  double nu;         // predicted rate (eq:fix-pt-conv)
+  int q;             // polynomial order
+  int sweeps;        // fixed-point sweeps per shifted solve
+};
+
+// A device buffer of one field per right-hand side: field r at p + r*rs (elements).
+template <typename T>
+struct Buf {
+  T* p;
+  long long rs;
+};
+
+enum StageKind { SK_NONE = 0, SK_FIRST = 1, SK_MID = 2, SK_LAST = 3, SK_FIRST_LAST = 4 };
+
+// What one node does in one stage (one stencil sweep) of the batched polynomial solve.
+//   FIRST      k = mdi((A - z0) y - f),   acc = y + k                (yzero: y = 0, no stencil)
+//   MID        k = mdi((A - z0) kin - cf f),   acc += k
+//   LAST       y = (acc + mdi((A - z0) kin - cf f)) * ip
+//   FIRST_LAST y_out = (y + mdi((A - z0) y - f)) * ip                 (q = 1)
+// With `final_quad` set, LAST / FIRST_LAST add wq * y_new into w instead of storing y.
+struct StageNode {
+  double mdr, mdi;   // -i delta / j
+  double cfr, cfi;   // coefficient of f
+  double z0r, z0i;
+  double ipr, ipi;   // 1 / ptilde(z)
+  double wqr, wqi;   // sigma_j / z_j
+  int kind, yzero;
+  long long in, kout, acc, yout;  // element offsets of the node's fields in the rhs workspace
+};
+
+struct StageArgs {
+  StageNode nd[MAXJ];
+  int nnodes;
+  int final_quad;
+};
+
+// Per-right-hand-side state of one GMRES / FGMRES cycle on the device.
+struct GmresDev {
+  int mmax;
+  double2* R;      // [r][(mmax+1)*mmax] upper triangle after rotations, column-major
+  double* cc;      // [r][mmax] rotation cosines
+  double2* ss;     // [r][mmax] rotation sines
+  double2* g;      // [r][mmax+1] rotated right-hand side beta e1
+  double2* y;      // [r][mmax] least-squares solution
+  double2* h1;     // [r][mmax+2] first Gram-Schmidt pass (+ ||w||^2 in slot k+1)
+  double2* h2;     // [r][mmax+2] second pass
+  double2* nrm;    // [r][2]
+  double* scal;    // [r][SC_COUNT]
+  int* kend;       // [r] columns of the least-squares problem
+  int* stopped;    // [r] 1 once the cycle of this rhs has ended
+};
+
+enum { SC_EST = 0, SC_INV = 1, SC_BETA = 2, SC_TOL = 3, SC_HN = 4, SC_DR = 5, SC_DI = 6,
+       SC_RES2 = 7, SC_COUNT = 8 };
+
+// Launch counter shared by every kernel wrapper.
+extern std::atomic<unsigned long long> g_launches;
+
+// ---- kernel wrappers (hz_kernels.cu); each returns cudaGetLastError() after launch ----
+template <typename T, typename R>
+cudaError_t launch_stencil(const Geom& g, const R* m, Buf<const T> x, Buf<T> y, int nvec,
+                           double zr, double zi, cudaStream_t st);
+
+template <typename T, typename R>
+cudaError_t launch_poly_stage(const Geom& g, const R* m, Buf<const T> f, T* ws, long long wrs,
+                              Buf<double2> w, int nvec, const StageArgs& a, cudaStream_t st);
+
+cudaError_t launch_convert_c128_c64(Buf<const double2> x, Buf<float2> y, long long n, int nvec,
+                                    cudaStream_t st);
+cudaError_t launch_convert_c64_c128(Buf<const float2> x, Buf<double2> y, long long n, int nvec,
+                                    cudaStream_t st);
+
+// Gram-Schmidt reductions over nb basis fields V_0..V_{nb-1} (V_i of rhs r at
+// V + r*vrs + i*vis) and one field w.  mode 0: h1[i] = <V_i, w>, h1[nb] = ||w||^2;
+// mode 1: w -= sum_i h1[i] V_i, then h2[i] = <V_i, w>;
+// mode 2: w -= sum_i h2[i] V_i, then ||w||^2, then the Givens step of column nb-1.
+cudaError_t launch_cgs(int mode, const double2* V, long long vis, long long vrs, int nb,
+                       Buf<double2> w, long long n, const GmresDev& gs, double2* partial,
+                       unsigned* counters, int nvec, double breakdown, cudaStream_t st);
+
+// dst[r] = src[r] * gs.scal[r][SC_INV]
+cudaError_t launch_scale(Buf<double2> dst, Buf<const double2> src, long long n, const GmresDev& gs,
+                         int nvec, cudaStream_t st);
+
+// out[r] = (accumulate ? out[r] : 0) + sum_{i<kend[r]} y[r][i] B_i + e_coef[r] * E[r]
+cudaError_t launch_combine(Buf<double2> out, const double2* B, long long bis, long long brs,
+                           const GmresDev& gs, Buf<const double2> E, int e_slot, int accumulate,
+                           long long n, int nvec, int kmax, cudaStream_t st);
+
+// y = R^{-1} g over kend[r] columns (one thread per rhs)
+cudaError_t launch_backsolve(const GmresDev& gs, int nvec, cudaStream_t st);
+
+// Starting vector of a cycle.  v0[r] = f[r] - fscale*A x[r] (x may be null = 0; A applied
+// in float64), then ||v0||^2 -> beta, inv, g[0] = beta, kend = 0, stopped = (beta == 0).
+cudaError_t launch_residual_start(const Geom& g, const double* m, Buf<const double2> f, double fs,
+                                  Buf<const double2> x, Buf<double2> v0, const GmresDev& gs,
+                                  double2* partial, unsigned* counters, int nvec, cudaStream_t st);
+
+// FCI step size: d = <Aw, r> / <Aw, Aw> into scal[SC_DR/SC_DI]; then v0 = r - d Aw and the
+// inner cycle start as in launch_residual_start.
+cudaError_t launch_fci_step(Buf<const double2> Aw, Buf<const double2> r, Buf<double2> v0,
+                            const GmresDev& gs, double2* partial, unsigned* counters,
+                            long long n, int nvec, cudaStream_t st);
+
+void count_launch();
+
+// ---- host set-up (hz_setup.cpp) ----
+struct Setup {
+  double c_min, s, b1, b2, rho2;
+  std::vector<double> m;  // c_min^2 / c^2
+};
+
+// Coefficients and spectrum rectangle of a problem (Lemma 3.1 with exact Weyl bounds).
+void setup_operator(const hz_grid& g, const double* c, Setup& out);
+
+// Nodes and weights of eq:quad-points, then per node (z0, delta, q, nu, sweeps) by the delta
+// search of eq:fix-pt-conv.  Returns false if some node has no converging order <= qmax.
+bool setup_nodes(const Setup& su, const hz_contour_opts& co, std::vector<NodeParams>& nodes,
+                 std::string& err);
+
+}  // namespace hz

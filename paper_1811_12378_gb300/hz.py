@@ -1,0 +1,328 @@
+"""Python binding of libhz: argument marshalling over the C ABI in include/hz.h.
+
+Every step of the method runs in libhz's CUDA kernels; this module only converts torch
+tensors and numpy arrays into pointers and sizes.  torch supplies device memory and
+streams.  If the library is missing, loading fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+HZ_C128 = 0
+HZ_MIXED_C64 = 1
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory",
+          4: "not converged", 5: "breakdown", 6: "diverged", 7: "set-up failed"}
+
+# every exported symbol declared in include/hz.h
+EXPORTS = ["hz_problem_create", "hz_plan", "hz_problem_destroy", "hz_problem_get_info",
+           "hz_problem_nodes", "hz_problem_set_nodes", "hz_apply_shifted", "hz_shifted_solve",
+           "hz_fci", "hz_solve", "hz_profile_enable", "hz_profile_read", "hz_status_string",
+           "hz_last_error", "hz_launch_count"]
+
+# kernel classes of hz_profile_read
+PROF_POLY, PROF_STENCIL, PROF_KRYLOV = 0, 1, 2
+
+
+class HzGrid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double),
+                ("omega", C.c_double), ("layer_cells", C.c_int), ("sigma_max", C.c_double)]
+
+
+class HzContour(C.Structure):
+    _fields_ = [("J", C.c_int), ("t", C.c_double), ("eps", C.c_double), ("qmax", C.c_int),
+                ("reduction", C.c_double)]
+
+
+class HzLimits(C.Structure):
+    _fields_ = [("nrhs_max", C.c_int), ("restart_max", C.c_int), ("inner_k_max", C.c_int)]
+
+
+class HzSolveOpts(C.Structure):
+    _fields_ = [("restart_m", C.c_int), ("inner_k", C.c_int), ("rtol", C.c_double),
+                ("max_cycles", C.c_int), ("precision", C.c_int), ("fixed_its", C.c_int)]
+
+
+class HzSolveStats(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("its", C.c_int), ("matvecs", C.c_longlong),
+                ("converged", C.c_int), ("rel_res_true", C.c_double)]
+
+
+class HzInfo(C.Structure):
+    _fields_ = [("s", C.c_double), ("b1", C.c_double), ("b2", C.c_double),
+                ("rho2", C.c_double), ("J", C.c_int), ("stages", C.c_int), ("n", C.c_longlong)]
+
+
+class HzError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libhz: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Load libhz (building it first if needed).  Raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libhz is not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int)
+    lib.hz_problem_create.argtypes = [C.POINTER(HzGrid), dp, C.POINTER(HzContour),
+                                      C.POINTER(HzLimits), C.POINTER(P)]
+    lib.hz_plan.argtypes = [C.POINTER(HzGrid), dp, C.POINTER(HzContour), C.POINTER(HzInfo),
+                            dp, dp, dp, dp, ip, dp, ip]
+    lib.hz_problem_destroy.argtypes = [P]
+    lib.hz_problem_get_info.argtypes = [P, C.POINTER(HzInfo)]
+    lib.hz_problem_nodes.argtypes = [P, dp, dp, dp, dp, ip, dp, ip]
+    lib.hz_problem_set_nodes.argtypes = [P, C.c_int, dp, dp, dp, dp, ip, ip]
+    lib.hz_apply_shifted.argtypes = [P, C.c_double, C.c_double, P, P, C.c_int, C.c_int, P]
+    lib.hz_shifted_solve.argtypes = [P, C.c_int, P, P, C.c_int, C.c_int, P]
+    lib.hz_fci.argtypes = [P, P, P, C.c_int, C.c_int, C.c_int, P]
+    lib.hz_solve.argtypes = [P, P, P, C.c_int, C.POINTER(HzSolveOpts), C.POINTER(HzSolveStats), P]
+    lib.hz_profile_enable.argtypes = [P, C.c_int]
+    lib.hz_profile_read.argtypes = [P, C.c_int, C.POINTER(C.c_longlong), dp, dp]
+    lib.hz_status_string.argtypes = [C.c_int]
+    lib.hz_status_string.restype = C.c_char_p
+    lib.hz_last_error.argtypes = []
+    lib.hz_last_error.restype = C.c_char_p
+    lib.hz_launch_count.argtypes = []
+    lib.hz_launch_count.restype = C.c_ulonglong
+    for name in EXPORTS:
+        fn = getattr(lib, name)
+        if name not in ("hz_status_string", "hz_last_error", "hz_launch_count"):
+            fn.restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int, lib=None, allow=()):
+    if status != 0 and status not in allow:
+        lib = lib or load()
+        raise HzError(status, lib.hz_last_error().decode())
+    return status
+
+
+def launch_count() -> int:
+    return int(load().hz_launch_count())
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _grid(nx, ny, nz, h, omega, layer_cells, sigma_max):
+    return HzGrid(int(nx), int(ny), int(nz), float(h), float(omega), int(layer_cells),
+                  float(sigma_max))
+
+
+def _tables_from(buf):
+    z, sg, z0, dl, q, nu, sw = buf
+    return {"z": z[0::2] + 1j * z[1::2], "sigma": sg[0::2] + 1j * sg[1::2],
+            "z0": z0[0::2] + 1j * z0[1::2], "delta": dl.copy(), "q": q.copy(), "nu": nu.copy(),
+            "sweeps": sw.copy()}
+
+
+def _new_tables(J):
+    return (np.zeros(2 * J), np.zeros(2 * J), np.zeros(2 * J), np.zeros(J),
+            np.zeros(J, dtype=np.int32), np.zeros(J), np.zeros(J, dtype=np.int32))
+
+
+def plan(c: np.ndarray, h: float, omega: float, layer_cells: int, sigma_max: float, J: int,
+         t: float, eps: float, qmax: int = 5, reduction: float = 5.0):
+    """Host-only set-up of libhz (no GPU): (info dict, node tables dict)."""
+    lib = load()
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    nz, ny, nx = c.shape
+    g = _grid(nx, ny, nz, h, omega, layer_cells, sigma_max)
+    co = HzContour(int(J), float(t), float(eps), int(qmax), float(reduction))
+    info = HzInfo()
+    tb = _new_tables(J)
+    _check(lib.hz_plan(C.byref(g), _dp(c), C.byref(co), C.byref(info), _dp(tb[0]), _dp(tb[1]),
+                       _dp(tb[2]), _dp(tb[3]), _ip(tb[4]), _dp(tb[5]), _ip(tb[6])), lib)
+    return _info_dict(info), _tables_from(tb)
+
+
+def _info_dict(info: HzInfo):
+    return {"s": info.s, "b1": info.b1, "b2": info.b2, "rho2": info.rho2, "J": info.J,
+            "stages": info.stages, "n": info.n}
+
+
+@dataclass
+class SolveStats:
+    cycles: int
+    its: int
+    matvecs: int
+    converged: bool
+    rel_res_true: float
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _dev_ptr(t, dtype, n):
+    import torch
+    if not t.is_cuda:
+        raise ValueError("libhz fields must be CUDA tensors")
+    if t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("fields must be contiguous")
+    if t.numel() % n:
+        raise ValueError(f"field size {t.numel()} is not a multiple of the grid size {n}")
+    return C.c_void_p(t.data_ptr()), t.numel() // n
+
+
+class Problem:
+    """A Helmholtz problem on the current CUDA device (wraps hz_problem_create).
+
+    c: wavespeed, numpy (nz, ny, nx).  All fields passed to the methods are contiguous CUDA
+    tensors of shape (nvec, nz, ny, nx) (or any shape with nvec*n elements), complex128 unless
+    a complex64 precision is asked for.
+    """
+
+    def __init__(self, c, h, omega, layer_cells, sigma_max, J, t, eps, qmax=5, reduction=5.0,
+                 nrhs_max=1, restart_max=30, inner_k_max=8):
+        self._lib = load()
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        self.shape = c.shape
+        nz, ny, nx = c.shape
+        self.n = nx * ny * nz
+        g = _grid(nx, ny, nz, h, omega, layer_cells, sigma_max)
+        co = HzContour(int(J), float(t), float(eps), int(qmax), float(reduction))
+        lim = HzLimits(int(nrhs_max), int(restart_max), int(inner_k_max))
+        handle = C.c_void_p()
+        _check(self._lib.hz_problem_create(C.byref(g), _dp(c), C.byref(co), C.byref(lim),
+                                           C.byref(handle)), self._lib)
+        self._h = handle
+        self.nrhs_max = nrhs_max
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hz_problem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def info(self):
+        info = HzInfo()
+        _check(self._lib.hz_problem_get_info(self._h, C.byref(info)), self._lib)
+        return _info_dict(info)
+
+    def profile(self, on: bool = True):
+        """Start (and zero) or stop per-kernel-class CUDA-event timing."""
+        _check(self._lib.hz_profile_enable(self._h, 1 if on else 0), self._lib)
+
+    def profile_read(self, cls: int):
+        """(launches, milliseconds, algorithmic bytes) of a kernel class since profile()."""
+        nl, ms, by = C.c_longlong(), C.c_double(), C.c_double()
+        _check(self._lib.hz_profile_read(self._h, int(cls), C.byref(nl), C.byref(ms),
+                                         C.byref(by)), self._lib)
+        return int(nl.value), float(ms.value), float(by.value)
+
+    def nodes(self):
+        J = self.info["J"]
+        tb = _new_tables(J)
+        _check(self._lib.hz_problem_nodes(self._h, _dp(tb[0]), _dp(tb[1]), _dp(tb[2]), _dp(tb[3]),
+                                          _ip(tb[4]), _dp(tb[5]), _ip(tb[6])), self._lib)
+        return _tables_from(tb)
+
+    def set_nodes(self, z, sigma, z0, delta, q, sweeps):
+        z = np.asarray(z, dtype=np.complex128)
+        J = len(z)
+        zr = np.ascontiguousarray(np.stack([z.real, z.imag], 1).ravel())
+        s = np.asarray(sigma, dtype=np.complex128)
+        sr = np.ascontiguousarray(np.stack([s.real, s.imag], 1).ravel())
+        z0 = np.asarray(z0, dtype=np.complex128)
+        z0r = np.ascontiguousarray(np.stack([z0.real, z0.imag], 1).ravel())
+        dl = np.ascontiguousarray(delta, dtype=np.float64)
+        qq = np.ascontiguousarray(q, dtype=np.int32)
+        sw = np.ascontiguousarray(sweeps, dtype=np.int32)
+        _check(self._lib.hz_problem_set_nodes(self._h, J, _dp(zr), _dp(sr), _dp(z0r), _dp(dl),
+                                              _ip(qq), _ip(sw)), self._lib)
+
+    def apply_shifted(self, x, z=0.0, out=None, precision=None, stream=None):
+        import torch
+        prec = precision if precision is not None else (
+            HZ_MIXED_C64 if x.dtype == torch.complex64 else HZ_C128)
+        dt = torch.complex64 if prec == HZ_MIXED_C64 else torch.complex128
+        xp, nvec = _dev_ptr(x, dt, self.n)
+        y = torch.empty_like(x) if out is None else out
+        yp, _ = _dev_ptr(y, dt, self.n)
+        z = complex(z)
+        _check(self._lib.hz_apply_shifted(self._h, z.real, z.imag, xp, yp, nvec, prec,
+                                          _stream(stream)), self._lib)
+        return y
+
+    def shifted_solve(self, node, f, out=None, precision=None, stream=None):
+        import torch
+        prec = precision if precision is not None else (
+            HZ_MIXED_C64 if f.dtype == torch.complex64 else HZ_C128)
+        dt = torch.complex64 if prec == HZ_MIXED_C64 else torch.complex128
+        fp, nvec = _dev_ptr(f, dt, self.n)
+        y = torch.empty_like(f) if out is None else out
+        yp, _ = _dev_ptr(y, dt, self.n)
+        _check(self._lib.hz_shifted_solve(self._h, int(node), fp, yp, nvec, prec,
+                                          _stream(stream)), self._lib)
+        return y
+
+    def fci(self, r, inner_k=4, precision=HZ_C128, out=None, stream=None):
+        import torch
+        rp, nvec = _dev_ptr(r, torch.complex128, self.n)
+        y = torch.empty_like(r) if out is None else out
+        yp, _ = _dev_ptr(y, torch.complex128, self.n)
+        _check(self._lib.hz_fci(self._h, rp, yp, nvec, int(inner_k), int(precision),
+                                _stream(stream)), self._lib)
+        return y
+
+    def solve(self, f, restart=30, inner_k=4, rtol=1e-8, max_cycles=50, precision=HZ_C128,
+              fixed_its=0, out=None, stream=None, check=True):
+        """FGMRES(restart) with FCI; f in physical units.  Returns (u, [SolveStats])."""
+        import torch
+        fp, nrhs = _dev_ptr(f, torch.complex128, self.n)
+        u = torch.empty_like(f) if out is None else out
+        up, _ = _dev_ptr(u, torch.complex128, self.n)
+        opts = HzSolveOpts(int(restart), int(inner_k), float(rtol), int(max_cycles),
+                           int(precision), int(fixed_its))
+        st = (HzSolveStats * max(nrhs, 1))()
+        status = self._lib.hz_solve(self._h, fp, up, nrhs, C.byref(opts), st, _stream(stream))
+        _check(status, self._lib, allow=() if check else (4,))
+        stats = [SolveStats(s.cycles, s.its, s.matvecs, bool(s.converged), s.rel_res_true)
+                 for s in st[:nrhs]]
+        return u, stats

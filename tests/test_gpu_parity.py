@@ -1,0 +1,272 @@
+"""GPU parity: every call of the C ABI against the CPU oracle on the same seeded inputs.
+
+Sizes span several 32x4 stencil tiles with ragged tails in x and y, 1x1x1 and degenerate
+grids, several right-hand sides per launch, and the full 64^3 Gaussian-bump workload.
+Tolerances (relative L2): float64 stencil 1e-14, float64 polynomial solve 1e-12, float64
+FCI 1e-11, float64 FGMRES iterates at a fixed step count 1e-9; complex64 stencil 2e-6,
+complex64 polynomial solve / mixed FCI 1e-5 (float32 rounding, about 1e-7 a step, through
+contracting iterations).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import hz_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1811_12378_gb300 as hzpkg  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def rel(a, b):
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def to_dev(x, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV).to(dtype).contiguous()
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+def oracle_of(wl):
+    op = O.make_operator(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max)
+    (b1, b2, rho2), nodes = O.setup_nodes(op, wl.J, wl.t, wl.eps)
+    return op, nodes
+
+
+def problem_of(wl, nodes=None, nrhs_max=4, restart_max=30, inner_k_max=8):
+    P = hzpkg.Problem(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, wl.J, wl.t, wl.eps,
+                      nrhs_max=nrhs_max, restart_max=restart_max, inner_k_max=inner_k_max)
+    if nodes is not None:
+        P.set_nodes([nd.z for nd in nodes], [nd.sigma for nd in nodes], [nd.z0 for nd in nodes],
+                    [nd.delta for nd in nodes], [nd.q for nd in nodes],
+                    [nd.sweeps for nd in nodes])
+    return P
+
+
+RAGGED = [((37, 19, 11), 3), ((33, 5, 2), 1), ((64, 64, 64), 8), ((1, 1, 1), 0), ((2, 7, 1), 1)]
+
+
+@pytest.mark.parametrize("shape,layer", RAGGED, ids=lambda v: str(v))
+def test_stencil_parity(shape, layer):
+    """(A - zI)x for 3 fields per launch, float64 and float32 paths (§7.1)."""
+    nx, ny, nz = shape
+    wl = W.small_case(11, nx, ny, nz, layer=layer, medium="bumps" if nx > 1 else "const")
+    op = O.make_operator(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max)
+    x = W.random_field(5, 3, nx, ny, nz)
+    with hzpkg.Problem(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, 4, 1.0, 1.0) as P:
+        for z in (0.0, 0.3 - 1.7j, -2.0 + 0.5j):
+            ref = np.stack([op.apply(x[v], z) for v in range(3)])
+            y = to_np(P.apply_shifted(to_dev(x), z))
+            assert rel(y, ref) <= 1e-14
+            y32 = to_np(P.apply_shifted(to_dev(x, torch.complex64), z))
+            assert rel(y32, ref) <= 2e-6
+
+
+def test_stencil_sine_modes_gpu():
+    """P1 on the GPU: sine modes are eigenvectors of the stencil with c = 1, no sponge."""
+    nx, ny, nz = 40, 21, 9
+    h = 1.0 / 41
+    c = np.ones((nz, ny, nx))
+    omega = 2 * math.pi / (8 * h)
+    s = 1.0 / omega ** 2
+    with hzpkg.Problem(c, h, omega, 0, 0.0, 4, 1.0, 1.0) as P:
+        for kx, ky, kz in [(1, 1, 1), (7, 20, 3), (40, 2, 9)]:
+            i = np.arange(1, nx + 1)
+            j = np.arange(1, ny + 1)
+            k = np.arange(1, nz + 1)
+            v = (np.sin(kz * np.pi * k / (nz + 1))[:, None, None]
+                 * np.sin(ky * np.pi * j / (ny + 1))[None, :, None]
+                 * np.sin(kx * np.pi * i / (nx + 1))[None, None, :]).astype(np.complex128)
+            lam = sum(4 / h ** 2 * math.sin(kk * math.pi / (2 * (nn + 1))) ** 2
+                      for kk, nn in ((kx, nx), (ky, ny), (kz, nz)))
+            mu = s * lam - 1.0
+            y = to_np(P.apply_shifted(to_dev(v[None])))[0]
+            scale = 12 / h ** 2 * s + 1.0   # bound of |A| on the grid
+            assert np.linalg.norm(y - mu * v) <= 1e-14 * scale * np.linalg.norm(v)
+
+
+@pytest.mark.parametrize("prec", [hzpkg.HZ_C128, hzpkg.HZ_MIXED_C64])
+def test_shifted_solve_parity(prec):
+    """Each node's polynomial solve (eq:fix-pt-exp) on 2 right-hand sides at once."""
+    wl = W.small_case(3, 13, 9, 7, layer=2, J=4)
+    op, nodes = oracle_of(wl)
+    f = W.random_field(17, 2, wl.nx, wl.ny, wl.nz)
+    dt = torch.complex128 if prec == hzpkg.HZ_C128 else torch.complex64
+    tol = 1e-12 if prec == hzpkg.HZ_C128 else 1e-5
+    with problem_of(wl, nodes) as P:
+        for j, nd in enumerate(nodes):
+            y = to_np(P.shifted_solve(j, to_dev(f, dt), precision=prec))
+            ref = np.stack([O.poly_solve(op, f[v], nd) for v in range(2)])
+            assert rel(y, ref) <= tol, (j, nd.q, nd.sweeps)
+
+
+def test_shifted_solve_q1_and_high_order():
+    """Orders 1 (ping-pong of y) and 5 through hz_problem_set_nodes."""
+    wl = W.small_case(8, 10, 6, 5, layer=1, J=3)
+    op, nodes = oracle_of(wl)
+    b1, b2, rho2 = O.spectrum_box(op)
+    custom = []
+    for nd, q, sw in zip(nodes, (1, 5, 2), (7, 2, 3)):
+        d, nu = O.optimize_delta(q, nd.z, nd.z0, O.box_boundary(b1, b2, rho2))
+        custom.append(O.NodeParams(nd.z, nd.sigma, nd.z0, d, q, nu, sw))
+    f = W.random_field(2, 1, wl.nx, wl.ny, wl.nz)
+    with problem_of(wl, custom) as P:
+        for j, nd in enumerate(custom):
+            y = to_np(P.shifted_solve(j, to_dev(f)))
+            assert rel(y[0], O.poly_solve(op, f[0], nd)) <= 1e-12
+
+
+@pytest.mark.parametrize("prec,kin", [(hzpkg.HZ_C128, 3), (hzpkg.HZ_C128, 0),
+                                      (hzpkg.HZ_MIXED_C64, 4)])
+def test_fci_parity(prec, kin):
+    """Algorithm 1 on 3 fields at once."""
+    wl = W.small_case(6, 23, 10, 9, layer=2, J=5)
+    op, nodes = oracle_of(wl)
+    r = W.random_field(9, 3, wl.nx, wl.ny, wl.nz)
+    with problem_of(wl, nodes) as P:
+        out = to_np(P.fci(to_dev(r), inner_k=kin, precision=prec))
+    ref = np.stack([O.fci(op, r[v], nodes, kin) for v in range(3)])
+    tol = 1e-11 if prec == hzpkg.HZ_C128 else 1e-5
+    assert rel(out, ref) <= tol
+
+
+def test_fci_eigenvector_exact_gpu():
+    """P7 through the GPU: FCI of a sine mode returns v / mu."""
+    nx, ny, nz = 6, 5, 7
+    h = 1.0 / 8
+    c = np.ones((nz, ny, nx))
+    omega = 2 * math.pi / (6 * h)
+    with hzpkg.Problem(c, h, omega, 0, 0.0, 4, 1.0, 0.5) as P:
+        i, j, k = np.arange(1, nx + 1), np.arange(1, ny + 1), np.arange(1, nz + 1)
+        v = (np.sin(2 * np.pi * k / (nz + 1))[:, None, None]
+             * np.sin(1 * np.pi * j / (ny + 1))[None, :, None]
+             * np.sin(3 * np.pi * i / (nx + 1))[None, None, :]).astype(np.complex128)
+        lam = sum(4 / h ** 2 * math.sin(kk * math.pi / (2 * (nn + 1))) ** 2
+                  for kk, nn in ((3, nx), (1, ny), (2, nz)))
+        mu = lam / omega ** 2 - 1.0
+        out = to_np(P.fci(to_dev(v[None]), inner_k=3))[0]
+        assert rel(out, v / mu) <= 1e-12
+
+
+def test_fci_full_size_gaussian_bumps_64():
+    """FCI at the full 64^3, J = 8 Gaussian-bump workload: float64 and mixed forms."""
+    wl = W.gaussian_bumps_64()
+    op, nodes = oracle_of(wl)
+    r = W.random_field(4, 1, wl.nx, wl.ny, wl.nz)
+    ref = O.fci(op, r[0], nodes, wl.k_in)
+    with problem_of(wl, nodes, nrhs_max=1, restart_max=30, inner_k_max=4) as P:
+        out = to_np(P.fci(to_dev(r), inner_k=wl.k_in))
+        assert rel(out[0], ref) <= 1e-11
+        outm = to_np(P.fci(to_dev(r), inner_k=wl.k_in, precision=hzpkg.HZ_MIXED_C64))
+        assert rel(outm[0], ref) <= 1e-5
+
+
+def test_solve_fixed_iterations_parity():
+    """FGMRES(5) iterates across two restarts equal the oracle's at a fixed step count."""
+    wl = W.small_case(3, 13, 9, 7, layer=2, J=4)
+    op, nodes = oracle_of(wl)
+    f = wl.f[0]
+    res = O.solve(op, op.s * f, nodes, m=5, k_in=3, rtol=1e-30, max_cycles=100, fixed_its=12)
+    with problem_of(wl, nodes, nrhs_max=1, restart_max=5, inner_k_max=3) as P:
+        u, st = P.solve(to_dev(f[None]), restart=5, inner_k=3, rtol=1e-30, max_cycles=100,
+                        fixed_its=12)
+    assert st[0].its == 12 and st[0].cycles == 3 == res.cycles
+    assert rel(to_np(u)[0], res.u) <= 1e-9
+    assert st[0].rel_res_true == pytest.approx(res.rel_res_true, rel=1e-6)
+
+
+def test_solve_point_source_32_converges_like_oracle():
+    """32^3 point source (c = 1, 10 ppw, J = 4): float64 FGMRES(30) reaches 1e-8 in the
+    oracle's step count; at that fixed count the iterates agree; the true residual is checked
+    with the oracle's operator."""
+    wl = W.point_source_32()
+    op, nodes = oracle_of(wl)
+    f = wl.f[0]
+    res = O.solve(op, op.s * f, nodes, m=30, k_in=4, rtol=1e-8, max_cycles=20)
+    with problem_of(wl, nodes, nrhs_max=1, restart_max=30, inner_k_max=4) as P:
+        u, st = P.solve(to_dev(f[None]), restart=30, inner_k=4, rtol=1e-8, max_cycles=20)
+        uf, stf = P.solve(to_dev(f[None]), restart=30, inner_k=4, rtol=1e-30, max_cycles=20,
+                          fixed_its=res.its)
+    assert st[0].converged and res.converged
+    assert abs(st[0].its - res.its) <= 1
+    ug = to_np(u)[0]
+    true = np.linalg.norm(op.s * f - op.apply(ug)) / np.linalg.norm(op.s * f)
+    assert true <= 1e-8
+    assert rel(to_np(uf)[0], res.u) <= 1e-9
+
+
+def test_mixed_solve_point_source_32():
+    """Mixed form (complex64 sweeps, float64 Krylov and residual) reaches the same 1e-8 true
+    residual; its error against the float64 solve is within the residual bound."""
+    wl = W.point_source_32()
+    op, nodes = oracle_of(wl)
+    f = wl.f[0]
+    with problem_of(wl, nodes, nrhs_max=1, restart_max=30, inner_k_max=4) as P:
+        u64, s64 = P.solve(to_dev(f[None]), restart=30, inner_k=4, rtol=1e-8, max_cycles=20)
+        u32, s32 = P.solve(to_dev(f[None]), restart=30, inner_k=4, rtol=1e-8, max_cycles=20,
+                           precision=hzpkg.HZ_MIXED_C64)
+    assert s32[0].converged
+    ug = to_np(u32)[0]
+    true = np.linalg.norm(op.s * f - op.apply(ug)) / np.linalg.norm(op.s * f)
+    assert true <= 1e-8
+    assert s32[0].its <= 1.25 * s64[0].its + 2
+
+
+def test_batched_rhs_equal_single_solves():
+    """Several right-hand sides in one call give the results of separate calls."""
+    wl = W.small_case(12, 12, 11, 10, nrhs=3, layer=2, J=4)
+    op, nodes = oracle_of(wl)
+    with problem_of(wl, nodes, nrhs_max=3, restart_max=8, inner_k_max=3) as P:
+        ub, sb = P.solve(to_dev(wl.f), restart=8, inner_k=3, rtol=1e-9, max_cycles=30)
+        for v in range(3):
+            u1, s1 = P.solve(to_dev(wl.f[v:v + 1]), restart=8, inner_k=3, rtol=1e-9,
+                             max_cycles=30)
+            assert s1[0].its == sb[v].its
+            assert rel(to_np(ub)[v], to_np(u1)[0]) <= 1e-14
+            true = np.linalg.norm(op.s * wl.f[v] - op.apply(to_np(ub)[v])) / np.linalg.norm(
+                op.s * wl.f[v])
+            assert true <= 1e-9
+
+
+def test_edge_cases():
+    wl = W.small_case(1, 4, 3, 2, layer=1, J=2)
+    with problem_of(wl, None, nrhs_max=2, restart_max=4, inner_k_max=2) as P:
+        n = P.n
+        # nvec = 0 is a no-op
+        e = torch.empty(0, dtype=torch.complex128, device=DEV)
+        assert P.apply_shifted(e).numel() == 0
+        # zero right-hand side: u = 0, converged
+        u, st = P.solve(torch.zeros(1, n, dtype=torch.complex128, device=DEV), restart=4,
+                        inner_k=2)
+        assert st[0].converged and float(u.abs().max()) == 0.0 and st[0].its == 0
+        # invalid arguments raise, no CPU fallback
+        f = torch.zeros(3, n, dtype=torch.complex128, device=DEV)
+        with pytest.raises(hzpkg.HzError):
+            P.shifted_solve(0, f)                                   # nvec > nrhs_max
+        with pytest.raises(hzpkg.HzError):
+            P.shifted_solve(5, f[:1])                               # node out of range
+        with pytest.raises(hzpkg.HzError):
+            P.fci(f[:1], inner_k=3)                                 # inner_k > max
+        with pytest.raises(hzpkg.HzError):
+            P.solve(f[:1], restart=5)                               # restart > max
+        with pytest.raises(ValueError):
+            P.apply_shifted(f.cpu())                                # host tensor
+
+
+def test_native_kernels_launch():
+    before = hzpkg.launch_count()
+    wl = W.small_case(1, 8, 8, 8, layer=1, J=2)
+    with problem_of(wl) as P:
+        P.apply_shifted(torch.ones(1, P.n, dtype=torch.complex128, device=DEV))
+        torch.cuda.synchronize()
+    assert hzpkg.launch_count() > before
