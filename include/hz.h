@@ -192,6 +192,24 @@ hz_status hz_profile_enable(hz_problem* p, int on);
 hz_status hz_profile_read(hz_problem* p, int cls, long long* launches, double* ms,
                           double* bytes);
 
+/* Residual without any device allocation, for callers that cannot call cudaMalloc (code
+ * running while their stream is being captured into a CUDA graph, allocators that own a
+ * fixed arena, hosts that control the GPU memory budget).  Needs no hz_problem.  For nvec
+ * double-complex fields (device, x fastest) computes r = fscale*f - A u with A the
+ * normalised operator of this header built from the device wavespeed c (nx*ny*nz doubles)
+ * and c_min = min c: m = c_min^2/c^2, s = c_min^2/omega^2; u may be null (r = fscale*f), r may
+ * be null (not stored).  norm2 (device, nvec doubles) receives ||r||^2; with
+ * fscale = c_min^2/omega^2 this is the residual hz_solve reports for u.  The paper has no
+ * counterpart: this is a deployment aid.
+ * Scratch lives in one static device array of 1 MiB (+256 bytes) that every device loading
+ * the library keeps until exit: nvec <= 64 and nvec * ceil(nx*ny*nz / 1024) <= 65536, else
+ * HZ_ERR_INVALID.  All calls share it: calls that overlap on the GPU race, so serialise
+ * them (one stream).  The first call on a device looks up the array's device address (with
+ * that device current); make it before any stream capture.  Asynchronous on `stream`. */
+hz_status hz_residual_noalloc(const hz_grid* grid, const double* c, double c_min, const void* f,
+                              double fscale, const void* u, void* r, double* norm2, int nvec,
+                              void* stream);
+
 /* Name of a status code. */
 const char* hz_status_string(hz_status s);
 

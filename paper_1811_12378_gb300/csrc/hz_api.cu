@@ -395,6 +395,10 @@ hz_status fill_scal_tol(hz_problem* p, GmresDev& gs, const std::vector<double>& 
 
 }  // namespace
 
+namespace hz {
+void set_last_error(const std::string& msg) { t_err = msg; }
+}  // namespace hz
+
 extern "C" {
 
 const char* hz_status_string(hz_status s) {

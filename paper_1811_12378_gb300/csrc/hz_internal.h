@@ -138,6 +138,9 @@ cudaError_t launch_fci_step(Buf<const double2> Aw, Buf<const double2> r, Buf<dou
 
 void count_launch();
 
+// Message returned by hz_last_error() on the calling thread.
+void set_last_error(const std::string& msg);
+
 // ---- host set-up (hz_setup.cpp) ----
 struct Setup {
   double c_min, s, b1, b2, rho2;

@@ -23,8 +23,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory",
 # every exported symbol declared in include/hz.h
 EXPORTS = ["hz_problem_create", "hz_plan", "hz_problem_destroy", "hz_problem_get_info",
            "hz_problem_nodes", "hz_problem_set_nodes", "hz_apply_shifted", "hz_shifted_solve",
-           "hz_fci", "hz_solve", "hz_profile_enable", "hz_profile_read", "hz_status_string",
-           "hz_last_error", "hz_launch_count"]
+           "hz_fci", "hz_solve", "hz_profile_enable", "hz_profile_read", "hz_residual_noalloc",
+           "hz_status_string", "hz_last_error", "hz_launch_count"]
 
 # kernel classes of hz_profile_read
 PROF_POLY, PROF_STENCIL, PROF_KRYLOV = 0, 1, 2
@@ -99,6 +99,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.hz_solve.argtypes = [P, P, P, C.c_int, C.POINTER(HzSolveOpts), C.POINTER(HzSolveStats), P]
     lib.hz_profile_enable.argtypes = [P, C.c_int]
     lib.hz_profile_read.argtypes = [P, C.c_int, C.POINTER(C.c_longlong), dp, dp]
+    lib.hz_residual_noalloc.argtypes = [C.POINTER(HzGrid), P, C.c_double, P, C.c_double, P, P, P,
+                                        C.c_int, P]
     lib.hz_status_string.argtypes = [C.c_int]
     lib.hz_status_string.restype = C.c_char_p
     lib.hz_last_error.argtypes = []
