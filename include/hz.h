@@ -83,8 +83,8 @@ typedef struct {
   double reduction;
 } hz_contour_opts;
 
-/* Workspace limits fixed at creation: right-hand sides per call, outer restart length,
- * inner GMRES steps. */
+/* Workspace limits fixed at creation: right-hand sides per call (nz * nrhs_max <= 65535),
+ * outer restart length (1..128), inner GMRES steps (0..128). */
 typedef struct {
   int nrhs_max;
   int restart_max;

@@ -21,8 +21,6 @@
 using hz::Buf;
 using hz::GmresDev;
 using hz::NodeParams;
-using hz::StageArgs;
-using hz::StageNode;
 
 namespace {
 
@@ -76,6 +74,7 @@ struct hz_problem {
   // device memory
   double* m64 = nullptr;
   float* m32 = nullptr;
+  double2* d64 = nullptr;    // [n] float64 diagonal 6 s/h^2 - m - i a
   void* poly = nullptr;      // [nrhs][4 J][n] fields (double2 or float2)
   float2* f32 = nullptr;     // [nrhs][n]
   double2* w = nullptr;      // [nrhs][n] quadrature sum
@@ -158,7 +157,7 @@ size_t gmres_carved_bytes(int nrhs, int M) {
 bool valid_grid(const hz_grid* g) {
   return g && g->nx >= 1 && g->ny >= 1 && g->nz >= 1 && g->h > 0 && std::isfinite(g->h) &&
          g->omega > 0 && std::isfinite(g->omega) && g->layer_cells >= 0 && g->sigma_max >= 0 &&
-         std::isfinite(g->sigma_max) && g->nz <= 65535;
+         std::isfinite(g->sigma_max) && g->ny <= 65535 && g->nz <= 65535;
 }
 
 // ------------------------------------------------------------------ kernel timing
@@ -247,19 +246,17 @@ hz_status run_poly(hz_problem* p, const R* m, Buf<const T> f, int nvec,
   std::vector<long long> ycur(nn);
   for (int s = 0; s < nn; ++s) ycur[s] = slots_of(s, n).Y;
   for (int t = 0; t < T_total; ++t) {
-    StageArgs a;
+    // the active nodes of this stage, compacted (one warp row of the kernel's block each)
+    hz::StageArgs<R> a;
     std::memset(&a, 0, sizeof(a));
-    a.nnodes = nn;
+    a.nnodes = 0;
     a.final_quad = (quad && t == T_total - 1) ? 1 : 0;
     for (int s = 0; s < nn; ++s) {
       const NodeParams& np = p->nodes[which[s]];
-      StageNode& sn = a.nd[s];
       const int Tj = np.q * np.sweeps;
       const int start = T_total - Tj;
-      if (t < start) {
-        sn.kind = hz::SK_NONE;
-        continue;
-      }
+      if (t < start) continue;
+      hz::StageNode<R>& sn = a.nd[a.nnodes++];
       const int tl = t - start;
       const int sweep = tl / np.q;
       const int jj = tl % np.q + 1;
@@ -275,14 +272,14 @@ hz_status run_poly(hz_problem* p, const R* m, Buf<const T> f, int nvec,
       const std::complex<double> ip = 1.0 / pz;
       const std::complex<double> md = std::complex<double>(0.0, -np.delta) / double(jj);
       const std::complex<double> wq = std::complex<double>(np.sr, np.si) / zz;
-      sn.mdr = md.real();
-      sn.mdi = md.imag();
-      sn.cfr = c[jj - 1].real();
-      sn.cfi = c[jj - 1].imag();
-      sn.z0r = np.z0r;
-      sn.z0i = np.z0i;
-      sn.ipr = ip.real();
-      sn.ipi = ip.imag();
+      sn.mdr = R(md.real());
+      sn.mdi = R(md.imag());
+      sn.cfr = R(c[jj - 1].real());
+      sn.cfi = R(c[jj - 1].imag());
+      sn.z0r = R(np.z0r);
+      sn.z0i = R(np.z0i);
+      sn.ipr = R(ip.real());
+      sn.ipi = R(ip.imag());
       sn.wqr = wq.real();
       sn.wqi = wq.imag();
       sn.acc = sl.ACC;
@@ -312,8 +309,8 @@ hz_status run_poly(hz_problem* p, const R* m, Buf<const T> f, int nvec,
     // algorithmic bytes per point: f and m once; per node FIRST y?(r) k(w) acc(w), MID k(r)
     // acc(r/w) k(w), LAST k(r) acc(r) y(w, or the float64 sum w once at the final stage)
     double bpp = double(sizeof(T)) * 1 + double(sizeof(R)) / nvec;
-    for (int s = 0; s < nn; ++s) {
-      const StageNode& sn = a.nd[s];
+    for (int s = 0; s < a.nnodes; ++s) {
+      const hz::StageNode<R>& sn = a.nd[s];
       const double e = sizeof(T);
       if (sn.kind == hz::SK_FIRST) bpp += (sn.yzero ? 2 : 3) * e;
       else if (sn.kind == hz::SK_MID) bpp += 4 * e;
@@ -343,8 +340,8 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
     HZ_TRY((run_poly<double2, double>(p, p->m64, r, nvec, all, true, wb, nullptr, st)));
   }
   // Aw, step d, inner start v0 = (r - d Aw)/||r - d Aw||
-  HZ_TIMED(p, 1, st, (stencil_bytes<double2, double>(n, nvec)),
-           (hz::launch_stencil<double2, double>(p->g, p->m64, Buf<const double2>{p->w, n},
+  HZ_TIMED(p, 1, st, (stencil_bytes<double2, double2>(n, nvec)),
+           (hz::launch_stencil_diag(p->g, p->d64, Buf<const double2>{p->w, n},
                                                 Buf<double2>{p->Aw, n}, nvec, 0.0, 0.0, st)));
   const long long vrs = (long long)(p->lim.inner_k_max + 1) * n;
   HZ_TIMED(p, 2, st, 16.0 * n * nvec * 5,
@@ -354,9 +351,8 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
                            nvec, st));
   for (int j = 0; j < kin; ++j) {
     Buf<double2> wj{p->Vin + (long long)(j + 1) * n, vrs};
-    HZ_TIMED(p, 1, st, (stencil_bytes<double2, double>(n, nvec)),
-             (hz::launch_stencil<double2, double>(
-                 p->g, p->m64, Buf<const double2>{p->Vin + (long long)j * n, vrs}, wj, nvec, 0.0,
+    HZ_TIMED(p, 1, st, (stencil_bytes<double2, double2>(n, nvec)),
+             (hz::launch_stencil_diag(p->g, p->d64, Buf<const double2>{p->Vin + (long long)j * n, vrs}, wj, nvec, 0.0,
                  0.0, st)));
     for (int mode = 0; mode < 3; ++mode)
       HZ_TIMED(p, 2, st, cgs_bytes(mode, n, j + 1, nvec),
@@ -432,8 +428,8 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
     return fail(HZ_ERR_INVALID, "invalid contour options (1 <= J <= 16, t > 0, eps > 0, "
                                 "1 <= qmax <= 12, reduction > 1)");
   if (!limits || limits->nrhs_max < 1 || limits->restart_max < 1 || limits->inner_k_max < 0 ||
-      limits->restart_max > 1000 || limits->inner_k_max > 1000)
-    return fail(HZ_ERR_INVALID, "invalid limits");
+      limits->restart_max > 128 || limits->inner_k_max > 128)
+    return fail(HZ_ERR_INVALID, "invalid limits (1 <= restart_max <= 128, 0 <= inner_k_max <= 128)");
   const long long n = (long long)grid->nx * grid->ny * grid->nz;
   for (long long i = 0; i < n; ++i)
     if (!(c_host[i] > 0) || !std::isfinite(c_host[i]))
@@ -463,6 +459,9 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   p->g.layer = grid->layer_cells;
   p->g.cs = p->su.s / (grid->h * grid->h);
   p->g.sig = grid->sigma_max;
+  p->g.csf = float(p->g.cs);
+  p->g.sigf = float(grid->sigma_max);
+  p->g.inv_layer_f = grid->layer_cells > 0 ? 1.0f / float(grid->layer_cells) : 0.0f;
   std::string err;
   if (!hz::setup_nodes(p->su, *contour, p->nodes, err)) {
     delete p;
@@ -473,6 +472,7 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   hz_status s;
   if ((s = dalloc(p, (void**)&p->m64, sizeof(double) * n)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->m32, sizeof(float) * n)) != HZ_OK) return bail(s);
+  if ((s = dalloc(p, (void**)&p->d64, sizeof(double2) * n)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, &p->poly, sizeof(double2) * 4 * (size_t)p->J * n * R)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->f32, sizeof(float2) * (size_t)n * R)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->w, sizeof(double2) * (size_t)n * R)) != HZ_OK) return bail(s);
@@ -520,6 +520,26 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   for (long long i = 0; i < n; ++i) m32[i] = float(p->su.m[i]);
   e = cudaMemcpy(p->m64, p->su.m.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->m32, m32.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    // diagonal of the float64 stencil: 6 s/h^2 - m - i a, a = sigma_max (depth/L)^2 m
+    std::vector<double2> dg(n);
+    const int L = grid->layer_cells;
+    auto dep = [L](int idx, int nn) { return std::max(0, L - std::min(idx, nn - 1 - idx)); };
+    for (int k = 0; k < grid->nz; ++k)
+      for (int j = 0; j < grid->ny; ++j)
+        for (int i = 0; i < grid->nx; ++i) {
+          const long long q = i + (long long)grid->nx * (j + (long long)grid->ny * k);
+          const double mp = p->su.m[q];
+          double ap = 0.0;
+          if (L > 0) {
+            const int d = std::max(dep(i, grid->nx), std::max(dep(j, grid->ny), dep(k, grid->nz)));
+            const double t = double(d) / double(L);
+            ap = (grid->sigma_max * (t * t)) * mp;
+          }
+          dg[q] = make_double2(6.0 * p->g.cs - mp, -ap);
+        }
+    e = cudaMemcpy(p->d64, dg.data(), sizeof(double2) * n, cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     delete p;
     return cuda_fail(e, "cudaMemcpy of coefficients");
@@ -682,8 +702,8 @@ hz_status hz_apply_shifted(hz_problem* p, double zr, double zi, const void* x, v
   cudaStream_t st = (cudaStream_t)stream;
   const long long n = p->g.n;
   if (precision == HZ_C128) {
-    HZ_TIMED(p, 1, st, (stencil_bytes<double2, double>(n, nvec)),
-             (hz::launch_stencil<double2, double>(p->g, p->m64,
+    HZ_TIMED(p, 1, st, (stencil_bytes<double2, double2>(n, nvec)),
+             (hz::launch_stencil_diag(p->g, p->d64,
                                                   Buf<const double2>{(const double2*)x, n},
                                                   Buf<double2>{(double2*)y, n}, nvec, zr, zi, st)));
   } else if (precision == HZ_MIXED_C64) {
@@ -832,8 +852,8 @@ hz_status hz_solve(hz_problem* p, const void* f, void* u, int nrhs, const hz_sol
       Buf<double2> zk{p->Z + (long long)k * n, zrs};
       HZ_TRY(run_fci(p, vk, zk, nrhs, K, opts->precision, st));
       Buf<double2> wk{p->V + (long long)(k + 1) * n, vrs};
-      HZ_TIMED(p, 1, st, (stencil_bytes<double2, double>(n, nrhs)),
-               (hz::launch_stencil<double2, double>(p->g, p->m64, Buf<const double2>{zk.p, zrs},
+      HZ_TIMED(p, 1, st, (stencil_bytes<double2, double2>(n, nrhs)),
+               (hz::launch_stencil_diag(p->g, p->d64, Buf<const double2>{zk.p, zrs},
                                                     wk, nrhs, 0.0, 0.0, st)));
       for (int mode = 0; mode < 3; ++mode)
         HZ_TIMED(p, 2, st, cgs_bytes(mode, n, k + 1, nrhs),

@@ -24,6 +24,9 @@ struct Geom {
   long long n;     // nx*ny*nz
   double cs;       // s / h^2: weight of the 7-point Laplacian
   double sig;      // sigma_max of the sponge
+  float csf;       // the same scalars in float32, so float32 kernels convert nothing
+  float sigf;
+  float inv_layer_f;
 };
 
 // Per-node parameters of the polynomial scheme (eq:fix-pt-exp) and the quadrature (§6).
@@ -52,18 +55,22 @@ enum StageKind { SK_NONE = 0, SK_FIRST = 1, SK_MID = 2, SK_LAST = 3, SK_FIRST_LA
 //   LAST       y = (acc + mdi((A - z0) kin - cf f)) * ip
 //   FIRST_LAST y_out = (y + mdi((A - z0) y - f)) * ip                 (q = 1)
 // With `final_quad` set, LAST / FIRST_LAST add wq * y_new into w instead of storing y.
+// The coefficients are held in the kernel's own real type R (float32 sweeps must not spend
+// the scarce float64 pipe on conversions); the quadrature weight is always float64.
+template <typename R>
 struct StageNode {
-  double mdr, mdi;   // -i delta / j
-  double cfr, cfi;   // coefficient of f
-  double z0r, z0i;
-  double ipr, ipi;   // 1 / ptilde(z)
+  R mdr, mdi;        // -i delta / j
+  R cfr, cfi;        // coefficient of f
+  R z0r, z0i;
+  R ipr, ipi;        // 1 / ptilde(z)
   double wqr, wqi;   // sigma_j / z_j
   int kind, yzero;
   long long in, kout, acc, yout;  // element offsets of the node's fields in the rhs workspace
 };
 
+template <typename R>
 struct StageArgs {
-  StageNode nd[MAXJ];
+  StageNode<R> nd[MAXJ];
   int nnodes;
   int final_quad;
 };
@@ -97,7 +104,11 @@ cudaError_t launch_stencil(const Geom& g, const R* m, Buf<const T> x, Buf<T> y, 
 
 template <typename T, typename R>
 cudaError_t launch_poly_stage(const Geom& g, const R* m, Buf<const T> f, T* ws, long long wrs,
-                              Buf<double2> w, int nvec, const StageArgs& a, cudaStream_t st);
+                              Buf<double2> w, int nvec, const StageArgs<R>& a, cudaStream_t st);
+
+// Float64 (A - zI)x from the precomputed diagonal dg = 6 s/h^2 - m - i a (one per point).
+cudaError_t launch_stencil_diag(const Geom& g, const double2* dg, Buf<const double2> x,
+                                Buf<double2> y, int nvec, double zr, double zi, cudaStream_t st);
 
 cudaError_t launch_convert_c128_c64(Buf<const double2> x, Buf<float2> y, long long n, int nvec,
                                     cudaStream_t st);

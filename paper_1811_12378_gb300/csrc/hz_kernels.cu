@@ -23,6 +23,9 @@ namespace {
 
 constexpr int BX = 32;  // stencil block: 32 x 4 points of one z-plane
 constexpr int BY = 4;
+constexpr int CG_WARPS = 8;  // Gram-Schmidt block: 8 warps x 32 lanes x 4 points
+constexpr int CG_PPL = 4;
+constexpr int CG_CHUNK = CG_WARPS * 32 * CG_PPL;
 
 // ---------------------------------------------------------------- complex helpers
 __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
@@ -48,13 +51,27 @@ __device__ __forceinline__ int depth1(int i, int n, int L) {
 }
 
 // Sponge damping a_p = sigma_max * (d/L)^2 * m_p (0 without a layer).
-template <typename R>
-__device__ __forceinline__ R sponge(const Geom& g, int i, int j, int k, R mp) {
-  if (g.layer <= 0) return R(0);
-  int d = max(depth1(i, g.nx, g.layer), max(depth1(j, g.ny, g.layer), depth1(k, g.nz, g.layer)));
-  R t = R(d) / R(g.layer);
-  return (R(g.sig) * (t * t)) * mp;
+__device__ __forceinline__ int sponge_depth(const Geom& g, int i, int j, int k) {
+  return max(depth1(i, g.nx, g.layer), max(depth1(j, g.ny, g.layer), depth1(k, g.nz, g.layer)));
 }
+template <typename R>
+__device__ __forceinline__ R sponge(const Geom& g, int i, int j, int k, R mp);
+template <>
+__device__ __forceinline__ double sponge<double>(const Geom& g, int i, int j, int k, double mp) {
+  if (g.layer <= 0) return 0.0;
+  const double t = double(sponge_depth(g, i, j, k)) / double(g.layer);
+  return (g.sig * (t * t)) * mp;
+}
+template <>
+__device__ __forceinline__ float sponge<float>(const Geom& g, int i, int j, int k, float mp) {
+  if (g.layer <= 0) return 0.f;
+  const float t = float(sponge_depth(g, i, j, k)) * g.inv_layer_f;
+  return (g.sigf * (t * t)) * mp;
+}
+
+template <typename R> __device__ __forceinline__ R lap_weight(const Geom& g);
+template <> __device__ __forceinline__ double lap_weight<double>(const Geom& g) { return g.cs; }
+template <> __device__ __forceinline__ float lap_weight<float>(const Geom& g) { return g.csf; }
 
 // Sum of the six neighbours of point p = (i, j, k); zero beyond the boundary.
 template <typename T>
@@ -93,34 +110,39 @@ k_stencil(Geom g, const R* __restrict__ m, const T* __restrict__ x, long long xr
   const T* xr = x + r * xrs;
   const R mp = m[p];
   const R ap = sponge<R>(g, i, j, k, mp);
-  y[r * yrs + p] = apply_point<T, R>(xr[p], nbsum(xr, p, i, j, k, g), R(g.cs), mp, ap, zr, zi);
+  y[r * yrs + p] = apply_point<T, R>(xr[p], nbsum(xr, p, i, j, k, g), lap_weight<R>(g), mp, ap,
+                                     zr, zi);
 }
 
 // ---------------------------------------------------------------- polynomial stage
-// One stencil sweep of every active node of the scheme eq:fix-pt-exp, all nodes of one
-// right-hand side handled by the same thread so that f and m are read once per point.
+// One stencil sweep of every active node of the scheme eq:fix-pt-exp.  A block covers 32
+// consecutive points of one grid row and all active nodes: warp y works on node y, so each
+// warp runs one node kind without divergence and the block's warps hide each other's load
+// latency; f and m are shared by the node warps through L1.  On the final stage of an FCI
+// application the block sums sigma_j/z_j y_j over its nodes in shared memory (float64) and
+// writes the quadrature sum w once, without storing the y_j.
 template <typename T, typename R>
-__global__ void __launch_bounds__(BX * BY)
+__global__ void __launch_bounds__(32 * MAXJ)
 k_poly_stage(Geom g, const R* __restrict__ m, const T* __restrict__ f, long long frs, T* ws,
-             long long wrs, double2* __restrict__ w, long long wwrs, const StageArgs a) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
+             long long wrs, double2* __restrict__ w, long long wwrs, const StageArgs<R> a) {
+  __shared__ double2 qs[MAXJ][32];
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y;
   const int k = blockIdx.z % g.nz;
   const int r = blockIdx.z / g.nz;
-  if (i >= g.nx || j >= g.ny) return;
-  const long long p = i + (long long)g.nx * (j + (long long)g.ny * k);
-  const T fp = f[r * frs + p];
-  const R mp = m[p];
-  const R ap = sponge<R>(g, i, j, k, mp);
-  const R cs = R(g.cs);
-  T* wsr = ws + r * wrs;
-  double wsx = 0.0, wsy = 0.0;
-  for (int q = 0; q < a.nnodes; ++q) {
-    const StageNode& nd = a.nd[q];
+  const int q = threadIdx.y;
+  const bool inside = i < g.nx;
+  double2 contrib = make_double2(0.0, 0.0);
+  if (inside) {
+    const long long p = i + (long long)g.nx * (j + (long long)g.ny * k);
+    const StageNode<R>& nd = a.nd[q];
     const int kind = nd.kind;
-    if (kind == SK_NONE) continue;
-    const T md = mk(R(nd.mdr), R(nd.mdi));
-    const R z0r = R(nd.z0r), z0i = R(nd.z0i);
+    T* wsr = ws + r * wrs;
+    const T fp = f[r * frs + p];
+    const R mp = m[p];
+    const R ap = sponge<R>(g, i, j, k, mp);
+    const R cs = lap_weight<R>(g);
+    const T md = mk(nd.mdr, nd.mdi);
     T yn;
     bool have_y = false;
     if (kind == SK_FIRST || kind == SK_FIRST_LAST) {
@@ -131,40 +153,51 @@ k_poly_stage(Geom g, const R* __restrict__ m, const T* __restrict__ f, long long
       } else {
         const T* yin = wsr + nd.in;
         yv = yin[p];
-        T Ay = apply_point<T, R>(yv, nbsum(yin, p, i, j, k, g), cs, mp, ap, z0r, z0i);
+        T Ay = apply_point<T, R>(yv, nbsum(yin, p, i, j, k, g), cs, mp, ap, nd.z0r, nd.z0i);
         kv = cmul(md, csub(Ay, fp));
       }
       if (kind == SK_FIRST) {
         wsr[nd.kout + p] = kv;
         wsr[nd.acc + p] = cadd(yv, kv);
       } else {
-        yn = cmul(cadd(yv, kv), mk(R(nd.ipr), R(nd.ipi)));
+        yn = cmul(cadd(yv, kv), mk(nd.ipr, nd.ipi));
         have_y = true;
       }
-    } else {
+    } else if (kind != SK_NONE) {
       const T* kin = wsr + nd.in;
-      T Ak = apply_point<T, R>(kin[p], nbsum(kin, p, i, j, k, g), cs, mp, ap, z0r, z0i);
-      T kv = cmul(md, csub(Ak, cmul(mk(R(nd.cfr), R(nd.cfi)), fp)));
-      T acc = wsr[nd.acc + p];
+      const T acc = wsr[nd.acc + p];
+      T Ak = apply_point<T, R>(kin[p], nbsum(kin, p, i, j, k, g), cs, mp, ap, nd.z0r, nd.z0i);
+      T kv = cmul(md, csub(Ak, cmul(mk(nd.cfr, nd.cfi), fp)));
       if (kind == SK_MID) {
         wsr[nd.kout + p] = kv;
         wsr[nd.acc + p] = cadd(acc, kv);
       } else {
-        yn = cmul(cadd(acc, kv), mk(R(nd.ipr), R(nd.ipi)));
+        yn = cmul(cadd(acc, kv), mk(nd.ipr, nd.ipi));
         have_y = true;
       }
     }
     if (have_y) {
       if (a.final_quad) {
         const double yr = double(yn.x), yi = double(yn.y);
-        wsx += nd.wqr * yr - nd.wqi * yi;
-        wsy += nd.wqr * yi + nd.wqi * yr;
+        contrib = make_double2(nd.wqr * yr - nd.wqi * yi, nd.wqr * yi + nd.wqi * yr);
       } else {
         wsr[nd.yout + p] = yn;
       }
     }
   }
-  if (a.final_quad) w[r * wwrs + p] = make_double2(wsx, wsy);
+  if (a.final_quad) {  // uniform over the launch
+    qs[q][threadIdx.x] = contrib;
+    __syncthreads();
+    if (q == 0 && inside) {
+      double sx = 0.0, sy = 0.0;
+      for (int t = 0; t < a.nnodes; ++t) {
+        sx += qs[t][threadIdx.x].x;
+        sy += qs[t][threadIdx.x].y;
+      }
+      const long long p = i + (long long)g.nx * (j + (long long)g.ny * k);
+      w[r * wwrs + p] = make_double2(sx, sy);
+    }
+  }
 }
 
 // ---------------------------------------------------------------- conversions
@@ -285,71 +318,181 @@ __device__ void givens_column(const GmresDev& gs, int r, int k, double brk) {
   if (brk_now || est <= sc[SC_TOL]) gs.stopped[r] = 1;
 }
 
+// Butterfly reduction of 8 per-lane complex partials over a warp: after the three exchange
+// steps each lane holds one vector's partial (vector index bits = lane bits 4, 3, 2), and two
+// more xor steps finish it.  18 float64 adds reduce 8 vectors, against 80 for 8 separate
+// shuffle trees -- float64 is the scarce pipe.  Lane l with (l & 3) == 0 ends with the sum
+// of vector ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 + ((l >> 2) & 1).
+__device__ __forceinline__ double2 warp_reduce8(double2 (&a)[8], int lane) {
+  double2 b4[4], b2[2];
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const double2 keep = h16 ? a[4 + t] : a[t];
+    const double2 give = h16 ? a[t] : a[4 + t];
+    b4[t] = make_double2(keep.x + __shfl_xor_sync(0xffffffffu, give.x, 16),
+                         keep.y + __shfl_xor_sync(0xffffffffu, give.y, 16));
+  }
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const double2 keep = h8 ? b4[2 + t] : b4[t];
+    const double2 give = h8 ? b4[t] : b4[2 + t];
+    b2[t] = make_double2(keep.x + __shfl_xor_sync(0xffffffffu, give.x, 8),
+                         keep.y + __shfl_xor_sync(0xffffffffu, give.y, 8));
+  }
+  const double2 keep = h4 ? b2[1] : b2[0];
+  const double2 give = h4 ? b2[0] : b2[1];
+  double x = keep.x + __shfl_xor_sync(0xffffffffu, give.x, 4);
+  double y = keep.y + __shfl_xor_sync(0xffffffffu, give.y, 4);
+  x += __shfl_xor_sync(0xffffffffu, x, 2);
+  y += __shfl_xor_sync(0xffffffffu, y, 2);
+  x += __shfl_xor_sync(0xffffffffu, x, 1);
+  y += __shfl_xor_sync(0xffffffffu, y, 1);
+  return make_double2(x, y);
+}
+
+// Classical Gram-Schmidt pieces in float64.  A block of CG_WARPS warps owns CG_CHUNK points;
+// lane l of warp w owns the CG_PPL points seg + l + 32 e, kept in registers, so every basis
+// field is read with coalesced 512-byte warp loads.  Dots are formed 8 basis fields at a time
+// and reduced by warp_reduce8; per-warp sums go through shared memory to one partial per
+// block, and the last block adds the partials in block order (warp per slot).
 template <int MODE>
-__global__ void __launch_bounds__(RED_THREADS)
+__global__ void __launch_bounds__(CG_WARPS * 32)
 k_cgs(const double2* __restrict__ V, long long vis, long long vrs, int nb, double2* w,
       long long wrs, long long n, GmresDev gs, double2* partial, unsigned* counters, double brk) {
-  __shared__ double2 sh[32];
+  extern __shared__ double2 sm[];  // hs[nb] | wp[CG_WARPS][nb + 8]
   const int r = blockIdx.y;
   if (gs.stopped[r]) return;
   const int M = gs.mmax;
-  const long long base = (long long)blockIdx.x * RED_CHUNK + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ldw = nb + 8;
+  const long long seg = (long long)blockIdx.x * CG_CHUNK + (long long)warp * 32 * CG_PPL + lane;
   double2* wr = w + r * wrs;
   const double2* Vr = V + r * vrs;
-  double2 wv[RED_PPT];
+  double2* hs = sm;
+  double2* wp = sm + nb;
+  if (MODE != 0) {
+    const double2* hp = (MODE == 1 ? gs.h1 : gs.h2) + (long long)r * (M + 2);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) hs[b] = hp[b];
+    __syncthreads();
+  }
+  double2 wv[CG_PPL];
 #pragma unroll
-  for (int e = 0; e < RED_PPT; ++e) {
-    const long long p = base + (long long)e * RED_THREADS;
+  for (int e = 0; e < CG_PPL; ++e) {
+    const long long p = seg + 32LL * e;
     wv[e] = p < n ? wr[p] : make_double2(0.0, 0.0);
   }
   if (MODE != 0) {
-    const double2* hp = (MODE == 1 ? gs.h1 : gs.h2) + (long long)r * (M + 2);
     for (int b = 0; b < nb; ++b) {
-      const double2 h = hp[b];
+      const double2 h = hs[b];
       const double2* vb = Vr + b * vis;
 #pragma unroll
-      for (int e = 0; e < RED_PPT; ++e) {
-        const long long p = base + (long long)e * RED_THREADS;
-        if (p < n) wv[e] = csub(wv[e], cmul(h, vb[p]));
+      for (int e = 0; e < CG_PPL; ++e) {
+        const long long p = seg + 32LL * e;
+        if (p < n) {
+          const double2 v = vb[p];
+          wv[e].x = fma(-h.x, v.x, fma(h.y, v.y, wv[e].x));
+          wv[e].y = fma(-h.x, v.y, fma(-h.y, v.x, wv[e].y));
+        }
       }
     }
 #pragma unroll
-    for (int e = 0; e < RED_PPT; ++e) {
-      const long long p = base + (long long)e * RED_THREADS;
+    for (int e = 0; e < CG_PPL; ++e) {
+      const long long p = seg + 32LL * e;
       if (p < n) wr[p] = wv[e];
     }
   }
-  double2* part = partial + (long long)r * (M + 2) * gridDim.x;
   if (MODE != 2) {
-    for (int b = 0; b < nb; ++b) {
-      const double2* vb = Vr + b * vis;
-      double2 s = make_double2(0.0, 0.0);
+    for (int b0 = 0; b0 < nb; b0 += 8) {
+      double2 acc[8];
 #pragma unroll
-      for (int e = 0; e < RED_PPT; ++e) {
-        const long long p = base + (long long)e * RED_THREADS;
-        if (p < n) s = cadd(s, cmulc(vb[p], wv[e]));
+      for (int t = 0; t < 8; ++t) acc[t] = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if (b0 + t < nb) {
+          const double2* vb = Vr + (b0 + t) * vis;
+#pragma unroll
+          for (int e = 0; e < CG_PPL; ++e) {
+            const long long p = seg + 32LL * e;
+            if (p < n) {
+              const double2 v = vb[p];
+              acc[t].x = fma(v.x, wv[e].x, fma(v.y, wv[e].y, acc[t].x));
+              acc[t].y = fma(v.x, wv[e].y, fma(-v.y, wv[e].x, acc[t].y));
+            }
+          }
+        }
       }
-      s = block_sum(s, sh);
-      if (threadIdx.x == 0) part[(long long)b * gridDim.x + blockIdx.x] = s;
+      const double2 red = warp_reduce8(acc, lane);
+      if ((lane & 3) == 0) {
+        const int t = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        wp[warp * ldw + b0 + t] = red;  // slots >= nb are padding
+      }
     }
   }
   if (MODE != 1) {
-    double s = 0.0;
+    double q = 0.0;
 #pragma unroll
-    for (int e = 0; e < RED_PPT; ++e) s += wv[e].x * wv[e].x + wv[e].y * wv[e].y;
-    double2 t = block_sum(make_double2(s, 0.0), sh);
-    const int slot = MODE == 0 ? nb : 0;
-    if (threadIdx.x == 0) part[(long long)slot * gridDim.x + blockIdx.x] = t;
+    for (int e = 0; e < CG_PPL; ++e) q = fma(wv[e].x, wv[e].x, fma(wv[e].y, wv[e].y, q));
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_down_sync(0xffffffffu, q, o);
+    if (lane == 0) wp[warp * ldw + (MODE == 0 ? nb : 0)] = make_double2(q, 0.0);
+  }
+  __syncthreads();
+  const int nslots = MODE == 0 ? nb + 1 : (MODE == 1 ? nb : 1);
+  double2* part = partial + (long long)r * (M + 2) * gridDim.x;
+  for (int sidx = threadIdx.x; sidx < nslots; sidx += blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int ww = 0; ww < CG_WARPS; ++ww) acc = cadd(acc, wp[ww * ldw + sidx]);
+    part[(long long)sidx * gridDim.x + blockIdx.x] = acc;
   }
   if (!last_block(counters + r)) return;
-  const int nslots = MODE == 0 ? nb + 1 : (MODE == 1 ? nb : 1);
   double2* out = MODE == 0 ? gs.h1 + (long long)r * (M + 2)
                : MODE == 1 ? gs.h2 + (long long)r * (M + 2) : gs.nrm + 2 * r;
-  finish_slots(part, nslots, out, sh);
+  for (int sidx = warp; sidx < nslots; sidx += CG_WARPS) {
+    double ax = 0.0, ay = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+      const double2 v = __ldcg(part + (long long)sidx * gridDim.x + b);
+      ax += v.x;
+      ay += v.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      ax += __shfl_down_sync(0xffffffffu, ax, o);
+      ay += __shfl_down_sync(0xffffffffu, ay, o);
+    }
+    if (lane == 0) out[sidx] = make_double2(ax, ay);
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     counters[r] = 0;
     if (MODE == 2) givens_column(gs, r, nb - 1, brk);
   }
+}
+
+// Float64 shifted stencil from the precomputed complex diagonal d = 6 s/h^2 - m - i a:
+//     (A - zI) x = (d - z) x - (s/h^2) * (sum of the 6 neighbours).
+// About 16 float64 operations a point (the float64 pipe is the scarce unit on GB300).
+__global__ void __launch_bounds__(BX * BY)
+k_stencil_diag(Geom g, const double2* __restrict__ dg, const double2* __restrict__ x,
+               long long xrs, double2* __restrict__ y, long long yrs, double zr, double zi) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int k = blockIdx.z % g.nz;
+  const int r = blockIdx.z / g.nz;
+  if (i >= g.nx || j >= g.ny) return;
+  const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+  const long long p = i + sy * j + sz * k;
+  const double2* xr = x + r * xrs;
+  const double2 z0 = make_double2(0.0, 0.0);
+  const double2 xm = i > 0 ? xr[p - 1] : z0, xp = i < g.nx - 1 ? xr[p + 1] : z0;
+  const double2 ym = j > 0 ? xr[p - sy] : z0, yp = j < g.ny - 1 ? xr[p + sy] : z0;
+  const double2 zm = k > 0 ? xr[p - sz] : z0, zp = k < g.nz - 1 ? xr[p + sz] : z0;
+  const double2 xc = xr[p];
+  const double2 d = dg[p];
+  const double nbx = ((xm.x + xp.x) + (ym.x + yp.x)) + (zm.x + zp.x);
+  const double nby = ((xm.y + xp.y) + (ym.y + yp.y)) + (zm.y + zp.y);
+  const double dr = d.x - zr, di = d.y - zi;
+  const double mcs = -g.cs;
+  y[r * yrs + p] = make_double2(fma(dr, xc.x, fma(-di, xc.y, mcs * nbx)),
+                                fma(dr, xc.y, fma(di, xc.x, mcs * nby)));
 }
 
 __global__ void k_scale(double2* __restrict__ dst, long long drs, const double2* __restrict__ src,
@@ -546,9 +689,9 @@ template cudaError_t launch_stencil<double2, double>(const Geom&, const double*,
 
 template <typename T, typename R>
 cudaError_t launch_poly_stage(const Geom& g, const R* m, Buf<const T> f, T* ws, long long wrs,
-                              Buf<double2> w, int nvec, const StageArgs& a, cudaStream_t st) {
-  dim3 blk(BX, BY, 1);
-  dim3 grd((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz * nvec);
+                              Buf<double2> w, int nvec, const StageArgs<R>& a, cudaStream_t st) {
+  dim3 blk(32, a.nnodes, 1);
+  dim3 grd((g.nx + 31) / 32, g.ny, g.nz * nvec);
   count_launch();
   k_poly_stage<T, R><<<grd, blk, 0, st>>>(g, m, f.p, f.rs, ws, wrs, w.p, w.rs, a);
   return cudaGetLastError();
@@ -556,11 +699,11 @@ cudaError_t launch_poly_stage(const Geom& g, const R* m, Buf<const T> f, T* ws, 
 
 template cudaError_t launch_poly_stage<float2, float>(const Geom&, const float*, Buf<const float2>,
                                                       float2*, long long, Buf<double2>, int,
-                                                      const StageArgs&, cudaStream_t);
+                                                      const StageArgs<float>&, cudaStream_t);
 template cudaError_t launch_poly_stage<double2, double>(const Geom&, const double*,
                                                         Buf<const double2>, double2*, long long,
-                                                        Buf<double2>, int, const StageArgs&,
-                                                        cudaStream_t);
+                                                        Buf<double2>, int,
+                                                        const StageArgs<double>&, cudaStream_t);
 
 cudaError_t launch_convert_c128_c64(Buf<const double2> x, Buf<float2> y, long long n, int nvec,
                                     cudaStream_t st) {
@@ -579,17 +722,27 @@ cudaError_t launch_convert_c64_c128(Buf<const float2> x, Buf<double2> y, long lo
 cudaError_t launch_cgs(int mode, const double2* V, long long vis, long long vrs, int nb,
                        Buf<double2> w, long long n, const GmresDev& gs, double2* partial,
                        unsigned* counters, int nvec, double breakdown, cudaStream_t st) {
-  dim3 grd(red_blocks(n), nvec);
+  dim3 grd(unsigned((n + CG_CHUNK - 1) / CG_CHUNK), nvec);
+  const size_t smem = sizeof(double2) * (size_t)(nb + CG_WARPS * (nb + 8));
   count_launch();
   if (mode == 0)
-    k_cgs<0><<<grd, RED_THREADS, 0, st>>>(V, vis, vrs, nb, w.p, w.rs, n, gs, partial, counters,
-                                          breakdown);
+    k_cgs<0><<<grd, CG_WARPS * 32, smem, st>>>(V, vis, vrs, nb, w.p, w.rs, n, gs, partial,
+                                               counters, breakdown);
   else if (mode == 1)
-    k_cgs<1><<<grd, RED_THREADS, 0, st>>>(V, vis, vrs, nb, w.p, w.rs, n, gs, partial, counters,
-                                          breakdown);
+    k_cgs<1><<<grd, CG_WARPS * 32, smem, st>>>(V, vis, vrs, nb, w.p, w.rs, n, gs, partial,
+                                               counters, breakdown);
   else
-    k_cgs<2><<<grd, RED_THREADS, 0, st>>>(V, vis, vrs, nb, w.p, w.rs, n, gs, partial, counters,
-                                          breakdown);
+    k_cgs<2><<<grd, CG_WARPS * 32, smem, st>>>(V, vis, vrs, nb, w.p, w.rs, n, gs, partial,
+                                               counters, breakdown);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil_diag(const Geom& g, const double2* dg, Buf<const double2> x,
+                                Buf<double2> y, int nvec, double zr, double zi, cudaStream_t st) {
+  dim3 blk(BX, BY, 1);
+  dim3 grd((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz * nvec);
+  count_launch();
+  k_stencil_diag<<<grd, blk, 0, st>>>(g, dg, x.p, x.rs, y.p, y.rs, zr, zi);
   return cudaGetLastError();
 }
 
