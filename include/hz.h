@@ -55,9 +55,14 @@ typedef enum {
 } hz_status;
 
 typedef enum {
-  HZ_C128 = 0,      /* everything complex128 / float64 ("plain" form) */
-  HZ_MIXED_C64 = 1  /* polynomial sweeps in complex64; quadrature sum, step d, inner and
-                       outer Arnoldi, Givens and true residual in float64 */
+  HZ_C128 = 0,        /* everything complex128 / float64 ("plain" form) */
+  HZ_MIXED_C64 = 1,   /* polynomial sweeps in complex64; quadrature sum, step d, inner and
+                         outer Arnoldi, Givens and true residual in float64 */
+  HZ_MIXED_C64_FCI32 = 2  /* the whole FCI preconditioner in complex64 (sweeps, step d, inner
+                         GMRES), except its quadrature sum, accumulated in float64; the outer
+                         FGMRES (CGS2 Arnoldi, Givens, updates) and the true residual in
+                         float64.  FGMRES admits a variable preconditioner, so the solution
+                         still reaches the float64 residual target. */
 } hz_precision;
 
 /* Grid and medium.  Interior points nx*ny*nz with spacing h; omega the angular frequency;
@@ -169,8 +174,8 @@ hz_status hz_shifted_solve(hz_problem* p, int node, const void* f, void* y, int 
 
 /* out = FCI(r) (Algorithm 1) for nvec double-complex fields: the J shifted solves, the
  * quadrature w = sum_j sigma_j/z_j y_j, the step d = argmin ||r - d A w||, inner_k GMRES
- * steps on A v = r - d A w, out = v + d w.  precision selects the field type of the
- * shifted solves; r and out are always double complex.  nvec <= nrhs_max. */
+ * steps on A v = r - d A w, out = v + d w.  precision (an hz_precision) selects where the
+ * work runs in complex64; r and out are always double complex.  nvec <= nrhs_max. */
 hz_status hz_fci(hz_problem* p, const void* r, void* out, int nvec, int inner_k, int precision,
                  void* stream);
 
@@ -216,7 +221,8 @@ const char* hz_status_string(hz_status s);
 /* Message of the last failure on the calling thread ("" if none). */
 const char* hz_last_error(void);
 
-/* Kernels this library has launched since it was loaded (all problems, all threads). */
+/* Kernels this library has launched since it was loaded (all problems, all threads;
+ * kernels replayed from the solver's CUDA graphs count once per replay). */
 unsigned long long hz_launch_count(void);
 
 #ifdef __cplusplus

@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libhz.so")
-SOURCES = ["hz_kernels.cu", "hz_api.cu", "hz_setup.cpp", "hz_noalloc.cu"]
+SOURCES = ["hz_kernels.cu", "hz_kernels32.cu", "hz_api.cu", "hz_setup.cpp", "hz_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -27,7 +27,7 @@ def _nvcc() -> str:
 def build(verbose: bool = False, force: bool = False) -> str:
     """Build _build/libhz.so if any source is newer than it; returns its path."""
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, "hz_internal.h"), os.path.join(INCLUDE, "hz.h")]
+    deps = srcs + [os.path.join(CSRC, "hz_internal.h"), os.path.join(CSRC, "hz_device.cuh"), os.path.join(INCLUDE, "hz.h")]
     if (not force and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps)):
         return LIB

@@ -80,6 +80,9 @@ struct hz_problem {
   double2* w = nullptr;      // [nrhs][n] quadrature sum
   double2* Aw = nullptr;     // [nrhs][n]
   double2* Vin = nullptr;    // [nrhs][kin+1][n] inner basis
+  float2* Vin32 = nullptr;   // [nrhs][kin+1][n] inner basis of the complex64 FCI form
+  float2* w32 = nullptr;     // [nrhs][n] quadrature sum rounded to complex64
+  float2* Aw32 = nullptr;    // [nrhs][n]
   double2* V = nullptr;      // [nrhs][m+1][n] outer basis
   double2* Z = nullptr;      // [nrhs][m][n] preconditioned directions
   double2* partial = nullptr;
@@ -97,7 +100,29 @@ struct hz_problem {
   bool prof_on = false;
   ProfClass prof[3];
 
+  // CUDA graphs of the outer FGMRES steps, one per step index k, valid for graph_key
+  // (right-hand sides, precision, inner steps); the solve runs on the library's own stream
+  // because the legacy default stream cannot be captured.
+  cudaStream_t own = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<cudaGraphExec_t> step_graphs;
+  std::vector<unsigned long long> step_kernels;  // kernels captured in each step graph
+  long long graph_key = -1;
+  bool graphs_on = true;
+
+  void drop_graphs() {
+    for (cudaGraphExec_t g : step_graphs)
+      if (g) cudaGraphExecDestroy(g);
+    step_graphs.clear();
+    step_kernels.clear();
+    graph_key = -1;
+  }
+
   ~hz_problem() {
+    drop_graphs();
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (own) cudaStreamDestroy(own);
     for (auto& c : prof)
       for (cudaEvent_t e : c.ev) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
@@ -332,17 +357,48 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
   std::vector<int> all(p->J);
   for (int j = 0; j < p->J; ++j) all[j] = j;
   Buf<double2> wb{p->w, n};
-  if (precision == HZ_MIXED_C64) {
+  if (precision != HZ_C128) {
     HZ_CUDA(hz::launch_convert_c128_c64(r, Buf<float2>{p->f32, n}, n, nvec, st));
     HZ_TRY((run_poly<float2, float>(p, p->m32, Buf<const float2>{p->f32, n}, nvec, all, true, wb,
                                     nullptr, st)));
   } else {
     HZ_TRY((run_poly<double2, double>(p, p->m64, r, nvec, all, true, wb, nullptr, st)));
   }
+  if (precision == HZ_MIXED_C64_FCI32) {
+    // step d and the inner GMRES on complex64 fields; w itself stays float64 for v + d w
+    const long long vrs = (long long)(p->lim.inner_k_max + 1) * n;
+    HZ_CUDA(hz::launch_convert_c128_c64(Buf<const double2>{p->w, n}, Buf<float2>{p->w32, n}, n,
+                                        nvec, st));
+    HZ_TIMED(p, 1, st, (stencil_bytes<float2, float>(n, nvec)),
+             (hz::launch_stencil<float2, float>(p->g, p->m32, Buf<const float2>{p->w32, n},
+                                                Buf<float2>{p->Aw32, n}, nvec, 0.0, 0.0, st)));
+    HZ_TIMED(p, 2, st, 8.0 * n * nvec * 5,
+             hz::launch_fci_step32(Buf<const float2>{p->Aw32, n}, Buf<const float2>{p->f32, n},
+                                   Buf<float2>{p->Vin32, vrs}, p->gin, p->partial, p->counters, n,
+                                   nvec, st));
+    HZ_CUDA(hz::launch_scale32(Buf<float2>{p->Vin32, vrs}, Buf<const float2>{p->Vin32, vrs}, n,
+                               p->gin, nvec, st));
+    for (int j = 0; j < kin; ++j) {
+      Buf<float2> wj{p->Vin32 + (long long)(j + 1) * n, vrs};
+      HZ_TIMED(p, 1, st, (stencil_bytes<float2, float>(n, nvec)),
+               (hz::launch_stencil<float2, float>(
+                   p->g, p->m32, Buf<const float2>{p->Vin32 + (long long)j * n, vrs}, wj, nvec,
+                   0.0, 0.0, st)));
+      for (int mode = 0; mode < 3; ++mode)
+        HZ_TIMED(p, 2, st, 0.5 * cgs_bytes(mode, n, j + 1, nvec),
+                 hz::launch_cgs32(mode, p->Vin32, n, vrs, j + 1, wj, n, p->gin, p->partial,
+                                  p->counters, nvec, kBreakdown, st));
+      HZ_CUDA(hz::launch_scale32(wj, Buf<const float2>{wj.p, vrs}, n, p->gin, nvec, st));
+    }
+    HZ_CUDA(hz::launch_backsolve(p->gin, nvec, st));
+    HZ_CUDA(hz::launch_combine_fci32(out, p->Vin32, n, vrs, p->gin, Buf<const double2>{p->w, n},
+                                     n, nvec, st));
+    return HZ_OK;
+  }
   // Aw, step d, inner start v0 = (r - d Aw)/||r - d Aw||
   HZ_TIMED(p, 1, st, (stencil_bytes<double2, double2>(n, nvec)),
            (hz::launch_stencil_diag(p->g, p->d64, Buf<const double2>{p->w, n},
-                                                Buf<double2>{p->Aw, n}, nvec, 0.0, 0.0, st)));
+                                    Buf<double2>{p->Aw, n}, nvec, 0.0, 0.0, st)));
   const long long vrs = (long long)(p->lim.inner_k_max + 1) * n;
   HZ_TIMED(p, 2, st, 16.0 * n * nvec * 5,
            hz::launch_fci_step(Buf<const double2>{p->Aw, n}, r, Buf<double2>{p->Vin, vrs}, p->gin,
@@ -352,8 +408,9 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
   for (int j = 0; j < kin; ++j) {
     Buf<double2> wj{p->Vin + (long long)(j + 1) * n, vrs};
     HZ_TIMED(p, 1, st, (stencil_bytes<double2, double2>(n, nvec)),
-             (hz::launch_stencil_diag(p->g, p->d64, Buf<const double2>{p->Vin + (long long)j * n, vrs}, wj, nvec, 0.0,
-                 0.0, st)));
+             (hz::launch_stencil_diag(p->g, p->d64,
+                                      Buf<const double2>{p->Vin + (long long)j * n, vrs}, wj, nvec,
+                                      0.0, 0.0, st)));
     for (int mode = 0; mode < 3; ++mode)
       HZ_TIMED(p, 2, st, cgs_bytes(mode, n, j + 1, nvec),
                hz::launch_cgs(mode, p->Vin, n, vrs, j + 1, wj, n, p->gin, p->partial, p->counters,
@@ -363,6 +420,65 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
   HZ_CUDA(hz::launch_backsolve(p->gin, nvec, st));
   HZ_CUDA(hz::launch_combine(out, p->Vin, n, vrs, p->gin, Buf<const double2>{p->w, n}, 0, 0, n,
                              nvec, kin, st));
+  return HZ_OK;
+}
+
+// One outer FGMRES step k on all right-hand sides: z_k = FCI(v_k), w = A z_k, CGS2 against
+// v_0..v_k with the Givens update of column k, v_{k+1} = w / h_{k+1,k}.
+hz_status outer_step_launches(hz_problem* p, int k, int nrhs, int K, int precision,
+                              cudaStream_t st) {
+  const long long n = p->g.n;
+  const long long vrs = (long long)(p->lim.restart_max + 1) * n;
+  const long long zrs = (long long)p->lim.restart_max * n;
+  GmresDev& go = p->gout;
+  Buf<const double2> vk{p->V + (long long)k * n, vrs};
+  Buf<double2> zk{p->Z + (long long)k * n, zrs};
+  HZ_TRY(run_fci(p, vk, zk, nrhs, K, precision, st));
+  Buf<double2> wk{p->V + (long long)(k + 1) * n, vrs};
+  HZ_TIMED(p, 1, st, (stencil_bytes<double2, double2>(n, nrhs)),
+           (hz::launch_stencil_diag(p->g, p->d64, Buf<const double2>{zk.p, zrs}, wk, nrhs, 0.0,
+                                    0.0, st)));
+  for (int mode = 0; mode < 3; ++mode)
+    HZ_TIMED(p, 2, st, cgs_bytes(mode, n, k + 1, nrhs),
+             hz::launch_cgs(mode, p->V, n, vrs, k + 1, wk, n, go, p->partial, p->counters, nrhs,
+                            kBreakdown, st));
+  HZ_CUDA(hz::launch_scale(wk, Buf<const double2>{wk.p, vrs}, n, go, nrhs, st));
+  return HZ_OK;
+}
+
+// The same step replayed from a CUDA graph captured on first use (the ~60 launches of a
+// step then cost one graph launch); plain launches while kernel timing is on.
+hz_status outer_step(hz_problem* p, int k, int nrhs, int K, int precision, cudaStream_t st) {
+  if (p->prof_on || !p->graphs_on) return outer_step_launches(p, k, nrhs, K, precision, st);
+  const long long key = ((long long)nrhs * 4 + precision) * 1024 + K;
+  if (p->graph_key != key) {
+    p->drop_graphs();
+    p->graph_key = key;
+    p->step_graphs.assign(p->lim.restart_max, nullptr);
+    p->step_kernels.assign(p->lim.restart_max, 0);
+  }
+  if (!p->step_graphs[k]) {
+    cudaGraph_t g = nullptr;
+    HZ_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const unsigned long long before = hz::g_launches.load();
+    const hz_status s = outer_step_launches(p, k, nrhs, K, precision, st);
+    // captured kernels did not run: take them off the launch count, add them per replay
+    p->step_kernels[k] = hz::g_launches.load() - before;
+    hz::g_launches.fetch_sub(p->step_kernels[k]);
+    const cudaError_t ec = cudaStreamEndCapture(st, &g);
+    if (s != HZ_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (ec != cudaSuccess) return cuda_fail(ec, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate");
+    p->step_graphs[k] = ex;
+  }
+  HZ_CUDA(cudaGraphLaunch(p->step_graphs[k], st));
+  hz::g_launches.fetch_add(p->step_kernels[k]);
   return HZ_OK;
 }
 
@@ -394,6 +510,11 @@ hz_status fill_scal_tol(hz_problem* p, GmresDev& gs, const std::vector<double>& 
 namespace hz {
 void set_last_error(const std::string& msg) { t_err = msg; }
 }  // namespace hz
+
+namespace {
+hz_status solve_on(hz_problem* p, const void* f, void* u, int nrhs, const hz_solve_opts* opts,
+                   hz_solve_stats* stats, cudaStream_t st);
+}  // namespace
 
 extern "C" {
 
@@ -479,6 +600,10 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   if ((s = dalloc(p, (void**)&p->Aw, sizeof(double2) * (size_t)n * R)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->Vin, sizeof(double2) * (size_t)n * (K + 1) * R)) != HZ_OK)
     return bail(s);
+  if ((s = dalloc(p, (void**)&p->Vin32, sizeof(float2) * (size_t)n * (K + 1) * R)) != HZ_OK)
+    return bail(s);
+  if ((s = dalloc(p, (void**)&p->w32, sizeof(float2) * (size_t)n * R)) != HZ_OK) return bail(s);
+  if ((s = dalloc(p, (void**)&p->Aw32, sizeof(float2) * (size_t)n * R)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->V, sizeof(double2) * (size_t)n * (M + 1) * R)) != HZ_OK)
     return bail(s);
   if ((s = dalloc(p, (void**)&p->Z, sizeof(double2) * (size_t)n * M * R)) != HZ_OK) return bail(s);
@@ -515,6 +640,18 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
       delete p;
       return cuda_fail(e, "cudaMemcpy of inner tolerances");
     }
+  }
+  if (cudaStreamCreateWithFlags(&p->own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    e = cudaGetLastError();
+    delete p;
+    return cuda_fail(e, "stream/event creation");
+  }
+  e = hz::prepare_kernels(std::max(M, K));
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "kernel attributes");
   }
   std::vector<float> m32(n);
   for (long long i = 0; i < n; ++i) m32[i] = float(p->su.m[i]);
@@ -688,6 +825,7 @@ hz_status hz_problem_set_nodes(hz_problem* p, int J, const double* z_ri, const d
   }
   p->nodes = nodes;
   p->J = J;
+  p->drop_graphs();  // captured steps hold the old node parameters
   return HZ_OK;
 }
 
@@ -754,7 +892,7 @@ hz_status hz_fci(hz_problem* p, const void* r, void* out, int nvec, int inner_k,
   if (nvec < 0 || nvec > p->lim.nrhs_max) return fail(HZ_ERR_INVALID, "nvec out of range");
   if (inner_k < 0 || inner_k > p->lim.inner_k_max)
     return fail(HZ_ERR_INVALID, "inner_k out of range");
-  if (precision != HZ_C128 && precision != HZ_MIXED_C64)
+  if (precision != HZ_C128 && precision != HZ_MIXED_C64 && precision != HZ_MIXED_C64_FCI32)
     return fail(HZ_ERR_INVALID, "unknown precision");
   if (nvec == 0) return HZ_OK;
   if (!r || !out) return fail(HZ_ERR_INVALID, "null field");
@@ -775,12 +913,30 @@ hz_status hz_solve(hz_problem* p, const void* f, void* u, int nrhs, const hz_sol
   if (K < 0 || K > p->lim.inner_k_max) return fail(HZ_ERR_INVALID, "inner_k out of range");
   if (opts->max_cycles < 0 || opts->fixed_its < 0 || !(opts->rtol >= 0))
     return fail(HZ_ERR_INVALID, "invalid max_cycles / fixed_its / rtol");
-  if (opts->precision != HZ_C128 && opts->precision != HZ_MIXED_C64)
+  if (opts->precision != HZ_C128 && opts->precision != HZ_MIXED_C64 &&
+      opts->precision != HZ_MIXED_C64_FCI32)
     return fail(HZ_ERR_INVALID, "unknown precision");
   if (nrhs == 0) return HZ_OK;
   if (!f || !u) return fail(HZ_ERR_INVALID, "null field");
   HZ_TRY(set_device(p));
-  cudaStream_t st = (cudaStream_t)stream;
+  // run on the library's stream, ordered after the caller's stream
+  const cudaStream_t user = (cudaStream_t)stream;
+  HZ_CUDA(cudaEventRecord(p->ev_in, user));
+  HZ_CUDA(cudaStreamWaitEvent(p->own, p->ev_in, 0));
+  const cudaStream_t st = p->own;
+  const hz_status status = solve_on(p, f, u, nrhs, opts, stats, st);
+  cudaEventRecord(p->ev_out, st);
+  cudaStreamWaitEvent(user, p->ev_out, 0);
+  return status;
+}
+
+}  // extern "C"
+
+namespace {
+
+hz_status solve_on(hz_problem* p, const void* f, void* u, int nrhs, const hz_solve_opts* opts,
+                   hz_solve_stats* stats, cudaStream_t st) {
+  const int M = opts->restart_m, K = opts->inner_k;
   const long long n = p->g.n;
   const long long vrs = (long long)(p->lim.restart_max + 1) * n;
   const long long zrs = (long long)p->lim.restart_max * n;
@@ -848,18 +1004,7 @@ hz_status hz_solve(hz_problem* p, const void* f, void* u, int nrhs, const hz_sol
     std::vector<int> active(nrhs);
     for (int r = 0; r < nrhs; ++r) active[r] = !done[r];
     for (int k = 0; k < M; ++k) {
-      Buf<const double2> vk{p->V + (long long)k * n, vrs};
-      Buf<double2> zk{p->Z + (long long)k * n, zrs};
-      HZ_TRY(run_fci(p, vk, zk, nrhs, K, opts->precision, st));
-      Buf<double2> wk{p->V + (long long)(k + 1) * n, vrs};
-      HZ_TIMED(p, 1, st, (stencil_bytes<double2, double2>(n, nrhs)),
-               (hz::launch_stencil_diag(p->g, p->d64, Buf<const double2>{zk.p, zrs},
-                                                    wk, nrhs, 0.0, 0.0, st)));
-      for (int mode = 0; mode < 3; ++mode)
-        HZ_TIMED(p, 2, st, cgs_bytes(mode, n, k + 1, nrhs),
-                 hz::launch_cgs(mode, p->V, n, vrs, k + 1, wk, n, go, p->partial, p->counters,
-                                nrhs, kBreakdown, st));
-      HZ_CUDA(hz::launch_scale(wk, Buf<const double2>{wk.p, vrs}, n, go, nrhs, st));
+      HZ_TRY(outer_step(p, k, nrhs, K, opts->precision, st));
       for (int r = 0; r < nrhs; ++r)
         if (active[r]) {
           its[r]++;
@@ -918,4 +1063,5 @@ hz_status hz_solve(hz_problem* p, const void* f, void* u, int nrhs, const hz_sol
   return ret;
 }
 
-}  // extern "C"
+}  // namespace
+

@@ -132,8 +132,11 @@ cudaError_t launch_combine(Buf<double2> out, const double2* B, long long bis, lo
                            const GmresDev& gs, Buf<const double2> E, int e_slot, int accumulate,
                            long long n, int nvec, int kmax, cudaStream_t st);
 
-// y = R^{-1} g over kend[r] columns (one thread per rhs)
+// y = R^{-1} g over kend[r] columns (one block per rhs)
 cudaError_t launch_backsolve(const GmresDev& gs, int nvec, cudaStream_t st);
+
+// One-time kernel attributes for restart lengths up to mmax (shared memory of k_backsolve).
+cudaError_t prepare_kernels(int mmax);
 
 // Starting vector of a cycle.  v0[r] = f[r] - fscale*A x[r] (x may be null = 0; A applied
 // in float64), then ||v0||^2 -> beta, inv, g[0] = beta, kend = 0, stopped = (beta == 0).
@@ -146,6 +149,19 @@ cudaError_t launch_residual_start(const Geom& g, const double* m, Buf<const doub
 cudaError_t launch_fci_step(Buf<const double2> Aw, Buf<const double2> r, Buf<double2> v0,
                             const GmresDev& gs, double2* partial, unsigned* counters,
                             long long n, int nvec, cudaStream_t st);
+
+// ---- complex64 FCI internals (hz_kernels32.cu), for HZ_MIXED_C64_FCI32 ----
+cudaError_t launch_cgs32(int mode, const float2* V, long long vis, long long vrs, int nb,
+                         Buf<float2> w, long long n, const GmresDev& gs, double2* partial,
+                         unsigned* counters, int nvec, double breakdown, cudaStream_t st);
+cudaError_t launch_scale32(Buf<float2> dst, Buf<const float2> src, long long n, const GmresDev& gs,
+                           int nvec, cudaStream_t st);
+cudaError_t launch_fci_step32(Buf<const float2> Aw, Buf<const float2> r, Buf<float2> v0,
+                              const GmresDev& gs, double2* partial, unsigned* counters,
+                              long long n, int nvec, cudaStream_t st);
+cudaError_t launch_combine_fci32(Buf<double2> out, const float2* B, long long bis, long long brs,
+                                 const GmresDev& gs, Buf<const double2> E, long long n, int nvec,
+                                 cudaStream_t st);
 
 void count_launch();
 

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "hz_internal.h"
+#include "hz_device.cuh"
 
 namespace hz {
 
@@ -26,20 +27,6 @@ constexpr int BY = 4;
 constexpr int CG_WARPS = 8;  // Gram-Schmidt block: 8 warps x 32 lanes x 4 points
 constexpr int CG_PPL = 4;
 constexpr int CG_CHUNK = CG_WARPS * 32 * CG_PPL;
-
-// ---------------------------------------------------------------- complex helpers
-__device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
-template <typename T> __device__ __forceinline__ T czero() { T z; z.x = 0; z.y = 0; return z; }
-template <typename T> __device__ __forceinline__ T cadd(T a, T b) { return mk(a.x + b.x, a.y + b.y); }
-template <typename T> __device__ __forceinline__ T csub(T a, T b) { return mk(a.x - b.x, a.y - b.y); }
-template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
-  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-// conj(a) * b
-__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
-  return mk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
-}
 
 template <typename T> struct Real;
 template <> struct Real<float2> { using type = float; };
@@ -221,103 +208,6 @@ __global__ void k_c64_to_c128(const float2* __restrict__ x, long long xrs, doubl
   }
 }
 
-// ---------------------------------------------------------------- reductions
-// Sum of v over the block; the result is valid in thread 0.  sh holds >= 32 entries.
-__device__ __forceinline__ double2 block_sum(double2 v, double2* sh) {
-  for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    v = lane < nw ? sh[lane] : make_double2(0.0, 0.0);
-    for (int o = 16; o > 0; o >>= 1) {
-      v.x += __shfl_down_sync(0xffffffffu, v.x, o);
-      v.y += __shfl_down_sync(0xffffffffu, v.y, o);
-    }
-  }
-  __syncthreads();
-  return v;
-}
-
-// Ticket of the last block of this rhs; true in every thread of that block.
-__device__ __forceinline__ bool last_block(unsigned* counter) {
-  __shared__ bool is_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (is_last) __threadfence();
-  return is_last;
-}
-
-// In the last block: out[s] = sum over blocks of part[s][b], s < nslots, in block order.
-__device__ void finish_slots(const double2* part, int nslots, double2* out, double2* sh) {
-  for (int s = 0; s < nslots; ++s) {
-    double2 acc = make_double2(0.0, 0.0);
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-      double2 v = __ldcg(part + (long long)s * gridDim.x + b);
-      acc.x += v.x;
-      acc.y += v.y;
-    }
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) out[s] = acc;
-  }
-}
-
-// Givens step for column k of rhs r (Saad's GMRES with complex rotations).
-__device__ void givens_column(const GmresDev& gs, int r, int k, double brk) {
-  const int M = gs.mmax;
-  const double2* h1 = gs.h1 + (long long)r * (M + 2);
-  const double2* h2 = gs.h2 + (long long)r * (M + 2);
-  double* sc = gs.scal + (long long)r * SC_COUNT;
-  const double hn = sqrt(gs.nrm[2 * r].x);
-  const double wn = sqrt(h1[k + 1].x);
-  double2* R = gs.R + (long long)r * (M + 1) * M + (long long)k * (M + 1);
-  for (int i = 0; i <= k; ++i) R[i] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
-  const double* cc = gs.cc + (long long)r * M;
-  const double2* ss = gs.ss + (long long)r * M;
-  for (int i = 0; i < k; ++i) {
-    const double c = cc[i];
-    const double2 s = ss[i], a = R[i], b = R[i + 1];
-    R[i] = cadd(mk(c * a.x, c * a.y), cmul(s, b));
-    R[i + 1] = cadd(mk(-(s.x * a.x + s.y * a.y), -(s.x * a.y - s.y * a.x)), mk(c * b.x, c * b.y));
-  }
-  double c;
-  double2 s;
-  const double2 a = R[k];
-  if (hn == 0.0) {
-    c = 1.0;
-    s = make_double2(0.0, 0.0);
-  } else if (a.x == 0.0 && a.y == 0.0) {
-    c = 0.0;
-    s = make_double2(1.0, 0.0);
-  } else {
-    const double ra = hypot(a.x, a.y);
-    const double rr = hypot(ra, hn);
-    c = ra / rr;
-    s = make_double2(a.x / ra * hn / rr, a.y / ra * hn / rr);
-  }
-  R[k] = cadd(mk(c * a.x, c * a.y), mk(s.x * hn, s.y * hn));
-  R[k + 1] = make_double2(0.0, 0.0);
-  gs.cc[(long long)r * M + k] = c;
-  gs.ss[(long long)r * M + k] = s;
-  double2* gg = gs.g + (long long)r * (M + 1);
-  const double2 gk = gg[k];
-  gg[k] = mk(c * gk.x, c * gk.y);
-  gg[k + 1] = mk(-(s.x * gk.x + s.y * gk.y), -(s.x * gk.y - s.y * gk.x));
-  const double est = hypot(gg[k + 1].x, gg[k + 1].y);
-  const bool brk_now = hn <= brk * wn;
-  sc[SC_EST] = est;
-  sc[SC_HN] = hn;
-  sc[SC_INV] = brk_now ? 0.0 : 1.0 / hn;
-  gs.kend[r] = k + 1;
-  if (brk_now || est <= sc[SC_TOL]) gs.stopped[r] = 1;
-}
-
 // Butterfly reduction of 8 per-lane complex partials over a warp: after the three exchange
 // steps each lane holds one vector's partial (vector index bits = lane bits 4, 3, 2), and two
 // more xor steps finish it.  18 float64 adds reduce 8 vectors, against 80 for 8 separate
@@ -461,10 +351,8 @@ k_cgs(const double2* __restrict__ V, long long vis, long long vrs, int nb, doubl
     if (lane == 0) out[sidx] = make_double2(ax, ay);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    counters[r] = 0;
-    if (MODE == 2) givens_column(gs, r, nb - 1, brk);
-  }
+  if (threadIdx.x == 0) counters[r] = 0;
+  if (MODE == 2) givens_column(gs, r, nb - 1, brk);  // whole block
 }
 
 // Float64 shifted stencil from the precomputed complex diagonal d = 6 s/h^2 - m - i a:
@@ -523,20 +411,42 @@ __global__ void k_combine(double2* out, long long ors, const double2* __restrict
   }
 }
 
-__global__ void k_backsolve(GmresDev gs, int nvec) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+// y = R^{-1} g over the kend[r] leading columns, one block per rhs.  The packed upper
+// triangle is staged in shared memory; warp 0 then sweeps the columns from the last one,
+// each lane updating its share of the remaining right-hand side.
+__global__ void __launch_bounds__(256) k_backsolve(GmresDev gs, int nvec) {
+  extern __shared__ double2 smb[];
+  const int r = blockIdx.x;
   if (r >= nvec) return;
   const int M = gs.mmax;
   const int kk = gs.kend[r];
   const double2* R = gs.R + (long long)r * (M + 1) * M;
   const double2* g = gs.g + (long long)r * (M + 1);
   double2* y = gs.y + (long long)r * M;
+  double2* T = smb;                 // column i at i(i+1)/2, rows 0..i
+  double2* s = smb + kk * (kk + 1) / 2;
+  for (int i = 0; i < kk; ++i)
+    for (int j = threadIdx.x; j <= i; j += blockDim.x)
+      T[i * (i + 1) / 2 + j] = R[j + (long long)i * (M + 1)];
+  for (int j = threadIdx.x; j < kk; j += blockDim.x) s[j] = g[j];
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
   for (int i = kk - 1; i >= 0; --i) {
-    double2 s = g[i];
-    for (int jj = i + 1; jj < kk; ++jj) s = csub(s, cmul(R[i + (long long)jj * (M + 1)], y[jj]));
-    const double2 d = R[i + (long long)i * (M + 1)];
-    const double den = d.x * d.x + d.y * d.y;
-    y[i] = make_double2((s.x * d.x + s.y * d.y) / den, (s.y * d.x - s.x * d.y) / den);
+    double yx = 0.0, yy = 0.0;
+    if (lane == 0) {
+      const double2 d = T[i * (i + 1) / 2 + i];
+      const double2 si = s[i];
+      const double den = d.x * d.x + d.y * d.y;
+      yx = (si.x * d.x + si.y * d.y) / den;
+      yy = (si.y * d.x - si.x * d.y) / den;
+      y[i] = make_double2(yx, yy);
+    }
+    yx = __shfl_sync(0xffffffffu, yx, 0);
+    yy = __shfl_sync(0xffffffffu, yy, 0);
+    const double2 yi = make_double2(yx, yy);
+    for (int j = lane; j < i; j += 32) s[j] = csub(s[j], cmul(T[i * (i + 1) / 2 + j], yi));
+    __syncwarp();
   }
 }
 
@@ -763,9 +673,18 @@ cudaError_t launch_combine(Buf<double2> out, const double2* B, long long bis, lo
   return cudaGetLastError();
 }
 
+cudaError_t prepare_kernels(int mmax) {
+  const int M = mmax > 0 ? mmax : 1;
+  const size_t smem = sizeof(double2) * ((size_t)M * (M + 1) / 2 + M);
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 cudaError_t launch_backsolve(const GmresDev& gs, int nvec, cudaStream_t st) {
+  const int M = gs.mmax > 0 ? gs.mmax : 1;
+  const size_t smem = sizeof(double2) * ((size_t)M * (M + 1) / 2 + M);
   count_launch();
-  k_backsolve<<<(nvec + 31) / 32, 32, 0, st>>>(gs, nvec);
+  k_backsolve<<<nvec, 256, smem, st>>>(gs, nvec);
   return cudaGetLastError();
 }
 
