@@ -189,7 +189,8 @@ hz_status hz_solve(hz_problem* p, const void* f, void* u, int nrhs, const hz_sol
 /* Kernel timing for roofline reports.  While enabled on a problem, each launch of a kernel
  * class is bracketed by CUDA events on its stream, and the algorithmic bytes it must move
  * (fields read and written once, neighbours not counted again) are added up.  Classes:
- * 0 = batched polynomial stage (eq:fix-pt-exp sweeps + quadrature), 1 = shifted stencil,
+ * 0 = batched polynomial stage (eq:fix-pt-exp sweeps + quadrature; timed as whole stage
+ * sequences, so its time includes the short gaps between stages), 1 = shifted stencil,
  * 2 = Krylov reductions (CGS2, norms, step d).  hz_profile_read synchronises the recorded
  * events and returns, per class, launches, total milliseconds and total algorithmic bytes
  * since the last enable; any output pointer may be null. */

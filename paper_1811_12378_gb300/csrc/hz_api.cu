@@ -75,6 +75,7 @@ struct hz_problem {
   double* m64 = nullptr;
   float* m32 = nullptr;
   double2* d64 = nullptr;    // [n] float64 diagonal 6 s/h^2 - m - i a
+  float2* d32 = nullptr;     // [n] the same diagonal rounded to complex64
   void* poly = nullptr;      // [nrhs][4 J][n] fields (double2 or float2)
   float2* f32 = nullptr;     // [nrhs][n]
   double2* w = nullptr;      // [nrhs][n] quadrature sum
@@ -259,7 +260,7 @@ Slots slots_of(int s, long long n) {
 // the last stage writes w = sum sigma_j/z_j y_j (double2, wbuf); otherwise node slot s ends
 // with its y in the returned offset yfinal[s] of the workspace.
 template <typename T, typename R>
-hz_status run_poly(hz_problem* p, const R* m, Buf<const T> f, int nvec,
+hz_status run_poly(hz_problem* p, const T* dg, Buf<const T> f, int nvec,
                    const std::vector<int>& which, bool quad, Buf<double2> wbuf,
                    std::vector<long long>* yfinal, cudaStream_t st) {
   const long long n = p->g.n;
@@ -270,6 +271,11 @@ hz_status run_poly(hz_problem* p, const R* m, Buf<const T> f, int nvec,
   for (int node : which) T_total = std::max(T_total, p->nodes[node].q * p->nodes[node].sweeps);
   std::vector<long long> ycur(nn);
   for (int s = 0; s < nn; ++s) ycur[s] = slots_of(s, n).Y;
+  // one event pair around the whole stage sequence (per-launch events would cost more than
+  // a 64^3 stage); launches and bytes are added per stage
+  ProfScope seq{p, 0, -1, st, 0.0};
+  HZ_TRY(seq.begin());
+  double seq_bytes = 0.0;
   for (int t = 0; t < T_total; ++t) {
     // the active nodes of this stage, compacted (one warp row of the kernel's block each)
     hz::StageArgs<R> a;
@@ -343,9 +349,12 @@ hz_status run_poly(hz_problem* p, const R* m, Buf<const T> f, int nvec,
       else if (sn.kind == hz::SK_FIRST_LAST) bpp += ((sn.yzero ? 0 : 1) + (a.final_quad ? 0 : 1)) * e;
     }
     if (a.final_quad) bpp += sizeof(double2);
-    HZ_TIMED(p, 0, st, bpp * double(n) * nvec,
-             (hz::launch_poly_stage<T, R>(p->g, m, f, ws, wrs, wbuf, nvec, a, st)));
+    HZ_CUDA((hz::launch_poly_stage<T, R>(p->g, dg, f, ws, wrs, wbuf, nvec, a, st)));
+    seq_bytes += bpp * double(n) * nvec;
   }
+  seq.bytes = seq_bytes;
+  HZ_TRY(seq.end());
+  if (seq.slot >= 0) p->prof[0].launches += T_total - 1;  // end() counted one
   if (yfinal) *yfinal = ycur;
   return HZ_OK;
 }
@@ -359,10 +368,10 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
   Buf<double2> wb{p->w, n};
   if (precision != HZ_C128) {
     HZ_CUDA(hz::launch_convert_c128_c64(r, Buf<float2>{p->f32, n}, n, nvec, st));
-    HZ_TRY((run_poly<float2, float>(p, p->m32, Buf<const float2>{p->f32, n}, nvec, all, true, wb,
+    HZ_TRY((run_poly<float2, float>(p, p->d32, Buf<const float2>{p->f32, n}, nvec, all, true, wb,
                                     nullptr, st)));
   } else {
-    HZ_TRY((run_poly<double2, double>(p, p->m64, r, nvec, all, true, wb, nullptr, st)));
+    HZ_TRY((run_poly<double2, double>(p, p->d64, r, nvec, all, true, wb, nullptr, st)));
   }
   if (precision == HZ_MIXED_C64_FCI32) {
     // step d and the inner GMRES on complex64 fields; w itself stays float64 for v + d w
@@ -594,6 +603,7 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   if ((s = dalloc(p, (void**)&p->m64, sizeof(double) * n)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->m32, sizeof(float) * n)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->d64, sizeof(double2) * n)) != HZ_OK) return bail(s);
+  if ((s = dalloc(p, (void**)&p->d32, sizeof(float2) * n)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, &p->poly, sizeof(double2) * 4 * (size_t)p->J * n * R)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->f32, sizeof(float2) * (size_t)n * R)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->w, sizeof(double2) * (size_t)n * R)) != HZ_OK) return bail(s);
@@ -676,6 +686,11 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
           dg[q] = make_double2(6.0 * p->g.cs - mp, -ap);
         }
     e = cudaMemcpy(p->d64, dg.data(), sizeof(double2) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      std::vector<float2> dg32(n);
+      for (long long q = 0; q < n; ++q) dg32[q] = make_float2(float(dg[q].x), float(dg[q].y));
+      e = cudaMemcpy(p->d32, dg32.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
+    }
   }
   if (e != cudaSuccess) {
     delete p;
@@ -870,11 +885,11 @@ hz_status hz_shifted_solve(hz_problem* p, int node, const void* f, void* y, int 
   Buf<double2> nob{nullptr, 0};
   size_t es;
   if (precision == HZ_C128) {
-    HZ_TRY((run_poly<double2, double>(p, p->m64, Buf<const double2>{(const double2*)f, n}, nvec,
+    HZ_TRY((run_poly<double2, double>(p, p->d64, Buf<const double2>{(const double2*)f, n}, nvec,
                                       which, false, nob, &yfin, st)));
     es = sizeof(double2);
   } else if (precision == HZ_MIXED_C64) {
-    HZ_TRY((run_poly<float2, float>(p, p->m32, Buf<const float2>{(const float2*)f, n}, nvec, which,
+    HZ_TRY((run_poly<float2, float>(p, p->d32, Buf<const float2>{(const float2*)f, n}, nvec, which,
                                     false, nob, &yfin, st)));
     es = sizeof(float2);
   } else {

@@ -102,8 +102,9 @@ template <typename T, typename R>
 cudaError_t launch_stencil(const Geom& g, const R* m, Buf<const T> x, Buf<T> y, int nvec,
                            double zr, double zi, cudaStream_t st);
 
+// dg: the operator's diagonal 6 s/h^2 - m - i a per point, in the field's precision.
 template <typename T, typename R>
-cudaError_t launch_poly_stage(const Geom& g, const R* m, Buf<const T> f, T* ws, long long wrs,
+cudaError_t launch_poly_stage(const Geom& g, const T* dg, Buf<const T> f, T* ws, long long wrs,
                               Buf<double2> w, int nvec, const StageArgs<R>& a, cudaStream_t st);
 
 // Float64 (A - zI)x from the precomputed diagonal dg = 6 s/h^2 - m - i a (one per point).

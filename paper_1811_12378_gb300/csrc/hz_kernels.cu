@@ -102,87 +102,125 @@ k_stencil(Geom g, const R* __restrict__ m, const T* __restrict__ x, long long xr
 }
 
 // ---------------------------------------------------------------- polynomial stage
-// One stencil sweep of every active node of the scheme eq:fix-pt-exp.  A block covers 32
-// consecutive points of one grid row and all active nodes: warp y works on node y, so each
-// warp runs one node kind without divergence and the block's warps hide each other's load
-// latency; f and m are shared by the node warps through L1.  On the final stage of an FCI
-// application the block sums sigma_j/z_j y_j over its nodes in shared memory (float64) and
-// writes the quadrature sum w once, without storing the y_j.
-template <typename T, typename R>
+// One stencil sweep of every active node of the scheme eq:fix-pt-exp.
+//
+// Block: 32 consecutive x-points of one grid row, times the active nodes (warp y works on
+// node y, so a warp runs one node kind without divergence and the node warps hide each
+// other's latency).  Each thread walks a column of ZC points along z: all loads of the column
+// are issued together, the z-neighbours of one point are the centres of the next, and the
+// operator's diagonal comes precomputed (dg = 6 s/h^2 - m - i a), so a point costs a few
+// dozen instructions.  Fields of one node are distinct buffers, so the __restrict__
+// qualifiers below hold.  On the final stage of an FCI application the block sums
+// sigma_j/z_j y_j over its nodes in shared memory (float64) and writes the quadrature sum w.
+template <typename T> struct RealOf;
+template <> struct RealOf<float2> { using type = float; };
+template <> struct RealOf<double2> { using type = double; };
+
+template <typename T, int ZC>
 __global__ void __launch_bounds__(32 * MAXJ)
-k_poly_stage(Geom g, const R* __restrict__ m, const T* __restrict__ f, long long frs, T* ws,
-             long long wrs, double2* __restrict__ w, long long wwrs, const StageArgs<R> a) {
-  __shared__ double2 qs[MAXJ][32];
+k_poly_stage(Geom g, const T* __restrict__ dg, const T* __restrict__ f, long long frs, T* ws,
+             long long wrs, double2* __restrict__ w, long long wwrs,
+             const StageArgs<typename RealOf<T>::type> a) {
+  using R = typename RealOf<T>::type;
+  extern __shared__ double2 qs[];  // [nnodes][ZC][32] on the final stage only
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y;
-  const int k = blockIdx.z % g.nz;
-  const int r = blockIdx.z / g.nz;
+  const int nzc = (g.nz + ZC - 1) / ZC;
+  const int k0 = (blockIdx.z % nzc) * ZC;
+  const int r = blockIdx.z / nzc;
   const int q = threadIdx.y;
   const bool inside = i < g.nx;
-  double2 contrib = make_double2(0.0, 0.0);
+  const long long sxy = (long long)g.nx * g.ny;
+  const long long p0 = i + (long long)g.nx * j + sxy * k0;
+  const StageNode<R>& nd = a.nd[q];
+  const int kind = nd.kind;
+  T yn[ZC];
+#pragma unroll
+  for (int t = 0; t < ZC; ++t) yn[t] = czero<T>();
   if (inside) {
-    const long long p = i + (long long)g.nx * (j + (long long)g.ny * k);
-    const StageNode<R>& nd = a.nd[q];
-    const int kind = nd.kind;
     T* wsr = ws + r * wrs;
-    const T fp = f[r * frs + p];
-    const R mp = m[p];
-    const R ap = sponge<R>(g, i, j, k, mp);
+    const T* __restrict__ fr = f + r * frs;
+    const T* __restrict__ in = wsr + nd.in;
+    const T* __restrict__ accin = wsr + nd.acc;
+    T* __restrict__ kout = wsr + nd.kout;
+    T* __restrict__ accout = wsr + nd.acc;
+    T* __restrict__ yout = wsr + nd.yout;
+    const bool first = kind == SK_FIRST || kind == SK_FIRST_LAST;
+    const bool stencil = !(first && nd.yzero);
+    const bool use_acc = kind == SK_MID || kind == SK_LAST;
+    const T zero = czero<T>();
+    T fv[ZC], dv[ZC], av[ZC], xm[ZC], xp[ZC], ym[ZC], yp[ZC], c[ZC + 2];
+#pragma unroll
+    for (int t = 0; t < ZC; ++t) {
+      const bool ok = k0 + t < g.nz;
+      const long long pp = p0 + sxy * t;
+      fv[t] = ok ? fr[pp] : zero;
+      dv[t] = ok ? dg[pp] : zero;
+      av[t] = (ok && use_acc) ? accin[pp] : zero;
+      xm[t] = (ok && stencil && i > 0) ? in[pp - 1] : zero;
+      xp[t] = (ok && stencil && i < g.nx - 1) ? in[pp + 1] : zero;
+      ym[t] = (ok && stencil && j > 0) ? in[pp - g.nx] : zero;
+      yp[t] = (ok && stencil && j < g.ny - 1) ? in[pp + g.nx] : zero;
+    }
+#pragma unroll
+    for (int t = 0; t < ZC + 2; ++t) {
+      const int kz = k0 + t - 1;
+      c[t] = (stencil && kz >= 0 && kz < g.nz) ? in[p0 + sxy * (t - 1)] : zero;
+    }
     const R cs = lap_weight<R>(g);
     const T md = mk(nd.mdr, nd.mdi);
-    T yn;
-    bool have_y = false;
-    if (kind == SK_FIRST || kind == SK_FIRST_LAST) {
-      T yv, kv;
-      if (nd.yzero) {
-        yv = czero<T>();
-        kv = cmul(md, mk(-fp.x, -fp.y));
+    const T cf = mk(nd.cfr, nd.cfi);
+    const T ip = mk(nd.ipr, nd.ipi);
+#pragma unroll
+    for (int t = 0; t < ZC; ++t) {
+      if (k0 + t >= g.nz) break;
+      const long long pp = p0 + sxy * t;
+      // (A - z0) x at this point, x = the node's input field
+      const T xc = c[t + 1];
+      const R nbx = ((xm[t].x + xp[t].x) + (ym[t].x + yp[t].x)) + (c[t].x + c[t + 2].x);
+      const R nby = ((xm[t].y + xp[t].y) + (ym[t].y + yp[t].y)) + (c[t].y + c[t + 2].y);
+      const R dr = dv[t].x - nd.z0r, di = dv[t].y - nd.z0i;
+      const T Ax = mk(dr * xc.x - di * xc.y - cs * nbx, dr * xc.y + di * xc.x - cs * nby);
+      if (first) {
+        // k1 = -i delta ((A - z0) y - f), acc = y + k1; with y = 0: k1 = -i delta (-f)
+        const T kv = cmul(md, csub(Ax, fv[t]));
+        if (kind == SK_FIRST) {
+          kout[pp] = kv;
+          accout[pp] = cadd(xc, kv);
+        } else {
+          yn[t] = cmul(cadd(xc, kv), ip);
+        }
       } else {
-        const T* yin = wsr + nd.in;
-        yv = yin[p];
-        T Ay = apply_point<T, R>(yv, nbsum(yin, p, i, j, k, g), cs, mp, ap, nd.z0r, nd.z0i);
-        kv = cmul(md, csub(Ay, fp));
+        const T kv = cmul(md, csub(Ax, cmul(cf, fv[t])));
+        if (kind == SK_MID) {
+          kout[pp] = kv;
+          accout[pp] = cadd(av[t], kv);
+        } else {
+          yn[t] = cmul(cadd(av[t], kv), ip);
+        }
       }
-      if (kind == SK_FIRST) {
-        wsr[nd.kout + p] = kv;
-        wsr[nd.acc + p] = cadd(yv, kv);
-      } else {
-        yn = cmul(cadd(yv, kv), mk(nd.ipr, nd.ipi));
-        have_y = true;
-      }
-    } else if (kind != SK_NONE) {
-      const T* kin = wsr + nd.in;
-      const T acc = wsr[nd.acc + p];
-      T Ak = apply_point<T, R>(kin[p], nbsum(kin, p, i, j, k, g), cs, mp, ap, nd.z0r, nd.z0i);
-      T kv = cmul(md, csub(Ak, cmul(mk(nd.cfr, nd.cfi), fp)));
-      if (kind == SK_MID) {
-        wsr[nd.kout + p] = kv;
-        wsr[nd.acc + p] = cadd(acc, kv);
-      } else {
-        yn = cmul(cadd(acc, kv), mk(nd.ipr, nd.ipi));
-        have_y = true;
-      }
-    }
-    if (have_y) {
-      if (a.final_quad) {
-        const double yr = double(yn.x), yi = double(yn.y);
-        contrib = make_double2(nd.wqr * yr - nd.wqi * yi, nd.wqr * yi + nd.wqi * yr);
-      } else {
-        wsr[nd.yout + p] = yn;
-      }
+      if (!a.final_quad && (kind == SK_LAST || kind == SK_FIRST_LAST)) yout[pp] = yn[t];
     }
   }
-  if (a.final_quad) {  // uniform over the launch
-    qs[q][threadIdx.x] = contrib;
+  if (a.final_quad) {  // uniform over the launch; every node is LAST or FIRST_LAST here
+#pragma unroll
+    for (int t = 0; t < ZC; ++t) {
+      const double yr = double(yn[t].x), yi = double(yn[t].y);
+      qs[(q * ZC + t) * 32 + threadIdx.x] =
+          make_double2(nd.wqr * yr - nd.wqi * yi, nd.wqr * yi + nd.wqi * yr);
+    }
     __syncthreads();
-    if (q == 0 && inside) {
-      double sx = 0.0, sy = 0.0;
-      for (int t = 0; t < a.nnodes; ++t) {
-        sx += qs[t][threadIdx.x].x;
-        sy += qs[t][threadIdx.x].y;
+    if (inside) {
+      for (int t = q; t < ZC; t += a.nnodes) {  // warp q sums column points q, q + nnodes, ...
+        if (k0 + t >= g.nz) break;
+        double sx = 0.0, sy = 0.0;
+        for (int u = 0; u < a.nnodes; ++u) {
+          const double2 v = qs[(u * ZC + t) * 32 + threadIdx.x];
+          sx += v.x;
+          sy += v.y;
+        }
+        w[r * wwrs + p0 + sxy * t] = make_double2(sx, sy);
       }
-      const long long p = i + (long long)g.nx * (j + (long long)g.ny * k);
-      w[r * wwrs + p] = make_double2(sx, sy);
     }
   }
 }
@@ -598,19 +636,21 @@ template cudaError_t launch_stencil<double2, double>(const Geom&, const double*,
                                                      double, double, cudaStream_t);
 
 template <typename T, typename R>
-cudaError_t launch_poly_stage(const Geom& g, const R* m, Buf<const T> f, T* ws, long long wrs,
+cudaError_t launch_poly_stage(const Geom& g, const T* dg, Buf<const T> f, T* ws, long long wrs,
                               Buf<double2> w, int nvec, const StageArgs<R>& a, cudaStream_t st) {
+  constexpr int ZC = sizeof(T) == 8 ? 4 : 2;  // z-column length (float2 : double2)
   dim3 blk(32, a.nnodes, 1);
-  dim3 grd((g.nx + 31) / 32, g.ny, g.nz * nvec);
+  dim3 grd((g.nx + 31) / 32, g.ny, ((g.nz + ZC - 1) / ZC) * nvec);
+  const size_t smem = a.final_quad ? sizeof(double2) * 32 * ZC * a.nnodes : 0;
   count_launch();
-  k_poly_stage<T, R><<<grd, blk, 0, st>>>(g, m, f.p, f.rs, ws, wrs, w.p, w.rs, a);
+  k_poly_stage<T, ZC><<<grd, blk, smem, st>>>(g, dg, f.p, f.rs, ws, wrs, w.p, w.rs, a);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_poly_stage<float2, float>(const Geom&, const float*, Buf<const float2>,
+template cudaError_t launch_poly_stage<float2, float>(const Geom&, const float2*, Buf<const float2>,
                                                       float2*, long long, Buf<double2>, int,
                                                       const StageArgs<float>&, cudaStream_t);
-template cudaError_t launch_poly_stage<double2, double>(const Geom&, const double*,
+template cudaError_t launch_poly_stage<double2, double>(const Geom&, const double2*,
                                                         Buf<const double2>, double2*, long long,
                                                         Buf<double2>, int,
                                                         const StageArgs<double>&, cudaStream_t);
