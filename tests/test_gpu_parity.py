@@ -127,13 +127,15 @@ def test_shifted_solve_q1_and_high_order():
 
 
 @pytest.mark.parametrize("prec,kin", [(hzpkg.HZ_C128, 3), (hzpkg.HZ_C128, 0),
-                                      (hzpkg.HZ_MIXED_C64, 4), (hzpkg.HZ_MIXED_C64_FCI32, 4)])
+                                      (hzpkg.HZ_MIXED_C64, 4), (hzpkg.HZ_MIXED_C64_FCI32, 4),
+                                      (hzpkg.HZ_MIXED_C64_FCI32, 0),
+                                      (hzpkg.HZ_MIXED_C64_FCI32, 10)])
 def test_fci_parity(prec, kin):
-    """Algorithm 1 on 3 fields at once."""
+    """Algorithm 1 on 3 fields at once (k_in = 0 and 10 cover the edges of the inner solve)."""
     wl = W.small_case(6, 23, 10, 9, layer=2, J=5)
     op, nodes = oracle_of(wl)
     r = W.random_field(9, 3, wl.nx, wl.ny, wl.nz)
-    with problem_of(wl, nodes) as P:
+    with problem_of(wl, nodes, inner_k_max=10) as P:
         out = to_np(P.fci(to_dev(r), inner_k=kin, precision=prec))
     ref = np.stack([O.fci(op, r[v], nodes, kin) for v in range(3)])
     tol = {hzpkg.HZ_C128: 1e-11, hzpkg.HZ_MIXED_C64: 1e-5, hzpkg.HZ_MIXED_C64_FCI32: 2e-5}[prec]
