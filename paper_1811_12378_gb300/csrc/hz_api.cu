@@ -73,7 +73,6 @@ struct hz_problem {
 
   // device memory
   double* m64 = nullptr;
-  float* m32 = nullptr;
   double2* d64 = nullptr;    // [n] float64 diagonal 6 s/h^2 - m - i a
   float2* d32 = nullptr;     // [n] the same diagonal rounded to complex64
   void* poly = nullptr;      // [nrhs][4 J][n] fields (double2 or float2)
@@ -378,8 +377,8 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
     const long long vrs = (long long)(p->lim.inner_k_max + 1) * n;
     HZ_CUDA(hz::launch_convert_c128_c64(Buf<const double2>{p->w, n}, Buf<float2>{p->w32, n}, n,
                                         nvec, st));
-    HZ_TIMED(p, 1, st, (stencil_bytes<float2, float>(n, nvec)),
-             (hz::launch_stencil<float2, float>(p->g, p->m32, Buf<const float2>{p->w32, n},
+    HZ_TIMED(p, 1, st, (stencil_bytes<float2, float2>(n, nvec)),
+             (hz::launch_stencil32(p->g, p->d32, Buf<const float2>{p->w32, n},
                                                 Buf<float2>{p->Aw32, n}, nvec, 0.0, 0.0, st)));
     HZ_TIMED(p, 2, st, 8.0 * n * nvec * 5,
              hz::launch_fci_step32(Buf<const float2>{p->Aw32, n}, Buf<const float2>{p->f32, n},
@@ -389,9 +388,9 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
                                p->gin, nvec, st));
     for (int j = 0; j < kin; ++j) {
       Buf<float2> wj{p->Vin32 + (long long)(j + 1) * n, vrs};
-      HZ_TIMED(p, 1, st, (stencil_bytes<float2, float>(n, nvec)),
-               (hz::launch_stencil<float2, float>(
-                   p->g, p->m32, Buf<const float2>{p->Vin32 + (long long)j * n, vrs}, wj, nvec,
+      HZ_TIMED(p, 1, st, (stencil_bytes<float2, float2>(n, nvec)),
+               (hz::launch_stencil32(
+                   p->g, p->d32, Buf<const float2>{p->Vin32 + (long long)j * n, vrs}, wj, nvec,
                    0.0, 0.0, st)));
       for (int mode = 0; mode < 3; ++mode)
         HZ_TIMED(p, 2, st, 0.5 * cgs_bytes(mode, n, j + 1, nvec),
@@ -590,8 +589,6 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   p->g.cs = p->su.s / (grid->h * grid->h);
   p->g.sig = grid->sigma_max;
   p->g.csf = float(p->g.cs);
-  p->g.sigf = float(grid->sigma_max);
-  p->g.inv_layer_f = grid->layer_cells > 0 ? 1.0f / float(grid->layer_cells) : 0.0f;
   std::string err;
   if (!hz::setup_nodes(p->su, *contour, p->nodes, err)) {
     delete p;
@@ -601,7 +598,6 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   const int R = limits->nrhs_max, M = limits->restart_max, K = limits->inner_k_max;
   hz_status s;
   if ((s = dalloc(p, (void**)&p->m64, sizeof(double) * n)) != HZ_OK) return bail(s);
-  if ((s = dalloc(p, (void**)&p->m32, sizeof(float) * n)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->d64, sizeof(double2) * n)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->d32, sizeof(float2) * n)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, &p->poly, sizeof(double2) * 4 * (size_t)p->J * n * R)) != HZ_OK) return bail(s);
@@ -663,10 +659,7 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
     delete p;
     return cuda_fail(e, "kernel attributes");
   }
-  std::vector<float> m32(n);
-  for (long long i = 0; i < n; ++i) m32[i] = float(p->su.m[i]);
   e = cudaMemcpy(p->m64, p->su.m.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(p->m32, m32.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
     // diagonal of the float64 stencil: 6 s/h^2 - m - i a, a = sigma_max (depth/L)^2 m
     std::vector<double2> dg(n);
@@ -860,8 +853,8 @@ hz_status hz_apply_shifted(hz_problem* p, double zr, double zi, const void* x, v
                                                   Buf<const double2>{(const double2*)x, n},
                                                   Buf<double2>{(double2*)y, n}, nvec, zr, zi, st)));
   } else if (precision == HZ_MIXED_C64) {
-    HZ_TIMED(p, 1, st, (stencil_bytes<float2, float>(n, nvec)),
-             (hz::launch_stencil<float2, float>(p->g, p->m32,
+    HZ_TIMED(p, 1, st, (stencil_bytes<float2, float2>(n, nvec)),
+             (hz::launch_stencil32(p->g, p->d32,
                                                 Buf<const float2>{(const float2*)x, n},
                                                 Buf<float2>{(float2*)y, n}, nvec, zr, zi, st)));
   } else {

@@ -24,9 +24,7 @@ struct Geom {
   long long n;     // nx*ny*nz
   double cs;       // s / h^2: weight of the 7-point Laplacian
   double sig;      // sigma_max of the sponge
-  float csf;       // the same scalars in float32, so float32 kernels convert nothing
-  float sigf;
-  float inv_layer_f;
+  float csf;       // s / h^2 in float32, so float32 kernels convert nothing
 };
 
 // Per-node parameters of the polynomial scheme (eq:fix-pt-exp) and the quadrature (§6).
@@ -98,14 +96,14 @@ enum { SC_EST = 0, SC_INV = 1, SC_BETA = 2, SC_TOL = 3, SC_HN = 4, SC_DR = 5, SC
 extern std::atomic<unsigned long long> g_launches;
 
 // ---- kernel wrappers (hz_kernels.cu); each returns cudaGetLastError() after launch ----
-template <typename T, typename R>
-cudaError_t launch_stencil(const Geom& g, const R* m, Buf<const T> x, Buf<T> y, int nvec,
-                           double zr, double zi, cudaStream_t st);
-
 // dg: the operator's diagonal 6 s/h^2 - m - i a per point, in the field's precision.
 template <typename T, typename R>
 cudaError_t launch_poly_stage(const Geom& g, const T* dg, Buf<const T> f, T* ws, long long wrs,
                               Buf<double2> w, int nvec, const StageArgs<R>& a, cudaStream_t st);
+
+// Complex64 (A - zI)x from the complex64 diagonal dg, z-columns of 4 points per thread.
+cudaError_t launch_stencil32(const Geom& g, const float2* dg, Buf<const float2> x, Buf<float2> y,
+                             int nvec, double zr, double zi, cudaStream_t st);
 
 // Float64 (A - zI)x from the precomputed diagonal dg = 6 s/h^2 - m - i a (one per point).
 cudaError_t launch_stencil_diag(const Geom& g, const double2* dg, Buf<const double2> x,

@@ -3,10 +3,10 @@
 // reductions (CGS2 dots, norms, Givens, back substitution, combinations).
 //
 // Operator (§7.1 eq:stiff-mass, Case One of §3): in normalised units
-//     (A - zI) x = cs * (6 x_p - sum of the 6 neighbours) - (m_p + z) x_p - i a_p x_p,
-// cs = s/h^2, zero Dirichlet ghosts, a_p = sigma_max (depth_p / layer)^2 m_p in the sponge.
-// The sponge depth is recomputed from the grid index, so the only coefficient field read
-// from memory is m.
+//     (A - zI) x = (dg - z) x_p - cs * (sum of the 6 neighbours),
+// dg = 6 cs - m_p - i a_p, cs = s/h^2, zero Dirichlet ghosts, a_p = sigma_max (depth_p /
+// layer)^2 m_p in the sponge.  dg is precomputed once per problem (complex64 and complex128
+// copies), so a stencil point reads its field and one diagonal value.
 //
 // Reductions are deterministic: each block writes its partial sums, the last block to finish
 // (atomic ticket) adds them in block order and resets the ticket.
@@ -49,13 +49,6 @@ __device__ __forceinline__ double sponge<double>(const Geom& g, int i, int j, in
   const double t = double(sponge_depth(g, i, j, k)) / double(g.layer);
   return (g.sig * (t * t)) * mp;
 }
-template <>
-__device__ __forceinline__ float sponge<float>(const Geom& g, int i, int j, int k, float mp) {
-  if (g.layer <= 0) return 0.f;
-  const float t = float(sponge_depth(g, i, j, k)) * g.inv_layer_f;
-  return (g.sigf * (t * t)) * mp;
-}
-
 template <typename R> __device__ __forceinline__ R lap_weight(const Geom& g);
 template <> __device__ __forceinline__ double lap_weight<double>(const Geom& g) { return g.cs; }
 template <> __device__ __forceinline__ float lap_weight<float>(const Geom& g) { return g.csf; }
@@ -83,22 +76,50 @@ __device__ __forceinline__ T apply_point(T xc, T nb, R cs, R mp, R ap, R zr, R z
   return mk(cs * t.x + dr * xc.x - di * xc.y, cs * t.y + dr * xc.y + di * xc.x);
 }
 
-// ---------------------------------------------------------------- stencil
-template <typename T, typename R>
-__global__ void __launch_bounds__(BX * BY)
-k_stencil(Geom g, const R* __restrict__ m, const T* __restrict__ x, long long xrs,
-          T* __restrict__ y, long long yrs, R zr, R zi) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const int k = blockIdx.z % g.nz;
-  const int r = blockIdx.z / g.nz;
+// Complex64 shifted stencil from the precomputed diagonal, z-columns of ZC points per thread
+// (all loads of a column issued together, z-neighbours shared between consecutive points):
+//     (A - zI) x = (dg - z) x - (s/h^2) * (sum of the 6 neighbours).
+template <int ZC>
+__global__ void __launch_bounds__(128)
+k_stencil32(Geom g, const float2* __restrict__ dg, const float2* __restrict__ x, long long xrs,
+            float2* __restrict__ y, long long yrs, float zr, float zi) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nzc = (g.nz + ZC - 1) / ZC;
+  const int k0 = (blockIdx.z % nzc) * ZC;
+  const int r = blockIdx.z / nzc;
   if (i >= g.nx || j >= g.ny) return;
-  const long long p = i + (long long)g.nx * (j + (long long)g.ny * k);
-  const T* xr = x + r * xrs;
-  const R mp = m[p];
-  const R ap = sponge<R>(g, i, j, k, mp);
-  y[r * yrs + p] = apply_point<T, R>(xr[p], nbsum(xr, p, i, j, k, g), lap_weight<R>(g), mp, ap,
-                                     zr, zi);
+  const long long sxy = (long long)g.nx * g.ny;
+  const long long p0 = i + (long long)g.nx * j + sxy * k0;
+  const float2* __restrict__ xr = x + r * xrs;
+  const float2 zero = make_float2(0.f, 0.f);
+  float2 dv[ZC], xm[ZC], xp[ZC], ym[ZC], yp[ZC], c[ZC + 2];
+#pragma unroll
+  for (int t = 0; t < ZC; ++t) {
+    const bool ok = k0 + t < g.nz;
+    const long long pp = p0 + sxy * t;
+    dv[t] = ok ? dg[pp] : zero;
+    xm[t] = (ok && i > 0) ? xr[pp - 1] : zero;
+    xp[t] = (ok && i < g.nx - 1) ? xr[pp + 1] : zero;
+    ym[t] = (ok && j > 0) ? xr[pp - g.nx] : zero;
+    yp[t] = (ok && j < g.ny - 1) ? xr[pp + g.nx] : zero;
+  }
+#pragma unroll
+  for (int t = 0; t < ZC + 2; ++t) {
+    const int kz = k0 + t - 1;
+    c[t] = (kz >= 0 && kz < g.nz) ? xr[p0 + sxy * (t - 1)] : zero;
+  }
+  const float cs = g.csf;
+#pragma unroll
+  for (int t = 0; t < ZC; ++t) {
+    if (k0 + t >= g.nz) break;
+    const float2 xc = c[t + 1];
+    const float nbx = ((xm[t].x + xp[t].x) + (ym[t].x + yp[t].x)) + (c[t].x + c[t + 2].x);
+    const float nby = ((xm[t].y + xp[t].y) + (ym[t].y + yp[t].y)) + (c[t].y + c[t + 2].y);
+    const float dr = dv[t].x - zr, di = dv[t].y - zi;
+    y[r * yrs + p0 + sxy * t] =
+        make_float2(dr * xc.x - di * xc.y - cs * nbx, dr * xc.y + di * xc.x - cs * nby);
+  }
 }
 
 // ---------------------------------------------------------------- polynomial stage
@@ -117,19 +138,19 @@ template <> struct RealOf<float2> { using type = float; };
 template <> struct RealOf<double2> { using type = double; };
 
 template <typename T, int ZC>
-__global__ void __launch_bounds__(32 * MAXJ)
+__global__ void __launch_bounds__(512)
 k_poly_stage(Geom g, const T* __restrict__ dg, const T* __restrict__ f, long long frs, T* ws,
              long long wrs, double2* __restrict__ w, long long wwrs,
              const StageArgs<typename RealOf<T>::type> a) {
   using R = typename RealOf<T>::type;
-  extern __shared__ double2 qs[];  // [nnodes][ZC][32] on the final stage only
+  extern __shared__ double2 qs[];  // [rows][nnodes][ZC][32] on the final stage only
   const int i = blockIdx.x * 32 + threadIdx.x;
-  const int j = blockIdx.y;
+  const int j = blockIdx.y * blockDim.z + threadIdx.z;
   const int nzc = (g.nz + ZC - 1) / ZC;
   const int k0 = (blockIdx.z % nzc) * ZC;
   const int r = blockIdx.z / nzc;
   const int q = threadIdx.y;
-  const bool inside = i < g.nx;
+  const bool inside = i < g.nx && j < g.ny;
   const long long sxy = (long long)g.nx * g.ny;
   const long long p0 = i + (long long)g.nx * j + sxy * k0;
   const StageNode<R>& nd = a.nd[q];
@@ -203,10 +224,11 @@ k_poly_stage(Geom g, const T* __restrict__ dg, const T* __restrict__ f, long lon
     }
   }
   if (a.final_quad) {  // uniform over the launch; every node is LAST or FIRST_LAST here
+    double2* qr = qs + (size_t)threadIdx.z * a.nnodes * ZC * 32;
 #pragma unroll
     for (int t = 0; t < ZC; ++t) {
       const double yr = double(yn[t].x), yi = double(yn[t].y);
-      qs[(q * ZC + t) * 32 + threadIdx.x] =
+      qr[(q * ZC + t) * 32 + threadIdx.x] =
           make_double2(nd.wqr * yr - nd.wqi * yi, nd.wqr * yi + nd.wqi * yr);
     }
     __syncthreads();
@@ -215,7 +237,7 @@ k_poly_stage(Geom g, const T* __restrict__ dg, const T* __restrict__ f, long lon
         if (k0 + t >= g.nz) break;
         double sx = 0.0, sy = 0.0;
         for (int u = 0; u < a.nnodes; ++u) {
-          const double2 v = qs[(u * ZC + t) * 32 + threadIdx.x];
+          const double2 v = qr[(u * ZC + t) * 32 + threadIdx.x];
           sx += v.x;
           sy += v.y;
         }
@@ -620,28 +642,14 @@ inline unsigned ew_blocks(long long n) {
 
 // ---------------------------------------------------------------- wrappers
 template <typename T, typename R>
-cudaError_t launch_stencil(const Geom& g, const R* m, Buf<const T> x, Buf<T> y, int nvec,
-                           double zr, double zi, cudaStream_t st) {
-  dim3 blk(BX, BY, 1);
-  dim3 grd((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz * nvec);
-  count_launch();
-  k_stencil<T, R><<<grd, blk, 0, st>>>(g, m, x.p, x.rs, y.p, y.rs, R(zr), R(zi));
-  return cudaGetLastError();
-}
-
-template cudaError_t launch_stencil<float2, float>(const Geom&, const float*, Buf<const float2>,
-                                                   Buf<float2>, int, double, double, cudaStream_t);
-template cudaError_t launch_stencil<double2, double>(const Geom&, const double*,
-                                                     Buf<const double2>, Buf<double2>, int,
-                                                     double, double, cudaStream_t);
-
-template <typename T, typename R>
 cudaError_t launch_poly_stage(const Geom& g, const T* dg, Buf<const T> f, T* ws, long long wrs,
                               Buf<double2> w, int nvec, const StageArgs<R>& a, cudaStream_t st) {
   constexpr int ZC = sizeof(T) == 8 ? 4 : 2;  // z-column length (float2 : double2)
-  dim3 blk(32, a.nnodes, 1);
-  dim3 grd((g.nx + 31) / 32, g.ny, ((g.nz + ZC - 1) / ZC) * nvec);
-  const size_t smem = a.final_quad ? sizeof(double2) * 32 * ZC * a.nnodes : 0;
+  // rows per block: at least 4 warps a block when few nodes are active
+  const int rows = a.nnodes >= 4 ? 1 : (a.nnodes == 1 ? 4 : 2);
+  dim3 blk(32, a.nnodes, rows);
+  dim3 grd((g.nx + 31) / 32, (g.ny + rows - 1) / rows, ((g.nz + ZC - 1) / ZC) * nvec);
+  const size_t smem = a.final_quad ? sizeof(double2) * 32 * ZC * a.nnodes * rows : 0;
   count_launch();
   k_poly_stage<T, ZC><<<grd, blk, smem, st>>>(g, dg, f.p, f.rs, ws, wrs, w.p, w.rs, a);
   return cudaGetLastError();
@@ -684,6 +692,16 @@ cudaError_t launch_cgs(int mode, const double2* V, long long vis, long long vrs,
   else
     k_cgs<2><<<grd, CG_WARPS * 32, smem, st>>>(V, vis, vrs, nb, w.p, w.rs, n, gs, partial,
                                                counters, breakdown);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil32(const Geom& g, const float2* dg, Buf<const float2> x, Buf<float2> y,
+                             int nvec, double zr, double zi, cudaStream_t st) {
+  constexpr int ZC = 4;
+  dim3 blk(32, 4, 1);
+  dim3 grd((g.nx + 31) / 32, (g.ny + 3) / 4, ((g.nz + ZC - 1) / ZC) * nvec);
+  count_launch();
+  k_stencil32<ZC><<<grd, blk, 0, st>>>(g, dg, x.p, x.rs, y.p, y.rs, float(zr), float(zi));
   return cudaGetLastError();
 }
 
