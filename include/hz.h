@@ -186,6 +186,18 @@ hz_status hz_fci(hz_problem* p, const void* r, void* out, int nvec, int inner_k,
 hz_status hz_solve(hz_problem* p, const void* f, void* u, int nrhs, const hz_solve_opts* opts,
                    hz_solve_stats* stats, void* stream);
 
+/* Solve several problems at once (instances of different grid sizes, media and contours,
+ * each with its own right-hand sides): the FGMRES cycles of all problems advance in lockstep,
+ * each problem's kernels on its own stream so that they overlap on the GPU, with one host
+ * synchronisation per outer step for all of them.  probs: nprob distinct problems on the
+ * current device; f[i], u[i]: device fields of problem i (nrhs[i] each, physical units as in
+ * hz_solve); stats: sum of nrhs[i] entries in problem order (may be null).  Results equal
+ * separate hz_solve calls.  Returns the first failure, else HZ_ERR_NOT_CONVERGED if any
+ * right-hand side missed rtol. */
+hz_status hz_solve_batched(hz_problem* const* probs, int nprob, const void* const* f,
+                           void* const* u, const int* nrhs, const hz_solve_opts* opts,
+                           hz_solve_stats* stats, void* stream);
+
 /* Kernel timing for roofline reports.  While enabled on a problem, each launch of a kernel
  * class is bracketed by CUDA events on its stream, and the algorithmic bytes it must move
  * (fields read and written once, neighbours not counted again) are added up.  Classes:

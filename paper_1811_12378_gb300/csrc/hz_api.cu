@@ -520,8 +520,29 @@ void set_last_error(const std::string& msg) { t_err = msg; }
 }  // namespace hz
 
 namespace {
+struct SolveState;
 hz_status solve_on(hz_problem* p, const void* f, void* u, int nrhs, const hz_solve_opts* opts,
                    hz_solve_stats* stats, cudaStream_t st);
+hz_status solve_batched_on(hz_problem* const* probs, int nprob, const void* const* f,
+                           void* const* u, const int* nrhs, const hz_solve_opts* opts,
+                           hz_solve_stats* stats);
+
+// Argument checks shared by hz_solve and hz_solve_batched.
+hz_status check_solve_args(const hz_problem* p, int nrhs, const hz_solve_opts* opts) {
+  if (!p) return fail(HZ_ERR_INVALID, "null problem");
+  if (!opts) return fail(HZ_ERR_INVALID, "opts is null");
+  if (nrhs < 0 || nrhs > p->lim.nrhs_max) return fail(HZ_ERR_INVALID, "nrhs out of range");
+  if (opts->restart_m < 1 || opts->restart_m > p->lim.restart_max)
+    return fail(HZ_ERR_INVALID, "restart_m out of range");
+  if (opts->inner_k < 0 || opts->inner_k > p->lim.inner_k_max)
+    return fail(HZ_ERR_INVALID, "inner_k out of range");
+  if (opts->max_cycles < 0 || opts->fixed_its < 0 || !(opts->rtol >= 0))
+    return fail(HZ_ERR_INVALID, "invalid max_cycles / fixed_its / rtol");
+  if (opts->precision != HZ_C128 && opts->precision != HZ_MIXED_C64 &&
+      opts->precision != HZ_MIXED_C64_FCI32)
+    return fail(HZ_ERR_INVALID, "unknown precision");
+  return HZ_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -913,17 +934,7 @@ hz_status hz_fci(hz_problem* p, const void* r, void* out, int nvec, int inner_k,
 
 hz_status hz_solve(hz_problem* p, const void* f, void* u, int nrhs, const hz_solve_opts* opts,
                    hz_solve_stats* stats, void* stream) {
-  HZ_TRY(check_problem(p));
-  if (!opts) return fail(HZ_ERR_INVALID, "opts is null");
-  if (nrhs < 0 || nrhs > p->lim.nrhs_max) return fail(HZ_ERR_INVALID, "nrhs out of range");
-  const int M = opts->restart_m, K = opts->inner_k;
-  if (M < 1 || M > p->lim.restart_max) return fail(HZ_ERR_INVALID, "restart_m out of range");
-  if (K < 0 || K > p->lim.inner_k_max) return fail(HZ_ERR_INVALID, "inner_k out of range");
-  if (opts->max_cycles < 0 || opts->fixed_its < 0 || !(opts->rtol >= 0))
-    return fail(HZ_ERR_INVALID, "invalid max_cycles / fixed_its / rtol");
-  if (opts->precision != HZ_C128 && opts->precision != HZ_MIXED_C64 &&
-      opts->precision != HZ_MIXED_C64_FCI32)
-    return fail(HZ_ERR_INVALID, "unknown precision");
+  HZ_TRY(check_solve_args(p, nrhs, opts));
   if (nrhs == 0) return HZ_OK;
   if (!f || !u) return fail(HZ_ERR_INVALID, "null field");
   HZ_TRY(set_device(p));
@@ -938,49 +949,104 @@ hz_status hz_solve(hz_problem* p, const void* f, void* u, int nrhs, const hz_sol
   return status;
 }
 
+hz_status hz_solve_batched(hz_problem* const* probs, int nprob, const void* const* f,
+                           void* const* u, const int* nrhs, const hz_solve_opts* opts,
+                           hz_solve_stats* stats, void* stream) {
+  if (nprob < 0 || (nprob > 0 && (!probs || !f || !u || !nrhs)))
+    return fail(HZ_ERR_INVALID, "null argument array");
+  if (nprob == 0) return HZ_OK;
+  int dev = -1;
+  HZ_CUDA(cudaGetDevice(&dev));
+  for (int i = 0; i < nprob; ++i) {
+    HZ_TRY(check_solve_args(probs[i], nrhs[i], opts));
+    if (nrhs[i] > 0 && (!f[i] || !u[i])) return fail(HZ_ERR_INVALID, "null field");
+    if (probs[i]->device != dev)
+      return fail(HZ_ERR_INVALID, "all problems must live on the current device");
+    for (int j = 0; j < i; ++j)
+      if (probs[j] == probs[i]) return fail(HZ_ERR_INVALID, "a problem appears twice");
+  }
+  const cudaStream_t user = (cudaStream_t)stream;
+  HZ_CUDA(cudaEventRecord(probs[0]->ev_in, user));
+  for (int i = 0; i < nprob; ++i) HZ_CUDA(cudaStreamWaitEvent(probs[i]->own, probs[0]->ev_in, 0));
+  const hz_status status = solve_batched_on(probs, nprob, f, u, nrhs, opts, stats);
+  for (int i = 0; i < nprob; ++i) {
+    cudaEventRecord(probs[i]->ev_out, probs[i]->own);
+    cudaStreamWaitEvent(user, probs[i]->ev_out, 0);
+  }
+  return status;
+}
+
 }  // extern "C"
 
 namespace {
 
-hz_status solve_on(hz_problem* p, const void* f, void* u, int nrhs, const hz_solve_opts* opts,
-                   hz_solve_stats* stats, cudaStream_t st) {
-  const int M = opts->restart_m, K = opts->inner_k;
-  const long long n = p->g.n;
-  const long long vrs = (long long)(p->lim.restart_max + 1) * n;
-  const long long zrs = (long long)p->lim.restart_max * n;
-  const bool fixed = opts->fixed_its > 0;
-  Buf<const double2> fb{(const double2*)f, n};
-  Buf<double2> ub{(double2*)u, n};
-  GmresDev& go = p->gout;
+// One FGMRES(m) solve with FCI as the right preconditioner, split into enqueue and host phases
+// so that several problems can advance in lockstep on their own streams (hz_solve_batched):
+// the host waits once per outer step for all of them, while their kernels overlap on the GPU.
+struct SolveState {
+  hz_problem* p;
+  const void* f;
+  void* u;
+  int nrhs;
+  const hz_solve_opts* o;
+  hz_solve_stats* stats;
+  cudaStream_t st;
+  int M = 0, K = 0;
+  long long n = 0, vrs = 0, zrs = 0, mv_fci = 0;
+  bool fixed = false;
+  std::vector<double> fnorm, rel;
+  std::vector<int> its, cycles, done, active;
+  std::vector<long long> mvs;
+  int cycle = 0, k = 0;
+  bool diverged = false, finished = false, in_cycle = false;
 
-  long long mv_fci = 1 + K;
-  for (const auto& nd : p->nodes) mv_fci += nd.q * nd.sweeps - 1;
-
-  std::vector<double> fnorm(nrhs, 0.0), rel(nrhs, 1.0);
-  std::vector<int> its(nrhs, 0), cycles(nrhs, 0), done(nrhs, 0);
-  std::vector<long long> mvs(nrhs, 0);
-  HZ_CUDA(cudaMemsetAsync(u, 0, sizeof(double2) * n * nrhs, st));
-
-  auto read_scal = [&](GmresDev& gs) -> hz_status {
-    HZ_CUDA(cudaMemcpyAsync(p->h_scal, gs.scal, sizeof(double) * hz::SC_COUNT * nrhs,
-                            cudaMemcpyDeviceToHost, st));
-    HZ_CUDA(cudaMemcpyAsync(p->h_stopped, gs.stopped, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
-    HZ_CUDA(cudaStreamSynchronize(st));
+  hz_status init() {
+    M = o->restart_m;
+    K = o->inner_k;
+    n = p->g.n;
+    vrs = (long long)(p->lim.restart_max + 1) * n;
+    zrs = (long long)p->lim.restart_max * n;
+    fixed = o->fixed_its > 0;
+    mv_fci = 1 + K;
+    for (const auto& nd : p->nodes) mv_fci += nd.q * nd.sweeps - 1;
+    fnorm.assign(nrhs, 0.0);
+    rel.assign(nrhs, 1.0);
+    its.assign(nrhs, 0);
+    cycles.assign(nrhs, 0);
+    done.assign(nrhs, 0);
+    active.assign(nrhs, 0);
+    mvs.assign(nrhs, 0);
+    HZ_CUDA(cudaMemsetAsync(u, 0, sizeof(double2) * n * nrhs, st));
     return HZ_OK;
-  };
+  }
 
-  int cycle = 0;
-  bool diverged = false;
-  for (;;) {
-    // true residual r = s f - A u, v0 = r/||r||
-    HZ_CUDA(hz::launch_residual_start(p->g, p->m64, fb, p->su.s,
+  hz_status enqueue_flags() {
+    GmresDev& go = p->gout;
+    HZ_CUDA(cudaMemcpyAsync(p->h_scal, go.scal, sizeof(double) * hz::SC_COUNT * nrhs,
+                            cudaMemcpyDeviceToHost, st));
+    HZ_CUDA(cudaMemcpyAsync(p->h_stopped, go.stopped, sizeof(int) * nrhs, cudaMemcpyDeviceToHost,
+                            st));
+    return HZ_OK;
+  }
+
+  // true residual r = s f - A u, v0 = r / ||r||
+  hz_status enqueue_cycle_start() {
+    GmresDev& go = p->gout;
+    HZ_CUDA(hz::launch_residual_start(p->g, p->m64, Buf<const double2>{(const double2*)f, n},
+                                      p->su.s,
                                       cycle == 0 ? Buf<const double2>{nullptr, 0}
                                                  : Buf<const double2>{(const double2*)u, n},
                                       Buf<double2>{p->V, vrs}, go, p->partial, p->counters, nrhs,
                                       st));
     for (int r = 0; r < nrhs; ++r) mvs[r] += cycle == 0 ? 0 : 1;
-    HZ_CUDA(hz::launch_scale(Buf<double2>{p->V, vrs}, Buf<const double2>{p->V, vrs}, n, go, nrhs, st));
-    HZ_TRY(read_scal(go));
+    HZ_CUDA(hz::launch_scale(Buf<double2>{p->V, vrs}, Buf<const double2>{p->V, vrs}, n, go, nrhs,
+                             st));
+    return enqueue_flags();
+  }
+
+  // after the stream synchronised: convergence per rhs; start the next cycle or finish
+  hz_status after_cycle_start() {
+    GmresDev& go = p->gout;
     bool all_done = true;
     for (int r = 0; r < nrhs; ++r) {
       const double beta = p->h_scal[r * hz::SC_COUNT + hz::SC_BETA];
@@ -992,83 +1058,171 @@ hz_status solve_on(hz_problem* p, const void* f, void* u, int nrhs, const hz_sol
       } else if (fnorm[r] == 0.0) {
         done[r] = 1;
       } else if (fixed) {
-        done[r] = its[r] >= opts->fixed_its ? 1 : 0;
+        done[r] = its[r] >= o->fixed_its ? 1 : 0;
       } else {
-        done[r] = rel[r] <= opts->rtol ? 1 : 0;
+        done[r] = rel[r] <= o->rtol ? 1 : 0;
       }
       all_done = all_done && done[r];
     }
-    if (all_done || cycle >= opts->max_cycles) break;
+    if (all_done || cycle >= o->max_cycles || diverged) {
+      finished = true;
+      return HZ_OK;
+    }
     ++cycle;
-    // per-rhs stop flags and tolerance of this cycle
     std::vector<double> tol(nrhs);
     for (int r = 0; r < nrhs; ++r) {
-      tol[r] = fixed ? -1.0 : opts->rtol * fnorm[r];
+      tol[r] = fixed ? -1.0 : o->rtol * fnorm[r];
       p->h_stopped[r] = done[r];
       if (!done[r]) cycles[r]++;
+      active[r] = !done[r];
     }
     HZ_TRY(fill_scal_tol(p, go, tol, nrhs, st));
-    HZ_CUDA(cudaMemcpyAsync(go.stopped, p->h_stopped, sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
-    std::vector<int> active(nrhs);
-    for (int r = 0; r < nrhs; ++r) active[r] = !done[r];
-    for (int k = 0; k < M; ++k) {
-      HZ_TRY(outer_step(p, k, nrhs, K, opts->precision, st));
-      for (int r = 0; r < nrhs; ++r)
-        if (active[r]) {
-          its[r]++;
-          mvs[r] += mv_fci + 1;
-        }
-      HZ_TRY(read_scal(go));
-      bool any_active = false;
-      bool push = false;
-      for (int r = 0; r < nrhs; ++r) {
-        if (!active[r]) continue;
-        if (!std::isfinite(p->h_scal[r * hz::SC_COUNT + hz::SC_EST])) {
-          diverged = true;
-          p->h_stopped[r] = 1;
-          push = true;
-        }
-        if (p->h_stopped[r]) {
-          active[r] = 0;
-          continue;
-        }
-        if (fixed && its[r] >= opts->fixed_its) {
-          p->h_stopped[r] = 1;
-          active[r] = 0;
-          push = true;
-          continue;
-        }
-        any_active = true;
+    HZ_CUDA(cudaMemcpyAsync(go.stopped, p->h_stopped, sizeof(int) * nrhs, cudaMemcpyHostToDevice,
+                            st));
+    k = 0;
+    in_cycle = true;
+    return HZ_OK;
+  }
+
+  hz_status enqueue_step() {
+    HZ_TRY(outer_step(p, k, nrhs, K, o->precision, st));
+    for (int r = 0; r < nrhs; ++r)
+      if (active[r]) {
+        its[r]++;
+        mvs[r] += mv_fci + 1;
       }
-      if (push)
-        HZ_CUDA(cudaMemcpyAsync(go.stopped, p->h_stopped, sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
-      if (!any_active) break;
+    return enqueue_flags();
+  }
+
+  // after the stream synchronised: stop flags; end the cycle when no rhs is left or m steps
+  hz_status after_step() {
+    GmresDev& go = p->gout;
+    bool any_active = false, push = false;
+    for (int r = 0; r < nrhs; ++r) {
+      if (!active[r]) continue;
+      if (!std::isfinite(p->h_scal[r * hz::SC_COUNT + hz::SC_EST])) {
+        diverged = true;
+        p->h_stopped[r] = 1;
+        push = true;
+      }
+      if (p->h_stopped[r]) {
+        active[r] = 0;
+        continue;
+      }
+      if (fixed && its[r] >= o->fixed_its) {
+        p->h_stopped[r] = 1;
+        active[r] = 0;
+        push = true;
+        continue;
+      }
+      any_active = true;
     }
-    // u += Z y (rhs that were done at the cycle start have kend = 0)
-    HZ_CUDA(hz::launch_backsolve(go, nrhs, st));
-    HZ_CUDA(hz::launch_combine(ub, p->Z, n, zrs, go, Buf<const double2>{nullptr, 0}, -1, 1, n, nrhs,
-                               M, st));
-    if (diverged) break;
+    if (push)
+      HZ_CUDA(cudaMemcpyAsync(go.stopped, p->h_stopped, sizeof(int) * nrhs, cudaMemcpyHostToDevice,
+                              st));
+    ++k;
+    if (!any_active || k >= M) {
+      // u += Z y (rhs done at the cycle start have kend = 0)
+      in_cycle = false;
+      HZ_CUDA(hz::launch_backsolve(go, nrhs, st));
+      HZ_CUDA(hz::launch_combine(Buf<double2>{(double2*)u, n}, p->Z, n, zrs, go,
+                                 Buf<const double2>{nullptr, 0}, -1, 1, n, nrhs, M, st));
+      if (diverged) finished = true;
+    }
+    return HZ_OK;
+  }
+
+  hz_status result() {
+    hz_status ret = HZ_OK;
+    for (int r = 0; r < nrhs; ++r) {
+      const bool conv = std::isfinite(rel[r]) && rel[r] <= o->rtol;
+      if (stats) {
+        stats[r].cycles = cycles[r];
+        stats[r].its = its[r];
+        stats[r].matvecs = mvs[r];
+        stats[r].converged = conv ? 1 : 0;
+        stats[r].rel_res_true = rel[r];
+      }
+      if (!conv && !fixed && ret == HZ_OK) ret = HZ_ERR_NOT_CONVERGED;
+    }
+    if (diverged) return fail(HZ_ERR_DIVERGED, "a residual became NaN or Inf");
+    if (ret == HZ_ERR_NOT_CONVERGED) t_err = "max_cycles reached above rtol";
+    return ret;
+  }
+};
+
+// Advances every state to the end in lockstep: a cycle start for all, then outer steps for all
+// that are inside a cycle, one host synchronisation per round.
+hz_status drive(std::vector<SolveState>& ss) {
+  for (auto& s : ss) HZ_TRY(s.init());
+  for (;;) {
+    bool any = false;
+    for (auto& s : ss)
+      if (!s.finished) {
+        HZ_TRY(s.enqueue_cycle_start());
+        any = true;
+      }
+    if (!any) break;
+    for (auto& s : ss)
+      if (!s.finished) HZ_CUDA(cudaStreamSynchronize(s.st));
+    for (auto& s : ss)
+      if (!s.finished) HZ_TRY(s.after_cycle_start());
+    for (;;) {
+      bool stepping = false;
+      for (auto& s : ss)
+        if (!s.finished && s.in_cycle) {
+          HZ_TRY(s.enqueue_step());
+          stepping = true;
+        }
+      if (!stepping) break;
+      for (auto& s : ss)
+        if (!s.finished && s.in_cycle) HZ_CUDA(cudaStreamSynchronize(s.st));
+      for (auto& s : ss)
+        if (!s.finished && s.in_cycle) HZ_TRY(s.after_step());
+    }
   }
   // the loop ends right after a residual evaluation, so rel[] is the final true residual
+  for (auto& s : ss) HZ_CUDA(cudaStreamSynchronize(s.st));
   hz_status ret = HZ_OK;
-  for (int r = 0; r < nrhs; ++r) {
-    const bool conv = std::isfinite(rel[r]) && rel[r] <= opts->rtol;
-    if (stats) {
-      stats[r].cycles = cycles[r];
-      stats[r].its = its[r];
-      stats[r].matvecs = mvs[r];
-      stats[r].converged = conv ? 1 : 0;
-      stats[r].rel_res_true = rel[r];
-    }
-    if (!conv && !fixed && ret == HZ_OK) ret = HZ_ERR_NOT_CONVERGED;
+  for (auto& s : ss) {
+    const hz_status r = s.result();
+    if (r != HZ_OK && (ret == HZ_OK || ret == HZ_ERR_NOT_CONVERGED)) ret = r;
   }
-  if (diverged) {
-    t_err = "a residual became NaN or Inf";
-    return HZ_ERR_DIVERGED;
-  }
-  if (ret == HZ_ERR_NOT_CONVERGED) t_err = "max_cycles reached above rtol";
   return ret;
+}
+
+hz_status solve_batched_on(hz_problem* const* probs, int nprob, const void* const* f,
+                           void* const* u, const int* nrhs, const hz_solve_opts* opts,
+                           hz_solve_stats* stats) {
+  std::vector<SolveState> ss;
+  long long off = 0;
+  for (int i = 0; i < nprob; ++i) {
+    if (nrhs[i] == 0) continue;
+    SolveState s;
+    s.p = probs[i];
+    s.f = f[i];
+    s.u = u[i];
+    s.nrhs = nrhs[i];
+    s.o = opts;
+    s.stats = stats ? stats + off : nullptr;
+    s.st = probs[i]->own;
+    ss.push_back(s);
+    off += nrhs[i];
+  }
+  return drive(ss);
+}
+
+hz_status solve_on(hz_problem* p, const void* f, void* u, int nrhs, const hz_solve_opts* opts,
+                   hz_solve_stats* stats, cudaStream_t st) {
+  std::vector<SolveState> ss(1);
+  ss[0].p = p;
+  ss[0].f = f;
+  ss[0].u = u;
+  ss[0].nrhs = nrhs;
+  ss[0].o = opts;
+  ss[0].stats = stats;
+  ss[0].st = st;
+  return drive(ss);
 }
 
 }  // namespace

@@ -24,7 +24,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory",
 # every exported symbol declared in include/hz.h
 EXPORTS = ["hz_problem_create", "hz_plan", "hz_problem_destroy", "hz_problem_get_info",
            "hz_problem_nodes", "hz_problem_set_nodes", "hz_apply_shifted", "hz_shifted_solve",
-           "hz_fci", "hz_solve", "hz_profile_enable", "hz_profile_read", "hz_residual_noalloc",
+           "hz_fci", "hz_solve", "hz_solve_batched", "hz_profile_enable", "hz_profile_read", "hz_residual_noalloc",
            "hz_status_string", "hz_last_error", "hz_launch_count"]
 
 # kernel classes of hz_profile_read
@@ -98,6 +98,9 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.hz_shifted_solve.argtypes = [P, C.c_int, P, P, C.c_int, C.c_int, P]
     lib.hz_fci.argtypes = [P, P, P, C.c_int, C.c_int, C.c_int, P]
     lib.hz_solve.argtypes = [P, P, P, C.c_int, C.POINTER(HzSolveOpts), C.POINTER(HzSolveStats), P]
+    lib.hz_solve_batched.argtypes = [C.POINTER(P), C.c_int, C.POINTER(P), C.POINTER(P),
+                                     C.POINTER(C.c_int), C.POINTER(HzSolveOpts),
+                                     C.POINTER(HzSolveStats), P]
     lib.hz_profile_enable.argtypes = [P, C.c_int]
     lib.hz_profile_read.argtypes = [P, C.c_int, C.POINTER(C.c_longlong), dp, dp]
     lib.hz_residual_noalloc.argtypes = [C.POINTER(HzGrid), P, C.c_double, P, C.c_double, P, P, P,
@@ -329,3 +332,33 @@ class Problem:
         stats = [SolveStats(s.cycles, s.its, s.matvecs, bool(s.converged), s.rel_res_true)
                  for s in st[:nrhs]]
         return u, stats
+
+
+def solve_batched(problems, fs, restart=30, inner_k=4, rtol=1e-8, max_cycles=50,
+                  precision=HZ_C128, fixed_its=0, outs=None, stream=None, check=True):
+    """hz_solve_batched over several Problems: fs[i] holds problem i's right-hand sides.
+    Returns ([u_i], [[SolveStats] per problem])."""
+    import torch
+    lib = load()
+    k = len(problems)
+    us = [torch.empty_like(f) for f in fs] if outs is None else outs
+    P = C.c_void_p
+    hp = (P * k)(*[p._h for p in problems])
+    fp = (P * k)()
+    up = (P * k)()
+    nr = (C.c_int * k)()
+    for i, (pr, f, u) in enumerate(zip(problems, fs, us)):
+        fp[i], nr[i] = _dev_ptr(f, torch.complex128, pr.n)
+        up[i], _ = _dev_ptr(u, torch.complex128, pr.n)
+    opts = HzSolveOpts(int(restart), int(inner_k), float(rtol), int(max_cycles), int(precision),
+                       int(fixed_its))
+    tot = max(1, sum(nr))
+    st = (HzSolveStats * tot)()
+    status = lib.hz_solve_batched(hp, k, fp, up, nr, C.byref(opts), st, _stream(stream))
+    _check(status, lib, allow=() if check else (4,))
+    out, off = [], 0
+    for i in range(k):
+        out.append([SolveStats(s.cycles, s.its, s.matvecs, bool(s.converged), s.rel_res_true)
+                    for s in st[off:off + nr[i]]])
+        off += nr[i]
+    return us, out

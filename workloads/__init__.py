@@ -182,3 +182,26 @@ def small_case(seed: int, nx: int, ny: int, nz: int, nrhs: int = 1, ppw: float =
     f = random_field(seed + 7, nrhs, nx, ny, nz)
     return Workload(f"small_{nx}x{ny}x{nz}", nx, ny, nz, h, omega_for_ppw(c, h, ppw), layer,
                     1.0, J, 1.0, 1.0, restart, k_in, 1e-8, c, f)
+
+
+def layered_batch(seed: int = 3, sizes=(48, 64, 96), per_size: int = 4, nrhs: int = 4,
+                  ppw: float = 8.0):
+    """Instances of uneven grid sizes (per_size each of sizes), each with its own seeded
+    layered medium (5 horizontal layers, c per layer ~ U[1.5, 4.5]), ppw points per
+    wavelength at its c_min, an 8-cell sponge, J = 8 and nrhs unit point sources 1/h^3 at
+    seeded core points."""
+    out = []
+    g = _rng(seed)
+    idx = 0
+    for N in sizes:
+        for _ in range(per_size):
+            h = 1.0 / (N + 1)
+            c = medium_layered(seed * 1000 + idx, N, N, N, nlayers=5, c_lo=1.5, c_hi=4.5)
+            f = np.zeros((nrhs, N, N, N), dtype=np.complex128)
+            for r in range(nrhs):
+                i, j, k = random_core_index(g, N, N, N, 8)
+                f[r, k, j, i] = 1.0 / h ** 3
+            out.append(Workload(f"layered_{N}_{idx}", N, N, N, h, omega_for_ppw(c, h, ppw), 8,
+                                1.0, 8, 1.0, default_eps(N, N, N), 30, 4, 1e-8, c, f))
+            idx += 1
+    return out
