@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--ncu-region", action="store_true",
                     help="bracket only the timed chosen-form steps with cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off) and skip the other passes")
+    ap.add_argument("--ncu-large", action="store_true",
+                    help="run only the 256^3 stencil / polynomial-stage bandwidth measurement, "
+                         "bracketed with cudaProfilerStart/Stop")
     return ap.parse_args()
 
 
@@ -198,7 +201,7 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def large_grid_bandwidth(hz, torch, dev, N=256):
+def large_grid_bandwidth(hz, torch, dev, N=256, profile_region=False):
     """Complex64 stencil and polynomial stage on an N^3 Gaussian-bump grid (fields >> L2):
     algorithmic GB/s from CUDA events, against the measured copy bandwidth."""
     import workloads as W
@@ -212,6 +215,8 @@ def large_grid_bandwidth(hz, torch, dev, N=256):
     for _ in range(3):
         P.apply_shifted(x, 0.3 - 1j, out=y)
     torch.cuda.synchronize()
+    if profile_region:
+        torch.cuda.profiler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = 20
     e0.record()
@@ -225,6 +230,9 @@ def large_grid_bandwidth(hz, torch, dev, N=256):
     P.shifted_solve(0, x, out=y)
     nl, ms, by = P.profile_read(hz.PROF_POLY)
     P.profile(False)
+    if profile_region:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     P.close()
     peak, kind = measured_peak_hbm()
     st_gbs = 24.0 * n / t_st / 1e9
@@ -448,6 +456,12 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.ncu_large:
+        import torch
+        import paper_1811_12378_gb300 as hz
+        print(json.dumps(large_grid_bandwidth(hz, torch, torch.device("cuda", 0),
+                                              profile_region=True)))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
