@@ -280,6 +280,17 @@ def batched_uneven(hz, torch, dev, precision):
             "batched_s": t_b, "sequential_s": t_s}
 
 
+def max_over_ranks_of(x: float, world: int, device) -> float:
+    """The largest of each rank's x (a time), through the process group when world > 1."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -329,11 +340,7 @@ def run_ours(args):
         return total, stats[0]
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_of(x, world, dev)
 
     chosen = hz.HZ_MIXED_C64_FCI32
     # warm-up (all forms)

@@ -294,6 +294,45 @@ def test_edge_cases():
             P.apply_shifted(f.cpu())                                # host tensor
 
 
+def test_failure_statuses():
+    """Non-convergence, divergence and a happy breakdown are reported, not hidden.  All are
+    made on the host side: a capped cycle count, a NaN planted in the right-hand side, and an
+    eigenvector right-hand side that FCI inverts exactly."""
+    wl = W.small_case(4, 9, 8, 7, layer=1, J=3)
+    with problem_of(wl, None, nrhs_max=1, restart_max=3, inner_k_max=2) as P:
+        f = to_dev(wl.f)
+        # max_cycles = 1 with an unreachable tolerance: HZ_ERR_NOT_CONVERGED, stats filled
+        with pytest.raises(hzpkg.HzError) as ei:
+            P.solve(f, restart=3, inner_k=2, rtol=1e-14, max_cycles=1)
+        assert ei.value.status == 4
+        u, st = P.solve(f, restart=3, inner_k=2, rtol=1e-14, max_cycles=1, check=False)
+        assert st[0].cycles == 1 and st[0].its == 3 and not st[0].converged
+        assert 0 < st[0].rel_res_true < 1
+        # a NaN in the right-hand side: HZ_ERR_DIVERGED
+        bad = f.clone()
+        bad.view(-1)[5] = complex(float("nan"), 0.0)
+        with pytest.raises(hzpkg.HzError) as ei:
+            P.solve(bad, restart=3, inner_k=2, rtol=1e-8, max_cycles=3)
+        assert ei.value.status == 6
+        # the problem stays usable
+        u, st = P.solve(f, restart=3, inner_k=2, rtol=1e-6, max_cycles=50)
+        assert st[0].converged
+    # eigenvector right-hand side, c = 1, no sponge: FCI returns v/mu, the first outer step
+    # breaks down happily and the solve ends exactly after one step
+    nx, ny, nz = 6, 5, 7
+    h = 1.0 / 8
+    c = np.ones((nz, ny, nx))
+    omega = 2 * math.pi / (6 * h)
+    with hzpkg.Problem(c, h, omega, 0, 0.0, 4, 1.0, 0.5, nrhs_max=1, restart_max=5,
+                       inner_k_max=3) as P:
+        i, j, k = np.arange(1, nx + 1), np.arange(1, ny + 1), np.arange(1, nz + 1)
+        v = (np.sin(2 * np.pi * k / (nz + 1))[:, None, None]
+             * np.sin(1 * np.pi * j / (ny + 1))[None, :, None]
+             * np.sin(3 * np.pi * i / (nx + 1))[None, None, :]).astype(np.complex128)
+        u, st = P.solve(to_dev(v[None]), restart=5, inner_k=3, rtol=1e-10, max_cycles=3)
+        assert st[0].converged and st[0].its == 1 and st[0].rel_res_true <= 1e-12
+
+
 def test_native_kernels_launch():
     before = hzpkg.launch_count()
     wl = W.small_case(1, 8, 8, 8, layer=1, J=2)
