@@ -89,11 +89,15 @@ typedef struct {
 } hz_contour_opts;
 
 /* Workspace limits fixed at creation: right-hand sides per call (nz * nrhs_max <= 65535),
- * outer restart length (1..128), inner GMRES steps (0..128). */
+ * outer restart length (1..128), inner GMRES steps (0..128).  autotune != 0 times the
+ * candidate tile shapes of the polynomial-stage and complex64 stencil kernels on this grid
+ * at creation (a few milliseconds) and keeps the fastest; 0 keeps fixed defaults.  Tiling
+ * changes no result: every candidate performs the same arithmetic per point. */
 typedef struct {
   int nrhs_max;
   int restart_max;
   int inner_k_max;
+  int autotune;
 } hz_limits;
 
 /* hz_solve settings.  restart_m <= restart_max, inner_k <= inner_k_max.  precision is an
@@ -125,6 +129,10 @@ typedef struct {
   int J;           /* contour nodes */
   int stages;      /* stencil sweeps of one FCI application (max over nodes of q*sweeps) */
   long long n;     /* grid points */
+  int tile_poly_zc[3];    /* polynomial stage z-column length for 1, 2-3, >= 4 active nodes */
+  int tile_poly_rows[3];  /* polynomial stage grid rows per block, same classes */
+  int tile_stencil_zc;    /* complex64 stencil z-column length */
+  int tile_stencil_rows;  /* complex64 stencil rows per block */
 } hz_problem_info;
 
 /* Create a problem: copy the wavespeed c_host (nx*ny*nz doubles, x fastest, host memory),

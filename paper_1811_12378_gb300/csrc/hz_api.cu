@@ -490,6 +490,97 @@ hz_status outer_step(hz_problem* p, int k, int nrhs, int K, int precision, cudaS
   return HZ_OK;
 }
 
+// Times the candidate tile shapes of the polynomial stage (per node-count class) and of the
+// complex64 stencil on this problem's grid and keeps the fastest (fields zeroed first; every
+// candidate computes the same values, only the launch shape differs).
+hz_status autotune(hz_problem* p) {
+  const cudaStream_t st = p->own;
+  const long long n = p->g.n;
+  const long long wrs = 4LL * p->J * n;
+  HZ_CUDA(cudaMemsetAsync(p->f32, 0, sizeof(float2) * n, st));
+  HZ_CUDA(cudaMemsetAsync(p->w32, 0, sizeof(float2) * n, st));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  HZ_CUDA(cudaEventCreate(&e0));
+  HZ_CUDA(cudaEventCreate(&e1));
+  auto timed = [&](auto launch) -> float {
+    float best = 1e30f;
+    if (launch() != cudaSuccess) return best;
+    cudaEventRecord(e0, st);
+    for (int rep = 0; rep < 5; ++rep)
+      if (launch() != cudaSuccess) return best;
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return best;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  const int J = p->J;
+  for (int cls = 0; cls < 3; ++cls) {
+    const int nn = cls == 0 ? 1 : (cls == 1 ? 2 : J);
+    if (nn > J || (cls == 2 && J < 4)) continue;
+    hz::StageArgs<float> a;
+    std::memset(&a, 0, sizeof(a));
+    a.nnodes = nn;
+    for (int s = 0; s < nn; ++s) {
+      const Slots sl = slots_of(s, n);
+      hz::StageNode<float>& sn = a.nd[s];
+      sn.kind = hz::SK_MID;
+      sn.mdr = 0.f;
+      sn.mdi = -0.1f;
+      sn.cfr = 1.f;
+      sn.ipr = 1.f;
+      sn.in = sl.KA;
+      sn.kout = sl.KB;
+      sn.acc = sl.ACC;
+    }
+    float best = 1e30f;
+    int bz = p->g.pzc[cls], br = p->g.prows[cls];
+    for (int zc : {1, 2, 4})
+      for (int rows : {1, 2, 4}) {
+        if (32 * nn * rows > 512) continue;
+        if (cls == 2 && sizeof(double2) * 32 * zc * J * rows > 48 * 1024) continue;
+        p->g.pzc[cls] = zc;
+        p->g.prows[cls] = rows;
+        const float t = timed([&] {
+          return hz::launch_poly_stage<float2, float>(p->g, p->d32,
+                                                      Buf<const float2>{p->f32, n},
+                                                      (float2*)p->poly, wrs,
+                                                      Buf<double2>{p->w, n}, 1, a, st);
+        });
+        if (t < best) {
+          best = t;
+          bz = zc;
+          br = rows;
+        }
+      }
+    p->g.pzc[cls] = bz;
+    p->g.prows[cls] = br;
+  }
+  float best = 1e30f;
+  int bz = p->g.szc, br = p->g.srows;
+  for (int zc : {2, 4, 8})
+    for (int rows : {2, 4, 8}) {
+      p->g.szc = zc;
+      p->g.srows = rows;
+      const float t = timed([&] {
+        return hz::launch_stencil32(p->g, p->d32, Buf<const float2>{p->w32, n},
+                                    Buf<float2>{p->Aw32, n}, 1, 0.0, 0.0, st);
+      });
+      if (t < best) {
+        best = t;
+        bz = zc;
+        br = rows;
+      }
+    }
+  p->g.szc = bz;
+  p->g.srows = br;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  return HZ_OK;
+}
+
 hz_status check_problem(const hz_problem* p) {
   if (!p) return fail(HZ_ERR_INVALID, "null problem");
   return HZ_OK;
@@ -610,6 +701,12 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   p->g.cs = p->su.s / (grid->h * grid->h);
   p->g.sig = grid->sigma_max;
   p->g.csf = float(p->g.cs);
+  for (int c = 0; c < 3; ++c) p->g.pzc[c] = 4;
+  p->g.prows[0] = 4;
+  p->g.prows[1] = 2;
+  p->g.prows[2] = 1;
+  p->g.szc = 4;
+  p->g.srows = 4;
   std::string err;
   if (!hz::setup_nodes(p->su, *contour, p->nodes, err)) {
     delete p;
@@ -710,6 +807,13 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
     delete p;
     return cuda_fail(e, "cudaMemcpy of coefficients");
   }
+  if (limits->autotune) {
+    const hz_status ts = autotune(p);
+    if (ts != HZ_OK) {
+      delete p;
+      return ts;
+    }
+  }
   *out = p;
   return HZ_OK;
 }
@@ -809,6 +913,12 @@ hz_status hz_problem_get_info(const hz_problem* p, hz_problem_info* info) {
   for (const auto& nd : p->nodes) T = std::max(T, nd.q * nd.sweeps);
   info->stages = T;
   info->n = p->g.n;
+  for (int c = 0; c < 3; ++c) {
+    info->tile_poly_zc[c] = p->g.pzc[c];
+    info->tile_poly_rows[c] = p->g.prows[c];
+  }
+  info->tile_stencil_zc = p->g.szc;
+  info->tile_stencil_rows = p->g.srows;
   return HZ_OK;
 }
 

@@ -25,7 +25,14 @@ struct Geom {
   double cs;       // s / h^2: weight of the 7-point Laplacian
   double sig;      // sigma_max of the sponge
   float csf;       // s / h^2 in float32, so float32 kernels convert nothing
+  // tile shapes chosen by the autotuner at problem creation (kernel launch parameters only)
+  int pzc[3];      // polynomial stage: z-column length for 1, 2-3, >= 4 active nodes
+  int prows[3];    // polynomial stage: grid rows per block for the same classes
+  int szc, srows;  // complex64 stencil: z-column length, rows per block
 };
+
+// Node-count class of a polynomial stage for the tile tables above.
+inline int stage_class(int nnodes) { return nnodes >= 4 ? 2 : (nnodes >= 2 ? 1 : 0); }
 
 // Per-node parameters of the polynomial scheme (eq:fix-pt-exp) and the quadrature (§6).
 struct NodeParams {

@@ -80,7 +80,7 @@ __device__ __forceinline__ T apply_point(T xc, T nb, R cs, R mp, R ap, R zr, R z
 // (all loads of a column issued together, z-neighbours shared between consecutive points):
 //     (A - zI) x = (dg - z) x - (s/h^2) * (sum of the 6 neighbours).
 template <int ZC>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
 k_stencil32(Geom g, const float2* __restrict__ dg, const float2* __restrict__ x, long long xrs,
             float2* __restrict__ y, long long yrs, float zr, float zi) {
   const int i = blockIdx.x * 32 + threadIdx.x;
@@ -644,14 +644,26 @@ inline unsigned ew_blocks(long long n) {
 template <typename T, typename R>
 cudaError_t launch_poly_stage(const Geom& g, const T* dg, Buf<const T> f, T* ws, long long wrs,
                               Buf<double2> w, int nvec, const StageArgs<R>& a, cudaStream_t st) {
-  constexpr int ZC = sizeof(T) == 8 ? 4 : 2;  // z-column length (float2 : double2)
-  // rows per block: at least 4 warps a block when few nodes are active
-  const int rows = a.nnodes >= 4 ? 1 : (a.nnodes == 1 ? 4 : 2);
+  const int cls = stage_class(a.nnodes);
+  int zc = g.pzc[cls];
+  if (sizeof(T) == 16 && zc > 2) zc = 2;  // float64 columns: register budget
+  const int rows = g.prows[cls];
   dim3 blk(32, a.nnodes, rows);
-  dim3 grd((g.nx + 31) / 32, (g.ny + rows - 1) / rows, ((g.nz + ZC - 1) / ZC) * nvec);
-  const size_t smem = a.final_quad ? sizeof(double2) * 32 * ZC * a.nnodes * rows : 0;
+  dim3 grd((g.nx + 31) / 32, (g.ny + rows - 1) / rows, ((g.nz + zc - 1) / zc) * nvec);
+  const size_t smem = a.final_quad ? sizeof(double2) * 32 * zc * a.nnodes * rows : 0;
   count_launch();
-  k_poly_stage<T, ZC><<<grd, blk, smem, st>>>(g, dg, f.p, f.rs, ws, wrs, w.p, w.rs, a);
+  switch (zc) {
+    case 1:
+      k_poly_stage<T, 1><<<grd, blk, smem, st>>>(g, dg, f.p, f.rs, ws, wrs, w.p, w.rs, a);
+      break;
+    case 2:
+      k_poly_stage<T, 2><<<grd, blk, smem, st>>>(g, dg, f.p, f.rs, ws, wrs, w.p, w.rs, a);
+      break;
+    default:
+      if constexpr (sizeof(T) == 8)
+        k_poly_stage<T, 4><<<grd, blk, smem, st>>>(g, dg, f.p, f.rs, ws, wrs, w.p, w.rs, a);
+      break;
+  }
   return cudaGetLastError();
 }
 
@@ -697,11 +709,21 @@ cudaError_t launch_cgs(int mode, const double2* V, long long vis, long long vrs,
 
 cudaError_t launch_stencil32(const Geom& g, const float2* dg, Buf<const float2> x, Buf<float2> y,
                              int nvec, double zr, double zi, cudaStream_t st) {
-  constexpr int ZC = 4;
-  dim3 blk(32, 4, 1);
-  dim3 grd((g.nx + 31) / 32, (g.ny + 3) / 4, ((g.nz + ZC - 1) / ZC) * nvec);
+  const int zc = g.szc, rows = g.srows;
+  dim3 blk(32, rows, 1);
+  dim3 grd((g.nx + 31) / 32, (g.ny + rows - 1) / rows, ((g.nz + zc - 1) / zc) * nvec);
   count_launch();
-  k_stencil32<ZC><<<grd, blk, 0, st>>>(g, dg, x.p, x.rs, y.p, y.rs, float(zr), float(zi));
+  switch (zc) {
+    case 2:
+      k_stencil32<2><<<grd, blk, 0, st>>>(g, dg, x.p, x.rs, y.p, y.rs, float(zr), float(zi));
+      break;
+    case 8:
+      k_stencil32<8><<<grd, blk, 0, st>>>(g, dg, x.p, x.rs, y.p, y.rs, float(zr), float(zi));
+      break;
+    default:
+      k_stencil32<4><<<grd, blk, 0, st>>>(g, dg, x.p, x.rs, y.p, y.rs, float(zr), float(zi));
+      break;
+  }
   return cudaGetLastError();
 }
 

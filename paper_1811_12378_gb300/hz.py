@@ -42,7 +42,8 @@ class HzContour(C.Structure):
 
 
 class HzLimits(C.Structure):
-    _fields_ = [("nrhs_max", C.c_int), ("restart_max", C.c_int), ("inner_k_max", C.c_int)]
+    _fields_ = [("nrhs_max", C.c_int), ("restart_max", C.c_int), ("inner_k_max", C.c_int),
+                ("autotune", C.c_int)]
 
 
 class HzSolveOpts(C.Structure):
@@ -57,7 +58,9 @@ class HzSolveStats(C.Structure):
 
 class HzInfo(C.Structure):
     _fields_ = [("s", C.c_double), ("b1", C.c_double), ("b2", C.c_double),
-                ("rho2", C.c_double), ("J", C.c_int), ("stages", C.c_int), ("n", C.c_longlong)]
+                ("rho2", C.c_double), ("J", C.c_int), ("stages", C.c_int), ("n", C.c_longlong),
+                ("tile_poly_zc", C.c_int * 3), ("tile_poly_rows", C.c_int * 3),
+                ("tile_stencil_zc", C.c_int), ("tile_stencil_rows", C.c_int)]
 
 
 class HzError(RuntimeError):
@@ -172,7 +175,9 @@ def plan(c: np.ndarray, h: float, omega: float, layer_cells: int, sigma_max: flo
 
 def _info_dict(info: HzInfo):
     return {"s": info.s, "b1": info.b1, "b2": info.b2, "rho2": info.rho2, "J": info.J,
-            "stages": info.stages, "n": info.n}
+            "stages": info.stages, "n": info.n,
+            "tile_poly_zc": list(info.tile_poly_zc), "tile_poly_rows": list(info.tile_poly_rows),
+            "tile_stencil": [info.tile_stencil_zc, info.tile_stencil_rows]}
 
 
 @dataclass
@@ -213,7 +218,7 @@ class Problem:
     """
 
     def __init__(self, c, h, omega, layer_cells, sigma_max, J, t, eps, qmax=5, reduction=5.0,
-                 nrhs_max=1, restart_max=30, inner_k_max=8):
+                 nrhs_max=1, restart_max=30, inner_k_max=8, autotune=True):
         self._lib = load()
         c = np.ascontiguousarray(c, dtype=np.float64)
         self.shape = c.shape
@@ -221,7 +226,7 @@ class Problem:
         self.n = nx * ny * nz
         g = _grid(nx, ny, nz, h, omega, layer_cells, sigma_max)
         co = HzContour(int(J), float(t), float(eps), int(qmax), float(reduction))
-        lim = HzLimits(int(nrhs_max), int(restart_max), int(inner_k_max))
+        lim = HzLimits(int(nrhs_max), int(restart_max), int(inner_k_max), 1 if autotune else 0)
         handle = C.c_void_p()
         _check(self._lib.hz_problem_create(C.byref(g), _dp(c), C.byref(co), C.byref(lim),
                                            C.byref(handle)), self._lib)

@@ -294,6 +294,27 @@ def test_edge_cases():
             P.apply_shifted(f.cpu())                                # host tensor
 
 
+def test_autotuned_tiles_give_identical_results():
+    """Tile shapes only change launch geometry: a problem with autotuning and one with the
+    fixed defaults give bit-identical complex64 stencils and FCI outputs."""
+    wl = W.small_case(14, 45, 13, 11, layer=2, J=5)
+    x = W.random_field(3, 2, wl.nx, wl.ny, wl.nz)
+    outs = []
+    for tune in (True, False):
+        P = hzpkg.Problem(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, wl.J, wl.t,
+                          wl.eps, nrhs_max=2, restart_max=4, inner_k_max=3, autotune=tune)
+        with P:
+            info = P.info
+            assert all(z in (1, 2, 4) for z in info["tile_poly_zc"])
+            assert all(r in (1, 2, 4) for r in info["tile_poly_rows"])
+            assert info["tile_stencil"][0] in (2, 4, 8) and info["tile_stencil"][1] in (2, 4, 8)
+            y = to_np(P.apply_shifted(to_dev(x, torch.complex64), 0.2 - 0.7j))
+            z = to_np(P.fci(to_dev(x), inner_k=3, precision=hzpkg.HZ_MIXED_C64_FCI32))
+            outs.append((y, z))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+
+
 def test_failure_statuses():
     """Non-convergence, divergence and a happy breakdown are reported, not hidden.  All are
     made on the host side: a capped cycle count, a NaN planted in the right-hand side, and an
