@@ -416,7 +416,8 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": "mixed, FCI in complex64: polynomial sweeps, "
-                   "step d and inner GMRES in complex64, quadrature sum accumulated in float64; "
+                   "step d and inner GMRES in complex64, quadrature sum accumulated in float pairs "
+                   "(~48 bits) and returned in float64; "
                    "outer FGMRES (CGS2 Arnoldi, Givens) and true residual in float64",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"replicas x{world}"},

@@ -56,10 +56,11 @@ typedef enum {
 
 typedef enum {
   HZ_C128 = 0,        /* everything complex128 / float64 ("plain" form) */
-  HZ_MIXED_C64 = 1,   /* polynomial sweeps in complex64; quadrature sum, step d, inner and
+  HZ_MIXED_C64 = 1,   /* polynomial sweeps in complex64; quadrature sum (float-pair
+                         accumulation, about 48 bits, returned as float64), step d, inner and
                          outer Arnoldi, Givens and true residual in float64 */
   HZ_MIXED_C64_FCI32 = 2  /* the whole FCI preconditioner in complex64 (sweeps, step d, inner
-                         GMRES), except its quadrature sum, accumulated in float64; the outer
+                         GMRES), except its quadrature sum, accumulated as in HZ_MIXED_C64; the outer
                          FGMRES (CGS2 Arnoldi, Givens, updates) and the true residual in
                          float64.  FGMRES admits a variable preconditioner, so the solution
                          still reaches the float64 residual target. */

@@ -256,12 +256,14 @@ Slots slots_of(int s, long long n) {
 }
 
 // Runs the batched scheme eq:fix-pt-exp for the nodes in `which` from y = 0.  With `quad`
-// the last stage writes w = sum sigma_j/z_j y_j (double2, wbuf); otherwise node slot s ends
-// with its y in the returned offset yfinal[s] of the workspace.
+// the last stage writes w = sum sigma_j/z_j y_j (double2, wbuf; and its complex64 rounding
+// into w32buf where that is given); otherwise node slot s ends with its y in the returned
+// offset yfinal[s] of the workspace.
 template <typename T, typename R>
 hz_status run_poly(hz_problem* p, const T* dg, Buf<const T> f, int nvec,
                    const std::vector<int>& which, bool quad, Buf<double2> wbuf,
-                   std::vector<long long>* yfinal, cudaStream_t st) {
+                   std::vector<long long>* yfinal, cudaStream_t st,
+                   Buf<float2> w32buf = Buf<float2>{nullptr, 0}) {
   const long long n = p->g.n;
   const int nn = (int)which.size();
   T* ws = (T*)p->poly;
@@ -312,6 +314,10 @@ hz_status run_poly(hz_problem* p, const T* dg, Buf<const T> f, int nvec,
       sn.ipi = R(ip.imag());
       sn.wqr = wq.real();
       sn.wqi = wq.imag();
+      sn.wrh = float(wq.real());
+      sn.wrl = float(wq.real() - double(sn.wrh));
+      sn.wih = float(wq.imag());
+      sn.wil = float(wq.imag() - double(sn.wih));
       sn.acc = sl.ACC;
       auto kbuf = [&](int step) { return (step % 2 == 1) ? sl.KA : sl.KB; };
       if (jj == 1) {
@@ -347,8 +353,8 @@ hz_status run_poly(hz_problem* p, const T* dg, Buf<const T> f, int nvec,
       else if (sn.kind == hz::SK_LAST) bpp += (a.final_quad ? 2 : 3) * e;
       else if (sn.kind == hz::SK_FIRST_LAST) bpp += ((sn.yzero ? 0 : 1) + (a.final_quad ? 0 : 1)) * e;
     }
-    if (a.final_quad) bpp += sizeof(double2);
-    HZ_CUDA((hz::launch_poly_stage<T, R>(p->g, dg, f, ws, wrs, wbuf, nvec, a, st)));
+    if (a.final_quad) bpp += sizeof(double2) + (w32buf.p ? sizeof(float2) : 0);
+    HZ_CUDA((hz::launch_poly_stage<T, R>(p->g, dg, f, ws, wrs, wbuf, w32buf, nvec, a, st)));
     seq_bytes += bpp * double(n) * nvec;
   }
   seq.bytes = seq_bytes;
@@ -366,17 +372,17 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
   for (int j = 0; j < p->J; ++j) all[j] = j;
   Buf<double2> wb{p->w, n};
   if (precision != HZ_C128) {
+    // the complex64 form of the FCI internals also takes w rounded to complex64
+    const Buf<float2> w32b{precision == HZ_MIXED_C64_FCI32 ? p->w32 : nullptr, n};
     HZ_CUDA(hz::launch_convert_c128_c64(r, Buf<float2>{p->f32, n}, n, nvec, st));
     HZ_TRY((run_poly<float2, float>(p, p->d32, Buf<const float2>{p->f32, n}, nvec, all, true, wb,
-                                    nullptr, st)));
+                                    nullptr, st, w32b)));
   } else {
     HZ_TRY((run_poly<double2, double>(p, p->d64, r, nvec, all, true, wb, nullptr, st)));
   }
   if (precision == HZ_MIXED_C64_FCI32) {
     // step d and the inner GMRES on complex64 fields; w itself stays float64 for v + d w
     const long long vrs = (long long)(p->lim.inner_k_max + 1) * n;
-    HZ_CUDA(hz::launch_convert_c128_c64(Buf<const double2>{p->w, n}, Buf<float2>{p->w32, n}, n,
-                                        nvec, st));
     HZ_TIMED(p, 1, st, (stencil_bytes<float2, float2>(n, nvec)),
              (hz::launch_stencil32(p->g, p->d32, Buf<const float2>{p->w32, n},
                                                 Buf<float2>{p->Aw32, n}, nvec, 0.0, 0.0, st)));
@@ -545,7 +551,8 @@ hz_status autotune(hz_problem* p) {
           return hz::launch_poly_stage<float2, float>(p->g, p->d32,
                                                       Buf<const float2>{p->f32, n},
                                                       (float2*)p->poly, wrs,
-                                                      Buf<double2>{p->w, n}, 1, a, st);
+                                                      Buf<double2>{p->w, n},
+                                                      Buf<float2>{nullptr, 0}, 1, a, st);
         });
         if (t < best) {
           best = t;

@@ -69,6 +69,7 @@ struct StageNode {
   R z0r, z0i;
   R ipr, ipi;        // 1 / ptilde(z)
   double wqr, wqi;   // sigma_j / z_j
+  float wrh, wrl, wih, wil;  // the same split into float pairs (hi + lo) for the complex64 sum
   int kind, yzero;
   long long in, kout, acc, yout;  // element offsets of the node's fields in the rhs workspace
 };
@@ -104,9 +105,12 @@ extern std::atomic<unsigned long long> g_launches;
 
 // ---- kernel wrappers (hz_kernels.cu); each returns cudaGetLastError() after launch ----
 // dg: the operator's diagonal 6 s/h^2 - m - i a per point, in the field's precision.
+// On the final stage (a.final_quad) w receives the quadrature sum in float64 and, where w32.p
+// is not null, also its complex64 rounding.
 template <typename T, typename R>
 cudaError_t launch_poly_stage(const Geom& g, const T* dg, Buf<const T> f, T* ws, long long wrs,
-                              Buf<double2> w, int nvec, const StageArgs<R>& a, cudaStream_t st);
+                              Buf<double2> w, Buf<float2> w32, int nvec, const StageArgs<R>& a,
+                              cudaStream_t st);
 
 // Complex64 (A - zI)x from the complex64 diagonal dg, z-columns of 4 points per thread.
 cudaError_t launch_stencil32(const Geom& g, const float2* dg, Buf<const float2> x, Buf<float2> y,

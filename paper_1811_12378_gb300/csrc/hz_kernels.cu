@@ -24,9 +24,7 @@ namespace {
 
 constexpr int BX = 32;  // stencil block: 32 x 4 points of one z-plane
 constexpr int BY = 4;
-constexpr int CG_WARPS = 8;  // Gram-Schmidt block: 8 warps x 32 lanes x 4 points
-constexpr int CG_PPL = 4;
-constexpr int CG_CHUNK = CG_WARPS * 32 * CG_PPL;
+constexpr int CG_WARPS = 8;  // Gram-Schmidt block: 8 warps x 32 lanes x PPL points (PPL >= 4)
 
 template <typename T> struct Real;
 template <> struct Real<float2> { using type = float; };
@@ -137,11 +135,34 @@ template <typename T> struct RealOf;
 template <> struct RealOf<float2> { using type = float; };
 template <> struct RealOf<double2> { using type = double; };
 
+// Float pairs (hi + lo, |lo| <= half an ulp of hi) for sums that float32 alone would round
+// too coarsely.  two_sum is Knuth's error-free sum; two_prod_ff(a, bh, bl) = a * (bh + bl) with
+// the product a * bh split exactly by an FMA.  The _rn intrinsics keep the compiler from
+// contracting or reordering these steps.
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return make_float2(s, e);
+}
+
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float2 s = two_sum(a.x, b.x);
+  const float lo = __fadd_rn(s.y, __fadd_rn(a.y, b.y));
+  return two_sum(s.x, lo);
+}
+
+__device__ __forceinline__ float2 two_prod_ff(float a, float bh, float bl) {
+  const float p = __fmul_rn(a, bh);
+  const float e = __fmaf_rn(a, bh, -p);
+  return two_sum(p, __fmaf_rn(a, bl, e));
+}
+
 template <typename T, int ZC>
 __global__ void __launch_bounds__(512)
 k_poly_stage(Geom g, const T* __restrict__ dg, const T* __restrict__ f, long long frs, T* ws,
-             long long wrs, double2* __restrict__ w, long long wwrs,
-             const StageArgs<typename RealOf<T>::type> a) {
+             long long wrs, double2* __restrict__ w, long long wwrs, float2* __restrict__ w32,
+             long long w32rs, const StageArgs<typename RealOf<T>::type> a) {
   using R = typename RealOf<T>::type;
   extern __shared__ double2 qs[];  // [rows][nnodes][ZC][32] on the final stage only
   const int i = blockIdx.x * 32 + threadIdx.x;
@@ -224,24 +245,57 @@ k_poly_stage(Geom g, const T* __restrict__ dg, const T* __restrict__ f, long lon
     }
   }
   if (a.final_quad) {  // uniform over the launch; every node is LAST or FIRST_LAST here
-    double2* qr = qs + (size_t)threadIdx.z * a.nnodes * ZC * 32;
+    if constexpr (sizeof(T) == 8) {
+      // complex64 y: each node's term (sigma_j / z_j) y_j as float pairs (hi + lo) from
+      // error-free products and sums, then a float-pair sum over the nodes (about 48 bits,
+      // no float64 instruction until the final conversion)
+      float4* qf = reinterpret_cast<float4*>(qs) + (size_t)threadIdx.z * a.nnodes * ZC * 32;
 #pragma unroll
-    for (int t = 0; t < ZC; ++t) {
-      const double yr = double(yn[t].x), yi = double(yn[t].y);
-      qr[(q * ZC + t) * 32 + threadIdx.x] =
-          make_double2(nd.wqr * yr - nd.wqi * yi, nd.wqr * yi + nd.wqi * yr);
-    }
-    __syncthreads();
-    if (inside) {
-      for (int t = q; t < ZC; t += a.nnodes) {  // warp q sums column points q, q + nnodes, ...
-        if (k0 + t >= g.nz) break;
-        double sx = 0.0, sy = 0.0;
-        for (int u = 0; u < a.nnodes; ++u) {
-          const double2 v = qr[(u * ZC + t) * 32 + threadIdx.x];
-          sx += v.x;
-          sy += v.y;
+      for (int t = 0; t < ZC; ++t) {
+        const float yr = yn[t].x, yi = yn[t].y;
+        float2 tx = two_prod_ff(yr, nd.wrh, nd.wrl), tx2 = two_prod_ff(yi, nd.wih, nd.wil);
+        float2 ty = two_prod_ff(yi, nd.wrh, nd.wrl), ty2 = two_prod_ff(yr, nd.wih, nd.wil);
+        tx = ff_add(tx, make_float2(-tx2.x, -tx2.y));
+        ty = ff_add(ty, ty2);
+        qf[(q * ZC + t) * 32 + threadIdx.x] = make_float4(tx.x, tx.y, ty.x, ty.y);
+      }
+      __syncthreads();
+      if (inside) {
+        for (int t = q; t < ZC; t += a.nnodes) {  // warp q sums column points q, q + nnodes, ...
+          if (k0 + t >= g.nz) break;
+          float2 sx = make_float2(0.f, 0.f), sy = make_float2(0.f, 0.f);
+          for (int u = 0; u < a.nnodes; ++u) {
+            const float4 v = qf[(u * ZC + t) * 32 + threadIdx.x];
+            sx = ff_add(sx, make_float2(v.x, v.y));
+            sy = ff_add(sy, make_float2(v.z, v.w));
+          }
+          const long long pp = p0 + sxy * t;
+          w[r * wwrs + pp] = make_double2(double(sx.x) + double(sx.y), double(sy.x) + double(sy.y));
+          if (w32) w32[r * w32rs + pp] = make_float2(__fadd_rn(sx.x, sx.y), __fadd_rn(sy.x, sy.y));
         }
-        w[r * wwrs + p0 + sxy * t] = make_double2(sx, sy);
+      }
+    } else {
+      double2* qr = qs + (size_t)threadIdx.z * a.nnodes * ZC * 32;
+#pragma unroll
+      for (int t = 0; t < ZC; ++t) {
+        const double yr = double(yn[t].x), yi = double(yn[t].y);
+        qr[(q * ZC + t) * 32 + threadIdx.x] =
+            make_double2(nd.wqr * yr - nd.wqi * yi, nd.wqr * yi + nd.wqi * yr);
+      }
+      __syncthreads();
+      if (inside) {
+        for (int t = q; t < ZC; t += a.nnodes) {  // warp q sums column points q, q + nnodes, ...
+          if (k0 + t >= g.nz) break;
+          double sx = 0.0, sy = 0.0;
+          for (int u = 0; u < a.nnodes; ++u) {
+            const double2 v = qr[(u * ZC + t) * 32 + threadIdx.x];
+            sx += v.x;
+            sy += v.y;
+          }
+          w[r * wwrs + p0 + sxy * t] = make_double2(sx, sy);
+          if (w32)
+            w32[r * w32rs + p0 + sxy * t] = make_float2(float(sx), float(sy));
+        }
       }
     }
   }
@@ -301,12 +355,12 @@ __device__ __forceinline__ double2 warp_reduce8(double2 (&a)[8], int lane) {
   return make_double2(x, y);
 }
 
-// Classical Gram-Schmidt pieces in float64.  A block of CG_WARPS warps owns CG_CHUNK points;
-// lane l of warp w owns the CG_PPL points seg + l + 32 e, kept in registers, so every basis
+// Classical Gram-Schmidt pieces in float64.  A block of CG_WARPS warps owns 256 PPL points;
+// lane l of warp w owns the PPL points seg + l + 32 e, kept in registers, so every basis
 // field is read with coalesced 512-byte warp loads.  Dots are formed 8 basis fields at a time
 // and reduced by warp_reduce8; per-warp sums go through shared memory to one partial per
 // block, and the last block adds the partials in block order (warp per slot).
-template <int MODE>
+template <int MODE, int PPL>
 __global__ void __launch_bounds__(CG_WARPS * 32)
 k_cgs(const double2* __restrict__ V, long long vis, long long vrs, int nb, double2* w,
       long long wrs, long long n, GmresDev gs, double2* partial, unsigned* counters, double brk) {
@@ -316,7 +370,8 @@ k_cgs(const double2* __restrict__ V, long long vis, long long vrs, int nb, doubl
   const int M = gs.mmax;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ldw = nb + 8;
-  const long long seg = (long long)blockIdx.x * CG_CHUNK + (long long)warp * 32 * CG_PPL + lane;
+  const long long seg =
+      (long long)blockIdx.x * (CG_WARPS * 32 * PPL) + (long long)warp * 32 * PPL + lane;
   double2* wr = w + r * wrs;
   const double2* Vr = V + r * vrs;
   double2* hs = sm;
@@ -326,9 +381,9 @@ k_cgs(const double2* __restrict__ V, long long vis, long long vrs, int nb, doubl
     for (int b = threadIdx.x; b < nb; b += blockDim.x) hs[b] = hp[b];
     __syncthreads();
   }
-  double2 wv[CG_PPL];
+  double2 wv[PPL];
 #pragma unroll
-  for (int e = 0; e < CG_PPL; ++e) {
+  for (int e = 0; e < PPL; ++e) {
     const long long p = seg + 32LL * e;
     wv[e] = p < n ? wr[p] : make_double2(0.0, 0.0);
   }
@@ -337,7 +392,7 @@ k_cgs(const double2* __restrict__ V, long long vis, long long vrs, int nb, doubl
       const double2 h = hs[b];
       const double2* vb = Vr + b * vis;
 #pragma unroll
-      for (int e = 0; e < CG_PPL; ++e) {
+      for (int e = 0; e < PPL; ++e) {
         const long long p = seg + 32LL * e;
         if (p < n) {
           const double2 v = vb[p];
@@ -347,7 +402,7 @@ k_cgs(const double2* __restrict__ V, long long vis, long long vrs, int nb, doubl
       }
     }
 #pragma unroll
-    for (int e = 0; e < CG_PPL; ++e) {
+    for (int e = 0; e < PPL; ++e) {
       const long long p = seg + 32LL * e;
       if (p < n) wr[p] = wv[e];
     }
@@ -362,7 +417,7 @@ k_cgs(const double2* __restrict__ V, long long vis, long long vrs, int nb, doubl
         if (b0 + t < nb) {
           const double2* vb = Vr + (b0 + t) * vis;
 #pragma unroll
-          for (int e = 0; e < CG_PPL; ++e) {
+          for (int e = 0; e < PPL; ++e) {
             const long long p = seg + 32LL * e;
             if (p < n) {
               const double2 v = vb[p];
@@ -382,7 +437,7 @@ k_cgs(const double2* __restrict__ V, long long vis, long long vrs, int nb, doubl
   if (MODE != 1) {
     double q = 0.0;
 #pragma unroll
-    for (int e = 0; e < CG_PPL; ++e) q = fma(wv[e].x, wv[e].x, fma(wv[e].y, wv[e].y, q));
+    for (int e = 0; e < PPL; ++e) q = fma(wv[e].x, wv[e].x, fma(wv[e].y, wv[e].y, q));
     for (int o = 16; o > 0; o >>= 1) q += __shfl_down_sync(0xffffffffu, q, o);
     if (lane == 0) wp[warp * ldw + (MODE == 0 ? nb : 0)] = make_double2(q, 0.0);
   }
@@ -643,7 +698,8 @@ inline unsigned ew_blocks(long long n) {
 // ---------------------------------------------------------------- wrappers
 template <typename T, typename R>
 cudaError_t launch_poly_stage(const Geom& g, const T* dg, Buf<const T> f, T* ws, long long wrs,
-                              Buf<double2> w, int nvec, const StageArgs<R>& a, cudaStream_t st) {
+                              Buf<double2> w, Buf<float2> w32, int nvec, const StageArgs<R>& a,
+                              cudaStream_t st) {
   const int cls = stage_class(a.nnodes);
   int zc = g.pzc[cls];
   if (sizeof(T) == 16 && zc > 2) zc = 2;  // float64 columns: register budget
@@ -654,25 +710,29 @@ cudaError_t launch_poly_stage(const Geom& g, const T* dg, Buf<const T> f, T* ws,
   count_launch();
   switch (zc) {
     case 1:
-      k_poly_stage<T, 1><<<grd, blk, smem, st>>>(g, dg, f.p, f.rs, ws, wrs, w.p, w.rs, a);
+      k_poly_stage<T, 1><<<grd, blk, smem, st>>>(g, dg, f.p, f.rs, ws, wrs, w.p, w.rs, w32.p,
+                                                 w32.rs, a);
       break;
     case 2:
-      k_poly_stage<T, 2><<<grd, blk, smem, st>>>(g, dg, f.p, f.rs, ws, wrs, w.p, w.rs, a);
+      k_poly_stage<T, 2><<<grd, blk, smem, st>>>(g, dg, f.p, f.rs, ws, wrs, w.p, w.rs, w32.p,
+                                                 w32.rs, a);
       break;
     default:
       if constexpr (sizeof(T) == 8)
-        k_poly_stage<T, 4><<<grd, blk, smem, st>>>(g, dg, f.p, f.rs, ws, wrs, w.p, w.rs, a);
+        k_poly_stage<T, 4><<<grd, blk, smem, st>>>(g, dg, f.p, f.rs, ws, wrs, w.p, w.rs, w32.p,
+                                                   w32.rs, a);
       break;
   }
   return cudaGetLastError();
 }
 
 template cudaError_t launch_poly_stage<float2, float>(const Geom&, const float2*, Buf<const float2>,
-                                                      float2*, long long, Buf<double2>, int,
-                                                      const StageArgs<float>&, cudaStream_t);
+                                                      float2*, long long, Buf<double2>,
+                                                      Buf<float2>, int, const StageArgs<float>&,
+                                                      cudaStream_t);
 template cudaError_t launch_poly_stage<double2, double>(const Geom&, const double2*,
                                                         Buf<const double2>, double2*, long long,
-                                                        Buf<double2>, int,
+                                                        Buf<double2>, Buf<float2>, int,
                                                         const StageArgs<double>&, cudaStream_t);
 
 cudaError_t launch_convert_c128_c64(Buf<const double2> x, Buf<float2> y, long long n, int nvec,
@@ -689,21 +749,65 @@ cudaError_t launch_convert_c64_c128(Buf<const float2> x, Buf<double2> y, long lo
   return cudaGetLastError();
 }
 
+// Points per lane of the float64 Gram-Schmidt kernels.  They are bound by the float64 pipe,
+// which the blocks resident on an SM share, so the time is set by the SM with the most work:
+// ceil(blocks * nvec / SMs) * PPL.  The smallest such PPL wins (ties: the smaller PPL).
+int cgs_ppl(long long n, int nvec) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  static const int cand[] = {4, 5, 6, 7, 8};
+  int best = 4;
+  long long best_cost = -1;
+  for (int ppl : cand) {
+    const long long blocks = (n + CG_WARPS * 32LL * ppl - 1) / (CG_WARPS * 32LL * ppl);
+    const long long cost = (blocks * nvec + sms - 1) / sms * ppl;
+    if (best_cost < 0 || cost < best_cost) {
+      best = ppl;
+      best_cost = cost;
+    }
+  }
+  return best;
+}
+
+template <int MODE, int PPL>
+void launch_cgs_ppl(const double2* V, long long vis, long long vrs, int nb, Buf<double2> w,
+                    long long n, const GmresDev& gs, double2* partial, unsigned* counters,
+                    int nvec, double breakdown, cudaStream_t st) {
+  const long long chunk = CG_WARPS * 32LL * PPL;
+  dim3 grd(unsigned((n + chunk - 1) / chunk), nvec);
+  const size_t smem = sizeof(double2) * (size_t)(nb + CG_WARPS * (nb + 8));
+  k_cgs<MODE, PPL><<<grd, CG_WARPS * 32, smem, st>>>(V, vis, vrs, nb, w.p, w.rs, n, gs, partial,
+                                                     counters, breakdown);
+}
+
+template <int MODE>
+void launch_cgs_mode(int ppl, const double2* V, long long vis, long long vrs, int nb,
+                     Buf<double2> w, long long n, const GmresDev& gs, double2* partial,
+                     unsigned* counters, int nvec, double breakdown, cudaStream_t st) {
+  switch (ppl) {
+    case 5: launch_cgs_ppl<MODE, 5>(V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st); break;
+    case 6: launch_cgs_ppl<MODE, 6>(V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st); break;
+    case 7: launch_cgs_ppl<MODE, 7>(V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st); break;
+    case 8: launch_cgs_ppl<MODE, 8>(V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st); break;
+    default: launch_cgs_ppl<MODE, 4>(V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st); break;
+  }
+}
+
 cudaError_t launch_cgs(int mode, const double2* V, long long vis, long long vrs, int nb,
                        Buf<double2> w, long long n, const GmresDev& gs, double2* partial,
                        unsigned* counters, int nvec, double breakdown, cudaStream_t st) {
-  dim3 grd(unsigned((n + CG_CHUNK - 1) / CG_CHUNK), nvec);
-  const size_t smem = sizeof(double2) * (size_t)(nb + CG_WARPS * (nb + 8));
+  const int ppl = cgs_ppl(n, nvec);
   count_launch();
   if (mode == 0)
-    k_cgs<0><<<grd, CG_WARPS * 32, smem, st>>>(V, vis, vrs, nb, w.p, w.rs, n, gs, partial,
-                                               counters, breakdown);
+    launch_cgs_mode<0>(ppl, V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st);
   else if (mode == 1)
-    k_cgs<1><<<grd, CG_WARPS * 32, smem, st>>>(V, vis, vrs, nb, w.p, w.rs, n, gs, partial,
-                                               counters, breakdown);
+    launch_cgs_mode<1>(ppl, V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st);
   else
-    k_cgs<2><<<grd, CG_WARPS * 32, smem, st>>>(V, vis, vrs, nb, w.p, w.rs, n, gs, partial,
-                                               counters, breakdown);
+    launch_cgs_mode<2>(ppl, V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st);
   return cudaGetLastError();
 }
 
