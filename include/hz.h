@@ -59,11 +59,17 @@ typedef enum {
   HZ_MIXED_C64 = 1,   /* polynomial sweeps in complex64; quadrature sum (float-pair
                          accumulation, about 48 bits, returned as float64), step d, inner and
                          outer Arnoldi, Givens and true residual in float64 */
-  HZ_MIXED_C64_FCI32 = 2  /* the whole FCI preconditioner in complex64 (sweeps, step d, inner
+  HZ_MIXED_C64_FCI32 = 2, /* the whole FCI preconditioner in complex64 (sweeps, step d, inner
                          GMRES), except its quadrature sum, accumulated as in HZ_MIXED_C64; the outer
                          FGMRES (CGS2 Arnoldi, Givens, updates) and the true residual in
                          float64.  FGMRES admits a variable preconditioner, so the solution
                          still reaches the float64 residual target. */
+  HZ_MIXED_C64_FF = 3  /* as HZ_MIXED_C64_FCI32, with the outer Arnoldi basis and its CGS2
+                         passes in float pairs (two float32 per value, about 48 significant
+                         bits, error-free float32 products and two-sum additions) instead of
+                         float64; Hessenberg, Givens, the solution update and the true
+                         residual stay float64.  Only hz_solve / hz_solve_batched distinguish
+                         it; hz_fci treats it as HZ_MIXED_C64_FCI32. */
 } hz_precision;
 
 /* Grid and medium.  Interior points nx*ny*nz with spacing h; omega the angular frequency;

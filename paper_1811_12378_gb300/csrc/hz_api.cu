@@ -365,22 +365,28 @@ hz_status run_poly(hz_problem* p, const T* dg, Buf<const T> f, int nvec,
 }
 
 // FCI (Algorithm 1) on nvec double-complex fields r -> out.
+// r_ff: r holds float pairs (the outer basis of HZ_MIXED_C64_FF); otherwise complex128.
 hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nvec, int kin,
-                  int precision, cudaStream_t st) {
+                  int precision, cudaStream_t st, bool r_ff = false) {
   const long long n = p->g.n;
+  const bool fci32 = precision == HZ_MIXED_C64_FCI32 || precision == HZ_MIXED_C64_FF;
   std::vector<int> all(p->J);
   for (int j = 0; j < p->J; ++j) all[j] = j;
   Buf<double2> wb{p->w, n};
   if (precision != HZ_C128) {
     // the complex64 form of the FCI internals also takes w rounded to complex64
-    const Buf<float2> w32b{precision == HZ_MIXED_C64_FCI32 ? p->w32 : nullptr, n};
-    HZ_CUDA(hz::launch_convert_c128_c64(r, Buf<float2>{p->f32, n}, n, nvec, st));
+    const Buf<float2> w32b{fci32 ? p->w32 : nullptr, n};
+    if (r_ff)
+      HZ_CUDA(hz::launch_convert_ff_c64(Buf<const float4>{(const float4*)r.p, r.rs},
+                                        Buf<float2>{p->f32, n}, n, nvec, st));
+    else
+      HZ_CUDA(hz::launch_convert_c128_c64(r, Buf<float2>{p->f32, n}, n, nvec, st));
     HZ_TRY((run_poly<float2, float>(p, p->d32, Buf<const float2>{p->f32, n}, nvec, all, true, wb,
                                     nullptr, st, w32b)));
   } else {
     HZ_TRY((run_poly<double2, double>(p, p->d64, r, nvec, all, true, wb, nullptr, st)));
   }
-  if (precision == HZ_MIXED_C64_FCI32) {
+  if (fci32) {
     // step d and the inner GMRES on complex64 fields; w itself stays float64 for v + d w
     const long long vrs = (long long)(p->lim.inner_k_max + 1) * n;
     HZ_TIMED(p, 1, st, (stencil_bytes<float2, float2>(n, nvec)),
@@ -404,7 +410,7 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
                                   p->counters, nvec, kBreakdown, st));
       HZ_CUDA(hz::launch_scale32(wj, Buf<const float2>{wj.p, vrs}, n, p->gin, nvec, st));
     }
-    HZ_CUDA(hz::launch_backsolve(p->gin, nvec, st));
+    HZ_CUDA(hz::launch_backsolve32(p->gin, nvec, st));
     HZ_CUDA(hz::launch_combine_fci32(out, p->Vin32, n, vrs, p->gin, Buf<const double2>{p->w, n},
                                      n, nvec, st));
     return HZ_OK;
@@ -447,7 +453,21 @@ hz_status outer_step_launches(hz_problem* p, int k, int nrhs, int K, int precisi
   GmresDev& go = p->gout;
   Buf<const double2> vk{p->V + (long long)k * n, vrs};
   Buf<double2> zk{p->Z + (long long)k * n, zrs};
-  HZ_TRY(run_fci(p, vk, zk, nrhs, K, precision, st));
+  const bool ff = precision == HZ_MIXED_C64_FF;
+  HZ_TRY(run_fci(p, vk, zk, nrhs, K, precision, st, ff));
+  if (ff) {
+    // the float-pair Arnoldi: w = A z_k stored as float pairs in v_{k+1}'s slot
+    Buf<float4> wf{(float4*)(p->V + (long long)(k + 1) * n), vrs};
+    HZ_TIMED(p, 1, st, 16.0 * 3 * n * nrhs,
+             (hz::launch_stencil_diag_ff(p->g, p->d64, Buf<const double2>{zk.p, zrs}, wf, nrhs,
+                                         st)));
+    for (int mode = 0; mode < 3; ++mode)
+      HZ_TIMED(p, 2, st, cgs_bytes(mode, n, k + 1, nrhs),
+               hz::launch_cgs_ff(mode, (const float4*)p->V, n, vrs, k + 1, wf, n, go, p->partial,
+                                 p->counters, nrhs, kBreakdown, st));
+    HZ_CUDA(hz::launch_scale_ff(wf, n, go, nrhs, st));
+    return HZ_OK;
+  }
   Buf<double2> wk{p->V + (long long)(k + 1) * n, vrs};
   HZ_TIMED(p, 1, st, (stencil_bytes<double2, double2>(n, nrhs)),
            (hz::launch_stencil_diag(p->g, p->d64, Buf<const double2>{zk.p, zrs}, wk, nrhs, 0.0,
@@ -637,7 +657,7 @@ hz_status check_solve_args(const hz_problem* p, int nrhs, const hz_solve_opts* o
   if (opts->max_cycles < 0 || opts->fixed_its < 0 || !(opts->rtol >= 0))
     return fail(HZ_ERR_INVALID, "invalid max_cycles / fixed_its / rtol");
   if (opts->precision != HZ_C128 && opts->precision != HZ_MIXED_C64 &&
-      opts->precision != HZ_MIXED_C64_FCI32)
+      opts->precision != HZ_MIXED_C64_FCI32 && opts->precision != HZ_MIXED_C64_FF)
     return fail(HZ_ERR_INVALID, "unknown precision");
   return HZ_OK;
 }
@@ -738,7 +758,7 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   if ((s = dalloc(p, (void**)&p->V, sizeof(double2) * (size_t)n * (M + 1) * R)) != HZ_OK)
     return bail(s);
   if ((s = dalloc(p, (void**)&p->Z, sizeof(double2) * (size_t)n * M * R)) != HZ_OK) return bail(s);
-  const long long nblk = (n + hz::RED_CHUNK - 1) / hz::RED_CHUNK;
+  const long long nblk = (n + hz::RED_MIN_CHUNK - 1) / hz::RED_MIN_CHUNK;
   const int slots = std::max(M, K) + 2;
   if ((s = dalloc(p, (void**)&p->partial, sizeof(double2) * (size_t)nblk * slots * R)) != HZ_OK)
     return bail(s);
@@ -780,6 +800,7 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
     return cuda_fail(e, "stream/event creation");
   }
   e = hz::prepare_kernels(std::max(M, K));
+  if (e == cudaSuccess) e = hz::prepare_kernels32(std::max(K, 1));
   if (e != cudaSuccess) {
     delete p;
     return cuda_fail(e, "kernel attributes");
@@ -1038,7 +1059,8 @@ hz_status hz_fci(hz_problem* p, const void* r, void* out, int nvec, int inner_k,
   if (nvec < 0 || nvec > p->lim.nrhs_max) return fail(HZ_ERR_INVALID, "nvec out of range");
   if (inner_k < 0 || inner_k > p->lim.inner_k_max)
     return fail(HZ_ERR_INVALID, "inner_k out of range");
-  if (precision != HZ_C128 && precision != HZ_MIXED_C64 && precision != HZ_MIXED_C64_FCI32)
+  if (precision != HZ_C128 && precision != HZ_MIXED_C64 && precision != HZ_MIXED_C64_FCI32 &&
+      precision != HZ_MIXED_C64_FF)
     return fail(HZ_ERR_INVALID, "unknown precision");
   if (nvec == 0) return HZ_OK;
   if (!r || !out) return fail(HZ_ERR_INVALID, "null field");
@@ -1156,8 +1178,12 @@ struct SolveState {
                                       Buf<double2>{p->V, vrs}, go, p->partial, p->counters, nrhs,
                                       st));
     for (int r = 0; r < nrhs; ++r) mvs[r] += cycle == 0 ? 0 : 1;
-    HZ_CUDA(hz::launch_scale(Buf<double2>{p->V, vrs}, Buf<const double2>{p->V, vrs}, n, go, nrhs,
-                             st));
+    if (o->precision == HZ_MIXED_C64_FF)
+      HZ_CUDA(hz::launch_scale_ff_from64(Buf<float4>{(float4*)p->V, vrs},
+                                         Buf<const double2>{p->V, vrs}, n, go, nrhs, st));
+    else
+      HZ_CUDA(hz::launch_scale(Buf<double2>{p->V, vrs}, Buf<const double2>{p->V, vrs}, n, go,
+                               nrhs, st));
     return enqueue_flags();
   }
 

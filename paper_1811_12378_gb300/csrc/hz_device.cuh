@@ -24,6 +24,97 @@ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
   return mk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
 
+// ---------------------------------------------------------------- float pairs
+// Float pairs (hi + lo, |lo| <= half an ulp of hi) for sums that float32 alone would round
+// too coarsely.  two_sum is Knuth's error-free sum; two_prod_ff(a, bh, bl) = a * (bh + bl) with
+// the product a * bh split exactly by an FMA.  The _rn intrinsics keep the compiler from
+// contracting or reordering these steps.
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return make_float2(s, e);
+}
+
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float2 s = two_sum(a.x, b.x);
+  const float lo = __fadd_rn(s.y, __fadd_rn(a.y, b.y));
+  return two_sum(s.x, lo);
+}
+
+__device__ __forceinline__ float2 two_prod_ff(float a, float bh, float bl) {
+  const float p = __fmul_rn(a, bh);
+  const float e = __fmaf_rn(a, bh, -p);
+  return two_sum(p, __fmaf_rn(a, bl, e));
+}
+
+// (hi, lo) -> the same value with |lo| <= half an ulp of hi, given |a| >= |b| (Dekker).
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+// acc += a * b for float pairs, with acc.lo left unnormalised (it gathers the rounding errors
+// of a few terms; ff_norm restores the pair): 1 multiply, 3 FMA, 1 two_sum, 2 adds.
+__device__ __forceinline__ void ff_acc_mul(float2& acc, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float2 s = two_sum(acc.x, p);
+  acc.x = s.x;
+  acc.y = __fadd_rn(acc.y, __fadd_rn(s.y, e));
+}
+
+__device__ __forceinline__ float2 ff_norm(float2 a) { return two_sum(a.x, a.y); }
+
+// float64 -> float pair (two float64-pipe conversions and one subtraction) and back.
+__device__ __forceinline__ float2 ff_from_d(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - double(h)));
+}
+__device__ __forceinline__ double d_from_ff(float2 a) { return double(a.x) + double(a.y); }
+
+// Complex float pairs: float4 (re.hi, re.lo, im.hi, im.lo).
+__device__ __forceinline__ float4 ffc_add(float4 a, float4 b) {
+  const float2 re = ff_add(make_float2(a.x, a.y), make_float2(b.x, b.y));
+  const float2 im = ff_add(make_float2(a.z, a.w), make_float2(b.z, b.w));
+  return make_float4(re.x, re.y, im.x, im.y);
+}
+__device__ __forceinline__ float4 ffc_of(float2 v) { return make_float4(v.x, 0.f, v.y, 0.f); }
+__device__ __forceinline__ float4 shfl_xor4(float4 v, int m) {
+  return make_float4(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m),
+                     __shfl_xor_sync(0xffffffffu, v.z, m), __shfl_xor_sync(0xffffffffu, v.w, m));
+}
+__device__ __forceinline__ double2 d_from_ffc(float4 v) {
+  return make_double2(d_from_ff(make_float2(v.x, v.y)), d_from_ff(make_float2(v.z, v.w)));
+}
+__device__ __forceinline__ float2 f_from_ffc(float4 v) {
+  return make_float2(__fadd_rn(v.x, v.y), __fadd_rn(v.z, v.w));
+}
+
+// In the last block, one warp: the float-pair sum over the G block partials of slot sidx
+// (part[sidx][b], float4), valid in every lane.  Float32 instructions only (on GB300 a
+// float64 instruction issues at 1/64 of the float32 rate, which made float64 partial sums the
+// longest part of the small reduction kernels); eight loads per lane in flight; fixed order.
+__device__ __forceinline__ float4 warp_sum_partials_ff(const float4* part, int sidx, int G,
+                                                       int lane) {
+  const float4* ps = part + (long long)sidx * G;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int b0 = 0; b0 < G; b0 += 32 * 8) {
+    float4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int b = b0 + u * 32 + lane;
+      v[u] = b < G ? __ldcg(ps + b) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc = ffc_add(acc, v[u]);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc = ffc_add(acc, shfl_xor4(acc, o));
+  return acc;
+}
+
 // ---------------------------------------------------------------- reductions
 // Sum of v over the block; the result is valid in thread 0.  sh holds >= 32 entries.
 __device__ __forceinline__ double2 block_sum(double2 v, double2* sh) {
@@ -61,14 +152,51 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
 __device__ void finish_slots(const double2* part, int nslots, double2* out, double2* sh) {
   for (int s = 0; s < nslots; ++s) {
     double2 acc = make_double2(0.0, 0.0);
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-      double2 v = __ldcg(part + (long long)s * gridDim.x + b);
-      acc.x += v.x;
-      acc.y += v.y;
+    for (int b0 = 0; b0 < (int)gridDim.x; b0 += 4 * blockDim.x) {
+      double2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int b = b0 + u * blockDim.x + threadIdx.x;
+        v[u] = b < (int)gridDim.x ? __ldcg(part + (long long)s * gridDim.x + b)
+                                  : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        acc.x += v[u].x;
+        acc.y += v[u].y;
+      }
     }
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) out[s] = acc;
   }
+}
+
+// In the last block, one warp: the sum over the G block partials of slot sidx (part[sidx][b]),
+// valid in lane 0.  Eight independent loads per lane are in flight at a time (a dependent
+// chain of L2 round trips here would be the longest part of a small reduction kernel); the
+// order of the additions is fixed, so results are bit-reproducible.
+__device__ __forceinline__ double2 warp_sum_partials(const double2* part, int sidx, int G,
+                                                     int lane) {
+  const double2* ps = part + (long long)sidx * G;
+  double ax = 0.0, ay = 0.0;
+  for (int b0 = 0; b0 < G; b0 += 32 * 8) {
+    double2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int b = b0 + u * 32 + lane;
+      v[u] = b < G ? __ldcg(ps + b) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      ax += v[u].x;
+      ay += v[u].y;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ax += __shfl_down_sync(0xffffffffu, ax, o);
+    ay += __shfl_down_sync(0xffffffffu, ay, o);
+  }
+  return make_double2(ax, ay);
 }
 
 // Givens step for column k of rhs r (Saad's GMRES with complex rotations), called by every

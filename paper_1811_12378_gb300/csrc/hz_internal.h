@@ -16,6 +16,8 @@ constexpr int MAXJ = 16;          // contour nodes per problem
 constexpr int RED_THREADS = 256;  // threads of a reduction block
 constexpr int RED_PPT = 4;        // points per thread in a reduction block
 constexpr int RED_CHUNK = RED_THREADS * RED_PPT;
+constexpr int RED_MIN_CHUNK = 256;  // smallest points per block of any reduction kernel
+                                    // (sizes the per-block partial sums)
 
 // Grid geometry and the scalars of the normalised operator (A = s L_h - diag(m) - i diag(a)).
 struct Geom {
@@ -145,8 +147,26 @@ cudaError_t launch_combine(Buf<double2> out, const double2* B, long long bis, lo
 // y = R^{-1} g over kend[r] columns (one block per rhs)
 cudaError_t launch_backsolve(const GmresDev& gs, int nvec, cudaStream_t st);
 
+// ---- float-pair outer Arnoldi of HZ_MIXED_C64_FF (hz_kernels_ff.cu); a complex element is a
+// float4 (re.hi, re.lo, im.hi, im.lo) in storage of the double2 layout ----
+cudaError_t launch_stencil_diag_ff(const Geom& g, const double2* dg, Buf<const double2> x,
+                                   Buf<float4> y, int nvec, cudaStream_t st);
+cudaError_t launch_cgs_ff(int mode, const float4* V, long long vis, long long vrs, int nb,
+                          Buf<float4> w, long long n, const GmresDev& gs, double2* partial,
+                          unsigned* counters, int nvec, double breakdown, cudaStream_t st);
+cudaError_t launch_scale_ff(Buf<float4> v, long long n, const GmresDev& gs, int nvec,
+                            cudaStream_t st);
+cudaError_t launch_scale_ff_from64(Buf<float4> dst, Buf<const double2> src, long long n,
+                                   const GmresDev& gs, int nvec, cudaStream_t st);
+cudaError_t launch_convert_ff_c64(Buf<const float4> x, Buf<float2> y, long long n, int nvec,
+                                  cudaStream_t st);
+
 // One-time kernel attributes for restart lengths up to mmax (shared memory of k_backsolve).
 cudaError_t prepare_kernels(int mmax);
+// The same for the float32 triangular solve of the complex64 FCI form (inner lengths).
+cudaError_t prepare_kernels32(int mmax);
+// y = R^{-1} g in float32 for the complex64 FCI form's inner GMRES (GmresDev storage float64).
+cudaError_t launch_backsolve32(const GmresDev& gs, int nvec, cudaStream_t st);
 
 // Starting vector of a cycle.  v0[r] = f[r] - fscale*A x[r] (x may be null = 0; A applied
 // in float64), then ||v0||^2 -> beta, inv, g[0] = beta, kend = 0, stopped = (beta == 0).

@@ -135,29 +135,6 @@ template <typename T> struct RealOf;
 template <> struct RealOf<float2> { using type = float; };
 template <> struct RealOf<double2> { using type = double; };
 
-// Float pairs (hi + lo, |lo| <= half an ulp of hi) for sums that float32 alone would round
-// too coarsely.  two_sum is Knuth's error-free sum; two_prod_ff(a, bh, bl) = a * (bh + bl) with
-// the product a * bh split exactly by an FMA.  The _rn intrinsics keep the compiler from
-// contracting or reordering these steps.
-__device__ __forceinline__ float2 two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return make_float2(s, e);
-}
-
-__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
-  const float2 s = two_sum(a.x, b.x);
-  const float lo = __fadd_rn(s.y, __fadd_rn(a.y, b.y));
-  return two_sum(s.x, lo);
-}
-
-__device__ __forceinline__ float2 two_prod_ff(float a, float bh, float bl) {
-  const float p = __fmul_rn(a, bh);
-  const float e = __fmaf_rn(a, bh, -p);
-  return two_sum(p, __fmaf_rn(a, bl, e));
-}
-
 template <typename T, int ZC>
 __global__ void __launch_bounds__(512)
 k_poly_stage(Geom g, const T* __restrict__ dg, const T* __restrict__ f, long long frs, T* ws,
@@ -453,17 +430,8 @@ k_cgs(const double2* __restrict__ V, long long vis, long long vrs, int nb, doubl
   double2* out = MODE == 0 ? gs.h1 + (long long)r * (M + 2)
                : MODE == 1 ? gs.h2 + (long long)r * (M + 2) : gs.nrm + 2 * r;
   for (int sidx = warp; sidx < nslots; sidx += CG_WARPS) {
-    double ax = 0.0, ay = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) {
-      const double2 v = __ldcg(part + (long long)sidx * gridDim.x + b);
-      ax += v.x;
-      ay += v.y;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      ax += __shfl_down_sync(0xffffffffu, ax, o);
-      ay += __shfl_down_sync(0xffffffffu, ay, o);
-    }
-    if (lane == 0) out[sidx] = make_double2(ax, ay);
+    const double2 t = warp_sum_partials(part, sidx, (int)gridDim.x, lane);
+    if (lane == 0) out[sidx] = t;
   }
   __syncthreads();
   if (threadIdx.x == 0) counters[r] = 0;
@@ -473,6 +441,9 @@ k_cgs(const double2* __restrict__ V, long long vis, long long vrs, int nb, doubl
 // Float64 shifted stencil from the precomputed complex diagonal d = 6 s/h^2 - m - i a:
 //     (A - zI) x = (d - z) x - (s/h^2) * (sum of the 6 neighbours).
 // About 16 float64 operations a point (the float64 pipe is the scarce unit on GB300).
+// FF: the result is stored as float pairs (float4 per complex point) for the float-pair
+// Arnoldi of HZ_MIXED_C64_FF.
+template <bool FF>
 __global__ void __launch_bounds__(BX * BY)
 k_stencil_diag(Geom g, const double2* __restrict__ dg, const double2* __restrict__ x,
                long long xrs, double2* __restrict__ y, long long yrs, double zr, double zi) {
@@ -494,8 +465,14 @@ k_stencil_diag(Geom g, const double2* __restrict__ dg, const double2* __restrict
   const double nby = ((xm.y + xp.y) + (ym.y + yp.y)) + (zm.y + zp.y);
   const double dr = d.x - zr, di = d.y - zi;
   const double mcs = -g.cs;
-  y[r * yrs + p] = make_double2(fma(dr, xc.x, fma(-di, xc.y, mcs * nbx)),
-                                fma(dr, xc.y, fma(di, xc.x, mcs * nby)));
+  const double yx = fma(dr, xc.x, fma(-di, xc.y, mcs * nbx));
+  const double yy = fma(dr, xc.y, fma(di, xc.x, mcs * nby));
+  if constexpr (FF) {
+    const float2 a = ff_from_d(yx), b = ff_from_d(yy);
+    reinterpret_cast<float4*>(y)[r * yrs + p] = make_float4(a.x, a.y, b.x, b.y);
+  } else {
+    y[r * yrs + p] = make_double2(yx, yy);
+  }
 }
 
 __global__ void k_scale(double2* __restrict__ dst, long long drs, const double2* __restrict__ src,
@@ -836,7 +813,17 @@ cudaError_t launch_stencil_diag(const Geom& g, const double2* dg, Buf<const doub
   dim3 blk(BX, BY, 1);
   dim3 grd((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz * nvec);
   count_launch();
-  k_stencil_diag<<<grd, blk, 0, st>>>(g, dg, x.p, x.rs, y.p, y.rs, zr, zi);
+  k_stencil_diag<false><<<grd, blk, 0, st>>>(g, dg, x.p, x.rs, y.p, y.rs, zr, zi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil_diag_ff(const Geom& g, const double2* dg, Buf<const double2> x,
+                                   Buf<float4> y, int nvec, cudaStream_t st) {
+  dim3 blk(BX, BY, 1);
+  dim3 grd((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz * nvec);
+  count_launch();
+  k_stencil_diag<true><<<grd, blk, 0, st>>>(g, dg, x.p, x.rs, reinterpret_cast<double2*>(y.p),
+                                            y.rs, 0.0, 0.0);
   return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@ from . import build as _build
 HZ_C128 = 0
 HZ_MIXED_C64 = 1
 HZ_MIXED_C64_FCI32 = 2
+HZ_MIXED_C64_FF = 3
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory",
           4: "not converged", 5: "breakdown", 6: "diverged", 7: "set-up failed"}

@@ -24,7 +24,8 @@ def _residual(op, f, u):
     return float(np.linalg.norm(sf - op.apply(u)) / np.linalg.norm(sf))
 
 
-@pytest.mark.parametrize("prec", [hzpkg.HZ_MIXED_C64_FCI32, hzpkg.HZ_C128])
+@pytest.mark.parametrize("prec", [hzpkg.HZ_MIXED_C64_FF, hzpkg.HZ_MIXED_C64_FCI32,
+                                  hzpkg.HZ_C128])
 def test_gaussian_bumps_64_solution_residual(prec):
     """The benchmark solve (64^3, J = 8, FGMRES(30), 1e-8) in the chosen and plain forms."""
     wl = W.gaussian_bumps_64()

@@ -209,7 +209,8 @@ def test_solve_point_source_32_converges_like_oracle():
     assert rel(to_np(uf)[0], res.u) <= 1e-9
 
 
-@pytest.mark.parametrize("prec", [hzpkg.HZ_MIXED_C64, hzpkg.HZ_MIXED_C64_FCI32])
+@pytest.mark.parametrize("prec", [hzpkg.HZ_MIXED_C64, hzpkg.HZ_MIXED_C64_FCI32,
+                                  hzpkg.HZ_MIXED_C64_FF])
 def test_mixed_solve_point_source_32(prec):
     """Mixed forms (complex64 sweeps, or the whole FCI in complex64; float64 outer Krylov and
     residual) reach the same 1e-8 true residual in about the float64 step count."""
@@ -225,6 +226,24 @@ def test_mixed_solve_point_source_32(prec):
     true = np.linalg.norm(op.s * f - op.apply(ug)) / np.linalg.norm(op.s * f)
     assert true <= 1e-8
     assert s32[0].its <= 1.25 * s64[0].its + 2
+
+
+def test_float_pair_arnoldi_matches_float64_arnoldi():
+    """HZ_MIXED_C64_FF differs from HZ_MIXED_C64_FCI32 only in the arithmetic of the outer
+    Arnoldi (float pairs, about 48 bits, against float64) and shares its complex64 FCI, so at
+    a fixed number of outer steps (two restart cycles) the iterates agree to near float64
+    rounding; 2 right-hand sides, ragged grid."""
+    wl = W.small_case(41, 13, 10, 9, nrhs=2, layer=2, J=4)
+    op, nodes = oracle_of(wl)
+    with problem_of(wl, nodes, nrhs_max=2, restart_max=6, inner_k_max=3) as P:
+        kw = dict(restart=6, inner_k=3, rtol=1e-30, max_cycles=3, fixed_its=11)
+        u64, s64 = P.solve(to_dev(wl.f), precision=hzpkg.HZ_MIXED_C64_FCI32, **kw)
+        uff, sff = P.solve(to_dev(wl.f), precision=hzpkg.HZ_MIXED_C64_FF, **kw)
+    assert [s.its for s in sff] == [s.its for s in s64] == [11, 11]
+    for v in range(2):
+        assert rel(to_np(uff)[v], to_np(u64)[v]) <= 1e-10
+        assert abs(sff[v].rel_res_true - s64[v].rel_res_true) <= 1e-10 * max(
+            s64[v].rel_res_true, 1e-300) + 1e-14
 
 
 def test_batched_rhs_equal_single_solves():
@@ -252,7 +271,7 @@ def test_solve_batched_equals_single_solves():
     probs = [problem_of(w, None, nrhs_max=2, restart_max=8, inner_k_max=3) for w in wls]
     try:
         fs = [to_dev(w.f) for w in wls]
-        for prec in (hzpkg.HZ_C128, hzpkg.HZ_MIXED_C64_FCI32):
+        for prec in (hzpkg.HZ_C128, hzpkg.HZ_MIXED_C64_FCI32, hzpkg.HZ_MIXED_C64_FF):
             us, sts = hzpkg.solve_batched(probs, fs, restart=8, inner_k=3, rtol=1e-9,
                                           max_cycles=40, precision=prec)
             for P, w, f, u, st in zip(probs, wls, fs, us, sts):
