@@ -389,22 +389,26 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
   if (fci32) {
     // step d and the inner GMRES on complex64 fields; w itself stays float64 for v + d w
     const long long vrs = (long long)(p->lim.inner_k_max + 1) * n;
-    HZ_TIMED(p, 1, st, (stencil_bytes<float2, float2>(n, nvec)),
-             (hz::launch_stencil32(p->g, p->d32, Buf<const float2>{p->w32, n},
-                                                Buf<float2>{p->Aw32, n}, nvec, 0.0, 0.0, st)));
-    HZ_TIMED(p, 2, st, 8.0 * n * nvec * 5,
-             hz::launch_fci_step32(Buf<const float2>{p->Aw32, n}, Buf<const float2>{p->f32, n},
-                                   Buf<float2>{p->Vin32, vrs}, p->gin, p->partial, p->counters, n,
-                                   nvec, st));
+    // Aw and d = (Aw)^H r / ||Aw||^2 in one launch, then v0 = r - d Aw and beta
+    HZ_TIMED(p, 1, st, (stencil_bytes<float2, float2>(n, nvec)) + 8.0 * n * nvec,
+             (hz::launch_stencil32_dots(1, p->g, p->d32, Buf<const float2>{p->w32, n},
+                                        Buf<float2>{p->Aw32, n}, p->f32, n, n, 1, p->gin,
+                                        p->partial, p->counters, nvec, st)));
+    HZ_TIMED(p, 2, st, 8.0 * n * nvec * 3,
+             hz::launch_fci_start32(Buf<const float2>{p->Aw32, n}, Buf<const float2>{p->f32, n},
+                                    Buf<float2>{p->Vin32, vrs}, p->gin, p->partial, p->counters,
+                                    n, nvec, st));
     HZ_CUDA(hz::launch_scale32(Buf<float2>{p->Vin32, vrs}, Buf<const float2>{p->Vin32, vrs}, n,
                                p->gin, nvec, st));
     for (int j = 0; j < kin; ++j) {
       Buf<float2> wj{p->Vin32 + (long long)(j + 1) * n, vrs};
-      HZ_TIMED(p, 1, st, (stencil_bytes<float2, float2>(n, nvec)),
-               (hz::launch_stencil32(
-                   p->g, p->d32, Buf<const float2>{p->Vin32 + (long long)j * n, vrs}, wj, nvec,
-                   0.0, 0.0, st)));
-      for (int mode = 0; mode < 3; ++mode)
+      // w = A v_j and the first CGS pass in one launch, then the second pass and Givens
+      HZ_TIMED(p, 1, st,
+               (stencil_bytes<float2, float2>(n, nvec)) + 0.5 * cgs_bytes(0, n, j + 1, nvec),
+               (hz::launch_stencil32_dots(
+                   0, p->g, p->d32, Buf<const float2>{p->Vin32 + (long long)j * n, vrs}, wj,
+                   p->Vin32, n, vrs, j + 1, p->gin, p->partial, p->counters, nvec, st)));
+      for (int mode = 1; mode < 3; ++mode)
         HZ_TIMED(p, 2, st, 0.5 * cgs_bytes(mode, n, j + 1, nvec),
                  hz::launch_cgs32(mode, p->Vin32, n, vrs, j + 1, wj, n, p->gin, p->partial,
                                   p->counters, nvec, kBreakdown, st));
@@ -528,17 +532,21 @@ hz_status autotune(hz_problem* p) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   HZ_CUDA(cudaEventCreate(&e0));
   HZ_CUDA(cudaEventCreate(&e1));
+  // best of 3 trials of 8 back-to-back launches (one trial is noisy at a few microseconds)
   auto timed = [&](auto launch) -> float {
     float best = 1e30f;
     if (launch() != cudaSuccess) return best;
-    cudaEventRecord(e0, st);
-    for (int rep = 0; rep < 5; ++rep)
-      if (launch() != cudaSuccess) return best;
-    cudaEventRecord(e1, st);
-    if (cudaEventSynchronize(e1) != cudaSuccess) return best;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    return ms;
+    for (int trial = 0; trial < 3; ++trial) {
+      cudaEventRecord(e0, st);
+      for (int rep = 0; rep < 8; ++rep)
+        if (launch() != cudaSuccess) return 1e30f;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best = std::min(best, ms);
+    }
+    return best;
   };
   const int J = p->J;
   for (int cls = 0; cls < 3; ++cls) {
@@ -758,7 +766,11 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   if ((s = dalloc(p, (void**)&p->V, sizeof(double2) * (size_t)n * (M + 1) * R)) != HZ_OK)
     return bail(s);
   if ((s = dalloc(p, (void**)&p->Z, sizeof(double2) * (size_t)n * M * R)) != HZ_OK) return bail(s);
-  const long long nblk = (n + hz::RED_MIN_CHUNK - 1) / hz::RED_MIN_CHUNK;
+  // block partial sums: linear reduction kernels (>= 256 points a block) and the fused
+  // stencil reductions (32 x 4 x 4 tiles, ragged at the edges)
+  const long long nblk = std::max<long long>(
+      (n + hz::RED_MIN_CHUNK - 1) / hz::RED_MIN_CHUNK,
+      (long long)((grid->nx + 31) / 32) * ((grid->ny + 3) / 4) * ((grid->nz + 3) / 4));
   const int slots = std::max(M, K) + 2;
   if ((s = dalloc(p, (void**)&p->partial, sizeof(double2) * (size_t)nblk * slots * R)) != HZ_OK)
     return bail(s);

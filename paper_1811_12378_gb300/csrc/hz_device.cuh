@@ -115,6 +115,47 @@ __device__ __forceinline__ float4 warp_sum_partials_ff(const float4* part, int s
   return acc;
 }
 
+// ---------------------------------------------------------------- complex64 stencil
+// y[t] = ((A - zI) x) at (i, j, k0 + t), t < ZC, from the precomputed complex64 diagonal
+// (dg = 6 s/h^2 - m - i a):  (dg - z) x - (s/h^2) * (sum of the 6 neighbours), Dirichlet
+// zeros outside.  All loads of the column are issued together and the z-neighbours of one
+// point are the centres of the next.  Points beyond nz give 0.  (i, j) must be inside.
+template <int ZC>
+__device__ __forceinline__ void stencil32_column(const Geom& g, const float2* __restrict__ dg,
+                                                 const float2* __restrict__ xr, int i, int j,
+                                                 int k0, float zr, float zi, float2 (&y)[ZC]) {
+  const long long sxy = (long long)g.nx * g.ny;
+  const long long p0 = i + (long long)g.nx * j + sxy * k0;
+  const float2 zero = make_float2(0.f, 0.f);
+  float2 dv[ZC], xm[ZC], xp[ZC], ym[ZC], yp[ZC], c[ZC + 2];
+#pragma unroll
+  for (int t = 0; t < ZC; ++t) {
+    const bool ok = k0 + t < g.nz;
+    const long long pp = p0 + sxy * t;
+    dv[t] = ok ? dg[pp] : zero;
+    xm[t] = (ok && i > 0) ? xr[pp - 1] : zero;
+    xp[t] = (ok && i < g.nx - 1) ? xr[pp + 1] : zero;
+    ym[t] = (ok && j > 0) ? xr[pp - g.nx] : zero;
+    yp[t] = (ok && j < g.ny - 1) ? xr[pp + g.nx] : zero;
+  }
+#pragma unroll
+  for (int t = 0; t < ZC + 2; ++t) {
+    const int kz = k0 + t - 1;
+    c[t] = (kz >= 0 && kz < g.nz) ? xr[p0 + sxy * (t - 1)] : zero;
+  }
+  const float cs = g.csf;
+#pragma unroll
+  for (int t = 0; t < ZC; ++t) {
+    const float2 xc = c[t + 1];
+    const float nbx = ((xm[t].x + xp[t].x) + (ym[t].x + yp[t].x)) + (c[t].x + c[t + 2].x);
+    const float nby = ((xm[t].y + xp[t].y) + (ym[t].y + yp[t].y)) + (c[t].y + c[t + 2].y);
+    const float dr = dv[t].x - zr, di = dv[t].y - zi;
+    y[t] = k0 + t < g.nz
+               ? make_float2(dr * xc.x - di * xc.y - cs * nbx, dr * xc.y + di * xc.x - cs * nby)
+               : zero;
+  }
+}
+
 // ---------------------------------------------------------------- reductions
 // Sum of v over the block; the result is valid in thread 0.  sh holds >= 32 entries.
 __device__ __forceinline__ double2 block_sum(double2 v, double2* sh) {

@@ -165,6 +165,17 @@ cudaError_t launch_convert_ff_c64(Buf<const float4> x, Buf<float2> y, long long 
 cudaError_t prepare_kernels(int mmax);
 // The same for the float32 triangular solve of the complex64 FCI form (inner lengths).
 cudaError_t prepare_kernels32(int mmax);
+// v0 = r - d Aw and the inner cycle start (the second half of launch_fci_step32).
+cudaError_t launch_fci_start32(Buf<const float2> Aw, Buf<const float2> r, Buf<float2> v0,
+                               const GmresDev& gs, double2* partial, unsigned* counters,
+                               long long n, int nvec, cudaStream_t st);
+// y = A x (complex64) fused with the reduction that consumes it: kind 0 = the first CGS pass
+// (h1 = V^H y over nb fields, ||y||^2), kind 1 = the FCI step size d = (Ax)^H V0 / ||Ax||^2
+// with V the single field V0.  Blocks of 512 points.
+cudaError_t launch_stencil32_dots(int kind, const Geom& g, const float2* dg, Buf<const float2> x,
+                                  Buf<float2> y, const float2* V, long long vis, long long vrs,
+                                  int nb, const GmresDev& gs, double2* partial,
+                                  unsigned* counters, int nvec, cudaStream_t st);
 // y = R^{-1} g in float32 for the complex64 FCI form's inner GMRES (GmresDev storage float64).
 cudaError_t launch_backsolve32(const GmresDev& gs, int nvec, cudaStream_t st);
 

@@ -75,8 +75,7 @@ __device__ __forceinline__ T apply_point(T xc, T nb, R cs, R mp, R ap, R zr, R z
 }
 
 // Complex64 shifted stencil from the precomputed diagonal, z-columns of ZC points per thread
-// (all loads of a column issued together, z-neighbours shared between consecutive points):
-//     (A - zI) x = (dg - z) x - (s/h^2) * (sum of the 6 neighbours).
+// (stencil32_column in hz_device.cuh).
 template <int ZC>
 __global__ void __launch_bounds__(256)
 k_stencil32(Geom g, const float2* __restrict__ dg, const float2* __restrict__ x, long long xrs,
@@ -89,35 +88,11 @@ k_stencil32(Geom g, const float2* __restrict__ dg, const float2* __restrict__ x,
   if (i >= g.nx || j >= g.ny) return;
   const long long sxy = (long long)g.nx * g.ny;
   const long long p0 = i + (long long)g.nx * j + sxy * k0;
-  const float2* __restrict__ xr = x + r * xrs;
-  const float2 zero = make_float2(0.f, 0.f);
-  float2 dv[ZC], xm[ZC], xp[ZC], ym[ZC], yp[ZC], c[ZC + 2];
+  float2 yv[ZC];
+  stencil32_column<ZC>(g, dg, x + r * xrs, i, j, k0, zr, zi, yv);
 #pragma unroll
-  for (int t = 0; t < ZC; ++t) {
-    const bool ok = k0 + t < g.nz;
-    const long long pp = p0 + sxy * t;
-    dv[t] = ok ? dg[pp] : zero;
-    xm[t] = (ok && i > 0) ? xr[pp - 1] : zero;
-    xp[t] = (ok && i < g.nx - 1) ? xr[pp + 1] : zero;
-    ym[t] = (ok && j > 0) ? xr[pp - g.nx] : zero;
-    yp[t] = (ok && j < g.ny - 1) ? xr[pp + g.nx] : zero;
-  }
-#pragma unroll
-  for (int t = 0; t < ZC + 2; ++t) {
-    const int kz = k0 + t - 1;
-    c[t] = (kz >= 0 && kz < g.nz) ? xr[p0 + sxy * (t - 1)] : zero;
-  }
-  const float cs = g.csf;
-#pragma unroll
-  for (int t = 0; t < ZC; ++t) {
-    if (k0 + t >= g.nz) break;
-    const float2 xc = c[t + 1];
-    const float nbx = ((xm[t].x + xp[t].x) + (ym[t].x + yp[t].x)) + (c[t].x + c[t + 2].x);
-    const float nby = ((xm[t].y + xp[t].y) + (ym[t].y + yp[t].y)) + (c[t].y + c[t + 2].y);
-    const float dr = dv[t].x - zr, di = dv[t].y - zi;
-    y[r * yrs + p0 + sxy * t] =
-        make_float2(dr * xc.x - di * xc.y - cs * nbx, dr * xc.y + di * xc.x - cs * nby);
-  }
+  for (int t = 0; t < ZC; ++t)
+    if (k0 + t < g.nz) y[r * yrs + p0 + sxy * t] = yv[t];
 }
 
 // ---------------------------------------------------------------- polynomial stage

@@ -260,6 +260,127 @@ k_cgs32(const float2* __restrict__ V, long long vis, long long vrs, int nb, floa
   if (MODE == 2 && warp == 0) givens_column32(gs, r, nb - 1, tot2.x, float(brk));
 }
 
+// Ticket of the last of G blocks of this rhs (grids of any shape); true in every thread of it.
+__device__ __forceinline__ bool last_of(unsigned* counter, unsigned G) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) is_last = (atomicAdd(counter, 1u) == G - 1);
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+// The complex64 stencil y = A x fused with the reduction that consumes it (saves a launch and a
+// re-read of y), block (32, rows), z-columns of ZC points:
+//   KIND 0 (first CGS pass of an inner Arnoldi step): h1 = V^H y over nb basis fields and
+//          ||y||^2 into slot nb, as k_cgs32<0>;
+//   KIND 1 (Algorithm 1 step 3): d = (Aw)^H r / ||Aw||^2 with V = r (one field), as
+//          k_fci_dots32.
+// Float32 products, float-pair sums across warps and blocks.
+template <int ZC, int KIND>
+__global__ void __launch_bounds__(128)
+k_stencil32_dots(Geom g, const float2* __restrict__ dg, const float2* __restrict__ x,
+                 long long xrs, float2* __restrict__ y, long long yrs,
+                 const float2* __restrict__ V, long long vis, long long vrs, int nb, GmresDev gs,
+                 double2* partial, unsigned* counters) {
+  extern __shared__ float2 wsm[];  // [rows][nb + 8] per-warp sums
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nzc = (g.nz + ZC - 1) / ZC;
+  const int zb = blockIdx.z % nzc;
+  const int k0 = zb * ZC;
+  const int r = blockIdx.z / nzc;
+  const int lane = threadIdx.x, warp = threadIdx.y, rows = blockDim.y;
+  const unsigned G = gridDim.x * gridDim.y * nzc;
+  const unsigned bl = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zb);
+  const bool inside = i < g.nx && j < g.ny;
+  const long long sxy = (long long)g.nx * g.ny;
+  const long long p0 = i + (long long)g.nx * j + sxy * k0;
+  float2 yv[ZC];
+#pragma unroll
+  for (int t = 0; t < ZC; ++t) yv[t] = make_float2(0.f, 0.f);
+  if (inside) {
+    stencil32_column<ZC>(g, dg, x + r * xrs, i, j, k0, 0.f, 0.f, yv);
+#pragma unroll
+    for (int t = 0; t < ZC; ++t)
+      if (k0 + t < g.nz) y[r * yrs + p0 + sxy * t] = yv[t];
+  }
+  if (KIND == 0 && gs.stopped[r]) return;  // uniform over the rhs: no reduction wanted
+  const int nsl = KIND == 0 ? nb : 1;  // dot slots; the norm goes to slot nsl
+  const int ldw = nsl + 8;
+  const float2* Vr = V + r * vrs;
+  for (int b0 = 0; b0 < nsl; b0 += 8) {
+    float2 vv[8][ZC];
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+#pragma unroll
+      for (int e = 0; e < ZC; ++e)
+        vv[t][e] = (inside && b0 + t < nsl && k0 + e < g.nz) ? Vr[(b0 + t) * vis + p0 + sxy * e]
+                                                             : make_float2(0.f, 0.f);
+    float2 acc[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      acc[t] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int e = 0; e < ZC; ++e) {
+        const float2 v = vv[t][e], w = yv[e];
+        if (KIND == 0) {  // conj(v) * y
+          acc[t].x = fmaf(v.x, w.x, fmaf(v.y, w.y, acc[t].x));
+          acc[t].y = fmaf(v.x, w.y, fmaf(-v.y, w.x, acc[t].y));
+        } else {  // conj(y) * v
+          acc[t].x = fmaf(w.x, v.x, fmaf(w.y, v.y, acc[t].x));
+          acc[t].y = fmaf(w.x, v.y, fmaf(-w.y, v.x, acc[t].y));
+        }
+      }
+    }
+    const float2 red = warp_reduce8f(acc, lane);
+    if ((lane & 3) == 0) {
+      const int t = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+      wsm[warp * ldw + b0 + t] = red;
+    }
+  }
+  float q = 0.f;
+#pragma unroll
+  for (int e = 0; e < ZC; ++e) q = fmaf(yv[e].x, yv[e].x, fmaf(yv[e].y, yv[e].y, q));
+  q = warp_sum(q);
+  if (lane == 0) wsm[warp * ldw + nsl] = make_float2(q, 0.f);
+  __syncthreads();
+  const int nslots = nsl + 1;
+  const int tid = threadIdx.x + 32 * threadIdx.y;
+  float4* part = reinterpret_cast<float4*>(partial) + (long long)r * (gs.mmax + 2) * G;
+  for (int sidx = tid; sidx < nslots; sidx += 32 * rows) {
+    float4 a = ffc_of(wsm[sidx]);
+    for (int ww = 1; ww < rows; ++ww) a = ffc_add(a, ffc_of(wsm[ww * ldw + sidx]));
+    part[(long long)sidx * G + bl] = a;
+  }
+  if (!last_of(counters + r, G)) return;
+  if (KIND == 0) {
+    double2* out = gs.h1 + (long long)r * (gs.mmax + 2);
+    for (int sidx = warp; sidx < nslots; sidx += rows) {
+      const float4 t = warp_sum_partials_ff(part, sidx, (int)G, lane);
+      if (lane == 0) out[sidx] = d_from_ffc(t);
+    }
+    __syncthreads();
+    if (tid == 0) counters[r] = 0;
+  } else {
+    __shared__ float4 tot[2];
+    for (int sidx = warp; sidx < 2; sidx += rows) {
+      const float4 t = warp_sum_partials_ff(part, sidx, (int)G, lane);
+      if (lane == 0) tot[sidx] = t;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      counters[r] = 0;
+      double* sc = gs.scal + (long long)r * SC_COUNT;
+      const float2 num = f_from_ffc(tot[0]);
+      const float den = f_from_ffc(tot[1]).x;
+      sc[SC_DR] = den != 0.f ? double(num.x / den) : 0.0;
+      sc[SC_DI] = den != 0.f ? double(num.y / den) : 0.0;
+    }
+  }
+}
+
 __global__ void k_scale32(float2* __restrict__ dst, long long drs, const float2* __restrict__ src,
                           long long srs, long long n, GmresDev gs) {
   const int r = blockIdx.y;
@@ -482,6 +603,16 @@ cudaError_t launch_scale32(Buf<float2> dst, Buf<const float2> src, long long n, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_fci_start32(Buf<const float2> Aw, Buf<const float2> r, Buf<float2> v0,
+                               const GmresDev& gs, double2* partial, unsigned* counters,
+                               long long n, int nvec, cudaStream_t st) {
+  dim3 grd(blocks32(n), nvec);
+  count_launch();
+  k_fci_start32<<<grd, C_WARPS * 32, 0, st>>>(Aw.p, Aw.rs, r.p, r.rs, v0.p, v0.rs, n, gs, partial,
+                                               counters);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fci_step32(Buf<const float2> Aw, Buf<const float2> r, Buf<float2> v0,
                               const GmresDev& gs, double2* partial, unsigned* counters,
                               long long n, int nvec, cudaStream_t st) {
@@ -493,6 +624,25 @@ cudaError_t launch_fci_step32(Buf<const float2> Aw, Buf<const float2> r, Buf<flo
   count_launch();
   k_fci_start32<<<grd, C_WARPS * 32, 0, st>>>(Aw.p, Aw.rs, r.p, r.rs, v0.p, v0.rs, n, gs, partial,
                                                counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil32_dots(int kind, const Geom& g, const float2* dg, Buf<const float2> x,
+                                  Buf<float2> y, const float2* V, long long vis, long long vrs,
+                                  int nb, const GmresDev& gs, double2* partial,
+                                  unsigned* counters, int nvec, cudaStream_t st) {
+  constexpr int ZC = 4, ROWS = 4;  // 512 points per block: within the partial-sum buffer
+  dim3 blk(32, ROWS, 1);
+  dim3 grd((g.nx + 31) / 32, (g.ny + ROWS - 1) / ROWS, ((g.nz + ZC - 1) / ZC) * nvec);
+  const int nsl = kind == 0 ? nb : 1;
+  const size_t smem = sizeof(float2) * (size_t)ROWS * (nsl + 8);
+  count_launch();
+  if (kind == 0)
+    k_stencil32_dots<ZC, 0><<<grd, blk, smem, st>>>(g, dg, x.p, x.rs, y.p, y.rs, V, vis, vrs, nb,
+                                                    gs, partial, counters);
+  else
+    k_stencil32_dots<ZC, 1><<<grd, blk, smem, st>>>(g, dg, x.p, x.rs, y.p, y.rs, V, vis, vrs, 1,
+                                                    gs, partial, counters);
   return cudaGetLastError();
 }
 
