@@ -8,6 +8,35 @@
 #include "hz_internal.h"
 
 namespace hz {
+
+// ---------------------------------------------------------------- programmatic dependent launch
+// Every kernel of the library starts with pdl_enter(): wait until the kernel before it on the
+// stream has completed and its writes are visible, then allow the next kernel to be launched.
+// Kernels are launched with programmatic stream serialization (launch_pdl), so a dependent
+// kernel's launch and block dispatch overlap the tail of the one before it instead of
+// starting after it (the solver is a chain of short dependent kernels; CUDA graphs keep the
+// programmatic edges).  Nothing is read or written before the wait, so the ordering of the
+// stream is unchanged.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 namespace {
 
 // ---------------------------------------------------------------- complex helpers

@@ -80,6 +80,7 @@ template <int ZC>
 __global__ void __launch_bounds__(256)
 k_stencil32(Geom g, const float2* __restrict__ dg, const float2* __restrict__ x, long long xrs,
             float2* __restrict__ y, long long yrs, float zr, float zi) {
+  pdl_enter();
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int nzc = (g.nz + ZC - 1) / ZC;
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(512)
 k_poly_stage(Geom g, const T* __restrict__ dg, const T* __restrict__ f, long long frs, T* ws,
              long long wrs, double2* __restrict__ w, long long wwrs, float2* __restrict__ w32,
              long long w32rs, const StageArgs<typename RealOf<T>::type> a) {
+  pdl_enter();
   using R = typename RealOf<T>::type;
   extern __shared__ double2 qs[];  // [rows][nnodes][ZC][32] on the final stage only
   const int i = blockIdx.x * 32 + threadIdx.x;
@@ -256,6 +258,7 @@ k_poly_stage(Geom g, const T* __restrict__ dg, const T* __restrict__ f, long lon
 // ---------------------------------------------------------------- conversions
 __global__ void k_c128_to_c64(const double2* __restrict__ x, long long xrs, float2* __restrict__ y,
                               long long yrs, long long n) {
+  pdl_enter();
   const int r = blockIdx.y;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
@@ -266,6 +269,7 @@ __global__ void k_c128_to_c64(const double2* __restrict__ x, long long xrs, floa
 
 __global__ void k_c64_to_c128(const float2* __restrict__ x, long long xrs, double2* __restrict__ y,
                               long long yrs, long long n) {
+  pdl_enter();
   const int r = blockIdx.y;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
@@ -316,6 +320,7 @@ template <int MODE, int PPL>
 __global__ void __launch_bounds__(CG_WARPS * 32)
 k_cgs(const double2* __restrict__ V, long long vis, long long vrs, int nb, double2* w,
       long long wrs, long long n, GmresDev gs, double2* partial, unsigned* counters, double brk) {
+  pdl_enter();
   extern __shared__ double2 sm[];  // hs[nb] | wp[CG_WARPS][nb + 8]
   const int r = blockIdx.y;
   if (gs.stopped[r]) return;
@@ -422,6 +427,7 @@ template <bool FF>
 __global__ void __launch_bounds__(BX * BY)
 k_stencil_diag(Geom g, const double2* __restrict__ dg, const double2* __restrict__ x,
                long long xrs, double2* __restrict__ y, long long yrs, double zr, double zi) {
+  pdl_enter();
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z % g.nz;
@@ -452,6 +458,7 @@ k_stencil_diag(Geom g, const double2* __restrict__ dg, const double2* __restrict
 
 __global__ void k_scale(double2* __restrict__ dst, long long drs, const double2* __restrict__ src,
                         long long srs, long long n, GmresDev gs) {
+  pdl_enter();
   const int r = blockIdx.y;
   const double s = gs.scal[(long long)r * SC_COUNT + SC_INV];
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
@@ -464,6 +471,7 @@ __global__ void k_scale(double2* __restrict__ dst, long long drs, const double2*
 __global__ void k_combine(double2* out, long long ors, const double2* __restrict__ B, long long bis,
                           long long brs, GmresDev gs, const double2* __restrict__ E, long long ers,
                           int use_e, int accumulate, long long n) {
+  pdl_enter();
   const int r = blockIdx.y;
   const int kk = gs.kend[r];
   const double2* y = gs.y + (long long)r * gs.mmax;
@@ -482,6 +490,7 @@ __global__ void k_combine(double2* out, long long ors, const double2* __restrict
 // triangle is staged in shared memory; warp 0 then sweeps the columns from the last one,
 // each lane updating its share of the remaining right-hand side.
 __global__ void __launch_bounds__(256) k_backsolve(GmresDev gs, int nvec) {
+  pdl_enter();
   extern __shared__ double2 smb[];
   const int r = blockIdx.x;
   if (r >= nvec) return;
@@ -534,6 +543,7 @@ k_residual_start(Geom g, const double* __restrict__ m, const double2* __restrict
                  long long frs, double fs, const double2* __restrict__ x, long long xrs,
                  double2* __restrict__ v0, long long vrs, GmresDev gs, double2* partial,
                  unsigned* counters) {
+  pdl_enter();
   __shared__ double2 sh[32];
   const int r = blockIdx.y;
   const long long base = (long long)blockIdx.x * RED_CHUNK + threadIdx.x;
@@ -576,6 +586,7 @@ k_residual_start(Geom g, const double* __restrict__ m, const double2* __restrict
 __global__ void __launch_bounds__(RED_THREADS)
 k_fci_dots(const double2* __restrict__ Aw, long long ars, const double2* __restrict__ rv,
            long long rrs, long long n, GmresDev gs, double2* partial, unsigned* counters) {
+  pdl_enter();
   __shared__ double2 sh[32];
   const int r = blockIdx.y;
   const long long base = (long long)blockIdx.x * RED_CHUNK + threadIdx.x;
@@ -612,6 +623,7 @@ __global__ void __launch_bounds__(RED_THREADS)
 k_fci_start(const double2* __restrict__ Aw, long long ars, const double2* __restrict__ rv,
             long long rrs, double2* __restrict__ v0, long long vrs, long long n, GmresDev gs,
             double2* partial, unsigned* counters) {
+  pdl_enter();
   __shared__ double2 sh[32];
   const int r = blockIdx.y;
   const long long base = (long long)blockIdx.x * RED_CHUNK + threadIdx.x;
@@ -662,20 +674,17 @@ cudaError_t launch_poly_stage(const Geom& g, const T* dg, Buf<const T> f, T* ws,
   count_launch();
   switch (zc) {
     case 1:
-      k_poly_stage<T, 1><<<grd, blk, smem, st>>>(g, dg, f.p, f.rs, ws, wrs, w.p, w.rs, w32.p,
-                                                 w32.rs, a);
-      break;
+      return launch_pdl(k_poly_stage<T, 1>, grd, blk, smem, st, g, dg, f.p, f.rs, ws, wrs, w.p,
+                        w.rs, w32.p, w32.rs, a);
     case 2:
-      k_poly_stage<T, 2><<<grd, blk, smem, st>>>(g, dg, f.p, f.rs, ws, wrs, w.p, w.rs, w32.p,
-                                                 w32.rs, a);
-      break;
+      return launch_pdl(k_poly_stage<T, 2>, grd, blk, smem, st, g, dg, f.p, f.rs, ws, wrs, w.p,
+                        w.rs, w32.p, w32.rs, a);
     default:
       if constexpr (sizeof(T) == 8)
-        k_poly_stage<T, 4><<<grd, blk, smem, st>>>(g, dg, f.p, f.rs, ws, wrs, w.p, w.rs, w32.p,
-                                                   w32.rs, a);
-      break;
+        return launch_pdl(k_poly_stage<T, 4>, grd, blk, smem, st, g, dg, f.p, f.rs, ws, wrs, w.p,
+                          w.rs, w32.p, w32.rs, a);
+      return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 template cudaError_t launch_poly_stage<float2, float>(const Geom&, const float2*, Buf<const float2>,
@@ -690,15 +699,13 @@ template cudaError_t launch_poly_stage<double2, double>(const Geom&, const doubl
 cudaError_t launch_convert_c128_c64(Buf<const double2> x, Buf<float2> y, long long n, int nvec,
                                     cudaStream_t st) {
   count_launch();
-  k_c128_to_c64<<<dim3(ew_blocks(n), nvec), 256, 0, st>>>(x.p, x.rs, y.p, y.rs, n);
-  return cudaGetLastError();
+  return launch_pdl(k_c128_to_c64, dim3(ew_blocks(n), nvec), 256, 0, st, x.p, x.rs, y.p, y.rs, n);
 }
 
 cudaError_t launch_convert_c64_c128(Buf<const float2> x, Buf<double2> y, long long n, int nvec,
                                     cudaStream_t st) {
   count_launch();
-  k_c64_to_c128<<<dim3(ew_blocks(n), nvec), 256, 0, st>>>(x.p, x.rs, y.p, y.rs, n);
-  return cudaGetLastError();
+  return launch_pdl(k_c64_to_c128, dim3(ew_blocks(n), nvec), 256, 0, st, x.p, x.rs, y.p, y.rs, n);
 }
 
 // Points per lane of the float64 Gram-Schmidt kernels.  They are bound by the float64 pipe,
@@ -726,26 +733,26 @@ int cgs_ppl(long long n, int nvec) {
 }
 
 template <int MODE, int PPL>
-void launch_cgs_ppl(const double2* V, long long vis, long long vrs, int nb, Buf<double2> w,
-                    long long n, const GmresDev& gs, double2* partial, unsigned* counters,
-                    int nvec, double breakdown, cudaStream_t st) {
+cudaError_t launch_cgs_ppl(const double2* V, long long vis, long long vrs, int nb, Buf<double2> w,
+                           long long n, const GmresDev& gs, double2* partial, unsigned* counters,
+                           int nvec, double breakdown, cudaStream_t st) {
   const long long chunk = CG_WARPS * 32LL * PPL;
   dim3 grd(unsigned((n + chunk - 1) / chunk), nvec);
   const size_t smem = sizeof(double2) * (size_t)(nb + CG_WARPS * (nb + 8));
-  k_cgs<MODE, PPL><<<grd, CG_WARPS * 32, smem, st>>>(V, vis, vrs, nb, w.p, w.rs, n, gs, partial,
-                                                     counters, breakdown);
+  return launch_pdl(k_cgs<MODE, PPL>, grd, dim3(CG_WARPS * 32), smem, st, V, vis, vrs, nb, w.p,
+                    w.rs, n, gs, partial, counters, breakdown);
 }
 
 template <int MODE>
-void launch_cgs_mode(int ppl, const double2* V, long long vis, long long vrs, int nb,
-                     Buf<double2> w, long long n, const GmresDev& gs, double2* partial,
-                     unsigned* counters, int nvec, double breakdown, cudaStream_t st) {
+cudaError_t launch_cgs_mode(int ppl, const double2* V, long long vis, long long vrs, int nb,
+                            Buf<double2> w, long long n, const GmresDev& gs, double2* partial,
+                            unsigned* counters, int nvec, double breakdown, cudaStream_t st) {
   switch (ppl) {
-    case 5: launch_cgs_ppl<MODE, 5>(V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st); break;
-    case 6: launch_cgs_ppl<MODE, 6>(V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st); break;
-    case 7: launch_cgs_ppl<MODE, 7>(V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st); break;
-    case 8: launch_cgs_ppl<MODE, 8>(V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st); break;
-    default: launch_cgs_ppl<MODE, 4>(V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st); break;
+    case 5: return launch_cgs_ppl<MODE, 5>(V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st);
+    case 6: return launch_cgs_ppl<MODE, 6>(V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st);
+    case 7: return launch_cgs_ppl<MODE, 7>(V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st);
+    case 8: return launch_cgs_ppl<MODE, 8>(V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st);
+    default: return launch_cgs_ppl<MODE, 4>(V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st);
   }
 }
 
@@ -755,12 +762,10 @@ cudaError_t launch_cgs(int mode, const double2* V, long long vis, long long vrs,
   const int ppl = cgs_ppl(n, nvec);
   count_launch();
   if (mode == 0)
-    launch_cgs_mode<0>(ppl, V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st);
-  else if (mode == 1)
-    launch_cgs_mode<1>(ppl, V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st);
-  else
-    launch_cgs_mode<2>(ppl, V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st);
-  return cudaGetLastError();
+    return launch_cgs_mode<0>(ppl, V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st);
+  if (mode == 1)
+    return launch_cgs_mode<1>(ppl, V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st);
+  return launch_cgs_mode<2>(ppl, V, vis, vrs, nb, w, n, gs, partial, counters, nvec, breakdown, st);
 }
 
 cudaError_t launch_stencil32(const Geom& g, const float2* dg, Buf<const float2> x, Buf<float2> y,
@@ -771,16 +776,15 @@ cudaError_t launch_stencil32(const Geom& g, const float2* dg, Buf<const float2> 
   count_launch();
   switch (zc) {
     case 2:
-      k_stencil32<2><<<grd, blk, 0, st>>>(g, dg, x.p, x.rs, y.p, y.rs, float(zr), float(zi));
-      break;
+      return launch_pdl(k_stencil32<2>, grd, blk, 0, st, g, dg, x.p, x.rs, y.p, y.rs, float(zr),
+                        float(zi));
     case 8:
-      k_stencil32<8><<<grd, blk, 0, st>>>(g, dg, x.p, x.rs, y.p, y.rs, float(zr), float(zi));
-      break;
+      return launch_pdl(k_stencil32<8>, grd, blk, 0, st, g, dg, x.p, x.rs, y.p, y.rs, float(zr),
+                        float(zi));
     default:
-      k_stencil32<4><<<grd, blk, 0, st>>>(g, dg, x.p, x.rs, y.p, y.rs, float(zr), float(zi));
-      break;
+      return launch_pdl(k_stencil32<4>, grd, blk, 0, st, g, dg, x.p, x.rs, y.p, y.rs, float(zr),
+                        float(zi));
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_stencil_diag(const Geom& g, const double2* dg, Buf<const double2> x,
@@ -788,8 +792,7 @@ cudaError_t launch_stencil_diag(const Geom& g, const double2* dg, Buf<const doub
   dim3 blk(BX, BY, 1);
   dim3 grd((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz * nvec);
   count_launch();
-  k_stencil_diag<false><<<grd, blk, 0, st>>>(g, dg, x.p, x.rs, y.p, y.rs, zr, zi);
-  return cudaGetLastError();
+  return launch_pdl(k_stencil_diag<false>, grd, blk, 0, st, g, dg, x.p, x.rs, y.p, y.rs, zr, zi);
 }
 
 cudaError_t launch_stencil_diag_ff(const Geom& g, const double2* dg, Buf<const double2> x,
@@ -797,16 +800,15 @@ cudaError_t launch_stencil_diag_ff(const Geom& g, const double2* dg, Buf<const d
   dim3 blk(BX, BY, 1);
   dim3 grd((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz * nvec);
   count_launch();
-  k_stencil_diag<true><<<grd, blk, 0, st>>>(g, dg, x.p, x.rs, reinterpret_cast<double2*>(y.p),
-                                            y.rs, 0.0, 0.0);
-  return cudaGetLastError();
+  return launch_pdl(k_stencil_diag<true>, grd, blk, 0, st, g, dg, x.p, x.rs,
+                    reinterpret_cast<double2*>(y.p), y.rs, 0.0, 0.0);
 }
 
 cudaError_t launch_scale(Buf<double2> dst, Buf<const double2> src, long long n, const GmresDev& gs,
                          int nvec, cudaStream_t st) {
   count_launch();
-  k_scale<<<dim3(ew_blocks(n), nvec), 256, 0, st>>>(dst.p, dst.rs, src.p, src.rs, n, gs);
-  return cudaGetLastError();
+  return launch_pdl(k_scale, dim3(ew_blocks(n), nvec), 256, 0, st, dst.p, dst.rs, src.p, src.rs, n,
+                    gs);
 }
 
 cudaError_t launch_combine(Buf<double2> out, const double2* B, long long bis, long long brs,
@@ -814,9 +816,8 @@ cudaError_t launch_combine(Buf<double2> out, const double2* B, long long bis, lo
                            long long n, int nvec, int kmax, cudaStream_t st) {
   (void)kmax;
   count_launch();
-  k_combine<<<dim3(ew_blocks(n), nvec), 256, 0, st>>>(out.p, out.rs, B, bis, brs, gs, E.p, E.rs,
-                                                      e_slot >= 0 ? 1 : 0, accumulate, n);
-  return cudaGetLastError();
+  return launch_pdl(k_combine, dim3(ew_blocks(n), nvec), 256, 0, st, out.p, out.rs, B, bis, brs, gs,
+                    E.p, E.rs, e_slot >= 0 ? 1 : 0, accumulate, n);
 }
 
 cudaError_t prepare_kernels(int mmax) {
@@ -830,8 +831,7 @@ cudaError_t launch_backsolve(const GmresDev& gs, int nvec, cudaStream_t st) {
   const int M = gs.mmax > 0 ? gs.mmax : 1;
   const size_t smem = sizeof(double2) * ((size_t)M * (M + 1) / 2 + M);
   count_launch();
-  k_backsolve<<<nvec, 256, smem, st>>>(gs, nvec);
-  return cudaGetLastError();
+  return launch_pdl(k_backsolve, nvec, 256, smem, st, gs, nvec);
 }
 
 cudaError_t launch_residual_start(const Geom& g, const double* m, Buf<const double2> f, double fs,
@@ -839,9 +839,8 @@ cudaError_t launch_residual_start(const Geom& g, const double* m, Buf<const doub
                                   double2* partial, unsigned* counters, int nvec,
                                   cudaStream_t st) {
   count_launch();
-  k_residual_start<<<dim3(red_blocks(g.n), nvec), RED_THREADS, 0, st>>>(
-      g, m, f.p, f.rs, fs, x.p, x.rs, v0.p, v0.rs, gs, partial, counters);
-  return cudaGetLastError();
+  return launch_pdl(k_residual_start, dim3(red_blocks(g.n), nvec), RED_THREADS, 0, st, g, m, f.p,
+                    f.rs, fs, x.p, x.rs, v0.p, v0.rs, gs, partial, counters);
 }
 
 cudaError_t launch_fci_step(Buf<const double2> Aw, Buf<const double2> r, Buf<double2> v0,
@@ -849,13 +848,12 @@ cudaError_t launch_fci_step(Buf<const double2> Aw, Buf<const double2> r, Buf<dou
                             long long n, int nvec, cudaStream_t st) {
   dim3 grd(red_blocks(n), nvec);
   count_launch();
-  k_fci_dots<<<grd, RED_THREADS, 0, st>>>(Aw.p, Aw.rs, r.p, r.rs, n, gs, partial, counters);
-  cudaError_t e = cudaGetLastError();
+  const cudaError_t e = launch_pdl(k_fci_dots, grd, RED_THREADS, 0, st, Aw.p, Aw.rs, r.p, r.rs, n,
+                                   gs, partial, counters);
   if (e != cudaSuccess) return e;
   count_launch();
-  k_fci_start<<<grd, RED_THREADS, 0, st>>>(Aw.p, Aw.rs, r.p, r.rs, v0.p, v0.rs, n, gs, partial,
-                                           counters);
-  return cudaGetLastError();
+  return launch_pdl(k_fci_start, grd, RED_THREADS, 0, st, Aw.p, Aw.rs, r.p, r.rs, v0.p, v0.rs, n,
+                    gs, partial, counters);
 }
 
 }  // namespace hz

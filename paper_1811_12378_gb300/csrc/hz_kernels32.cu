@@ -148,6 +148,7 @@ template <int MODE>
 __global__ void __launch_bounds__(C_WARPS * 32)
 k_cgs32(const float2* __restrict__ V, long long vis, long long vrs, int nb, float2* w,
         long long wrs, long long n, GmresDev gs, double2* partial, unsigned* counters, double brk) {
+  pdl_enter();
   extern __shared__ double2 sm[];  // wp[C_WARPS][nb + 8] | hs[nb] (float2 each)
   const int r = blockIdx.y;
   if (gs.stopped[r]) return;
@@ -284,6 +285,7 @@ k_stencil32_dots(Geom g, const float2* __restrict__ dg, const float2* __restrict
                  long long xrs, float2* __restrict__ y, long long yrs,
                  const float2* __restrict__ V, long long vis, long long vrs, int nb, GmresDev gs,
                  double2* partial, unsigned* counters) {
+  pdl_enter();
   extern __shared__ float2 wsm[];  // [rows][nb + 8] per-warp sums
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -383,6 +385,7 @@ k_stencil32_dots(Geom g, const float2* __restrict__ dg, const float2* __restrict
 
 __global__ void k_scale32(float2* __restrict__ dst, long long drs, const float2* __restrict__ src,
                           long long srs, long long n, GmresDev gs) {
+  pdl_enter();
   const int r = blockIdx.y;
   const float s = float(gs.scal[(long long)r * SC_COUNT + SC_INV]);
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
@@ -397,6 +400,7 @@ __global__ void k_scale32(float2* __restrict__ dst, long long drs, const float2*
 __global__ void __launch_bounds__(C_WARPS * 32)
 k_fci_dots32(const float2* __restrict__ Aw, long long ars, const float2* __restrict__ rv,
              long long rrs, long long n, GmresDev gs, double2* partial, unsigned* counters) {
+  pdl_enter();
   const int r = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long seg = (long long)blockIdx.x * C_CHUNK + (long long)warp * 32 * C_PPL + lane;
@@ -449,6 +453,7 @@ __global__ void __launch_bounds__(C_WARPS * 32)
 k_fci_start32(const float2* __restrict__ Aw, long long ars, const float2* __restrict__ rv,
               long long rrs, float2* __restrict__ v0, long long vrs, long long n, GmresDev gs,
               double2* partial, unsigned* counters) {
+  pdl_enter();
   __shared__ float2 dsh;
   const int r = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -502,6 +507,7 @@ k_fci_start32(const float2* __restrict__ Aw, long long ars, const float2* __rest
 // triangle and g are converted into shared memory by all lanes, lane 0 divides, the lanes
 // update the remaining right-hand side (the float64 storage of GmresDev is kept).
 __global__ void __launch_bounds__(32) k_backsolve32(GmresDev gs, int nvec) {
+  pdl_enter();
   extern __shared__ float2 smt[];  // packed triangle (column i at i(i+1)/2) | right-hand side
   const int r = blockIdx.x;
   if (r >= nvec) return;
@@ -546,6 +552,7 @@ __global__ void k_combine_fci32(double2* __restrict__ out, long long ors,
                                 const float2* __restrict__ B, long long bis, long long brs,
                                 GmresDev gs, const double2* __restrict__ E, long long ers,
                                 long long n) {
+  pdl_enter();
   __shared__ float2 ys[128];
   __shared__ double2 dsh;
   const int r = blockIdx.y;
@@ -585,22 +592,20 @@ cudaError_t launch_cgs32(int mode, const float2* V, long long vis, long long vrs
   const size_t smem = sizeof(float2) * ((size_t)C_WARPS * (nb + 8) + (size_t)nb);
   count_launch();
   if (mode == 0)
-    k_cgs32<0><<<grd, C_WARPS * 32, smem, st>>>(V, vis, vrs, nb, w.p, w.rs, n, gs, partial,
-                                                counters, breakdown);
-  else if (mode == 1)
-    k_cgs32<1><<<grd, C_WARPS * 32, smem, st>>>(V, vis, vrs, nb, w.p, w.rs, n, gs, partial,
-                                                counters, breakdown);
-  else
-    k_cgs32<2><<<grd, C_WARPS * 32, smem, st>>>(V, vis, vrs, nb, w.p, w.rs, n, gs, partial,
-                                                counters, breakdown);
-  return cudaGetLastError();
+    return launch_pdl(k_cgs32<0>, grd, C_WARPS * 32, smem, st, V, vis, vrs, nb, w.p, w.rs, n, gs,
+                      partial, counters, breakdown);
+  if (mode == 1)
+    return launch_pdl(k_cgs32<1>, grd, C_WARPS * 32, smem, st, V, vis, vrs, nb, w.p, w.rs, n, gs,
+                      partial, counters, breakdown);
+  return launch_pdl(k_cgs32<2>, grd, C_WARPS * 32, smem, st, V, vis, vrs, nb, w.p, w.rs, n, gs, partial,
+                    counters, breakdown);
 }
 
 cudaError_t launch_scale32(Buf<float2> dst, Buf<const float2> src, long long n, const GmresDev& gs,
                            int nvec, cudaStream_t st) {
   count_launch();
-  k_scale32<<<dim3(ew_blocks32(n), nvec), 256, 0, st>>>(dst.p, dst.rs, src.p, src.rs, n, gs);
-  return cudaGetLastError();
+  return launch_pdl(k_scale32, dim3(ew_blocks32(n), nvec), 256, 0, st, dst.p, dst.rs, src.p, src.rs,
+                    n, gs);
 }
 
 cudaError_t launch_fci_start32(Buf<const float2> Aw, Buf<const float2> r, Buf<float2> v0,
@@ -608,9 +613,8 @@ cudaError_t launch_fci_start32(Buf<const float2> Aw, Buf<const float2> r, Buf<fl
                                long long n, int nvec, cudaStream_t st) {
   dim3 grd(blocks32(n), nvec);
   count_launch();
-  k_fci_start32<<<grd, C_WARPS * 32, 0, st>>>(Aw.p, Aw.rs, r.p, r.rs, v0.p, v0.rs, n, gs, partial,
-                                               counters);
-  return cudaGetLastError();
+  return launch_pdl(k_fci_start32, grd, C_WARPS * 32, 0, st, Aw.p, Aw.rs, r.p, r.rs, v0.p, v0.rs, n,
+                    gs, partial, counters);
 }
 
 cudaError_t launch_fci_step32(Buf<const float2> Aw, Buf<const float2> r, Buf<float2> v0,
@@ -618,13 +622,12 @@ cudaError_t launch_fci_step32(Buf<const float2> Aw, Buf<const float2> r, Buf<flo
                               long long n, int nvec, cudaStream_t st) {
   dim3 grd(blocks32(n), nvec);
   count_launch();
-  k_fci_dots32<<<grd, C_WARPS * 32, 0, st>>>(Aw.p, Aw.rs, r.p, r.rs, n, gs, partial, counters);
-  cudaError_t e = cudaGetLastError();
+  const cudaError_t e = launch_pdl(k_fci_dots32, grd, C_WARPS * 32, 0, st, Aw.p, Aw.rs, r.p,
+                                   r.rs, n, gs, partial, counters);
   if (e != cudaSuccess) return e;
   count_launch();
-  k_fci_start32<<<grd, C_WARPS * 32, 0, st>>>(Aw.p, Aw.rs, r.p, r.rs, v0.p, v0.rs, n, gs, partial,
-                                               counters);
-  return cudaGetLastError();
+  return launch_pdl(k_fci_start32, grd, C_WARPS * 32, 0, st, Aw.p, Aw.rs, r.p, r.rs, v0.p, v0.rs, n,
+                    gs, partial, counters);
 }
 
 cudaError_t launch_stencil32_dots(int kind, const Geom& g, const float2* dg, Buf<const float2> x,
@@ -638,12 +641,10 @@ cudaError_t launch_stencil32_dots(int kind, const Geom& g, const float2* dg, Buf
   const size_t smem = sizeof(float2) * (size_t)ROWS * (nsl + 8);
   count_launch();
   if (kind == 0)
-    k_stencil32_dots<ZC, 0><<<grd, blk, smem, st>>>(g, dg, x.p, x.rs, y.p, y.rs, V, vis, vrs, nb,
-                                                    gs, partial, counters);
-  else
-    k_stencil32_dots<ZC, 1><<<grd, blk, smem, st>>>(g, dg, x.p, x.rs, y.p, y.rs, V, vis, vrs, 1,
-                                                    gs, partial, counters);
-  return cudaGetLastError();
+    return launch_pdl(k_stencil32_dots<ZC, 0>, grd, blk, smem, st, g, dg, x.p, x.rs, y.p, y.rs, V,
+                      vis, vrs, nb, gs, partial, counters);
+  return launch_pdl(k_stencil32_dots<ZC, 1>, grd, blk, smem, st, g, dg, x.p, x.rs, y.p, y.rs, V,
+                    vis, vrs, 1, gs, partial, counters);
 }
 
 size_t backsolve32_smem(int mmax) { return sizeof(float2) * ((size_t)mmax * (mmax + 1) / 2 + mmax); }
@@ -656,8 +657,7 @@ cudaError_t prepare_kernels32(int mmax) {
 cudaError_t launch_backsolve32(const GmresDev& gs, int nvec, cudaStream_t st) {
   if (gs.mmax > 128) return cudaErrorInvalidValue;
   count_launch();
-  k_backsolve32<<<nvec, 32, backsolve32_smem(gs.mmax), st>>>(gs, nvec);
-  return cudaGetLastError();
+  return launch_pdl(k_backsolve32, nvec, 32, backsolve32_smem(gs.mmax), st, gs, nvec);
 }
 
 cudaError_t launch_combine_fci32(Buf<double2> out, const float2* B, long long bis, long long brs,
@@ -665,9 +665,8 @@ cudaError_t launch_combine_fci32(Buf<double2> out, const float2* B, long long bi
                                  cudaStream_t st) {
   if (gs.mmax > 128) return cudaErrorInvalidValue;
   count_launch();
-  k_combine_fci32<<<dim3(ew_blocks32(n), nvec), 256, 0, st>>>(out.p, out.rs, B, bis, brs, gs, E.p,
-                                                              E.rs, n);
-  return cudaGetLastError();
+  return launch_pdl(k_combine_fci32, dim3(ew_blocks32(n), nvec), 256, 0, st, out.p, out.rs, B, bis,
+                    brs, gs, E.p, E.rs, n);
 }
 
 }  // namespace hz

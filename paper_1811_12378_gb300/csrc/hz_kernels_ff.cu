@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(F_WARPS * 32)
 k_cgs_ff(const float4* __restrict__ V, long long vis, long long vrs, int nb, float4* w,
          long long wrs, long long n, GmresDev gs, double2* partial, unsigned* counters,
          double brk) {
+  pdl_enter();
   extern __shared__ float4 sm4[];  // wp[F_WARPS][nb + 8] | hs[nb] (float-pair complex each)
   const int r = blockIdx.y;
   if (gs.stopped[r]) return;
@@ -199,6 +200,7 @@ k_cgs_ff(const float4* __restrict__ V, long long vis, long long vrs, int nb, flo
 
 // v = w * (1 / h_{k+1,k}) in place on float pairs; the float64 scale is split once per block.
 __global__ void k_scale_ff(float4* v, long long vrs, long long n, GmresDev gs) {
+  pdl_enter();
   __shared__ float2 s_ff;
   const int r = blockIdx.y;
   if (threadIdx.x == 0) s_ff = ff_from_d(gs.scal[(long long)r * SC_COUNT + SC_INV]);
@@ -220,6 +222,7 @@ __global__ void k_scale_ff(float4* v, long long vrs, long long n, GmresDev gs) {
 // (each element is read and rewritten by one thread).
 __global__ void k_scale_ff_from64(float4* dst, long long drs, const double2* src, long long srs,
                                   long long n, GmresDev gs) {
+  pdl_enter();
   const int r = blockIdx.y;
   const double s = gs.scal[(long long)r * SC_COUNT + SC_INV];
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
@@ -233,6 +236,7 @@ __global__ void k_scale_ff_from64(float4* dst, long long drs, const double2* src
 // The complex64 rounding of a float-pair field (its hi parts).
 __global__ void k_ff_to_c64(const float4* __restrict__ x, long long xrs, float2* __restrict__ y,
                             long long yrs, long long n) {
+  pdl_enter();
   const int r = blockIdx.y;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
@@ -255,37 +259,32 @@ cudaError_t launch_cgs_ff(int mode, const float4* V, long long vis, long long vr
   const size_t smem = sizeof(float4) * ((size_t)F_WARPS * (nb + 8) + (size_t)nb);
   count_launch();
   if (mode == 0)
-    k_cgs_ff<0><<<grd, F_WARPS * 32, smem, st>>>(V, vis, vrs, nb, w.p, w.rs, n, gs, partial,
-                                                 counters, breakdown);
-  else if (mode == 1)
-    k_cgs_ff<1><<<grd, F_WARPS * 32, smem, st>>>(V, vis, vrs, nb, w.p, w.rs, n, gs, partial,
-                                                 counters, breakdown);
-  else
-    k_cgs_ff<2><<<grd, F_WARPS * 32, smem, st>>>(V, vis, vrs, nb, w.p, w.rs, n, gs, partial,
-                                                 counters, breakdown);
-  return cudaGetLastError();
+    return launch_pdl(k_cgs_ff<0>, grd, F_WARPS * 32, smem, st, V, vis, vrs, nb, w.p, w.rs, n, gs,
+                      partial, counters, breakdown);
+  if (mode == 1)
+    return launch_pdl(k_cgs_ff<1>, grd, F_WARPS * 32, smem, st, V, vis, vrs, nb, w.p, w.rs, n, gs,
+                      partial, counters, breakdown);
+  return launch_pdl(k_cgs_ff<2>, grd, F_WARPS * 32, smem, st, V, vis, vrs, nb, w.p, w.rs, n, gs, partial,
+                    counters, breakdown);
 }
 
 cudaError_t launch_scale_ff(Buf<float4> v, long long n, const GmresDev& gs, int nvec,
                             cudaStream_t st) {
   count_launch();
-  k_scale_ff<<<dim3(ff_ew_blocks(n), nvec), 256, 0, st>>>(v.p, v.rs, n, gs);
-  return cudaGetLastError();
+  return launch_pdl(k_scale_ff, dim3(ff_ew_blocks(n), nvec), 256, 0, st, v.p, v.rs, n, gs);
 }
 
 cudaError_t launch_scale_ff_from64(Buf<float4> dst, Buf<const double2> src, long long n,
                                    const GmresDev& gs, int nvec, cudaStream_t st) {
   count_launch();
-  k_scale_ff_from64<<<dim3(ff_ew_blocks(n), nvec), 256, 0, st>>>(dst.p, dst.rs, src.p, src.rs,
-                                                                 n, gs);
-  return cudaGetLastError();
+  return launch_pdl(k_scale_ff_from64, dim3(ff_ew_blocks(n), nvec), 256, 0, st, dst.p, dst.rs,
+                    src.p, src.rs, n, gs);
 }
 
 cudaError_t launch_convert_ff_c64(Buf<const float4> x, Buf<float2> y, long long n, int nvec,
                                   cudaStream_t st) {
   count_launch();
-  k_ff_to_c64<<<dim3(ff_ew_blocks(n), nvec), 256, 0, st>>>(x.p, x.rs, y.p, y.rs, n);
-  return cudaGetLastError();
+  return launch_pdl(k_ff_to_c64, dim3(ff_ew_blocks(n), nvec), 256, 0, st, x.p, x.rs, y.p, y.rs, n);
 }
 
 }  // namespace hz
