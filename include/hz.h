@@ -222,6 +222,15 @@ hz_status hz_solve_batched(hz_problem* const* probs, int nprob, const void* cons
  * events and returns, per class, launches, total milliseconds and total algorithmic bytes
  * since the last enable; any output pointer may be null. */
 hz_status hz_profile_enable(hz_problem* p, int on);
+
+/* Selects how the complex64 forms run steps 3-5 of Algorithm 1 (step d, the inner GMRES,
+ * v + d w) for a single right-hand side: on = 1 (the default) as one cooperative kernel whose
+ * phases are separated by a grid-wide barrier, where the grid fits on the device and k_in <= 16;
+ * on = 0 as one kernel per Arnoldi piece.  The two differ only in the order of float32
+ * roundings.  Several right-hand sides per call, and problems solved together by
+ * hz_solve_batched, always use the per-piece kernels.  A barrier that waits longer than about
+ * a second gives up, and the next hz_solve on the problem returns HZ_ERR_CUDA. */
+hz_status hz_problem_fused_tail(hz_problem* p, int on);
 hz_status hz_profile_read(hz_problem* p, int cls, long long* launches, double* ms,
                           double* bytes);
 

@@ -110,6 +110,14 @@ struct hz_problem {
   long long graph_key = -1;
   bool graphs_on = true;
 
+  // the complex64 FCI tail as one cooperative kernel (hz_fci_tail32.cu): grid plans for
+  // k_in <= 4 and k_in <= TAIL_KMAX (ppt 0: does not fit), its barrier words and error flag
+  bool tail_on = true;       // hz_problem_fused_tail
+  bool tail_solo = true;     // false while several problems run concurrently (batched solve)
+  bool tail_used = false;
+  int tail_ppt[2] = {0, 0}, tail_blocks[2] = {0, 0};
+  unsigned* tail_bar = nullptr;  // [0] arrivals, [1] generation, [2] error flag
+
   void drop_graphs() {
     for (cudaGraphExec_t g : step_graphs)
       if (g) cudaGraphExecDestroy(g);
@@ -366,6 +374,22 @@ hz_status run_poly(hz_problem* p, const T* dg, Buf<const T> f, int nvec,
 
 // FCI (Algorithm 1) on nvec double-complex fields r -> out.
 // r_ff: r holds float pairs (the outer basis of HZ_MIXED_C64_FF); otherwise complex128.
+// After a synchronisation: a grid barrier of the cooperative FCI tail that gave up leaves its
+// flag set; report it once and reset the barrier words for the next launch.
+hz_status check_tail_fault(hz_problem* p) {
+  if (!p->tail_used) return HZ_OK;
+  unsigned w[3] = {0, 0, 0};
+  HZ_CUDA(cudaMemcpy(w, p->tail_bar, sizeof(w), cudaMemcpyDeviceToHost));
+  if (w[2] == 0) return HZ_OK;
+  HZ_CUDA(cudaMemset(p->tail_bar, 0, sizeof(unsigned) * 4));
+  return fail(HZ_ERR_CUDA, "a grid barrier of the cooperative FCI kernel timed out");
+}
+
+bool tail_fits(const hz_problem* p, int nvec, int kin) {
+  const int c = kin <= 4 ? 0 : 1;
+  return p->tail_on && p->tail_solo && nvec == 1 && kin <= hz::TAIL_KMAX && p->tail_ppt[c] > 0;
+}
+
 hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nvec, int kin,
                   int precision, cudaStream_t st, bool r_ff = false) {
   const long long n = p->g.n;
@@ -385,6 +409,16 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
                                     nullptr, st, w32b)));
   } else {
     HZ_TRY((run_poly<double2, double>(p, p->d64, r, nvec, all, true, wb, nullptr, st)));
+  }
+  if (fci32 && tail_fits(p, nvec, kin)) {
+    // steps 3-5 in one cooperative launch
+    const int c = kin <= 4 ? 0 : 1;
+    HZ_TIMED(p, 2, st, 8.0 * n * (6.0 + 4.0 * kin * (kin + 3)),
+             hz::launch_fci_tail32(p->g, p->d32, p->w32, p->f32, p->w, p->Vin32, out.p,
+                                   p->partial, p->tail_bar, (int*)(p->tail_bar + 2), n, kin,
+                                   kBreakdown, p->tail_ppt[c], p->tail_blocks[c], st));
+    p->tail_used = true;
+    return HZ_OK;
   }
   if (fci32) {
     // step d and the inner GMRES on complex64 fields; w itself stays float64 for v + d w
@@ -488,7 +522,8 @@ hz_status outer_step_launches(hz_problem* p, int k, int nrhs, int K, int precisi
 // step then cost one graph launch); plain launches while kernel timing is on.
 hz_status outer_step(hz_problem* p, int k, int nrhs, int K, int precision, cudaStream_t st) {
   if (p->prof_on || !p->graphs_on) return outer_step_launches(p, k, nrhs, K, precision, st);
-  const long long key = ((long long)nrhs * 4 + precision) * 1024 + K;
+  const long long key =
+      (((long long)nrhs * 4 + precision) * 1024 + K) * 2 + (tail_fits(p, nrhs, K) ? 1 : 0);
   if (p->graph_key != key) {
     p->drop_graphs();
     p->graph_key = key;
@@ -775,6 +810,7 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   if ((s = dalloc(p, (void**)&p->partial, sizeof(double2) * (size_t)nblk * slots * R)) != HZ_OK)
     return bail(s);
   if ((s = dalloc(p, (void**)&p->counters, sizeof(unsigned) * R)) != HZ_OK) return bail(s);
+  if ((s = dalloc(p, (void**)&p->tail_bar, sizeof(unsigned) * 4)) != HZ_OK) return bail(s);
   const size_t gb = gmres_carved_bytes(R, M) + gmres_carved_bytes(R, K) + 1024;
   if ((s = dalloc(p, &p->gmem, gb)) != HZ_OK) return bail(s);
   char* cur = (char*)p->gmem;
@@ -847,6 +883,14 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
     delete p;
     return cuda_fail(e, "cudaMemcpy of coefficients");
   }
+  e = cudaMemset(p->tail_bar, 0, sizeof(unsigned) * 4);
+  if (e == cudaSuccess) e = hz::fci_tail32_plan(n, std::min(K, 4), &p->tail_ppt[0], &p->tail_blocks[0]);
+  if (e == cudaSuccess && K > 4)
+    e = hz::fci_tail32_plan(n, hz::TAIL_KMAX, &p->tail_ppt[1], &p->tail_blocks[1]);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "cooperative FCI tail set-up");
+  }
   if (limits->autotune) {
     const hz_status ts = autotune(p);
     if (ts != HZ_OK) {
@@ -897,6 +941,13 @@ hz_status hz_plan(const hz_grid* grid, const double* c_host, const hz_contour_op
     if (nu) nu[j] = nd.nu;
     if (sweeps) sweeps[j] = nd.sweeps;
   }
+  return HZ_OK;
+}
+
+hz_status hz_problem_fused_tail(hz_problem* p, int on) {
+  HZ_TRY(check_problem(p));
+  if (p->tail_on != (on != 0)) p->drop_graphs();
+  p->tail_on = on != 0;
   return HZ_OK;
 }
 
@@ -1338,6 +1389,7 @@ hz_status drive(std::vector<SolveState>& ss) {
   }
   // the loop ends right after a residual evaluation, so rel[] is the final true residual
   for (auto& s : ss) HZ_CUDA(cudaStreamSynchronize(s.st));
+  for (auto& s : ss) HZ_TRY(check_tail_fault(s.p));
   hz_status ret = HZ_OK;
   for (auto& s : ss) {
     const hz_status r = s.result();
@@ -1349,6 +1401,19 @@ hz_status drive(std::vector<SolveState>& ss) {
 hz_status solve_batched_on(hz_problem* const* probs, int nprob, const void* const* f,
                            void* const* u, const int* nrhs, const hz_solve_opts* opts,
                            hz_solve_stats* stats) {
+  // grid-wide barriers of cooperative kernels on concurrent streams could wait on each other's
+  // resources: problems solved together use the multi-kernel FCI tail
+  struct Solo {
+    hz_problem* const* pr;
+    int np;
+    Solo(hz_problem* const* a, int b) : pr(a), np(b) {
+      if (np > 1)
+        for (int i = 0; i < np; ++i) pr[i]->tail_solo = false;
+    }
+    ~Solo() {
+      for (int i = 0; i < np; ++i) pr[i]->tail_solo = true;
+    }
+  } solo(probs, nprob);
   std::vector<SolveState> ss;
   long long off = 0;
   for (int i = 0; i < nprob; ++i) {

@@ -185,6 +185,42 @@ __device__ __forceinline__ void stencil32_column(const Geom& g, const float2* __
   }
 }
 
+// Butterfly reduction of 8 per-lane float2 partials over a warp (same lane map as the float64
+// version in hz_kernels.cu): lane l with (l & 3) == 0 ends with the sum of vector
+// ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 + ((l >> 2) & 1).
+__device__ __forceinline__ float2 warp_reduce8f(float2 (&a)[8], int lane) {
+  float2 b4[4], b2[2];
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const float2 keep = h16 ? a[4 + t] : a[t];
+    const float2 give = h16 ? a[t] : a[4 + t];
+    b4[t] = make_float2(keep.x + __shfl_xor_sync(0xffffffffu, give.x, 16),
+                        keep.y + __shfl_xor_sync(0xffffffffu, give.y, 16));
+  }
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const float2 keep = h8 ? b4[2 + t] : b4[t];
+    const float2 give = h8 ? b4[t] : b4[2 + t];
+    b2[t] = make_float2(keep.x + __shfl_xor_sync(0xffffffffu, give.x, 8),
+                        keep.y + __shfl_xor_sync(0xffffffffu, give.y, 8));
+  }
+  const float2 keep = h4 ? b2[1] : b2[0];
+  const float2 give = h4 ? b2[0] : b2[1];
+  float x = keep.x + __shfl_xor_sync(0xffffffffu, give.x, 4);
+  float y = keep.y + __shfl_xor_sync(0xffffffffu, give.y, 4);
+  x += __shfl_xor_sync(0xffffffffu, x, 2);
+  y += __shfl_xor_sync(0xffffffffu, y, 2);
+  x += __shfl_xor_sync(0xffffffffu, x, 1);
+  y += __shfl_xor_sync(0xffffffffu, y, 1);
+  return make_float2(x, y);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // ---------------------------------------------------------------- reductions
 // Sum of v over the block; the result is valid in thread 0.  sh holds >= 32 entries.
 __device__ __forceinline__ double2 block_sum(double2 v, double2* sh) {

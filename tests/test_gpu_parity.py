@@ -142,6 +142,25 @@ def test_fci_parity(prec, kin):
     assert rel(out, ref) <= tol
 
 
+@pytest.mark.parametrize("kin", [0, 1, 4, 10])
+def test_fci_fused_tail_one_rhs(kin):
+    """Steps 3-5 of Algorithm 1 for one right-hand side as one cooperative kernel (k_in up to 4
+    and up to 16 use different instances): against the oracle, and against the per-piece
+    kernels, which differ from it only in the order of float32 roundings."""
+    wl = W.small_case(16, 22, 13, 9, layer=2, J=5)
+    op, nodes = oracle_of(wl)
+    r = W.random_field(19, 1, wl.nx, wl.ny, wl.nz)
+    with problem_of(wl, nodes, nrhs_max=1, inner_k_max=10) as P:
+        fused = to_np(P.fci(to_dev(r), inner_k=kin, precision=hzpkg.HZ_MIXED_C64_FCI32))
+        fused2 = to_np(P.fci(to_dev(r), inner_k=kin, precision=hzpkg.HZ_MIXED_C64_FCI32))
+        P.fused_tail(False)
+        piece = to_np(P.fci(to_dev(r), inner_k=kin, precision=hzpkg.HZ_MIXED_C64_FCI32))
+    ref = O.fci(op, r[0], nodes, kin)
+    assert np.array_equal(fused, fused2)
+    assert rel(fused[0], ref) <= 2e-5
+    assert rel(fused[0], piece[0]) <= 2e-5
+
+
 def test_fci_eigenvector_exact_gpu():
     """P7 through the GPU: FCI of a sine mode returns v / mu."""
     nx, ny, nz = 6, 5, 7
