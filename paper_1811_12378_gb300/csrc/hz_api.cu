@@ -414,7 +414,7 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
     // steps 3-5 in one cooperative launch
     const int c = kin <= 4 ? 0 : 1;
     HZ_TIMED(p, 2, st, 8.0 * n * (6.0 + 4.0 * kin * (kin + 3)),
-             hz::launch_fci_tail32(p->g, p->d32, p->w32, p->f32, p->w, p->Vin32, out.p,
+             hz::launch_fci_tail32(p->g, p->d32, p->w32, p->f32, p->w, p->Vin32, p->Aw32, out.p,
                                    p->partial, p->tail_bar, (int*)(p->tail_bar + 2), n, kin,
                                    kBreakdown, p->tail_ppt[c], p->tail_blocks[c], st));
     p->tail_used = true;

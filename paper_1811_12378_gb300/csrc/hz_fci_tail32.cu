@@ -10,6 +10,9 @@
 // same scalars (d, beta, the Hessenberg column, the Givens rotation, y) redundantly in float32,
 // so no scalar has to be broadcast through memory and no further barrier is spent on it.
 // Fields written inside the kernel are read through L2 (__ldcg): L1 is not coherent across SMs.
+// The next basis vector is published unnormalised (scratch field W) together with its norm's
+// reduction, and the stencil of the next step scales A W by 1/h: that saves the barrier a
+// normalised copy would need (3 barriers per Arnoldi step, 2 for step d and beta).
 //
 // The barrier spins with a bound (about a second); a block that gives up sets the error flag
 // and returns, the others then skip their waits, and the host reports the flag after the
@@ -65,6 +68,7 @@ struct Tail {
   const float2* f32;   // r (the FCI input) in complex64
   const double2* w64;  // quadrature sum in float64
   float2* V;           // inner basis, kin + 1 fields of n
+  float2* W;           // scratch field: the next basis vector before its normalisation
   double2* out;        // FCI output
   float4* part;        // [slots][gridDim.x] block partial sums
   unsigned* bar;       // barrier counter and generation
@@ -135,11 +139,22 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
   const float cs = g.csf;
   const long long sxy = (long long)g.nx * g.ny;
 
-  // (A x)(p) from a field x written earlier in this kernel or before it
-  auto apply = [&](const float2* x, long long p, bool via_l2) -> float2 {
-    const int i = int(p % g.nx);
-    const int j = int((p / g.nx) % g.ny);
-    const int k = int(p / sxy);
+  // grid coordinates of this thread's points (n < 2^31)
+  int ci[PPT], cj[PPT], ck[PPT];
+#pragma unroll
+  for (int e = 0; e < PPT; ++e) {
+    const long long p = t0 + e * T;
+    const int pi = p < n ? int(p) : 0;
+    const int nxy = g.nx * g.ny;
+    ck[e] = pi / nxy;
+    const int rem = pi - ck[e] * nxy;
+    cj[e] = rem / g.nx;
+    ci[e] = rem - cj[e] * g.nx;
+  }
+
+  // (A x)(p) for own point e, from a field x written earlier in this kernel or before it
+  auto apply = [&](const float2* x, int e, long long p, bool via_l2) -> float2 {
+    const int i = ci[e], j = cj[e], k = ck[e];
     auto ld = [&](long long q) { return via_l2 ? __ldcg(x + q) : __ldg(x + q); };
     const float2 xc = ld(p);
     const float2 xm = i > 0 ? ld(p - 1) : zero, xp = i < g.nx - 1 ? ld(p + 1) : zero;
@@ -161,7 +176,7 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
       aw[e] = zero;
       rv[e] = zero;
       if (p < n) {
-        aw[e] = apply(a.w32, p, false);
+        aw[e] = apply(a.w32, e, p, false);
         rv[e] = __ldg(a.f32 + p);
         v[0].x = fmaf(aw[e].x, rv[e].x, fmaf(aw[e].y, rv[e].y, v[0].x));
         v[0].y = fmaf(aw[e].x, rv[e].y, fmaf(-aw[e].y, rv[e].x, v[0].y));
@@ -188,6 +203,11 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
                           rv[e].y - (d.x * aw[e].y + d.y * aw[e].x));
       v[0].x = fmaf(wv[e].x, wv[e].x, fmaf(wv[e].y, wv[e].y, v[0].x));
     }
+#pragma unroll
+    for (int e = 0; e < PPT; ++e) {
+      const long long p = t0 + e * T;
+      if (p < n) a.W[p] = wv[e];
+    }
     block_partial<1, LDW>(a, v, 1, wsum);
   }
   if (!grid_sync(a.bar, G, a.err)) return;
@@ -211,8 +231,7 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
 
   // ---- inner GMRES (Algorithm 1 step 4), CGS2 Arnoldi with Givens rotations
   for (int j = 0; j < a.kin && !stop_s; ++j) {
-    if (!grid_sync(a.bar, G, a.err)) return;  // v_j complete before its stencil
-    const float2* vj = a.V + (long long)j * n;
+    const float invj = inv_s;  // v_j = W / h: W is complete since the last barrier
     const int nb = j + 1;
     // w = A v_j, first pass h1 = V^H w, ||w||^2
     {
@@ -224,7 +243,8 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
         const long long p = t0 + e * T;
         wv[e] = zero;
         if (p < n) {
-          wv[e] = apply(vj, p, true);
+          const float2 aw_ = apply(a.W, e, p, true);
+          wv[e] = make_float2(aw_.x * invj, aw_.y * invj);
 #pragma unroll
           for (int b = 0; b < KC + 1; ++b) {
             if (b < nb) {
@@ -294,6 +314,7 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
             }
           }
           v[0].x = fmaf(wv[e].x, wv[e].x, fmaf(wv[e].y, wv[e].y, v[0].x));
+          a.W[p] = wv[e];  // every read of W in this step came before the first barrier
         }
       }
       block_partial<1, LDW>(a, v, 1, wsum);
@@ -417,6 +438,11 @@ cudaError_t launch_kc(const cudaLaunchConfig_t& cfg, int ppt, const Tail& a) {
 }  // namespace
 
 cudaError_t fci_tail32_plan(long long n, int kin, int* ppt, int* blocks) {
+  if (n > 0x7fffffffLL) {
+    *ppt = 0;
+    *blocks = 0;
+    return cudaSuccess;
+  }
   *ppt = 0;
   *blocks = 0;
   int dev = 0, sms = 0, coop = 0;
@@ -439,10 +465,11 @@ cudaError_t fci_tail32_plan(long long n, int kin, int* ppt, int* blocks) {
 }
 
 cudaError_t launch_fci_tail32(const Geom& g, const float2* dg, const float2* w32,
-                              const float2* f32, const double2* w64, float2* V, double2* out,
+                              const float2* f32, const double2* w64, float2* V, float2* W,
+                              double2* out,
                               double2* partial, unsigned* bar, int* err, long long n, int kin,
                               double brk, int ppt, int blocks, cudaStream_t st) {
-  if (kin > TAIL_KMAX || blocks < 1) return cudaErrorInvalidValue;
+  if (kin > TAIL_KMAX || blocks < 1 || n > 0x7fffffffLL) return cudaErrorInvalidValue;
   Tail a;
   a.g = g;
   a.dg = dg;
@@ -450,6 +477,7 @@ cudaError_t launch_fci_tail32(const Geom& g, const float2* dg, const float2* w32
   a.f32 = f32;
   a.w64 = w64;
   a.V = V;
+  a.W = W;
   a.out = out;
   a.part = reinterpret_cast<float4*>(partial);
   a.bar = bar;

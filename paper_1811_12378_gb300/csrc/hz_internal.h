@@ -182,9 +182,11 @@ constexpr int TAIL_KMAX = 16;
 // steps); *ppt = 0 where it does not fit or cooperative launch is unavailable.
 cudaError_t fci_tail32_plan(long long n, int kin, int* ppt, int* blocks);
 // Steps 3-5 of Algorithm 1 for one right-hand side: d from A w32 and f32, inner GMRES(kin) on
-// V (kin + 1 fields), out = V y + d w64.  bar: 2 zeroed counters; err: set on a barrier timeout.
+// V (kin + 1 fields; W: one scratch field), out = V y + d w64.  bar: 2 zeroed counters; err:
+// set on a barrier timeout.  n < 2^31.
 cudaError_t launch_fci_tail32(const Geom& g, const float2* dg, const float2* w32,
-                              const float2* f32, const double2* w64, float2* V, double2* out,
+                              const float2* f32, const double2* w64, float2* V, float2* W,
+                              double2* out,
                               double2* partial, unsigned* bar, int* err, long long n, int kin,
                               double brk, int ppt, int blocks, cudaStream_t st);
 // y = R^{-1} g in float32 for the complex64 FCI form's inner GMRES (GmresDev storage float64).
