@@ -263,31 +263,23 @@ Slots slots_of(int s, long long n) {
   return {b, b + n, b + 2 * n, b + 3 * n};
 }
 
-// Runs the batched scheme eq:fix-pt-exp for the nodes in `which` from y = 0.  With `quad`
-// the last stage writes w = sum sigma_j/z_j y_j (double2, wbuf; and its complex64 rounding
-// into w32buf where that is given); otherwise node slot s ends with its y in the returned
-// offset yfinal[s] of the workspace.
-template <typename T, typename R>
-hz_status run_poly(hz_problem* p, const T* dg, Buf<const T> f, int nvec,
-                   const std::vector<int>& which, bool quad, Buf<double2> wbuf,
-                   std::vector<long long>* yfinal, cudaStream_t st,
-                   Buf<float2> w32buf = Buf<float2>{nullptr, 0}) {
+// The stage schedule of the batched scheme eq:fix-pt-exp for the nodes in `which` from y = 0:
+// schedules are right-aligned, so every node's last sweep ends on the last stage; stage t
+// lists its active nodes (compacted) with their step kind, coefficients and workspace slots.
+// With `quad` the last stage is marked to form the quadrature sum instead of writing y.
+// ycur returns each node slot's final y offset.
+template <typename R>
+void build_schedule(const hz_problem* p, const std::vector<int>& which, bool quad,
+                    std::vector<hz::StageArgs<R>>& out, std::vector<long long>& ycur) {
   const long long n = p->g.n;
   const int nn = (int)which.size();
-  T* ws = (T*)p->poly;
-  const long long wrs = 4LL * p->J * n;  // elements of T per rhs
   int T_total = 0;
   for (int node : which) T_total = std::max(T_total, p->nodes[node].q * p->nodes[node].sweeps);
-  std::vector<long long> ycur(nn);
+  ycur.assign(nn, 0);
   for (int s = 0; s < nn; ++s) ycur[s] = slots_of(s, n).Y;
-  // one event pair around the whole stage sequence (per-launch events would cost more than
-  // a 64^3 stage); launches and bytes are added per stage
-  ProfScope seq{p, 0, -1, st, 0.0};
-  HZ_TRY(seq.begin());
-  double seq_bytes = 0.0;
+  out.assign(T_total, hz::StageArgs<R>{});
   for (int t = 0; t < T_total; ++t) {
-    // the active nodes of this stage, compacted (one warp row of the kernel's block each)
-    hz::StageArgs<R> a;
+    hz::StageArgs<R>& a = out[t];
     std::memset(&a, 0, sizeof(a));
     a.nnodes = 0;
     a.final_quad = (quad && t == T_total - 1) ? 1 : 0;
@@ -350,20 +342,51 @@ hz_status run_poly(hz_problem* p, const T* dg, Buf<const T> f, int nvec,
         ycur[s] = sl.Y;
       }
     }
-    // algorithmic bytes per point: f and m once; per node FIRST y?(r) k(w) acc(w), MID k(r)
-    // acc(r/w) k(w), LAST k(r) acc(r) y(w, or the float64 sum w once at the final stage)
-    double bpp = double(sizeof(T)) * 1 + double(sizeof(R)) / nvec;
-    for (int s = 0; s < a.nnodes; ++s) {
-      const hz::StageNode<R>& sn = a.nd[s];
-      const double e = sizeof(T);
-      if (sn.kind == hz::SK_FIRST) bpp += (sn.yzero ? 2 : 3) * e;
-      else if (sn.kind == hz::SK_MID) bpp += 4 * e;
-      else if (sn.kind == hz::SK_LAST) bpp += (a.final_quad ? 2 : 3) * e;
-      else if (sn.kind == hz::SK_FIRST_LAST) bpp += ((sn.yzero ? 0 : 1) + (a.final_quad ? 0 : 1)) * e;
-    }
-    if (a.final_quad) bpp += sizeof(double2) + (w32buf.p ? sizeof(float2) : 0);
-    HZ_CUDA((hz::launch_poly_stage<T, R>(p->g, dg, f, ws, wrs, wbuf, w32buf, nvec, a, st)));
-    seq_bytes += bpp * double(n) * nvec;
+  }
+}
+
+// Algorithmic bytes per point of one stage: f and the diagonal once; per node FIRST y?(r) k(w)
+// acc(w), MID k(r) acc(r/w) k(w), LAST k(r) acc(r) y(w, or the float64 sum w once at the
+// final stage).
+template <typename T, typename R>
+double stage_bytes_per_point(const hz::StageArgs<R>& a, int nvec, bool w32) {
+  double bpp = double(sizeof(T)) * 1 + double(sizeof(R)) / nvec;
+  for (int s = 0; s < a.nnodes; ++s) {
+    const hz::StageNode<R>& sn = a.nd[s];
+    const double e = sizeof(T);
+    if (sn.kind == hz::SK_FIRST) bpp += (sn.yzero ? 2 : 3) * e;
+    else if (sn.kind == hz::SK_MID) bpp += 4 * e;
+    else if (sn.kind == hz::SK_LAST) bpp += (a.final_quad ? 2 : 3) * e;
+    else if (sn.kind == hz::SK_FIRST_LAST) bpp += ((sn.yzero ? 0 : 1) + (a.final_quad ? 0 : 1)) * e;
+  }
+  if (a.final_quad) bpp += sizeof(double2) + (w32 ? sizeof(float2) : 0);
+  return bpp;
+}
+
+// Runs the batched scheme eq:fix-pt-exp for the nodes in `which` from y = 0, one launch per
+// stage.  With `quad` the last stage writes w = sum sigma_j/z_j y_j (double2, wbuf; and its
+// complex64 rounding into w32buf where that is given); otherwise node slot s ends with its y
+// in the returned offset yfinal[s] of the workspace.
+template <typename T, typename R>
+hz_status run_poly(hz_problem* p, const T* dg, Buf<const T> f, int nvec,
+                   const std::vector<int>& which, bool quad, Buf<double2> wbuf,
+                   std::vector<long long>* yfinal, cudaStream_t st,
+                   Buf<float2> w32buf = Buf<float2>{nullptr, 0}) {
+  const long long n = p->g.n;
+  T* ws = (T*)p->poly;
+  const long long wrs = 4LL * p->J * n;  // elements of T per rhs
+  std::vector<hz::StageArgs<R>> sched;
+  std::vector<long long> ycur;
+  build_schedule<R>(p, which, quad, sched, ycur);
+  const int T_total = (int)sched.size();
+  // one event pair around the whole stage sequence (per-launch events would cost more than
+  // a 64^3 stage); launches and bytes are added per stage
+  ProfScope seq{p, 0, -1, st, 0.0};
+  HZ_TRY(seq.begin());
+  double seq_bytes = 0.0;
+  for (int t = 0; t < T_total; ++t) {
+    HZ_CUDA((hz::launch_poly_stage<T, R>(p->g, dg, f, ws, wrs, wbuf, w32buf, nvec, sched[t], st)));
+    seq_bytes += stage_bytes_per_point<T, R>(sched[t], nvec, w32buf.p != nullptr) * double(n) * nvec;
   }
   seq.bytes = seq_bytes;
   HZ_TRY(seq.end());
@@ -405,8 +428,8 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
                                         Buf<float2>{p->f32, n}, n, nvec, st));
     else
       HZ_CUDA(hz::launch_convert_c128_c64(r, Buf<float2>{p->f32, n}, n, nvec, st));
-    HZ_TRY((run_poly<float2, float>(p, p->d32, Buf<const float2>{p->f32, n}, nvec, all, true, wb,
-                                    nullptr, st, w32b)));
+    HZ_TRY((run_poly<float2, float>(p, p->d32, Buf<const float2>{p->f32, n}, nvec, all, true,
+                                    wb, nullptr, st, w32b)));
   } else {
     HZ_TRY((run_poly<double2, double>(p, p->d64, r, nvec, all, true, wb, nullptr, st)));
   }
@@ -801,11 +824,23 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   if ((s = dalloc(p, (void**)&p->V, sizeof(double2) * (size_t)n * (M + 1) * R)) != HZ_OK)
     return bail(s);
   if ((s = dalloc(p, (void**)&p->Z, sizeof(double2) * (size_t)n * M * R)) != HZ_OK) return bail(s);
-  // block partial sums: linear reduction kernels (>= 256 points a block) and the fused
-  // stencil reductions (32 x 4 x 4 tiles, ragged at the edges)
+  // grids of the cooperative kernels (whole numbers of blocks per SM)
+  {
+    cudaError_t pe = hz::fci_tail32_plan(n, std::min(K, 4), &p->tail_ppt[0], &p->tail_blocks[0]);
+    if (pe == cudaSuccess && K > 4)
+      pe = hz::fci_tail32_plan(n, hz::TAIL_KMAX, &p->tail_ppt[1], &p->tail_blocks[1]);
+    if (pe != cudaSuccess) {
+      delete p;
+      return cuda_fail(pe, "cooperative kernel plans");
+    }
+  }
+  // block partial sums: linear reduction kernels (>= 256 points a block), the fused stencil
+  // reductions (32 x 4 x 4 tiles, ragged at the edges) and the cooperative FCI tail
   const long long nblk = std::max<long long>(
-      (n + hz::RED_MIN_CHUNK - 1) / hz::RED_MIN_CHUNK,
-      (long long)((grid->nx + 31) / 32) * ((grid->ny + 3) / 4) * ((grid->nz + 3) / 4));
+      std::max<long long>((n + hz::RED_MIN_CHUNK - 1) / hz::RED_MIN_CHUNK,
+                          (long long)((grid->nx + 31) / 32) * ((grid->ny + 3) / 4) *
+                              ((grid->nz + 3) / 4)),
+      std::max(p->tail_blocks[0], p->tail_blocks[1]));
   const int slots = std::max(M, K) + 2;
   if ((s = dalloc(p, (void**)&p->partial, sizeof(double2) * (size_t)nblk * slots * R)) != HZ_OK)
     return bail(s);
@@ -884,9 +919,6 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
     return cuda_fail(e, "cudaMemcpy of coefficients");
   }
   e = cudaMemset(p->tail_bar, 0, sizeof(unsigned) * 4);
-  if (e == cudaSuccess) e = hz::fci_tail32_plan(n, std::min(K, 4), &p->tail_ppt[0], &p->tail_blocks[0]);
-  if (e == cudaSuccess && K > 4)
-    e = hz::fci_tail32_plan(n, hz::TAIL_KMAX, &p->tail_ppt[1], &p->tail_blocks[1]);
   if (e != cudaSuccess) {
     delete p;
     return cuda_fail(e, "cooperative FCI tail set-up");

@@ -221,6 +221,45 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// ---------------------------------------------------------------- grid barrier
+constexpr long long kGridSpins = 1LL << 23;  // about a second of polling
+
+// Grid barrier over nblocks resident blocks: bar[0] counts arrivals, bar[1] is the generation.
+// Arrival is an acquire-release atomic (it publishes the block's writes, ordered before it by
+// the block barrier, and the last arriver sees everyone's); the last arriver resets the count
+// and releases the next generation; the others poll the generation with acquire loads, first
+// back to back, then with a short sleep.  false if this block gave up (or another already
+// had): the caller returns.
+__device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned gen, old;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(bar + 1) : "memory");
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
+    if (old == nblocks - 1) {
+      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
+      ok = 1;
+    } else {
+      ok = 0;
+      for (long long it = 0; it < kGridSpins; ++it) {
+        unsigned now;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(now) : "l"(bar + 1) : "memory");
+        if (now != gen) {
+          ok = 1;
+          break;
+        }
+        if (*(volatile int*)err) break;
+        if (it >= 64) __nanosleep(32);
+      }
+      if (!ok) atomicExch(err, 1);
+    }
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
 // ---------------------------------------------------------------- reductions
 // Sum of v over the block; the result is valid in thread 0.  sh holds >= 32 entries.
 __device__ __forceinline__ double2 block_sum(double2 v, double2* sh) {

@@ -9,7 +9,8 @@
 // after each barrier every block reads all blocks' partial sums (float pairs) and computes the
 // same scalars (d, beta, the Hessenberg column, the Givens rotation, y) redundantly in float32,
 // so no scalar has to be broadcast through memory and no further barrier is spent on it.
-// Fields written inside the kernel are read through L2 (__ldcg): L1 is not coherent across SMs.
+// Fields written inside the kernel are read with ordinary loads (never the read-only path): the
+// grid barrier's acquire makes the other blocks' writes visible to them.
 // The next basis vector is published unnormalised (scratch field W) together with its norm's
 // reduction, and the stencil of the next step scales A W by 1/h: that saves the barrier a
 // normalised copy would need (3 barriers per Arnoldi step, 2 for step d and beta).
@@ -19,50 +20,15 @@
 // solve.  One right-hand side, k_in <= TAIL_KMAX (instances for k_in <= 4 and <= 16).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "hz_device.cuh"
 #include "hz_internal.h"
 
 namespace hz {
 namespace {
 
-constexpr int TB = 256;                  // threads per block
-constexpr long long kSpins = 1LL << 23;  // barrier spin bound (x ~100 ns)
-
-// Grid barrier over nblocks resident blocks: bar[0] counts arrivals, bar[1] is the generation.
-// Arrival is an acquire-release atomic (it publishes the block's writes, ordered before it by
-// the block barrier, and the last arriver sees everyone's); the last arriver resets the count
-// and releases the next generation; the others poll the generation with acquire loads, first
-// back to back, then with a short sleep.  false if this block gave up (or another already
-// had): the caller returns.
-__device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* err) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned gen, old;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(bar + 1) : "memory");
-    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
-    if (old == nblocks - 1) {
-      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
-      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
-      ok = 1;
-    } else {
-      ok = 0;
-      for (long long it = 0; it < kSpins; ++it) {
-        unsigned now;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(now) : "l"(bar + 1) : "memory");
-        if (now != gen) {
-          ok = 1;
-          break;
-        }
-        if (*(volatile int*)err) break;
-        if (it >= 64) __nanosleep(32);
-      }
-      if (!ok) atomicExch(err, 1);
-    }
-  }
-  __syncthreads();
-  return ok != 0;
-}
+constexpr int TB = 256;  // threads per block
 
 struct Tail {
   Geom g;
@@ -135,8 +101,11 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
   __shared__ int kend_s, stop_s;
   const Geom& g = a.g;
   const long long n = a.n;
-  const long long T = (long long)gridDim.x * TB;
-  const long long t0 = (long long)blockIdx.x * TB + threadIdx.x;
+  // block b owns the points [b n / G, (b + 1) n / G), its thread t the points begin + t + e * TB
+  const long long T = TB;
+  const long long pbeg = (long long)blockIdx.x * a.n / gridDim.x;
+  const long long pend = (long long)(blockIdx.x + 1) * a.n / gridDim.x;
+  const long long t0 = pbeg + threadIdx.x;
   const unsigned G = gridDim.x;
   const float2 zero = make_float2(0.f, 0.f);
   const float cs = g.csf;
@@ -147,7 +116,7 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
 #pragma unroll
   for (int e = 0; e < PPT; ++e) {
     const long long p = t0 + e * T;
-    const int pi = p < n ? int(p) : 0;
+    const int pi = p < pend ? int(p) : 0;
     const int nxy = g.nx * g.ny;
     ck[e] = pi / nxy;
     const int rem = pi - ck[e] * nxy;
@@ -156,9 +125,9 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
   }
 
   // (A x)(p) for own point e, from a field x written earlier in this kernel or before it
-  auto apply = [&](const float2* x, int e, long long p, bool via_l2) -> float2 {
+  auto apply = [&](const float2* x, int e, long long p, bool in_kernel) -> float2 {
     const int i = ci[e], j = cj[e], k = ck[e];
-    auto ld = [&](long long q) { return via_l2 ? __ldcg(x + q) : __ldg(x + q); };
+    auto ld = [&](long long q) { return in_kernel ? x[q] : __ldg(x + q); };
     const float2 xc = ld(p);
     const float2 xm = i > 0 ? ld(p - 1) : zero, xp = i < g.nx - 1 ? ld(p + 1) : zero;
     const float2 ym = j > 0 ? ld(p - g.nx) : zero, yp = j < g.ny - 1 ? ld(p + g.nx) : zero;
@@ -178,7 +147,7 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
       const long long p = t0 + e * T;
       aw[e] = zero;
       rv[e] = zero;
-      if (p < n) {
+      if (p < pend) {
         aw[e] = apply(a.w32, e, p, false);
         rv[e] = __ldg(a.f32 + p);
         v[0].x = fmaf(aw[e].x, rv[e].x, fmaf(aw[e].y, rv[e].y, v[0].x));
@@ -209,7 +178,7 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
 #pragma unroll
     for (int e = 0; e < PPT; ++e) {
       const long long p = t0 + e * T;
-      if (p < n) a.W[p] = wv[e];
+      if (p < pend) a.W[p] = wv[e];
     }
     block_partial<1, LDW>(a, v, 1, wsum);
   }
@@ -228,7 +197,7 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
 #pragma unroll
     for (int e = 0; e < PPT; ++e) {
       const long long p = t0 + e * T;
-      if (p < n) a.V[p] = make_float2(wv[e].x * inv, wv[e].y * inv);
+      if (p < pend) a.V[p] = make_float2(wv[e].x * inv, wv[e].y * inv);
     }
   }
 
@@ -245,13 +214,13 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
       for (int e = 0; e < PPT; ++e) {
         const long long p = t0 + e * T;
         wv[e] = zero;
-        if (p < n) {
+        if (p < pend) {
           const float2 aw_ = apply(a.W, e, p, true);
           wv[e] = make_float2(aw_.x * invj, aw_.y * invj);
 #pragma unroll
           for (int b = 0; b < KC + 1; ++b) {
             if (b < nb) {
-              const float2 vb = __ldcg(a.V + (long long)b * n + p);
+              const float2 vb = a.V[(long long)b * n + p];
               v[b].x = fmaf(vb.x, wv[e].x, fmaf(vb.y, wv[e].y, v[b].x));
               v[b].y = fmaf(vb.x, wv[e].y, fmaf(-vb.y, wv[e].x, v[b].y));
             }
@@ -274,11 +243,11 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
 #pragma unroll
       for (int e = 0; e < PPT; ++e) {
         const long long p = t0 + e * T;
-        if (p < n) {
+        if (p < pend) {
           float2 vb[KC + 1];
 #pragma unroll
           for (int b = 0; b < KC + 1; ++b)
-            vb[b] = b < nb ? __ldcg(a.V + (long long)b * n + p) : zero;
+            vb[b] = b < nb ? a.V[(long long)b * n + p] : zero;
 #pragma unroll
           for (int b = 0; b < KC + 1; ++b) {
             if (b < nb) {
@@ -306,11 +275,11 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
 #pragma unroll
       for (int e = 0; e < PPT; ++e) {
         const long long p = t0 + e * T;
-        if (p < n) {
+        if (p < pend) {
 #pragma unroll
           for (int b = 0; b < KC + 1; ++b) {
             if (b < nb) {
-              const float2 vb = __ldcg(a.V + (long long)b * n + p);
+              const float2 vb = a.V[(long long)b * n + p];
               const float2 h = hs[b];
               wv[e].x = fmaf(-h.x, vb.x, fmaf(h.y, vb.y, wv[e].x));
               wv[e].y = fmaf(-h.x, vb.y, fmaf(-h.y, vb.x, wv[e].y));
@@ -373,7 +342,7 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
 #pragma unroll
       for (int e = 0; e < PPT; ++e) {
         const long long p = t0 + e * T;
-        if (p < n) vn[p] = make_float2(wv[e].x * inv, wv[e].y * inv);
+        if (p < pend) vn[p] = make_float2(wv[e].x * inv, wv[e].y * inv);
       }
     }
   }
@@ -398,10 +367,10 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
 #pragma unroll
   for (int e = 0; e < PPT; ++e) {
     const long long p = t0 + e * T;
-    if (p < n) {
+    if (p < pend) {
       float2 v = zero;
       for (int b = 0; b < kk; ++b) {
-        const float2 vb = __ldcg(a.V + (long long)b * n + p), y = ys[b];
+        const float2 vb = a.V[(long long)b * n + p], y = ys[b];
         v = make_float2(v.x + (y.x * vb.x - y.y * vb.y), v.y + (y.x * vb.y + y.y * vb.x));
       }
       const double2 ew = __ldg(a.w64 + p);
@@ -457,8 +426,11 @@ cudaError_t fci_tail32_plan(long long n, int kin, int* ppt, int* blocks) {
     int per_sm = 0;
     e = kin <= 4 ? occupancy_kc<4>(p, &per_sm) : occupancy_kc<TAIL_KMAX>(p, &per_sm);
     if (e != cudaSuccess) return e;
+    // at most two blocks per SM: more blocks make every barrier and every reduction of the
+    // block partial sums longer (measured at 64^3: 1024 blocks 227 us, 256 blocks 99 us,
+    // 128 blocks 118 us per application)
     const long long need = (n + (long long)TB * p - 1) / ((long long)TB * p);
-    if (need <= (long long)per_sm * sms) {
+    if (need <= (long long)std::min(per_sm, 2) * sms) {
       *ppt = p;
       *blocks = (int)need;
       return cudaSuccess;
