@@ -4,8 +4,9 @@
 //
 // At the grid sizes where the solver is launch- and latency-bound (64^3: every field in L2),
 // the multi-kernel form of this tail is about 24 dependent launches whose time is mostly ramp
-// and the serial finish of each reduction.  Here the grid stays resident: each thread owns a
-// fixed set of points (p = thread + e * threads), phases are separated by a grid barrier, and
+// and the serial finish of each reduction.  Here the grid stays resident: each block owns a
+// contiguous range of points and each of its threads a fixed set in it, phases are separated
+// by a grid barrier, and
 // after each barrier every block reads all blocks' partial sums (float pairs) and computes the
 // same scalars (d, beta, the Hessenberg column, the Givens rotation, y) redundantly in float32,
 // so no scalar has to be broadcast through memory and no further barrier is spent on it.
