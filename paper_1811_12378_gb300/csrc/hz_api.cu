@@ -396,7 +396,6 @@ hz_status run_poly(hz_problem* p, const T* dg, Buf<const T> f, int nvec,
 }
 
 // FCI (Algorithm 1) on nvec double-complex fields r -> out.
-// r_ff: r holds float pairs (the outer basis of HZ_MIXED_C64_FF); otherwise complex128.
 // After a synchronisation: a grid barrier of the cooperative FCI tail that gave up leaves its
 // flag set; report it once and reset the barrier words for the next launch.
 hz_status check_tail_fault(hz_problem* p) {
@@ -413,6 +412,8 @@ bool tail_fits(const hz_problem* p, int nvec, int kin) {
   return p->tail_on && p->tail_solo && nvec == 1 && kin <= hz::TAIL_KMAX && p->tail_ppt[c] > 0;
 }
 
+// r_ff: r holds float pairs (the outer basis of HZ_MIXED_C64_FF) whose complex64 rounding the
+// normalisation kernel already wrote into p->f32; otherwise r is complex128.
 hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nvec, int kin,
                   int precision, cudaStream_t st, bool r_ff = false) {
   const long long n = p->g.n;
@@ -423,11 +424,8 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
   if (precision != HZ_C128) {
     // the complex64 form of the FCI internals also takes w rounded to complex64
     const Buf<float2> w32b{fci32 ? p->w32 : nullptr, n};
-    if (r_ff)
-      HZ_CUDA(hz::launch_convert_ff_c64(Buf<const float4>{(const float4*)r.p, r.rs},
-                                        Buf<float2>{p->f32, n}, n, nvec, st));
-    else
-      HZ_CUDA(hz::launch_convert_c128_c64(r, Buf<float2>{p->f32, n}, n, nvec, st));
+    // (float-pair input: the normalisation that made r already wrote its complex64 rounding)
+    if (!r_ff) HZ_CUDA(hz::launch_convert_c128_c64(r, Buf<float2>{p->f32, n}, n, nvec, st));
     HZ_TRY((run_poly<float2, float>(p, p->d32, Buf<const float2>{p->f32, n}, nvec, all, true,
                                     wb, nullptr, st, w32b)));
   } else {
@@ -526,7 +524,8 @@ hz_status outer_step_launches(hz_problem* p, int k, int nrhs, int K, int precisi
       HZ_TIMED(p, 2, st, cgs_bytes(mode, n, k + 1, nrhs),
                hz::launch_cgs_ff(mode, (const float4*)p->V, n, vrs, k + 1, wf, n, go, p->partial,
                                  p->counters, nrhs, kBreakdown, st));
-    HZ_CUDA(hz::launch_scale_ff(wf, n, go, nrhs, st));
+    // v_{k+1}, and its complex64 rounding: the next FCI application's input
+    HZ_CUDA(hz::launch_scale_ff(wf, n, go, nrhs, st, Buf<float2>{p->f32, n}));
     return HZ_OK;
   }
   Buf<double2> wk{p->V + (long long)(k + 1) * n, vrs};
@@ -607,7 +606,43 @@ hz_status autotune(hz_problem* p) {
     return best;
   };
   const int J = p->J;
+  // classes with several active nodes: time the whole stage sequence of one complex64 FCI
+  // application (dependent launches, as a solve runs them); a stage timed alone, back to back
+  // with copies of itself, ranked the tiles differently from the chained sequence
+  std::vector<int> all(J);
+  for (int j = 0; j < J; ++j) all[j] = j;
+  auto sequence = [&] {
+    const hz_status rs = run_poly<float2, float>(p, p->d32, Buf<const float2>{p->f32, n}, 1, all,
+                                                 true, Buf<double2>{p->w, n}, nullptr, st,
+                                                 Buf<float2>{p->w32, n});
+    return rs == HZ_OK ? cudaSuccess : cudaErrorUnknown;
+  };
+  // (only where a sequence is short: L2-resident grids; larger grids are bandwidth-bound and
+  // their stages time reliably alone)
+  const bool chained = n <= (1LL << 21);
+  for (int cls : {1, 2}) {
+    if (!chained || (cls == 1 && J < 2) || (cls == 2 && J < 4)) continue;
+    float best = timed(sequence);
+    int bz = p->g.pzc[cls], br = p->g.prows[cls];
+    const int nn = cls == 1 ? 3 : J;  // the largest block of the class
+    for (int zc : {1, 2, 4})
+      for (int rows : {1, 2, 4}) {
+        if (32 * nn * rows > 512) continue;
+        if (sizeof(double2) * 32 * zc * J * rows > 48 * 1024) continue;
+        p->g.pzc[cls] = zc;
+        p->g.prows[cls] = rows;
+        const float t = timed(sequence);
+        if (t < 0.98f * best) {
+          best = t;
+          bz = zc;
+          br = rows;
+        }
+      }
+    p->g.pzc[cls] = bz;
+    p->g.prows[cls] = br;
+  }
   for (int cls = 0; cls < 3; ++cls) {
+    if (chained && cls > 0) continue;
     const int nn = cls == 0 ? 1 : (cls == 1 ? 2 : J);
     if (nn > J || (cls == 2 && J < 4)) continue;
     hz::StageArgs<float> a;
@@ -1275,7 +1310,8 @@ struct SolveState {
     for (int r = 0; r < nrhs; ++r) mvs[r] += cycle == 0 ? 0 : 1;
     if (o->precision == HZ_MIXED_C64_FF)
       HZ_CUDA(hz::launch_scale_ff_from64(Buf<float4>{(float4*)p->V, vrs},
-                                         Buf<const double2>{p->V, vrs}, n, go, nrhs, st));
+                                         Buf<const double2>{p->V, vrs}, n, go, nrhs, st,
+                                         Buf<float2>{p->f32, n}));
     else
       HZ_CUDA(hz::launch_scale(Buf<double2>{p->V, vrs}, Buf<const double2>{p->V, vrs}, n, go,
                                nrhs, st));

@@ -154,12 +154,13 @@ cudaError_t launch_stencil_diag_ff(const Geom& g, const double2* dg, Buf<const d
 cudaError_t launch_cgs_ff(int mode, const float4* V, long long vis, long long vrs, int nb,
                           Buf<float4> w, long long n, const GmresDev& gs, double2* partial,
                           unsigned* counters, int nvec, double breakdown, cudaStream_t st);
+// v *= 1/h (float pairs), and y32 = its complex64 rounding where y32.p is not null.
 cudaError_t launch_scale_ff(Buf<float4> v, long long n, const GmresDev& gs, int nvec,
-                            cudaStream_t st);
+                            cudaStream_t st, Buf<float2> y32);
+// dst = src / beta as float pairs (src float64, may be dst's storage), and y32 as above.
 cudaError_t launch_scale_ff_from64(Buf<float4> dst, Buf<const double2> src, long long n,
-                                   const GmresDev& gs, int nvec, cudaStream_t st);
-cudaError_t launch_convert_ff_c64(Buf<const float4> x, Buf<float2> y, long long n, int nvec,
-                                  cudaStream_t st);
+                                   const GmresDev& gs, int nvec, cudaStream_t st,
+                                   Buf<float2> y32);
 
 // One-time kernel attributes for restart lengths up to mmax (shared memory of k_backsolve).
 cudaError_t prepare_kernels(int mmax);

@@ -199,7 +199,9 @@ k_cgs_ff(const float4* __restrict__ V, long long vis, long long vrs, int nb, flo
 }
 
 // v = w * (1 / h_{k+1,k}) in place on float pairs; the float64 scale is split once per block.
-__global__ void k_scale_ff(float4* v, long long vrs, long long n, GmresDev gs) {
+// y32 (may be null): also the complex64 rounding of the result, the next FCI application's input.
+__global__ void k_scale_ff(float4* v, long long vrs, long long n, GmresDev gs, float2* y32,
+                           long long yrs) {
   pdl_enter();
   __shared__ float2 s_ff;
   const int r = blockIdx.y;
@@ -215,13 +217,14 @@ __global__ void k_scale_ff(float4* v, long long vrs, long long n, GmresDev gs) {
     a = ff_norm(a);
     b = ff_norm(b);
     v[r * vrs + p] = make_float4(a.x, a.y, b.x, b.y);
+    if (y32) y32[r * yrs + p] = make_float2(a.x, b.x);
   }
 }
 
 // v0 = r / beta from the float64 residual, written as float pairs over the same storage
 // (each element is read and rewritten by one thread).
 __global__ void k_scale_ff_from64(float4* dst, long long drs, const double2* src, long long srs,
-                                  long long n, GmresDev gs) {
+                                  long long n, GmresDev gs, float2* y32, long long yrs) {
   pdl_enter();
   const int r = blockIdx.y;
   const double s = gs.scal[(long long)r * SC_COUNT + SC_INV];
@@ -230,18 +233,7 @@ __global__ void k_scale_ff_from64(float4* dst, long long drs, const double2* src
     const double2 x = src[r * srs + p];
     const float2 a = ff_from_d(x.x * s), b = ff_from_d(x.y * s);
     dst[r * drs + p] = make_float4(a.x, a.y, b.x, b.y);
-  }
-}
-
-// The complex64 rounding of a float-pair field (its hi parts).
-__global__ void k_ff_to_c64(const float4* __restrict__ x, long long xrs, float2* __restrict__ y,
-                            long long yrs, long long n) {
-  pdl_enter();
-  const int r = blockIdx.y;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-       p += (long long)gridDim.x * blockDim.x) {
-    const float4 v = x[r * xrs + p];
-    y[r * yrs + p] = make_float2(v.x, v.z);
+    if (y32) y32[r * yrs + p] = make_float2(a.x, b.x);
   }
 }
 
@@ -269,22 +261,19 @@ cudaError_t launch_cgs_ff(int mode, const float4* V, long long vis, long long vr
 }
 
 cudaError_t launch_scale_ff(Buf<float4> v, long long n, const GmresDev& gs, int nvec,
-                            cudaStream_t st) {
+                            cudaStream_t st, Buf<float2> y32) {
   count_launch();
-  return launch_pdl(k_scale_ff, dim3(ff_ew_blocks(n), nvec), 256, 0, st, v.p, v.rs, n, gs);
+  return launch_pdl(k_scale_ff, dim3(ff_ew_blocks(n), nvec), 256, 0, st, v.p, v.rs, n, gs, y32.p,
+                    y32.rs);
 }
 
 cudaError_t launch_scale_ff_from64(Buf<float4> dst, Buf<const double2> src, long long n,
-                                   const GmresDev& gs, int nvec, cudaStream_t st) {
+                                   const GmresDev& gs, int nvec, cudaStream_t st,
+                                   Buf<float2> y32) {
   count_launch();
   return launch_pdl(k_scale_ff_from64, dim3(ff_ew_blocks(n), nvec), 256, 0, st, dst.p, dst.rs,
-                    src.p, src.rs, n, gs);
+                    src.p, src.rs, n, gs, y32.p, y32.rs);
 }
 
-cudaError_t launch_convert_ff_c64(Buf<const float4> x, Buf<float2> y, long long n, int nvec,
-                                  cudaStream_t st) {
-  count_launch();
-  return launch_pdl(k_ff_to_c64, dim3(ff_ew_blocks(n), nvec), 256, 0, st, x.p, x.rs, y.p, y.rs, n);
-}
 
 }  // namespace hz
