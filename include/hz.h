@@ -231,6 +231,15 @@ hz_status hz_profile_enable(hz_problem* p, int on);
  * hz_solve_batched, always use the per-piece kernels.  A barrier that waits longer than about
  * a second gives up, and the next hz_solve on the problem returns HZ_ERR_CUDA. */
 hz_status hz_problem_fused_tail(hz_problem* p, int on);
+
+/* Selects how HZ_MIXED_C64_FF runs each outer Arnoldi step of FGMRES (Section 3: w = A z_k,
+ * the two classical Gram-Schmidt passes against v_0..v_k, the Givens rotation of the new
+ * Hessenberg column, v_{k+1} = w / h_{k+1,k}) for a single right-hand side: on = 1 (the
+ * default) as one cooperative kernel with three grid-wide barriers, where the grid fits on the
+ * device; on = 0 as five kernels.  The two differ only in the grouping of the float-pair global
+ * sums.  Several right-hand sides per call, and hz_solve_batched, always use the five kernels.
+ * A barrier timeout is reported as for hz_problem_fused_tail. */
+hz_status hz_problem_fused_arnoldi(hz_problem* p, int on);
 hz_status hz_profile_read(hz_problem* p, int cls, long long* launches, double* ms,
                           double* bytes);
 

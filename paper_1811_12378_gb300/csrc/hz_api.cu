@@ -117,6 +117,10 @@ struct hz_problem {
   bool tail_used = false;
   int tail_ppt[2] = {0, 0}, tail_blocks[2] = {0, 0};
   unsigned* tail_bar = nullptr;  // [0] arrivals, [1] generation, [2] error flag
+  // the outer float-pair Arnoldi step as one cooperative kernel (hz_arnoldi_ff.cu), sharing
+  // the barrier words and the error flag of the FCI tail (the two never run concurrently)
+  bool arn_on = true;  // hz_problem_fused_arnoldi
+  int arn_ppt = 0, arn_blocks = 0;
 
   void drop_graphs() {
     for (cudaGraphExec_t g : step_graphs)
@@ -404,12 +408,16 @@ hz_status check_tail_fault(hz_problem* p) {
   HZ_CUDA(cudaMemcpy(w, p->tail_bar, sizeof(w), cudaMemcpyDeviceToHost));
   if (w[2] == 0) return HZ_OK;
   HZ_CUDA(cudaMemset(p->tail_bar, 0, sizeof(unsigned) * 4));
-  return fail(HZ_ERR_CUDA, "a grid barrier of the cooperative FCI kernel timed out");
+  return fail(HZ_ERR_CUDA, "a grid barrier of a cooperative kernel timed out");
 }
 
 bool tail_fits(const hz_problem* p, int nvec, int kin) {
   const int c = kin <= 4 ? 0 : 1;
   return p->tail_on && p->tail_solo && nvec == 1 && kin <= hz::TAIL_KMAX && p->tail_ppt[c] > 0;
+}
+
+bool arnoldi_fits(const hz_problem* p, int nvec) {
+  return p->arn_on && p->tail_solo && nvec == 1 && p->arn_ppt > 0;
 }
 
 // r_ff: r holds float pairs (the outer basis of HZ_MIXED_C64_FF) whose complex64 rounding the
@@ -517,6 +525,15 @@ hz_status outer_step_launches(hz_problem* p, int k, int nrhs, int K, int precisi
   if (ff) {
     // the float-pair Arnoldi: w = A z_k stored as float pairs in v_{k+1}'s slot
     Buf<float4> wf{(float4*)(p->V + (long long)(k + 1) * n), vrs};
+    if (arnoldi_fits(p, nrhs)) {
+      // one cooperative launch: stencil, CGS2 (V read once per pass), Givens, normalisation
+      HZ_TIMED(p, 2, st, 16.0 * n * (3.0 + 3.0 * (k + 1)) + 8.0 * n,
+               hz::launch_arnoldi_ff(p->g, p->d64, zk.p, (const float4*)p->V, wf.p, p->f32, go,
+                                     p->partial, p->tail_bar, (int*)(p->tail_bar + 2), n, k + 1,
+                                     kBreakdown, p->arn_ppt, p->arn_blocks, st));
+      p->tail_used = true;
+      return HZ_OK;
+    }
     HZ_TIMED(p, 1, st, 16.0 * 3 * n * nrhs,
              (hz::launch_stencil_diag_ff(p->g, p->d64, Buf<const double2>{zk.p, zrs}, wf, nrhs,
                                          st)));
@@ -545,7 +562,8 @@ hz_status outer_step_launches(hz_problem* p, int k, int nrhs, int K, int precisi
 hz_status outer_step(hz_problem* p, int k, int nrhs, int K, int precision, cudaStream_t st) {
   if (p->prof_on || !p->graphs_on) return outer_step_launches(p, k, nrhs, K, precision, st);
   const long long key =
-      (((long long)nrhs * 4 + precision) * 1024 + K) * 2 + (tail_fits(p, nrhs, K) ? 1 : 0);
+      ((((long long)nrhs * 4 + precision) * 1024 + K) * 2 + (tail_fits(p, nrhs, K) ? 1 : 0)) * 2 +
+      (arnoldi_fits(p, nrhs) ? 1 : 0);
   if (p->graph_key != key) {
     p->drop_graphs();
     p->graph_key = key;
@@ -864,20 +882,24 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
     cudaError_t pe = hz::fci_tail32_plan(n, std::min(K, 4), &p->tail_ppt[0], &p->tail_blocks[0]);
     if (pe == cudaSuccess && K > 4)
       pe = hz::fci_tail32_plan(n, hz::TAIL_KMAX, &p->tail_ppt[1], &p->tail_blocks[1]);
+    if (pe == cudaSuccess) pe = hz::arnoldi_ff_plan(n, M, &p->arn_ppt, &p->arn_blocks);
     if (pe != cudaSuccess) {
       delete p;
       return cuda_fail(pe, "cooperative kernel plans");
     }
   }
-  // block partial sums: linear reduction kernels (>= 256 points a block), the fused stencil
-  // reductions (32 x 4 x 4 tiles, ragged at the edges) and the cooperative FCI tail
+  // block partial sums (16 bytes each): linear reduction kernels (>= 256 points a block) and
+  // the fused stencil reductions (32 x 4 x 4 tiles, ragged at the edges), (slots x blocks) per
+  // rhs; the cooperative kernels, two alternating areas of their slots x blocks
   const long long nblk = std::max<long long>(
-      std::max<long long>((n + hz::RED_MIN_CHUNK - 1) / hz::RED_MIN_CHUNK,
-                          (long long)((grid->nx + 31) / 32) * ((grid->ny + 3) / 4) *
-                              ((grid->nz + 3) / 4)),
-      std::max(p->tail_blocks[0], p->tail_blocks[1]));
+      (n + hz::RED_MIN_CHUNK - 1) / hz::RED_MIN_CHUNK,
+      (long long)((grid->nx + 31) / 32) * ((grid->ny + 3) / 4) * ((grid->nz + 3) / 4));
   const int slots = std::max(M, K) + 2;
-  if ((s = dalloc(p, (void**)&p->partial, sizeof(double2) * (size_t)nblk * slots * R)) != HZ_OK)
+  const long long npart = std::max(
+      {nblk * slots * R,
+       2LL * (hz::TAIL_KMAX + 2) * std::max(p->tail_blocks[0], p->tail_blocks[1]),
+       2LL * (M + 2) * p->arn_blocks});
+  if ((s = dalloc(p, (void**)&p->partial, sizeof(double2) * (size_t)npart)) != HZ_OK)
     return bail(s);
   if ((s = dalloc(p, (void**)&p->counters, sizeof(unsigned) * R)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->tail_bar, sizeof(unsigned) * 4)) != HZ_OK) return bail(s);
@@ -1015,6 +1037,13 @@ hz_status hz_problem_fused_tail(hz_problem* p, int on) {
   HZ_TRY(check_problem(p));
   if (p->tail_on != (on != 0)) p->drop_graphs();
   p->tail_on = on != 0;
+  return HZ_OK;
+}
+
+hz_status hz_problem_fused_arnoldi(hz_problem* p, int on) {
+  HZ_TRY(check_problem(p));
+  if (p->arn_on != (on != 0)) p->drop_graphs();
+  p->arn_on = on != 0;
   return HZ_OK;
 }
 

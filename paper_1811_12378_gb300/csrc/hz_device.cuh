@@ -185,6 +185,37 @@ __device__ __forceinline__ void stencil32_column(const Geom& g, const float2* __
   }
 }
 
+// ---------------------------------------------------------------- float-pair complex fields
+__device__ __forceinline__ float2 re_of(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 im_of(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// Butterfly reduce-scatter of 8 complex float-pair partials over a warp (the lane map of
+// warp_reduce8 in hz_kernels.cu): lane l with (l & 3) == 0 ends with the sum of vector
+// ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 + ((l >> 2) & 1).
+__device__ __forceinline__ float4 warp_reduce8_ff(float4 (&a)[8], int lane) {
+  float4 b4[4], b2[2];
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const float4 keep = h16 ? a[4 + t] : a[t];
+    const float4 give = h16 ? a[t] : a[4 + t];
+    b4[t] = ffc_add(keep, shfl_xor4(give, 16));
+  }
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const float4 keep = h8 ? b4[2 + t] : b4[t];
+    const float4 give = h8 ? b4[t] : b4[2 + t];
+    b2[t] = ffc_add(keep, shfl_xor4(give, 8));
+  }
+  const float4 keep = h4 ? b2[1] : b2[0];
+  const float4 give = h4 ? b2[0] : b2[1];
+  float4 x = ffc_add(keep, shfl_xor4(give, 4));
+  x = ffc_add(x, shfl_xor4(x, 2));
+  x = ffc_add(x, shfl_xor4(x, 1));
+  return x;
+}
+
 // Butterfly reduction of 8 per-lane float2 partials over a warp (same lane map as the float64
 // version in hz_kernels.cu): lane l with (l & 3) == 0 ends with the sum of vector
 // ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 + ((l >> 2) & 1).
@@ -345,41 +376,76 @@ __device__ __forceinline__ double2 warp_sum_partials(const double2* part, int si
 }
 
 // Givens step for column k of rhs r (Saad's GMRES with complex rotations), called by every
-// thread of one block.  The new Hessenberg column and the previous rotations are staged in
-// shared memory first, so the sequential rotation sweep of thread 0 does not wait on a
-// global-memory round trip per rotation.
+// thread of one block; warp 0 does the work.
+//
+// Applying rotations 0..k-1 to the new column h is a chain through one value: with t_0 = h_0,
+// rotation i leaves R_i = c_i t_i + s_i h_{i+1} and passes on t_{i+1} = -conj(s_i) t_i +
+// c_i h_{i+1}.  That recurrence is affine in t, so the warp evaluates it as a prefix scan of
+// the maps t -> a t + b (lane l composes a chunk of ceil(k/32) consecutive rotations, a
+// Kogge-Stone scan over the lanes gives each chunk its incoming t, then the chunks produce
+// their R_i): about 10 + 2 ceil(k/32) dependent float64 steps in place of 2k, which matters on
+// a GPU whose float64 pipe spends 64 cycles on each warp instruction.  Since |a| = |s_i| <= 1
+// the composed maps do not grow; the rounding differs from the sequential sweep only in order.
 constexpr int kGivMax = 130;  // restart lengths up to 128
 
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {  // a b + c
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+
+__device__ __forceinline__ double2 shfl_up2(double2 v, int o) {
+  return make_double2(__shfl_up_sync(0xffffffffu, v.x, o), __shfl_up_sync(0xffffffffu, v.y, o));
+}
+
 __device__ void givens_column(const GmresDev& gs, int r, int k, double brk) {
-  __shared__ double2 sR[kGivMax];
-  __shared__ double scc[kGivMax];
-  __shared__ double2 sss[kGivMax];
+  __syncthreads();  // the caller's stores of h1, h2 and the norm come first
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
   const int M = gs.mmax;
   const double2* h1 = gs.h1 + (long long)r * (M + 2);
   const double2* h2 = gs.h2 + (long long)r * (M + 2);
   const double* cc = gs.cc + (long long)r * M;
   const double2* ss = gs.ss + (long long)r * M;
-  for (int i = threadIdx.x; i <= k; i += blockDim.x) {
-    sR[i] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
-    if (i < k) {
-      scc[i] = cc[i];
-      sss[i] = ss[i];
+  double2* R = gs.R + (long long)r * (M + 1) * M + (long long)k * (M + 1);
+  auto hcol = [&](int i) { return make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y); };
+  const int q = (k + 31) / 32;  // rotations per lane
+  const int i0 = min(lane * q, k), i1 = min(i0 + q, k);
+  // this lane's maps composed: t -> A t + B
+  double2 A = make_double2(1.0, 0.0), B = make_double2(0.0, 0.0);
+  for (int i = i0; i < i1; ++i) {
+    const double c = cc[i];
+    const double2 s = ss[i], al = make_double2(-s.x, s.y), hn1 = hcol(i + 1);
+    B = cfma(al, B, make_double2(c * hn1.x, c * hn1.y));
+    A = cmul(al, A);
+  }
+  // inclusive scan over the lanes (earlier lanes' maps applied first), then shifted by one
+  for (int o = 1; o < 32; o <<= 1) {
+    const double2 Ap = shfl_up2(A, o), Bp = shfl_up2(B, o);
+    if (lane >= o) {
+      B = cfma(A, Bp, B);
+      A = cmul(A, Ap);
     }
   }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
+  double2 Ax = shfl_up2(A, 1), Bx = shfl_up2(B, 1);
+  if (lane == 0) {
+    Ax = make_double2(1.0, 0.0);
+    Bx = make_double2(0.0, 0.0);
+  }
+  double2 t = cfma(Ax, hcol(0), Bx);  // t_{i0}
+  for (int i = i0; i < i1; ++i) {
+    const double c = cc[i];
+    const double2 s = ss[i], hn1 = hcol(i + 1);
+    R[i] = cfma(s, hn1, make_double2(c * t.x, c * t.y));
+    t = cfma(make_double2(-s.x, s.y), t, make_double2(c * hn1.x, c * hn1.y));
+  }
+  // the lane holding t_k: the one whose chunk ends at rotation k - 1 (lane 0 when k = 0)
+  const int last = k == 0 ? 0 : (k - 1) / q;
+  if (lane != last) return;
   double* sc = gs.scal + (long long)r * SC_COUNT;
   const double hn = sqrt(gs.nrm[2 * r].x);
   const double wn = sqrt(h1[k + 1].x);
-  for (int i = 0; i < k; ++i) {
-    const double c = scc[i];
-    const double2 s = sss[i], a = sR[i], b = sR[i + 1];
-    sR[i] = cadd(mk(c * a.x, c * a.y), cmul(s, b));
-    sR[i + 1] = cadd(mk(-(s.x * a.x + s.y * a.y), -(s.x * a.y - s.y * a.x)), mk(c * b.x, c * b.y));
-  }
   double c;
   double2 s;
-  const double2 a = sR[k];
+  const double2 a = t;
   if (hn == 0.0) {
     c = 1.0;
     s = make_double2(0.0, 0.0);
@@ -388,13 +454,12 @@ __device__ void givens_column(const GmresDev& gs, int r, int k, double brk) {
     s = make_double2(1.0, 0.0);
   } else {
     const double ra = hypot(a.x, a.y);
-    const double rr = hypot(ra, hn);
-    c = ra / rr;
-    s = make_double2(a.x / ra * hn / rr, a.y / ra * hn / rr);
+    const double irr = 1.0 / hypot(ra, hn);
+    c = ra * irr;
+    const double f = hn * irr / ra;
+    s = make_double2(a.x * f, a.y * f);
   }
-  sR[k] = cadd(mk(c * a.x, c * a.y), mk(s.x * hn, s.y * hn));
-  double2* R = gs.R + (long long)r * (M + 1) * M + (long long)k * (M + 1);
-  for (int i = 0; i <= k; ++i) R[i] = sR[i];
+  R[k] = cadd(mk(c * a.x, c * a.y), mk(s.x * hn, s.y * hn));
   R[k + 1] = make_double2(0.0, 0.0);
   gs.cc[(long long)r * M + k] = c;
   gs.ss[(long long)r * M + k] = s;
@@ -410,6 +475,174 @@ __device__ void givens_column(const GmresDev& gs, int r, int k, double brk) {
   sc[SC_INV] = brk_now ? 0.0 : 1.0 / hn;
   gs.kend[r] = k + 1;
   if (brk_now || est <= sc[SC_TOL]) gs.stopped[r] = 1;
+}
+
+// ---------------------------------------------------------------- float-pair Givens step
+// Double-float arithmetic after Dekker (1971): a value is hi + lo with |lo| <= half an ulp of
+// hi; products split exactly by an FMA, quotients and square roots by one correction step
+// from the float32 result.  About 48 significant bits; float32 instructions only.
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, e));
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ float2 ff_sub(float2 a, float2 b) { return ff_add(a, neg(b)); }
+__device__ __forceinline__ float2 ff_scale2(float2 a, float s) {  // s a power of two: exact
+  return make_float2(a.x * s, a.y * s);
+}
+// a / b: q1 = a.hi / b.hi, then the remainder a - q1 b (exact products) divided once more
+__device__ __forceinline__ float2 ff_div(float2 a, float2 b) {
+  const float q1 = __fdiv_rn(a.x, b.x);
+  const float2 r = ff_sub(a, ff_mul(b, make_float2(q1, 0.f)));
+  return fast_two_sum(q1, __fdiv_rn(r.x, b.x));
+}
+// sqrt(x), x >= 0: y = sqrt(x.hi) rounded, corrected by (x - y^2) / (2 y) with y^2 exact
+__device__ __forceinline__ float2 ff_sqrt(float2 x) {
+  if (!(x.x > 0.f)) return make_float2(0.f, 0.f);
+  const float y = __fsqrt_rn(x.x);
+  const float p = __fmul_rn(y, y);
+  const float e = __fmaf_rn(y, y, -p);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(x.x, p), e), x.y);
+  return fast_two_sum(y, __fdiv_rn(r, __fmul_rn(2.f, y)));
+}
+__device__ __forceinline__ bool ff_le(float2 a, float2 b) {
+  return a.x < b.x || (a.x == b.x && a.y <= b.y);
+}
+// complex float pairs, float4 (re.hi, re.lo, im.hi, im.lo)
+__device__ __forceinline__ float4 ffc(float2 re, float2 im) {
+  return make_float4(re.x, re.y, im.x, im.y);
+}
+__device__ __forceinline__ float4 ffc_mul(float4 a, float4 b) {
+  const float2 ar = re_of(a), ai = im_of(a), br = re_of(b), bi = im_of(b);
+  return ffc(ff_sub(ff_mul(ar, br), ff_mul(ai, bi)), ff_add(ff_mul(ar, bi), ff_mul(ai, br)));
+}
+__device__ __forceinline__ float4 ffc_rmul(float2 c, float4 a) {  // real c times complex a
+  return ffc(ff_mul(c, re_of(a)), ff_mul(c, im_of(a)));
+}
+__device__ __forceinline__ float4 ffc_mconj(float4 s) {  // -conj(s)
+  return make_float4(-s.x, -s.y, s.z, s.w);
+}
+__device__ __forceinline__ float4 ffc_from_d(double2 v) {
+  return ffc(ff_from_d(v.x), ff_from_d(v.y));
+}
+__device__ __forceinline__ float4 shfl_up4(float4 v, int o) {
+  return make_float4(__shfl_up_sync(0xffffffffu, v.x, o), __shfl_up_sync(0xffffffffu, v.y, o),
+                     __shfl_up_sync(0xffffffffu, v.z, o), __shfl_up_sync(0xffffffffu, v.w, o));
+}
+// 2^-e with 2^e near the largest of the given magnitudes (0 -> 1): exact rescaling that keeps
+// squares inside the float32 range
+__device__ __forceinline__ float ff_pow2_scale(float m) {
+  return m > 0.f ? ldexpf(1.f, -ilogbf(m)) : 1.f;
+}
+__device__ __forceinline__ float2 ffc_abs(float4 v) {
+  const float sc = ff_pow2_scale(fmaxf(fabsf(v.x), fabsf(v.z)));
+  const float2 re = ff_scale2(re_of(v), sc), im = ff_scale2(im_of(v), sc);
+  return ff_scale2(ff_sqrt(ff_add(ff_mul(re, re), ff_mul(im, im))), 1.f / sc);
+}
+
+// The breakdown test and the scale of the next basis vector from ||w||^2 after (hn2) and
+// before (wn2) the orthogonalisation: *inv = 1 / h_{k+1,k}, or 0 when h_{k+1,k} <= brk ||w||
+// (the test of the float64 Givens step).  Every caller gets the same bits from the same sums.
+__device__ __forceinline__ bool ff_step_inv(float2 hn2, float2 wn2, float brk, float2* hn,
+                                            float2* inv) {
+  *hn = ff_sqrt(hn2);
+  const float2 wn = ff_sqrt(wn2);
+  const bool brk_now = ff_le(*hn, ff_mul(make_float2(brk, 0.f), wn));
+  *inv = brk_now ? make_float2(0.f, 0.f) : ff_div(make_float2(1.f, 0.f), *hn);
+  return brk_now;
+}
+
+// Givens step for column k of rhs r in float pairs (the float-pair outer Arnoldi form), called
+// by every thread of one block; warp 0 works.  col[0..k] is the new Hessenberg column h1 + h2
+// (shared memory, float pairs), hn2 / wn2 as for ff_step_inv.  The sweep over the previous
+// rotations is the prefix scan of givens_column, here on the float32 pipes (a float64
+// instruction issues at 1/64 of their rate).  The rotations are kept as float pairs in the
+// storage of gs.cc / gs.ss (a float2 per cosine, a float4 per sine); R, g and the scalars are
+// written in float64.
+__device__ void givens_column_ff(const GmresDev& gs, int r, int k, double brk, const float4* col,
+                                 float2 hn2, float2 wn2) {
+  __syncthreads();  // col, and the caller's stores, come first
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  const int M = gs.mmax;
+  float2* ccf = reinterpret_cast<float2*>(gs.cc + (long long)r * M);
+  float4* ssf = reinterpret_cast<float4*>(gs.ss + (long long)r * M);
+  double2* R = gs.R + (long long)r * (M + 1) * M + (long long)k * (M + 1);
+  const float4 one = make_float4(1.f, 0.f, 0.f, 0.f), zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int q = (k + 31) / 32;
+  const int i0 = min(lane * q, k), i1 = min(i0 + q, k);
+  float4 A = one, B = zero4;
+  for (int i = i0; i < i1; ++i) {
+    const float2 c = ccf[i];
+    const float4 al = ffc_mconj(ssf[i]);
+    B = ffc_add(ffc_mul(al, B), ffc_rmul(c, col[i + 1]));
+    A = ffc_mul(al, A);
+  }
+  for (int o = 1; o < 32; o <<= 1) {
+    const float4 Ap = shfl_up4(A, o), Bp = shfl_up4(B, o);
+    if (lane >= o) {
+      B = ffc_add(ffc_mul(A, Bp), B);
+      A = ffc_mul(A, Ap);
+    }
+  }
+  float4 Ax = shfl_up4(A, 1), Bx = shfl_up4(B, 1);
+  if (lane == 0) {
+    Ax = one;
+    Bx = zero4;
+  }
+  float4 t = ffc_add(ffc_mul(Ax, col[0]), Bx);  // t_{i0}
+  for (int i = i0; i < i1; ++i) {
+    const float2 c = ccf[i];
+    const float4 s = ssf[i], hn1 = col[i + 1];
+    R[i] = d_from_ffc(ffc_add(ffc_mul(s, hn1), ffc_rmul(c, t)));
+    t = ffc_add(ffc_mul(ffc_mconj(s), t), ffc_rmul(c, hn1));
+  }
+  const int last = k == 0 ? 0 : (k - 1) / q;
+  if (lane != last) return;
+  double* sc = gs.scal + (long long)r * SC_COUNT;
+  float2 hn, inv;
+  const bool brk_now = ff_step_inv(hn2, wn2, float(brk), &hn, &inv);
+  float2 c;
+  float4 s;
+  const float4 a = t;
+  if (hn.x == 0.f) {
+    c = make_float2(1.f, 0.f);
+    s = zero4;
+  } else if (a.x == 0.f && a.z == 0.f) {
+    c = make_float2(0.f, 0.f);
+    s = one;
+  } else {
+    // c = |a| / rho, s = (a / |a|) hn / rho, rho = sqrt(|a|^2 + hn^2), from values rescaled
+    // by a power of two (the ratios do not change)
+    const float sc2 = ff_pow2_scale(fmaxf(fmaxf(fabsf(a.x), fabsf(a.z)), hn.x));
+    const float2 ar = ff_scale2(re_of(a), sc2), ai = ff_scale2(im_of(a), sc2);
+    const float2 hs = ff_scale2(hn, sc2);
+    const float2 ra2 = ff_add(ff_mul(ar, ar), ff_mul(ai, ai));
+    const float2 ra = ff_sqrt(ra2);
+    const float2 rho = ff_sqrt(ff_add(ra2, ff_mul(hs, hs)));
+    c = ff_div(ra, rho);
+    const float2 f = ff_div(hs, ff_mul(ra, rho));
+    s = ffc(ff_mul(ar, f), ff_mul(ai, f));
+  }
+  // R_kk = c a + s hn
+  const float4 rkk = ffc_add(ffc_rmul(c, a), ffc(ff_mul(re_of(s), hn), ff_mul(im_of(s), hn)));
+  ccf[k] = c;
+  ssf[k] = s;
+  double2* gg = gs.g + (long long)r * (M + 1);
+  const float4 gk = ffc_from_d(gg[k]);
+  const float4 gk1 = ffc_mul(ffc_mconj(s), gk);
+  const float2 est = ffc_abs(gk1);
+  R[k] = d_from_ffc(rkk);
+  R[k + 1] = make_double2(0.0, 0.0);
+  gg[k] = d_from_ffc(ffc_rmul(c, gk));
+  gg[k + 1] = d_from_ffc(gk1);
+  const double estd = d_from_ff(est);
+  sc[SC_EST] = estd;
+  sc[SC_HN] = d_from_ff(hn);
+  sc[SC_INV] = d_from_ff(inv);
+  gs.kend[r] = k + 1;
+  if (brk_now || estd <= sc[SC_TOL]) gs.stopped[r] = 1;
 }
 
 }  // namespace

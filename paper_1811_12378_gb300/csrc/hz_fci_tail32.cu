@@ -48,12 +48,21 @@ struct Tail {
   float brk;
 };
 
+// The partial sums of phase q live in half (q & 1) of the partial buffer, (KC + 2) slots of G
+// blocks each: a block that has passed barrier q + 1 writes phase q + 2 while no block can
+// still be reading phase q (every block finished that reduction before arriving at q + 1),
+// whereas one shared area would let a fast block overwrite sums a slow block is still adding.
+template <int KC>
+__device__ __forceinline__ float4* part_of(const Tail& a, int q) {
+  return a.part + (long long)(q & 1) * (KC + 2) * gridDim.x;
+}
+
 // Block partial of ns complex slots: the threads' values in v[0..ns) are summed over the warp
 // (butterfly, 8 at a time), over the block's warps as float pairs, and written to
 // part[s * G + block].
 // wsum has (TB / 32) rows of LDW entries.
 template <int NS, int LDW>
-__device__ __forceinline__ void block_partial(const Tail& a, float2 (&v)[NS], int ns,
+__device__ __forceinline__ void block_partial(float4* part, float2 (&v)[NS], int ns,
                                               float2* wsum) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -74,15 +83,15 @@ __device__ __forceinline__ void block_partial(const Tail& a, float2 (&v)[NS], in
   for (int s = threadIdx.x; s < ns; s += TB) {
     float4 t = ffc_of(wsum[s]);
     for (int w = 1; w < TB / 32; ++w) t = ffc_add(t, ffc_of(wsum[w * LDW + s]));
-    a.part[(long long)s * gridDim.x + blockIdx.x] = t;
+    part[(long long)s * gridDim.x + blockIdx.x] = t;
   }
 }
 
 // After the barrier: every block sums all blocks' partials of ns slots into hs[] (float32).
-__device__ __forceinline__ void grid_reduce(const Tail& a, int ns, float2* hs) {
+__device__ __forceinline__ void grid_reduce(const float4* part, int ns, float2* hs) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int s = warp; s < ns; s += TB / 32) {
-    const float4 t = warp_sum_partials_ff(a.part, s, (int)gridDim.x, lane);
+    const float4 t = warp_sum_partials_ff(part, s, (int)gridDim.x, lane);
     if (lane == 0) hs[s] = f_from_ffc(t);
   }
   __syncthreads();
@@ -156,10 +165,10 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
         v[1].x = fmaf(aw[e].x, aw[e].x, fmaf(aw[e].y, aw[e].y, v[1].x));
       }
     }
-    block_partial<2, LDW>(a, v, 2, wsum);
+    block_partial<2, LDW>(part_of<KC>(a, 0), v, 2, wsum);
   }
   if (!grid_sync(a.bar, G, a.err)) return;
-  grid_reduce(a, 2, hs);
+  grid_reduce(part_of<KC>(a, 0), 2, hs);
   if (threadIdx.x == 0) {
     const float den = hs[1].x;
     dsh = den != 0.f ? make_float2(hs[0].x / den, hs[0].y / den) : zero;
@@ -181,10 +190,10 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
       const long long p = t0 + e * T;
       if (p < pend) a.W[p] = wv[e];
     }
-    block_partial<1, LDW>(a, v, 1, wsum);
+    block_partial<1, LDW>(part_of<KC>(a, 1), v, 1, wsum);
   }
   if (!grid_sync(a.bar, G, a.err)) return;
-  grid_reduce(a, 1, hs);
+  grid_reduce(part_of<KC>(a, 1), 1, hs);
   if (threadIdx.x == 0) {
     const float beta = sqrtf(hs[0].x);
     gg[0] = make_float2(beta, 0.f);
@@ -232,10 +241,10 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
 #pragma unroll
       for (int s = 0; s < KC + 1; ++s)
         if (s == nb) v[s] = v[KC + 1];  // the norm goes to slot nb
-      block_partial<KC + 2, LDW>(a, v, nb + 1, wsum);
+      block_partial<KC + 2, LDW>(part_of<KC>(a, 3 * j + 2), v, nb + 1, wsum);
     }
     if (!grid_sync(a.bar, G, a.err)) return;
-    grid_reduce(a, nb + 1, h1s);
+    grid_reduce(part_of<KC>(a, 3 * j + 2), nb + 1, h1s);
     // w -= V h1, second pass h2 = V^H w
     {
       float2 v[KC + 1];
@@ -266,10 +275,10 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
           }
         }
       }
-      block_partial<KC + 1, LDW>(a, v, nb, wsum);
+      block_partial<KC + 1, LDW>(part_of<KC>(a, 3 * j + 3), v, nb, wsum);
     }
     if (!grid_sync(a.bar, G, a.err)) return;
-    grid_reduce(a, nb, hs);
+    grid_reduce(part_of<KC>(a, 3 * j + 3), nb, hs);
     // w -= V h2, ||w||^2
     {
       float2 v[1] = {zero};
@@ -290,7 +299,7 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
           a.W[p] = wv[e];  // every read of W in this step came before the first barrier
         }
       }
-      block_partial<1, LDW>(a, v, 1, wsum);
+      block_partial<1, LDW>(part_of<KC>(a, 3 * j + 4), v, 1, wsum);
     }
     // the Hessenberg column h1 + h2, with h2 kept before hs is overwritten
     if (threadIdx.x <= j) {
@@ -298,7 +307,7 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
       h1s[threadIdx.x] = make_float2(h1s[threadIdx.x].x + h2.x, h1s[threadIdx.x].y + h2.y);
     }
     if (!grid_sync(a.bar, G, a.err)) return;
-    grid_reduce(a, 1, hs);
+    grid_reduce(part_of<KC>(a, 3 * j + 4), 1, hs);
     if (threadIdx.x == 0) {
       // Givens step for column j (the same arithmetic as the multi-kernel float32 form)
       const float hn = sqrtf(hs[0].x), wn = sqrtf(h1s[nb].x);

@@ -184,11 +184,23 @@ constexpr int TAIL_KMAX = 16;
 cudaError_t fci_tail32_plan(long long n, int kin, int* ppt, int* blocks);
 // Steps 3-5 of Algorithm 1 for one right-hand side: d from A w32 and f32, inner GMRES(kin) on
 // V (kin + 1 fields; W: one scratch field), out = V y + d w64.  bar: 2 zeroed counters; err:
-// set on a barrier timeout.  n < 2^31.
+// set on a barrier timeout.  partial: at least 2 (TAIL_KMAX + 2) blocks float4.  n < 2^31.
 cudaError_t launch_fci_tail32(const Geom& g, const float2* dg, const float2* w32,
                               const float2* f32, const double2* w64, float2* V, float2* W,
                               double2* out,
                               double2* partial, unsigned* bar, int* err, long long n, int kin,
+                              double brk, int ppt, int blocks, cudaStream_t st);
+// ---- one outer float-pair Arnoldi step as one cooperative kernel (hz_arnoldi_ff.cu) ----
+// Points per thread and grid size for n points and restart length mmax; *ppt = 0 where the
+// grid cannot be co-resident or cooperative launch is unavailable.
+cudaError_t arnoldi_ff_plan(long long n, int mmax, int* ppt, int* blocks);
+// For one right-hand side and nb = k + 1 basis fields V (float pairs): w = A z (dg: float64
+// diagonal), CGS2 against V into gs.h1, gs.h2, gs.nrm, the Givens step of column k, and
+// vnext = w / h_{k+1,k} with its complex64 rounding y32.  Does nothing once gs.stopped[0] is
+// set.  partial: at least 2 (gs.mmax + 2) blocks float4; bar, err as launch_fci_tail32.
+cudaError_t launch_arnoldi_ff(const Geom& g, const double2* dg, const double2* z,
+                              const float4* V, float4* vnext, float2* y32, const GmresDev& gs,
+                              double2* partial, unsigned* bar, int* err, long long n, int nb,
                               double brk, int ppt, int blocks, cudaStream_t st);
 // y = R^{-1} g in float32 for the complex64 FCI form's inner GMRES (GmresDev storage float64).
 cudaError_t launch_backsolve32(const GmresDev& gs, int nvec, cudaStream_t st);

@@ -387,7 +387,7 @@ k_cgs(const double2* __restrict__ V, long long vis, long long vrs, int nb, doubl
       const double2 red = warp_reduce8(acc, lane);
       if ((lane & 3) == 0) {
         const int t = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-        wp[warp * ldw + b0 + t] = red;  // slots >= nb are padding
+        if (b0 + t < nb) wp[warp * ldw + b0 + t] = red;  // slot nb is the norm's (mode 0)
       }
     }
   }

@@ -190,7 +190,7 @@ k_cgs32(const float2* __restrict__ V, long long vis, long long vrs, int nb, floa
       const float2 red = warp_reduce8f(acc, lane);
       if ((lane & 3) == 0) {
         const int t = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-        wp[warp * ldw + b0 + t] = red;
+        if (b0 + t < nb) wp[warp * ldw + b0 + t] = red;  // slot nb is the norm's (mode 0)
       }
     }
   }

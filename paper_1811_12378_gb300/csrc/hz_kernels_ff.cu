@@ -20,36 +20,6 @@ constexpr int F_WARPS = 8;  // block: 8 warps x 32 lanes x 2 points
 constexpr int F_PPL = 2;
 constexpr int F_CHUNK = F_WARPS * 32 * F_PPL;
 
-__device__ __forceinline__ float2 re_of(float4 v) { return make_float2(v.x, v.y); }
-__device__ __forceinline__ float2 im_of(float4 v) { return make_float2(v.z, v.w); }
-__device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
-
-// Butterfly reduce-scatter of 8 complex float-pair partials over a warp (the lane map of
-// warp_reduce8 in hz_kernels.cu): lane l with (l & 3) == 0 ends with the sum of vector
-// ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 + ((l >> 2) & 1).
-__device__ __forceinline__ float4 warp_reduce8_ff(float4 (&a)[8], int lane) {
-  float4 b4[4], b2[2];
-  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    const float4 keep = h16 ? a[4 + t] : a[t];
-    const float4 give = h16 ? a[t] : a[4 + t];
-    b4[t] = ffc_add(keep, shfl_xor4(give, 16));
-  }
-#pragma unroll
-  for (int t = 0; t < 2; ++t) {
-    const float4 keep = h8 ? b4[2 + t] : b4[t];
-    const float4 give = h8 ? b4[t] : b4[2 + t];
-    b2[t] = ffc_add(keep, shfl_xor4(give, 8));
-  }
-  const float4 keep = h4 ? b2[1] : b2[0];
-  const float4 give = h4 ? b2[0] : b2[1];
-  float4 x = ffc_add(keep, shfl_xor4(give, 4));
-  x = ffc_add(x, shfl_xor4(x, 2));
-  x = ffc_add(x, shfl_xor4(x, 1));
-  return x;
-}
-
 // Classical Gram-Schmidt pieces on float-pair fields, modes as in the float64 k_cgs:
 //   0: h1 = V^H w and ||w||^2;  1: w -= V h1, then h2 = V^H w;  2: w -= V h2, ||w||^2 and the
 //   Givens step of the column.  Lane l of warp w owns the F_PPL points seg + l + 32 e.  Basis
@@ -161,7 +131,7 @@ k_cgs_ff(const float4* __restrict__ V, long long vis, long long vrs, int nb, flo
       const float4 red = warp_reduce8_ff(acc, lane);
       if ((lane & 3) == 0) {
         const int t = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-        wp[warp * ldw + b0 + t] = red;
+        if (b0 + t < nb) wp[warp * ldw + b0 + t] = red;  // slot nb is the norm's (mode 0)
       }
     }
   }
@@ -189,13 +159,25 @@ k_cgs_ff(const float4* __restrict__ V, long long vis, long long vrs, int nb, flo
   if (!last_block(counters + r)) return;
   double2* out = MODE == 0 ? gs.h1 + (long long)r * (M + 2)
                : MODE == 1 ? gs.h2 + (long long)r * (M + 2) : gs.nrm + 2 * r;
+  __shared__ float2 s_hn2;
   for (int sidx = warp; sidx < nslots; sidx += F_WARPS) {
     const float4 t = warp_sum_partials_ff(part, sidx, (int)gridDim.x, lane);
-    if (lane == 0) out[sidx] = d_from_ffc(t);
+    if (lane == 0) {
+      out[sidx] = d_from_ffc(t);
+      if (MODE == 2) s_hn2 = make_float2(t.x, t.y);
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) counters[r] = 0;
-  if (MODE == 2) givens_column(gs, r, nb - 1, brk);  // whole block
+  if (MODE == 2) {
+    // the Hessenberg column h1 + h2 as float pairs (the float64 copies convert back exactly)
+    const double2* h1 = gs.h1 + (long long)r * (M + 2);
+    const double2* h2 = gs.h2 + (long long)r * (M + 2);
+    float4* col = sm4;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+      col[i] = ffc_add(ffc_from_d(h1[i]), ffc_from_d(h2[i]));
+    givens_column_ff(gs, r, nb - 1, brk, col, s_hn2, ff_from_d(h1[nb].x));  // whole block
+  }
 }
 
 // v = w * (1 / h_{k+1,k}) in place on float pairs; the float64 scale is split once per block.

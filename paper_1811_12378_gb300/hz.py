@@ -26,7 +26,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory",
 EXPORTS = ["hz_problem_create", "hz_plan", "hz_problem_destroy", "hz_problem_get_info",
            "hz_problem_nodes", "hz_problem_set_nodes", "hz_apply_shifted", "hz_shifted_solve",
            "hz_fci", "hz_solve", "hz_solve_batched", "hz_profile_enable", "hz_profile_read",
-           "hz_problem_fused_tail", "hz_residual_noalloc",
+           "hz_problem_fused_tail", "hz_problem_fused_arnoldi", "hz_residual_noalloc",
            "hz_status_string", "hz_last_error", "hz_launch_count"]
 
 # kernel classes of hz_profile_read
@@ -108,6 +108,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                                      C.POINTER(HzSolveStats), P]
     lib.hz_profile_enable.argtypes = [P, C.c_int]
     lib.hz_problem_fused_tail.argtypes = [P, C.c_int]
+    lib.hz_problem_fused_arnoldi.argtypes = [P, C.c_int]
     lib.hz_profile_read.argtypes = [P, C.c_int, C.POINTER(C.c_longlong), dp, dp]
     lib.hz_residual_noalloc.argtypes = [C.POINTER(HzGrid), P, C.c_double, P, C.c_double, P, P, P,
                                         C.c_int, P]
@@ -262,6 +263,10 @@ class Problem:
     def fused_tail(self, on: bool = True):
         """Complex64 FCI steps 3-5 as one cooperative kernel (default) or one kernel per piece."""
         _check(self._lib.hz_problem_fused_tail(self._h, 1 if on else 0), self._lib)
+
+    def fused_arnoldi(self, on: bool = True):
+        """Float-pair outer Arnoldi step as one cooperative kernel (default) or five kernels."""
+        _check(self._lib.hz_problem_fused_arnoldi(self._h, 1 if on else 0), self._lib)
 
     def profile(self, on: bool = True):
         """Start (and zero) or stop per-kernel-class CUDA-event timing."""

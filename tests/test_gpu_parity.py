@@ -265,6 +265,32 @@ def test_float_pair_arnoldi_matches_float64_arnoldi():
             s64[v].rel_res_true, 1e-300) + 1e-14
 
 
+@pytest.mark.parametrize("restart", [5, 12])
+def test_float_pair_arnoldi_fused_one_rhs(restart):
+    """One right-hand side: the outer float-pair Arnoldi step as one cooperative kernel (the
+    default) against its five-kernel form, which has the same per-point arithmetic and groups
+    the global float-pair sums differently, and against the float64 outer Arnoldi; a fixed
+    number of outer steps over three cycles (restart 12: basis counts past one group of 8),
+    ragged grid; the cooperative form is deterministic."""
+    wl = W.small_case(43, 13, 10, 9, nrhs=1, layer=2, J=4)
+    op, nodes = oracle_of(wl)
+    its = 2 * restart + 1
+    with problem_of(wl, nodes, nrhs_max=1, restart_max=restart, inner_k_max=3) as P:
+        kw = dict(restart=restart, inner_k=3, rtol=1e-30, max_cycles=3, fixed_its=its)
+        ua, sa = P.solve(to_dev(wl.f), precision=hzpkg.HZ_MIXED_C64_FF, **kw)
+        ub, sb = P.solve(to_dev(wl.f), precision=hzpkg.HZ_MIXED_C64_FF, **kw)
+        P.fused_arnoldi(False)
+        uc, sc = P.solve(to_dev(wl.f), precision=hzpkg.HZ_MIXED_C64_FF, **kw)
+        ud, sd = P.solve(to_dev(wl.f), precision=hzpkg.HZ_MIXED_C64_FCI32, **kw)
+    assert [s.its for s in (sa[0], sb[0], sc[0], sd[0])] == [its] * 4
+    assert np.array_equal(to_np(ua), to_np(ub))
+    for u, st in ((uc, sc), (ud, sd)):
+        assert rel(to_np(ua)[0], to_np(u)[0]) <= 1e-10
+        # a 1e-10 relative change of u moves r = s f - A u by up to ||A|| ||u|| 1e-10, about
+        # the condition number (here ~1e3) times 1e-10 relative to ||s f||
+        assert abs(sa[0].rel_res_true - st[0].rel_res_true) <= 1e-7 * st[0].rel_res_true + 1e-13
+
+
 def test_batched_rhs_equal_single_solves():
     """Several right-hand sides in one call give the results of separate calls."""
     wl = W.small_case(12, 12, 11, 10, nrhs=3, layer=2, J=4)
