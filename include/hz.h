@@ -234,12 +234,15 @@ hz_status hz_problem_fused_tail(hz_problem* p, int on);
 
 /* Selects how HZ_MIXED_C64_FF runs each outer Arnoldi step of FGMRES (Section 3: w = A z_k,
  * the two classical Gram-Schmidt passes against v_0..v_k, the Givens rotation of the new
- * Hessenberg column, v_{k+1} = w / h_{k+1,k}) for a single right-hand side: on = 1 (the
- * default) as one cooperative kernel with three grid-wide barriers, where the grid fits on the
- * device; on = 0 as five kernels.  The two differ only in the grouping of the float-pair global
- * sums.  Several right-hand sides per call, and hz_solve_batched, always use the five kernels.
- * A barrier timeout is reported as for hz_problem_fused_tail. */
-hz_status hz_problem_fused_arnoldi(hz_problem* p, int on);
+ * Hessenberg column, v_{k+1} = w / h_{k+1,k}) for a single right-hand side.  mode = 1 (the
+ * default): one cooperative kernel with two grid-wide barriers, where the grid fits on the
+ * device; h_{k+1,k} comes from ||w'||^2 - ||V^H w'||^2 after the second pass (w' the vector
+ * after the first), or, where that difference would cancel, from a third summed norm.
+ * mode = 2: the same kernel, always summing the norm.  mode = 0: five kernels (stencil, three
+ * Gram-Schmidt passes, normalisation).  The modes differ only in rounding.  Several right-hand
+ * sides per call, and hz_solve_batched, always use mode 0.  Other modes: HZ_ERR_INVALID.  A
+ * barrier timeout is reported as for hz_problem_fused_tail. */
+hz_status hz_problem_fused_arnoldi(hz_problem* p, int mode);
 hz_status hz_profile_read(hz_problem* p, int cls, long long* launches, double* ms,
                           double* bytes);
 

@@ -119,7 +119,7 @@ struct hz_problem {
   unsigned* tail_bar = nullptr;  // [0] arrivals, [1] generation, [2] error flag
   // the outer float-pair Arnoldi step as one cooperative kernel (hz_arnoldi_ff.cu), sharing
   // the barrier words and the error flag of the FCI tail (the two never run concurrently)
-  bool arn_on = true;  // hz_problem_fused_arnoldi
+  int arn_mode = 1;  // hz_problem_fused_arnoldi: 0 five kernels, 1 cooperative, 2 summed norm
   int arn_ppt = 0, arn_blocks = 0;
 
   void drop_graphs() {
@@ -417,7 +417,7 @@ bool tail_fits(const hz_problem* p, int nvec, int kin) {
 }
 
 bool arnoldi_fits(const hz_problem* p, int nvec) {
-  return p->arn_on && p->tail_solo && nvec == 1 && p->arn_ppt > 0;
+  return p->arn_mode != 0 && p->tail_solo && nvec == 1 && p->arn_ppt > 0;
 }
 
 // r_ff: r holds float pairs (the outer basis of HZ_MIXED_C64_FF) whose complex64 rounding the
@@ -530,7 +530,8 @@ hz_status outer_step_launches(hz_problem* p, int k, int nrhs, int K, int precisi
       HZ_TIMED(p, 2, st, 16.0 * n * (3.0 + 3.0 * (k + 1)) + 8.0 * n,
                hz::launch_arnoldi_ff(p->g, p->d64, zk.p, (const float4*)p->V, wf.p, p->f32, go,
                                      p->partial, p->tail_bar, (int*)(p->tail_bar + 2), n, k + 1,
-                                     kBreakdown, p->arn_ppt, p->arn_blocks, st));
+                                     kBreakdown, p->arn_mode == 1 ? 1 : 0, p->arn_ppt,
+                                     p->arn_blocks, st));
       p->tail_used = true;
       return HZ_OK;
     }
@@ -563,7 +564,7 @@ hz_status outer_step(hz_problem* p, int k, int nrhs, int K, int precision, cudaS
   if (p->prof_on || !p->graphs_on) return outer_step_launches(p, k, nrhs, K, precision, st);
   const long long key =
       ((((long long)nrhs * 4 + precision) * 1024 + K) * 2 + (tail_fits(p, nrhs, K) ? 1 : 0)) * 2 +
-      (arnoldi_fits(p, nrhs) ? 1 : 0);
+      (arnoldi_fits(p, nrhs) ? 1 : 0) + 2 * (p->arn_mode == 2 ? 1 : 0);
   if (p->graph_key != key) {
     p->drop_graphs();
     p->graph_key = key;
@@ -1040,10 +1041,11 @@ hz_status hz_problem_fused_tail(hz_problem* p, int on) {
   return HZ_OK;
 }
 
-hz_status hz_problem_fused_arnoldi(hz_problem* p, int on) {
+hz_status hz_problem_fused_arnoldi(hz_problem* p, int mode) {
   HZ_TRY(check_problem(p));
-  if (p->arn_on != (on != 0)) p->drop_graphs();
-  p->arn_on = on != 0;
+  if (mode < 0 || mode > 2) return fail(HZ_ERR_INVALID, "hz_problem_fused_arnoldi: mode 0, 1 or 2");
+  if (p->arn_mode != mode) p->drop_graphs();
+  p->arn_mode = mode;
   return HZ_OK;
 }
 

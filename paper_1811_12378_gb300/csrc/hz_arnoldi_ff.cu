@@ -10,7 +10,8 @@
 // The five launches of that form spend much of their time in ramps, in a partial second wave
 // and in the serial finish of each reduction by its last block; here the grid stays resident
 // (two blocks on every SM), each block owns a contiguous range of points and keeps its part of
-// w in shared memory through every pass, and the passes are separated by three grid barriers.  After each barrier every
+// w in shared memory through every pass, and the passes are separated by two grid barriers
+// (three where the Pythagorean norm of the last pass would cancel, see below).  After each barrier every
 // block adds all blocks' float-pair partials in the same fixed order, so every block holds the
 // same float64 coefficients without a broadcast.  Block 0 alone writes the Hessenberg column
 // and runs the Givens step.
@@ -43,6 +44,7 @@ struct Arn {
   int* err;
   long long n;
   int nb;
+  int pyth;  // 0: always sum the norm of the last pass
   double brk;
 };
 
@@ -201,7 +203,7 @@ __device__ __forceinline__ void grid_reduce(const float4* part, int ns, float4* 
                                             int nneg) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int s = warp; s < ns; s += AWARPS) {
-    const float4 v = warp_sum_partials_ff(part, s, (int)gridDim.x, lane);
+    const float4 v = warp_sum_partials_ffn(part, s, (int)gridDim.x, lane);
     if (lane == 0) {
       h[s] = v;
       if (s < nneg) hf[s] = make_float4(-v.x, -v.y, -v.z, -v.w);
@@ -214,7 +216,8 @@ __global__ void __launch_bounds__(AT, 2) k_arnoldi_ff(Arn a, int ppt) {
   pdl_enter();
   // sw[ppt][AT] | wp[AWARPS][nb + 8] | hf, h1f, h2f[nb + 1] (float pairs)
   extern __shared__ float4 sm4[];
-  __shared__ float2 s_inv;
+  __shared__ float2 s_inv, s_hn2;
+  __shared__ int s_fast;
   if (a.gs.stopped[0]) return;  // uniform: no block of this grid writes it before barrier 1
   const int nb = a.nb, ldw = nb + 8;
   float4* sw = sm4;
@@ -271,20 +274,49 @@ __global__ void __launch_bounds__(AT, 2) k_arnoldi_ff(Arn a, int ppt) {
   if (!grid_sync(a.bar, G, a.err)) return;
   grid_reduce(arn_part(a, 0), nb + 1, h1f, hf, nb);
 
-  // ---- second pass: w -= V h1, h2 = V^H w
+  // ---- second pass: w -= V h1, then h2 = V^H w and ||w||^2 (slot nb)
   update(a, P, sw, hf);
   warp_dots(a, P, sw, wp, ldw);
-  block_partial(arn_part(a, 1), wp, ldw, nb);
+  warp_norm(P, sw, wp, ldw, nb);
+  block_partial(arn_part(a, 1), wp, ldw, nb + 1);
   if (!grid_sync(a.bar, G, a.err)) return;
-  grid_reduce(arn_part(a, 1), nb, h2f, hf, nb);
+  grid_reduce(arn_part(a, 1), nb + 1, h2f, hf, nb);
 
-  // ---- w -= V h2, ||w||^2
-  update(a, P, sw, hf);
-  warp_norm(P, sw, wp, ldw, 0);
-  block_partial(arn_part(a, 2), wp, ldw, 1);
-  if (!grid_sync(a.bar, G, a.err)) return;
-  grid_reduce(arn_part(a, 2), 1, wp, hf, 0);  // ||w||^2 to wp[0]
-  const float2 hn2 = re_of(wp[0]), wn2 = re_of(h1f[nb]);
+  // ---- h_{k+1,k}^2 = ||w - V h2||^2 = ||w||^2 - ||h2||^2: V is orthonormal and w already
+  // nearly orthogonal to it, so the second pass removes little and the difference keeps its
+  // accuracy; then no further reduction is needed.  Where the second pass removed more than
+  // three quarters of ||w||^2 (w close to the span of V, the subtraction would cancel), the
+  // norm of w - V h2 is summed instead.  Every block sees the same sums: the branch is uniform.
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    float2 q = make_float2(0.f, 0.f);
+    for (int b = lane; b < nb; b += 32) {
+      const float4 h = h2f[b];
+      q = ff_add(q, ff_add(ff_mul(re_of(h), re_of(h)), ff_mul(im_of(h), im_of(h))));
+    }
+    for (int o = 16; o > 0; o >>= 1)
+      q = ff_add(q, make_float2(__shfl_xor_sync(0xffffffffu, q.x, o),
+                                __shfl_xor_sync(0xffffffffu, q.y, o)));
+    if (lane == 0) {
+      const float2 wq = re_of(h2f[nb]);
+      const float2 hp = ff_sub(wq, q);
+      s_fast = a.pyth && hp.x > 0.25f * wq.x ? 1 : 0;
+      s_hn2 = hp;
+    }
+  }
+  __syncthreads();
+  float2 hn2;
+  update(a, P, sw, hf);  // w -= V h2
+  if (s_fast) {
+    hn2 = s_hn2;
+  } else {
+    warp_norm(P, sw, wp, ldw, 0);
+    block_partial(arn_part(a, 2), wp, ldw, 1);
+    if (!grid_sync(a.bar, G, a.err)) return;
+    grid_reduce(arn_part(a, 2), 1, wp, hf, 0);  // ||w||^2 to wp[0]
+    hn2 = re_of(wp[0]);
+  }
+  const float2 wn2 = re_of(h1f[nb]);
 
   // ---- v_{k+1} = w / h_{k+1,k} (zero at a breakdown), as the Givens step decides it
   if (threadIdx.x == 0) {
@@ -356,7 +388,7 @@ cudaError_t arnoldi_ff_plan(long long n, int mmax, int* ppt, int* blocks) {
 cudaError_t launch_arnoldi_ff(const Geom& g, const double2* dg, const double2* z,
                               const float4* V, float4* vnext, float2* y32, const GmresDev& gs,
                               double2* partial, unsigned* bar, int* err, long long n, int nb,
-                              double brk, int ppt, int blocks, cudaStream_t st) {
+                              double brk, int pyth, int ppt, int blocks, cudaStream_t st) {
   if (nb < 1 || nb > gs.mmax || blocks < 1 || ppt < 1 || ppt > ARN_PPT_MAX ||
       (long long)blocks * ppt * AT < n || n > 0x7fffffffLL)
     return cudaErrorInvalidValue;
@@ -373,6 +405,7 @@ cudaError_t launch_arnoldi_ff(const Geom& g, const double2* dg, const double2* z
   a.err = err;
   a.n = n;
   a.nb = nb;
+  a.pyth = pyth;
   a.brk = brk;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

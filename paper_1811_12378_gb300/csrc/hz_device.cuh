@@ -144,6 +144,36 @@ __device__ __forceinline__ float4 warp_sum_partials_ff(const float4* part, int s
   return acc;
 }
 
+// The same sum in compact code, for the cooperative kernels.  Their reductions and Givens step
+// run between long passes that have pushed them out of the instruction cache, and there an
+// unrolled float-pair sequence costs several cycles per instruction in fetches (measured: the
+// cooperative outer Arnoldi step 1.5% faster per solve with this form, while the short
+// reduction kernels were 1.5% slower with it); one out-of-line add serves every step.
+__device__ __noinline__ float4 ffc_add_n(float4 a, float4 b) { return ffc_add(a, b); }
+
+__device__ __forceinline__ float4 warp_sum_partials_ffn(const float4* part, int sidx, int G,
+                                                        int lane) {
+  const float4* ps = part + (long long)sidx * G;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int b0 = 0; b0 < G; b0 += 32 * 8) {
+    float4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int b = b0 + u * 32 + lane;
+      v[u] = b < G ? __ldcg(ps + b) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // a pairwise tree over the eight loads, then into the running sum
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = ffc_add_n(v[u], v[u + 4]);
+    v[0] = ffc_add_n(v[0], v[2]);
+    v[1] = ffc_add_n(v[1], v[3]);
+    acc = ffc_add_n(acc, ffc_add_n(v[0], v[1]));
+  }
+#pragma unroll 1
+  for (int o = 16; o > 0; o >>= 1) acc = ffc_add_n(acc, shfl_xor4(acc, o));
+  return acc;
+}
+
 // ---------------------------------------------------------------- complex64 stencil
 // y[t] = ((A - zI) x) at (i, j, k0 + t), t < ZC, from the precomputed complex64 diagonal
 // (dg = 6 s/h^2 - m - i a):  (dg - z) x - (s/h^2) * (sum of the 6 neighbours), Dirichlet
@@ -418,6 +448,7 @@ __device__ void givens_column(const GmresDev& gs, int r, int k, double brk) {
     A = cmul(al, A);
   }
   // inclusive scan over the lanes (earlier lanes' maps applied first), then shifted by one
+#pragma unroll 1
   for (int o = 1; o < 32; o <<= 1) {
     const double2 Ap = shfl_up2(A, o), Bp = shfl_up2(B, o);
     if (lane >= o) {
@@ -513,13 +544,17 @@ __device__ __forceinline__ bool ff_le(float2 a, float2 b) {
 __device__ __forceinline__ float4 ffc(float2 re, float2 im) {
   return make_float4(re.x, re.y, im.x, im.y);
 }
-__device__ __forceinline__ float4 ffc_mul(float4 a, float4 b) {
+// (out of line: the float-pair Givens step below runs from a cold instruction cache, see
+// warp_sum_partials_ffn)
+__device__ __noinline__ float4 ffc_mul(float4 a, float4 b) {
   const float2 ar = re_of(a), ai = im_of(a), br = re_of(b), bi = im_of(b);
   return ffc(ff_sub(ff_mul(ar, br), ff_mul(ai, bi)), ff_add(ff_mul(ar, bi), ff_mul(ai, br)));
 }
-__device__ __forceinline__ float4 ffc_rmul(float2 c, float4 a) {  // real c times complex a
+__device__ __noinline__ float4 ffc_rmul(float2 c, float4 a) {  // real c times complex a
   return ffc(ff_mul(c, re_of(a)), ff_mul(c, im_of(a)));
 }
+__device__ __noinline__ float2 ff_div_n(float2 a, float2 b) { return ff_div(a, b); }
+__device__ __noinline__ float2 ff_sqrt_n(float2 x) { return ff_sqrt(x); }
 __device__ __forceinline__ float4 ffc_mconj(float4 s) {  // -conj(s)
   return make_float4(-s.x, -s.y, s.z, s.w);
 }
@@ -538,7 +573,7 @@ __device__ __forceinline__ float ff_pow2_scale(float m) {
 __device__ __forceinline__ float2 ffc_abs(float4 v) {
   const float sc = ff_pow2_scale(fmaxf(fabsf(v.x), fabsf(v.z)));
   const float2 re = ff_scale2(re_of(v), sc), im = ff_scale2(im_of(v), sc);
-  return ff_scale2(ff_sqrt(ff_add(ff_mul(re, re), ff_mul(im, im))), 1.f / sc);
+  return ff_scale2(ff_sqrt_n(ff_add(ff_mul(re, re), ff_mul(im, im))), 1.f / sc);
 }
 
 // The breakdown test and the scale of the next basis vector from ||w||^2 after (hn2) and
@@ -546,10 +581,10 @@ __device__ __forceinline__ float2 ffc_abs(float4 v) {
 // (the test of the float64 Givens step).  Every caller gets the same bits from the same sums.
 __device__ __forceinline__ bool ff_step_inv(float2 hn2, float2 wn2, float brk, float2* hn,
                                             float2* inv) {
-  *hn = ff_sqrt(hn2);
-  const float2 wn = ff_sqrt(wn2);
+  *hn = ff_sqrt_n(hn2);
+  const float2 wn = ff_sqrt_n(wn2);
   const bool brk_now = ff_le(*hn, ff_mul(make_float2(brk, 0.f), wn));
-  *inv = brk_now ? make_float2(0.f, 0.f) : ff_div(make_float2(1.f, 0.f), *hn);
+  *inv = brk_now ? make_float2(0.f, 0.f) : ff_div_n(make_float2(1.f, 0.f), *hn);
   return brk_now;
 }
 
@@ -576,13 +611,14 @@ __device__ void givens_column_ff(const GmresDev& gs, int r, int k, double brk, c
   for (int i = i0; i < i1; ++i) {
     const float2 c = ccf[i];
     const float4 al = ffc_mconj(ssf[i]);
-    B = ffc_add(ffc_mul(al, B), ffc_rmul(c, col[i + 1]));
+    B = ffc_add_n(ffc_mul(al, B), ffc_rmul(c, col[i + 1]));
     A = ffc_mul(al, A);
   }
+#pragma unroll 1
   for (int o = 1; o < 32; o <<= 1) {
     const float4 Ap = shfl_up4(A, o), Bp = shfl_up4(B, o);
     if (lane >= o) {
-      B = ffc_add(ffc_mul(A, Bp), B);
+      B = ffc_add_n(ffc_mul(A, Bp), B);
       A = ffc_mul(A, Ap);
     }
   }
@@ -591,12 +627,12 @@ __device__ void givens_column_ff(const GmresDev& gs, int r, int k, double brk, c
     Ax = one;
     Bx = zero4;
   }
-  float4 t = ffc_add(ffc_mul(Ax, col[0]), Bx);  // t_{i0}
+  float4 t = ffc_add_n(ffc_mul(Ax, col[0]), Bx);  // t_{i0}
   for (int i = i0; i < i1; ++i) {
     const float2 c = ccf[i];
     const float4 s = ssf[i], hn1 = col[i + 1];
-    R[i] = d_from_ffc(ffc_add(ffc_mul(s, hn1), ffc_rmul(c, t)));
-    t = ffc_add(ffc_mul(ffc_mconj(s), t), ffc_rmul(c, hn1));
+    R[i] = d_from_ffc(ffc_add_n(ffc_mul(s, hn1), ffc_rmul(c, t)));
+    t = ffc_add_n(ffc_mul(ffc_mconj(s), t), ffc_rmul(c, hn1));
   }
   const int last = k == 0 ? 0 : (k - 1) / q;
   if (lane != last) return;
@@ -619,14 +655,14 @@ __device__ void givens_column_ff(const GmresDev& gs, int r, int k, double brk, c
     const float2 ar = ff_scale2(re_of(a), sc2), ai = ff_scale2(im_of(a), sc2);
     const float2 hs = ff_scale2(hn, sc2);
     const float2 ra2 = ff_add(ff_mul(ar, ar), ff_mul(ai, ai));
-    const float2 ra = ff_sqrt(ra2);
-    const float2 rho = ff_sqrt(ff_add(ra2, ff_mul(hs, hs)));
-    c = ff_div(ra, rho);
-    const float2 f = ff_div(hs, ff_mul(ra, rho));
+    const float2 ra = ff_sqrt_n(ra2);
+    const float2 rho = ff_sqrt_n(ff_add(ra2, ff_mul(hs, hs)));
+    c = ff_div_n(ra, rho);
+    const float2 f = ff_div_n(hs, ff_mul(ra, rho));
     s = ffc(ff_mul(ar, f), ff_mul(ai, f));
   }
   // R_kk = c a + s hn
-  const float4 rkk = ffc_add(ffc_rmul(c, a), ffc(ff_mul(re_of(s), hn), ff_mul(im_of(s), hn)));
+  const float4 rkk = ffc_add_n(ffc_rmul(c, a), ffc(ff_mul(re_of(s), hn), ff_mul(im_of(s), hn)));
   ccf[k] = c;
   ssf[k] = s;
   double2* gg = gs.g + (long long)r * (M + 1);

@@ -91,7 +91,7 @@ __device__ __forceinline__ void block_partial(float4* part, float2 (&v)[NS], int
 __device__ __forceinline__ void grid_reduce(const float4* part, int ns, float2* hs) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int s = warp; s < ns; s += TB / 32) {
-    const float4 t = warp_sum_partials_ff(part, s, (int)gridDim.x, lane);
+    const float4 t = warp_sum_partials_ffn(part, s, (int)gridDim.x, lane);
     if (lane == 0) hs[s] = f_from_ffc(t);
   }
   __syncthreads();

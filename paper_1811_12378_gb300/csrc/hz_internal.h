@@ -197,11 +197,13 @@ cudaError_t arnoldi_ff_plan(long long n, int mmax, int* ppt, int* blocks);
 // For one right-hand side and nb = k + 1 basis fields V (float pairs): w = A z (dg: float64
 // diagonal), CGS2 against V into gs.h1, gs.h2, gs.nrm, the Givens step of column k, and
 // vnext = w / h_{k+1,k} with its complex64 rounding y32.  Does nothing once gs.stopped[0] is
-// set.  partial: at least 2 (gs.mmax + 2) blocks float4; bar, err as launch_fci_tail32.
+// set.  pyth: take h_{k+1,k} from ||w||^2 - ||h2||^2 where that does not cancel (0: always
+// sum the norm of the last pass).  partial: at least 2 (gs.mmax + 2) blocks float4; bar, err
+// as launch_fci_tail32.
 cudaError_t launch_arnoldi_ff(const Geom& g, const double2* dg, const double2* z,
                               const float4* V, float4* vnext, float2* y32, const GmresDev& gs,
                               double2* partial, unsigned* bar, int* err, long long n, int nb,
-                              double brk, int ppt, int blocks, cudaStream_t st);
+                              double brk, int pyth, int ppt, int blocks, cudaStream_t st);
 // y = R^{-1} g in float32 for the complex64 FCI form's inner GMRES (GmresDev storage float64).
 cudaError_t launch_backsolve32(const GmresDev& gs, int nvec, cudaStream_t st);
 

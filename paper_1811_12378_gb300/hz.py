@@ -264,9 +264,10 @@ class Problem:
         """Complex64 FCI steps 3-5 as one cooperative kernel (default) or one kernel per piece."""
         _check(self._lib.hz_problem_fused_tail(self._h, 1 if on else 0), self._lib)
 
-    def fused_arnoldi(self, on: bool = True):
-        """Float-pair outer Arnoldi step as one cooperative kernel (default) or five kernels."""
-        _check(self._lib.hz_problem_fused_arnoldi(self._h, 1 if on else 0), self._lib)
+    def fused_arnoldi(self, mode=1):
+        """Float-pair outer Arnoldi step: 1 one cooperative kernel (default), 2 the same with
+        the last norm always summed, 0 (or False) five kernels."""
+        _check(self._lib.hz_problem_fused_arnoldi(self._h, int(mode)), self._lib)
 
     def profile(self, on: bool = True):
         """Start (and zero) or stop per-kernel-class CUDA-event timing."""

@@ -268,7 +268,8 @@ def test_float_pair_arnoldi_matches_float64_arnoldi():
 @pytest.mark.parametrize("restart", [5, 12])
 def test_float_pair_arnoldi_fused_one_rhs(restart):
     """One right-hand side: the outer float-pair Arnoldi step as one cooperative kernel (the
-    default) against its five-kernel form, which has the same per-point arithmetic and groups
+    default, h_{k+1,k} from the Pythagorean difference) against the same kernel summing the
+    last norm, against its five-kernel form, which has the same per-point arithmetic and groups
     the global float-pair sums differently, and against the float64 outer Arnoldi; a fixed
     number of outer steps over three cycles (restart 12: basis counts past one group of 8),
     ragged grid; the cooperative form is deterministic."""
@@ -279,12 +280,16 @@ def test_float_pair_arnoldi_fused_one_rhs(restart):
         kw = dict(restart=restart, inner_k=3, rtol=1e-30, max_cycles=3, fixed_its=its)
         ua, sa = P.solve(to_dev(wl.f), precision=hzpkg.HZ_MIXED_C64_FF, **kw)
         ub, sb = P.solve(to_dev(wl.f), precision=hzpkg.HZ_MIXED_C64_FF, **kw)
+        P.fused_arnoldi(2)  # the same kernel with the last norm always summed
+        ue, se = P.solve(to_dev(wl.f), precision=hzpkg.HZ_MIXED_C64_FF, **kw)
         P.fused_arnoldi(False)
         uc, sc = P.solve(to_dev(wl.f), precision=hzpkg.HZ_MIXED_C64_FF, **kw)
         ud, sd = P.solve(to_dev(wl.f), precision=hzpkg.HZ_MIXED_C64_FCI32, **kw)
-    assert [s.its for s in (sa[0], sb[0], sc[0], sd[0])] == [its] * 4
+        with pytest.raises(hzpkg.HzError):
+            P.fused_arnoldi(3)
+    assert [s.its for s in (sa[0], sb[0], sc[0], sd[0], se[0])] == [its] * 5
     assert np.array_equal(to_np(ua), to_np(ub))
-    for u, st in ((uc, sc), (ud, sd)):
+    for u, st in ((uc, sc), (ud, sd), (ue, se)):
         assert rel(to_np(ua)[0], to_np(u)[0]) <= 1e-10
         # a 1e-10 relative change of u moves r = s f - A u by up to ||A|| ||u|| 1e-10, about
         # the condition number (here ~1e3) times 1e-10 relative to ||s f||
