@@ -578,7 +578,7 @@ __device__ __forceinline__ float2 ffc_abs(float4 v) {
 
 // The breakdown test and the scale of the next basis vector from ||w||^2 after (hn2) and
 // before (wn2) the orthogonalisation: *inv = 1 / h_{k+1,k}, or 0 when h_{k+1,k} <= brk ||w||
-// (the test of the float64 Givens step).  Every caller gets the same bits from the same sums.
+// (the test of givens_column).  Every caller gets the same bits from the same sums.
 __device__ __forceinline__ bool ff_step_inv(float2 hn2, float2 wn2, float brk, float2* hn,
                                             float2* inv) {
   *hn = ff_sqrt_n(hn2);

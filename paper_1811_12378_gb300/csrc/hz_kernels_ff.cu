@@ -6,8 +6,8 @@
 // (hi + lo, about 48 significant bits): a complex element is a float4 (re.hi, re.lo, im.hi,
 // im.lo), 16 bytes like a double2.  Products are error-free float32 transformations (FMA),
 // sums are two-sum chains, so the CGS2 passes run on the float32 pipes.  Dots are accumulated
-// across warps and blocks as float pairs too and converted to float64 once per value; the
-// Hessenberg/Givens state stays float64, as in the float64 form.
+// across warps and blocks as float pairs too and stored in float64 once per value; the Givens
+// step (givens_column_ff) also runs in float pairs and stores R, g and the scalars in float64.
 #include <cuda_runtime.h>
 
 #include "hz_device.cuh"
