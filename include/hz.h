@@ -225,13 +225,16 @@ hz_status hz_solve_batched(hz_problem* const* probs, int nprob, const void* cons
 hz_status hz_profile_enable(hz_problem* p, int on);
 
 /* Selects how the complex64 forms run steps 3-5 of Algorithm 1 (step d, the inner GMRES,
- * v + d w) for a single right-hand side: on = 1 (the default) as one cooperative kernel whose
- * phases are separated by a grid-wide barrier, where the grid fits on the device and k_in <= 16;
- * on = 0 as one kernel per Arnoldi piece.  The two differ only in the order of float32
- * roundings.  Several right-hand sides per call, and problems solved together by
- * hz_solve_batched, always use the per-piece kernels.  A barrier that waits longer than about
- * a second gives up, and the next hz_solve on the problem returns HZ_ERR_CUDA. */
-hz_status hz_problem_fused_tail(hz_problem* p, int on);
+ * v + d w) for a single right-hand side.  mode = 1 (the default): one cooperative kernel whose
+ * phases are separated by grid-wide barriers, where the grid fits on the device and
+ * k_in <= 16; each h_{j+1,j} comes from ||w'||^2 - ||V^H w'||^2 after the second Gram-Schmidt
+ * pass (w' the vector after the first), or, where that difference would cancel, from a summed
+ * norm.  mode = 2: the same kernel, always summing the norm.  mode = 0: one kernel per Arnoldi
+ * piece.  The modes differ only in float32 rounding.  Several right-hand sides per call, and
+ * problems solved together by hz_solve_batched, always use mode 0.  Other modes:
+ * HZ_ERR_INVALID.  A barrier that waits longer than about a second gives up, and the next
+ * hz_solve on the problem returns HZ_ERR_CUDA. */
+hz_status hz_problem_fused_tail(hz_problem* p, int mode);
 
 /* Selects how HZ_MIXED_C64_FF runs each outer Arnoldi step of FGMRES (Section 3: w = A z_k,
  * the two classical Gram-Schmidt passes against v_0..v_k, the Givens rotation of the new

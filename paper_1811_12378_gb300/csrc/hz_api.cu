@@ -112,7 +112,7 @@ struct hz_problem {
 
   // the complex64 FCI tail as one cooperative kernel (hz_fci_tail32.cu): grid plans for
   // k_in <= 4 and k_in <= TAIL_KMAX (ppt 0: does not fit), its barrier words and error flag
-  bool tail_on = true;       // hz_problem_fused_tail
+  int tail_mode = 1;         // hz_problem_fused_tail: 0 per piece, 1 cooperative, 2 summed norm
   bool tail_solo = true;     // false while several problems run concurrently (batched solve)
   bool tail_used = false;
   int tail_ppt[2] = {0, 0}, tail_blocks[2] = {0, 0};
@@ -413,7 +413,8 @@ hz_status check_tail_fault(hz_problem* p) {
 
 bool tail_fits(const hz_problem* p, int nvec, int kin) {
   const int c = kin <= 4 ? 0 : 1;
-  return p->tail_on && p->tail_solo && nvec == 1 && kin <= hz::TAIL_KMAX && p->tail_ppt[c] > 0;
+  return p->tail_mode != 0 && p->tail_solo && nvec == 1 && kin <= hz::TAIL_KMAX &&
+         p->tail_ppt[c] > 0;
 }
 
 bool arnoldi_fits(const hz_problem* p, int nvec) {
@@ -445,7 +446,8 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
     HZ_TIMED(p, 2, st, 8.0 * n * (6.0 + 4.0 * kin * (kin + 3)),
              hz::launch_fci_tail32(p->g, p->d32, p->w32, p->f32, p->w, p->Vin32, p->Aw32, out.p,
                                    p->partial, p->tail_bar, (int*)(p->tail_bar + 2), n, kin,
-                                   kBreakdown, p->tail_ppt[c], p->tail_blocks[c], st));
+                                   kBreakdown, p->tail_mode == 1 ? 1 : 0, p->tail_ppt[c],
+                                   p->tail_blocks[c], st));
     p->tail_used = true;
     return HZ_OK;
   }
@@ -564,7 +566,8 @@ hz_status outer_step(hz_problem* p, int k, int nrhs, int K, int precision, cudaS
   if (p->prof_on || !p->graphs_on) return outer_step_launches(p, k, nrhs, K, precision, st);
   const long long key =
       ((((long long)nrhs * 4 + precision) * 1024 + K) * 2 + (tail_fits(p, nrhs, K) ? 1 : 0)) * 2 +
-      (arnoldi_fits(p, nrhs) ? 1 : 0) + 2 * (p->arn_mode == 2 ? 1 : 0);
+      (arnoldi_fits(p, nrhs) ? 1 : 0) + 2 * (p->arn_mode == 2 ? 1 : 0) +
+      4 * (p->tail_mode == 2 ? 1 : 0);
   if (p->graph_key != key) {
     p->drop_graphs();
     p->graph_key = key;
@@ -1034,10 +1037,11 @@ hz_status hz_plan(const hz_grid* grid, const double* c_host, const hz_contour_op
   return HZ_OK;
 }
 
-hz_status hz_problem_fused_tail(hz_problem* p, int on) {
+hz_status hz_problem_fused_tail(hz_problem* p, int mode) {
   HZ_TRY(check_problem(p));
-  if (p->tail_on != (on != 0)) p->drop_graphs();
-  p->tail_on = on != 0;
+  if (mode < 0 || mode > 2) return fail(HZ_ERR_INVALID, "hz_problem_fused_tail: mode 0, 1 or 2");
+  if (p->tail_mode != mode) p->drop_graphs();
+  p->tail_mode = mode;
   return HZ_OK;
 }
 

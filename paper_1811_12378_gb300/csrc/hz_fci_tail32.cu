@@ -45,6 +45,7 @@ struct Tail {
   int* err;
   long long n;
   int kin;
+  int pyth;  // 0: always sum the norm after the second Gram-Schmidt pass
   float brk;
 };
 
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
   __shared__ float2 snn[KC], gg[KC + 1], ys[KC];
   __shared__ float2 dsh;
   __shared__ float inv_s;
-  __shared__ int kend_s, stop_s;
+  __shared__ int kend_s, stop_s, fast_s;
   const Geom& g = a.g;
   const long long n = a.n;
   // block b owns the points [b n / G, (b + 1) n / G), its thread t the points begin + t + e * TB
@@ -211,6 +212,45 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
     }
   }
 
+  // Givens step for column j with h_{j+1,j} = hn (thread 0; the same arithmetic as the
+  // multi-kernel float32 form)
+  auto givens = [&](int j, float hn) {
+    const float wn = sqrtf(h1s[j + 1].x);
+    float2* col = R + j * (KC + 1);
+    for (int i = 0; i <= j; ++i) col[i] = h1s[i];
+    for (int i = 0; i < j; ++i) {
+      const float c = csn[i];
+      const float2 s = snn[i], x = col[i], y = col[i + 1];
+      col[i] = make_float2(c * x.x + (s.x * y.x - s.y * y.y), c * x.y + (s.x * y.y + s.y * y.x));
+      col[i + 1] = make_float2(-(s.x * x.x + s.y * x.y) + c * y.x, -(s.x * x.y - s.y * x.x) + c * y.y);
+    }
+    float c;
+    float2 s;
+    const float2 x = col[j];
+    if (hn == 0.f) {
+      c = 1.f;
+      s = zero;
+    } else if (x.x == 0.f && x.y == 0.f) {
+      c = 0.f;
+      s = make_float2(1.f, 0.f);
+    } else {
+      const float ra = hypotf(x.x, x.y);
+      const float rr = hypotf(ra, hn);
+      c = ra / rr;
+      s = make_float2(x.x / ra * hn / rr, x.y / ra * hn / rr);
+    }
+    col[j] = make_float2(c * x.x + s.x * hn, c * x.y + s.y * hn);
+    csn[j] = c;
+    snn[j] = s;
+    const float2 gk = gg[j];
+    gg[j] = make_float2(c * gk.x, c * gk.y);
+    gg[j + 1] = make_float2(-(s.x * gk.x + s.y * gk.y), -(s.x * gk.y - s.y * gk.x));
+    const bool brk_now = hn <= a.brk * wn;
+    inv_s = brk_now ? 0.f : 1.f / hn;
+    kend_s = j + 1;
+    stop_s = brk_now ? 1 : 0;
+  };
+
   // ---- inner GMRES (Algorithm 1 step 4), CGS2 Arnoldi with Givens rotations
   for (int j = 0; j < a.kin && !stop_s; ++j) {
     const float invj = inv_s;  // v_j = W / h: W is complete since the last barrier
@@ -245,11 +285,11 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
     }
     if (!grid_sync(a.bar, G, a.err)) return;
     grid_reduce(part_of<KC>(a, 3 * j + 2), nb + 1, h1s);
-    // w -= V h1, second pass h2 = V^H w
+    // w -= V h1, second pass h2 = V^H w and ||w||^2 (slot nb)
     {
-      float2 v[KC + 1];
+      float2 v[KC + 2];
 #pragma unroll
-      for (int s = 0; s < KC + 1; ++s) v[s] = zero;
+      for (int s = 0; s < KC + 2; ++s) v[s] = zero;
 #pragma unroll
       for (int e = 0; e < PPT; ++e) {
         const long long p = t0 + e * T;
@@ -273,13 +313,38 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
               v[b].y = fmaf(vb[b].x, wv[e].y, fmaf(-vb[b].y, wv[e].x, v[b].y));
             }
           }
+          v[KC + 1].x = fmaf(wv[e].x, wv[e].x, fmaf(wv[e].y, wv[e].y, v[KC + 1].x));
         }
       }
-      block_partial<KC + 1, LDW>(part_of<KC>(a, 3 * j + 3), v, nb, wsum);
+#pragma unroll
+      for (int s = 0; s < KC + 1; ++s)
+        if (s == nb) v[s] = v[KC + 1];
+      block_partial<KC + 2, LDW>(part_of<KC>(a, 3 * j + 3), v, nb + 1, wsum);
     }
     if (!grid_sync(a.bar, G, a.err)) return;
-    grid_reduce(part_of<KC>(a, 3 * j + 3), nb, hs);
-    // w -= V h2, ||w||^2
+    grid_reduce(part_of<KC>(a, 3 * j + 3), nb + 1, hs);
+    // the Hessenberg column h1 + h2 (hs keeps h2 for the last pass)
+    if (threadIdx.x <= j) {
+      const float2 h2 = hs[threadIdx.x];
+      h1s[threadIdx.x] = make_float2(h1s[threadIdx.x].x + h2.x, h1s[threadIdx.x].y + h2.y);
+    }
+    __syncthreads();
+    // h_{j+1,j}^2 = ||w||^2 - ||h2||^2 for the w of this pass: V is orthonormal and w already
+    // nearly orthogonal to it, so the last pass removes little and the difference keeps its
+    // accuracy, and no reduction of ||w - V h2||^2 is needed.  Where the last pass removes more
+    // than three quarters of ||w||^2 (the difference would cancel) that norm is summed.  Every
+    // block computes the same scalars, so the branch is uniform over the grid.
+    if (threadIdx.x == 0) {
+      float q = 0.f;
+      for (int b = 0; b <= j; ++b) q = fmaf(hs[b].x, hs[b].x, fmaf(hs[b].y, hs[b].y, q));
+      const float wq = hs[nb].x, hp = wq - q;
+      fast_s = a.pyth && hp > 0.25f * wq ? 1 : 0;
+      if (fast_s) givens(j, sqrtf(hp));
+    }
+    __syncthreads();
+    const bool fast = fast_s;
+    const bool more = j + 1 < a.kin;
+    // w -= V h2 (and ||w||^2 where it is summed)
     {
       float2 v[1] = {zero};
 #pragma unroll
@@ -296,57 +361,31 @@ __global__ void __launch_bounds__(TB) k_fci_tail32(Tail a) {
             }
           }
           v[0].x = fmaf(wv[e].x, wv[e].x, fmaf(wv[e].y, wv[e].y, v[0].x));
-          a.W[p] = wv[e];  // every read of W in this step came before the first barrier
+          // every read of W in this step came before the first barrier
+          if (!fast || more) a.W[p] = wv[e];
         }
       }
-      block_partial<1, LDW>(part_of<KC>(a, 3 * j + 4), v, 1, wsum);
+      if (!fast) block_partial<1, LDW>(part_of<KC>(a, 3 * j + 4), v, 1, wsum);
     }
-    // the Hessenberg column h1 + h2, with h2 kept before hs is overwritten
-    if (threadIdx.x <= j) {
-      const float2 h2 = hs[threadIdx.x];
-      h1s[threadIdx.x] = make_float2(h1s[threadIdx.x].x + h2.x, h1s[threadIdx.x].y + h2.y);
+    if (fast) {
+      // v_{j+1} now; the barrier only where a next step's stencil reads W
+      if (!stop_s && more) {
+        const float inv = inv_s;
+        float2* vn = a.V + (long long)(j + 1) * n;
+#pragma unroll
+        for (int e = 0; e < PPT; ++e) {
+          const long long p = t0 + e * T;
+          if (p < pend) vn[p] = make_float2(wv[e].x * inv, wv[e].y * inv);
+        }
+        if (!grid_sync(a.bar, G, a.err)) return;
+      }
+      continue;
     }
     if (!grid_sync(a.bar, G, a.err)) return;
     grid_reduce(part_of<KC>(a, 3 * j + 4), 1, hs);
-    if (threadIdx.x == 0) {
-      // Givens step for column j (the same arithmetic as the multi-kernel float32 form)
-      const float hn = sqrtf(hs[0].x), wn = sqrtf(h1s[nb].x);
-      float2* col = R + j * (KC + 1);
-      for (int i = 0; i <= j; ++i) col[i] = h1s[i];
-      for (int i = 0; i < j; ++i) {
-        const float c = csn[i];
-        const float2 s = snn[i], x = col[i], y = col[i + 1];
-        col[i] = make_float2(c * x.x + (s.x * y.x - s.y * y.y), c * x.y + (s.x * y.y + s.y * y.x));
-        col[i + 1] = make_float2(-(s.x * x.x + s.y * x.y) + c * y.x, -(s.x * x.y - s.y * x.x) + c * y.y);
-      }
-      float c;
-      float2 s;
-      const float2 x = col[j];
-      if (hn == 0.f) {
-        c = 1.f;
-        s = zero;
-      } else if (x.x == 0.f && x.y == 0.f) {
-        c = 0.f;
-        s = make_float2(1.f, 0.f);
-      } else {
-        const float ra = hypotf(x.x, x.y);
-        const float rr = hypotf(ra, hn);
-        c = ra / rr;
-        s = make_float2(x.x / ra * hn / rr, x.y / ra * hn / rr);
-      }
-      col[j] = make_float2(c * x.x + s.x * hn, c * x.y + s.y * hn);
-      csn[j] = c;
-      snn[j] = s;
-      const float2 gk = gg[j];
-      gg[j] = make_float2(c * gk.x, c * gk.y);
-      gg[j + 1] = make_float2(-(s.x * gk.x + s.y * gk.y), -(s.x * gk.y - s.y * gk.x));
-      const bool brk_now = hn <= a.brk * wn;
-      inv_s = brk_now ? 0.f : 1.f / hn;
-      kend_s = j + 1;
-      stop_s = brk_now ? 1 : 0;
-    }
+    if (threadIdx.x == 0) givens(j, sqrtf(hs[0].x));
     __syncthreads();
-    if (!stop_s && j + 1 < a.kin) {
+    if (!stop_s && more) {
       const float inv = inv_s;
       float2* vn = a.V + (long long)(j + 1) * n;
 #pragma unroll
@@ -453,7 +492,7 @@ cudaError_t launch_fci_tail32(const Geom& g, const float2* dg, const float2* w32
                               const float2* f32, const double2* w64, float2* V, float2* W,
                               double2* out,
                               double2* partial, unsigned* bar, int* err, long long n, int kin,
-                              double brk, int ppt, int blocks, cudaStream_t st) {
+                              double brk, int pyth, int ppt, int blocks, cudaStream_t st) {
   if (kin > TAIL_KMAX || blocks < 1 || n > 0x7fffffffLL) return cudaErrorInvalidValue;
   Tail a;
   a.g = g;
@@ -469,6 +508,7 @@ cudaError_t launch_fci_tail32(const Geom& g, const float2* dg, const float2* w32
   a.err = err;
   a.n = n;
   a.kin = kin;
+  a.pyth = pyth;
   a.brk = float(brk);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

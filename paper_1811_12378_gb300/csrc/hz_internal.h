@@ -184,12 +184,14 @@ constexpr int TAIL_KMAX = 16;
 cudaError_t fci_tail32_plan(long long n, int kin, int* ppt, int* blocks);
 // Steps 3-5 of Algorithm 1 for one right-hand side: d from A w32 and f32, inner GMRES(kin) on
 // V (kin + 1 fields; W: one scratch field), out = V y + d w64.  bar: 2 zeroed counters; err:
-// set on a barrier timeout.  partial: at least 2 (TAIL_KMAX + 2) blocks float4.  n < 2^31.
+// set on a barrier timeout.  partial: at least 2 (TAIL_KMAX + 2) blocks float4.  pyth: take
+// each h_{j+1,j} from ||w||^2 - ||h2||^2 where that does not cancel (0: always sum the norm of
+// the last Gram-Schmidt pass).  n < 2^31.
 cudaError_t launch_fci_tail32(const Geom& g, const float2* dg, const float2* w32,
                               const float2* f32, const double2* w64, float2* V, float2* W,
                               double2* out,
                               double2* partial, unsigned* bar, int* err, long long n, int kin,
-                              double brk, int ppt, int blocks, cudaStream_t st);
+                              double brk, int pyth, int ppt, int blocks, cudaStream_t st);
 // ---- one outer float-pair Arnoldi step as one cooperative kernel (hz_arnoldi_ff.cu) ----
 // Points per thread and grid size for n points and restart length mmax; *ppt = 0 where the
 // grid cannot be co-resident or cooperative launch is unavailable.

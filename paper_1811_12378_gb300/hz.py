@@ -260,9 +260,11 @@ class Problem:
         _check(self._lib.hz_problem_get_info(self._h, C.byref(info)), self._lib)
         return _info_dict(info)
 
-    def fused_tail(self, on: bool = True):
-        """Complex64 FCI steps 3-5 as one cooperative kernel (default) or one kernel per piece."""
-        _check(self._lib.hz_problem_fused_tail(self._h, 1 if on else 0), self._lib)
+    def fused_tail(self, mode=1):
+        """Complex64 FCI steps 3-5: 1 one cooperative kernel (default), 2 the same with the
+        norm after the second Gram-Schmidt pass always summed, 0 (or False) one kernel per
+        piece."""
+        _check(self._lib.hz_problem_fused_tail(self._h, int(mode)), self._lib)
 
     def fused_arnoldi(self, mode=1):
         """Float-pair outer Arnoldi step: 1 one cooperative kernel (default), 2 the same with

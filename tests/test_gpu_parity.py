@@ -145,20 +145,26 @@ def test_fci_parity(prec, kin):
 @pytest.mark.parametrize("kin", [0, 1, 4, 10])
 def test_fci_fused_tail_one_rhs(kin):
     """Steps 3-5 of Algorithm 1 for one right-hand side as one cooperative kernel (k_in up to 4
-    and up to 16 use different instances): against the oracle, and against the per-piece
-    kernels, which differ from it only in the order of float32 roundings."""
+    and up to 16 use different instances), with h_{j+1,j} from the Pythagorean difference (the
+    default) or summed: against the oracle, and against the per-piece kernels, which differ
+    from it only in float32 rounding; deterministic."""
     wl = W.small_case(16, 22, 13, 9, layer=2, J=5)
     op, nodes = oracle_of(wl)
     r = W.random_field(19, 1, wl.nx, wl.ny, wl.nz)
     with problem_of(wl, nodes, nrhs_max=1, inner_k_max=10) as P:
         fused = to_np(P.fci(to_dev(r), inner_k=kin, precision=hzpkg.HZ_MIXED_C64_FCI32))
         fused2 = to_np(P.fci(to_dev(r), inner_k=kin, precision=hzpkg.HZ_MIXED_C64_FCI32))
+        P.fused_tail(2)  # the norm after the second Gram-Schmidt pass always summed
+        summed = to_np(P.fci(to_dev(r), inner_k=kin, precision=hzpkg.HZ_MIXED_C64_FCI32))
         P.fused_tail(False)
         piece = to_np(P.fci(to_dev(r), inner_k=kin, precision=hzpkg.HZ_MIXED_C64_FCI32))
+        with pytest.raises(hzpkg.HzError):
+            P.fused_tail(-1)
     ref = O.fci(op, r[0], nodes, kin)
     assert np.array_equal(fused, fused2)
-    assert rel(fused[0], ref) <= 2e-5
-    assert rel(fused[0], piece[0]) <= 2e-5
+    for out in (fused, summed):
+        assert rel(out[0], ref) <= 2e-5
+        assert rel(out[0], piece[0]) <= 2e-5
 
 
 def test_fci_eigenvector_exact_gpu():
