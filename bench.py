@@ -424,9 +424,8 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "form": "mixed, FCI in complex64: polynomial sweeps, "
                    "step d and inner GMRES in complex64, quadrature sum accumulated in float pairs "
                    "(~48 bits) and returned in float64; "
-                   "outer FGMRES Arnoldi basis, CGS2 and Givens rotations in float pairs (two "
-                   "float32, ~48 bits); Hessenberg storage, solution update and true residual in "
-                   "float64",
+                   "outer FGMRES Arnoldi basis and CGS2 in float pairs (two float32, ~48 bits); "
+                   "Hessenberg, Givens, solution update and true residual in float64",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"replicas x{world}"},
         "its": st_mixed.its, "matvecs": st_mixed.matvecs,

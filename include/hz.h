@@ -64,13 +64,12 @@ typedef enum {
                          FGMRES (CGS2 Arnoldi, Givens, updates) and the true residual in
                          float64.  FGMRES admits a variable preconditioner, so the solution
                          still reaches the float64 residual target. */
-  HZ_MIXED_C64_FF = 3  /* as HZ_MIXED_C64_FCI32, with the outer Arnoldi basis, its CGS2
-                         passes and the Givens rotations in float pairs (two float32 per value,
-                         about 48 significant bits, error-free float32 products and two-sum
-                         additions) instead of float64; the Hessenberg matrix and rotated
-                         right-hand side are stored, and the solution update and the true
-                         residual computed, in float64.  Only hz_solve / hz_solve_batched
-                         distinguish it; hz_fci treats it as HZ_MIXED_C64_FCI32. */
+  HZ_MIXED_C64_FF = 3  /* as HZ_MIXED_C64_FCI32, with the outer Arnoldi basis and its CGS2
+                         passes in float pairs (two float32 per value, about 48 significant
+                         bits, error-free float32 products and two-sum additions) instead of
+                         float64; Hessenberg, Givens, the solution update and the true
+                         residual stay float64.  Only hz_solve / hz_solve_batched distinguish
+                         it; hz_fci treats it as HZ_MIXED_C64_FCI32. */
 } hz_precision;
 
 /* Grid and medium.  Interior points nx*ny*nz with spacing h; omega the angular frequency;

@@ -2,7 +2,8 @@
 // cooperative kernel: w = A z_k (float64 stencil, rounded to float pairs), the two classical
 // Gram-Schmidt passes against v_0..v_k, ||w||, the Givens step of the new Hessenberg column
 // and v_{k+1} = w / h_{k+1,k} with its complex64 rounding, the next FCI application's input
-// (the Arnoldi process of FGMRES, Section 3, with the CGS2 orthogonalisation).
+// (the Arnoldi process of FGMRES, Section 3, with the CGS2 orthogonalisation).  The Givens step
+// and its least-squares state are float64 (givens_column, block 0).
 //
 // Per point the arithmetic is that of the multi-kernel form (k_stencil_diag<true>,
 // k_cgs_ff<0..2>, k_scale_ff): the same float-pair products in the same order, the same
@@ -318,11 +319,11 @@ __global__ void __launch_bounds__(AT, 1) k_arnoldi_ff(Arn a, int ppt) {
   }
   const float2 wn2 = re_of(h1f[nb]);
 
-  // ---- v_{k+1} = w / h_{k+1,k} (zero at a breakdown), as the Givens step decides it
+  // ---- v_{k+1} = w / h_{k+1,k} (zero at a breakdown): the float64 test and scale of the
+  // Givens step (givens_column), from the same float64 values it reads
   if (threadIdx.x == 0) {
-    float2 hn, inv;
-    ff_step_inv(hn2, wn2, float(a.brk), &hn, &inv);
-    s_inv = inv;
+    const double hn = sqrt(d_from_ff(hn2)), wn = sqrt(d_from_ff(wn2));
+    s_inv = ff_from_d(hn <= a.brk * wn ? 0.0 : 1.0 / hn);
   }
   __syncthreads();
   {
@@ -343,9 +344,13 @@ __global__ void __launch_bounds__(AT, 1) k_arnoldi_ff(Arn a, int ppt) {
     }
   }
   if (blockIdx.x == 0) {
-    float4* col = wp + 8;  // past ||w||^2; wp holds AWARPS (nb + 8) >= nb + 9 entries
-    for (int i = threadIdx.x; i < nb; i += AT) col[i] = ffc_add(h1f[i], h2f[i]);
-    givens_column_ff(a.gs, 0, nb - 1, a.brk, col, hn2, wn2);
+    // the Hessenberg column and the norms in float64 for the Givens step (float64 least squares)
+    for (int i = threadIdx.x; i <= nb; i += AT) {
+      a.gs.h1[i] = d_from_ffc(h1f[i]);
+      if (i < nb) a.gs.h2[i] = d_from_ffc(h2f[i]);
+    }
+    if (threadIdx.x == 0) a.gs.nrm[0] = make_double2(d_from_ff(hn2), 0.0);
+    givens_column(a.gs, 0, nb - 1, a.brk);  // starts with a block barrier
   }
 }
 

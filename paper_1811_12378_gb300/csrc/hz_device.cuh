@@ -144,8 +144,8 @@ __device__ __forceinline__ float4 warp_sum_partials_ff(const float4* part, int s
   return acc;
 }
 
-// The same sum in compact code, for the cooperative kernels.  Their reductions and Givens step
-// run between long passes that have pushed them out of the instruction cache, and there an
+// The same sum in compact code, for the cooperative kernels.  Their reductions run between long
+// passes that have pushed them out of the instruction cache, and there an
 // unrolled float-pair sequence costs several cycles per instruction in fetches (measured: the
 // cooperative outer Arnoldi step 1.5% faster per solve with this form, while the short
 // reduction kernels were 1.5% slower with it); one out-of-line add serves every step.
@@ -508,10 +508,9 @@ __device__ void givens_column(const GmresDev& gs, int r, int k, double brk) {
   if (brk_now || est <= sc[SC_TOL]) gs.stopped[r] = 1;
 }
 
-// ---------------------------------------------------------------- float-pair Givens step
-// Double-float arithmetic after Dekker (1971): a value is hi + lo with |lo| <= half an ulp of
-// hi; products split exactly by an FMA, quotients and square roots by one correction step
-// from the float32 result.  About 48 significant bits; float32 instructions only.
+// ---------------------------------------------------------------- float-pair products
+// Double-float product after Dekker (1971): hi from the float32 product, its rounding error
+// exactly from an FMA, the cross terms added; about 48 significant bits.
 __device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
   const float p = __fmul_rn(a.x, b.x);
   float e = __fmaf_rn(a.x, b.x, -p);
@@ -519,167 +518,6 @@ __device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
   return fast_two_sum(p, e);
 }
 __device__ __forceinline__ float2 ff_sub(float2 a, float2 b) { return ff_add(a, neg(b)); }
-__device__ __forceinline__ float2 ff_scale2(float2 a, float s) {  // s a power of two: exact
-  return make_float2(a.x * s, a.y * s);
-}
-// a / b: q1 = a.hi / b.hi, then the remainder a - q1 b (exact products) divided once more
-__device__ __forceinline__ float2 ff_div(float2 a, float2 b) {
-  const float q1 = __fdiv_rn(a.x, b.x);
-  const float2 r = ff_sub(a, ff_mul(b, make_float2(q1, 0.f)));
-  return fast_two_sum(q1, __fdiv_rn(r.x, b.x));
-}
-// sqrt(x), x >= 0: y = sqrt(x.hi) rounded, corrected by (x - y^2) / (2 y) with y^2 exact
-__device__ __forceinline__ float2 ff_sqrt(float2 x) {
-  if (!(x.x > 0.f)) return make_float2(0.f, 0.f);
-  const float y = __fsqrt_rn(x.x);
-  const float p = __fmul_rn(y, y);
-  const float e = __fmaf_rn(y, y, -p);
-  const float r = __fadd_rn(__fsub_rn(__fsub_rn(x.x, p), e), x.y);
-  return fast_two_sum(y, __fdiv_rn(r, __fmul_rn(2.f, y)));
-}
-__device__ __forceinline__ bool ff_le(float2 a, float2 b) {
-  return a.x < b.x || (a.x == b.x && a.y <= b.y);
-}
-// complex float pairs, float4 (re.hi, re.lo, im.hi, im.lo)
-__device__ __forceinline__ float4 ffc(float2 re, float2 im) {
-  return make_float4(re.x, re.y, im.x, im.y);
-}
-// (out of line: the float-pair Givens step below runs from a cold instruction cache, see
-// warp_sum_partials_ffn)
-__device__ __noinline__ float4 ffc_mul(float4 a, float4 b) {
-  const float2 ar = re_of(a), ai = im_of(a), br = re_of(b), bi = im_of(b);
-  return ffc(ff_sub(ff_mul(ar, br), ff_mul(ai, bi)), ff_add(ff_mul(ar, bi), ff_mul(ai, br)));
-}
-__device__ __noinline__ float4 ffc_rmul(float2 c, float4 a) {  // real c times complex a
-  return ffc(ff_mul(c, re_of(a)), ff_mul(c, im_of(a)));
-}
-__device__ __noinline__ float2 ff_div_n(float2 a, float2 b) { return ff_div(a, b); }
-__device__ __noinline__ float2 ff_sqrt_n(float2 x) { return ff_sqrt(x); }
-__device__ __forceinline__ float4 ffc_mconj(float4 s) {  // -conj(s)
-  return make_float4(-s.x, -s.y, s.z, s.w);
-}
-__device__ __forceinline__ float4 ffc_from_d(double2 v) {
-  return ffc(ff_from_d(v.x), ff_from_d(v.y));
-}
-__device__ __forceinline__ float4 shfl_up4(float4 v, int o) {
-  return make_float4(__shfl_up_sync(0xffffffffu, v.x, o), __shfl_up_sync(0xffffffffu, v.y, o),
-                     __shfl_up_sync(0xffffffffu, v.z, o), __shfl_up_sync(0xffffffffu, v.w, o));
-}
-// 2^-e with 2^e near the largest of the given magnitudes (0 -> 1): exact rescaling that keeps
-// squares inside the float32 range
-__device__ __forceinline__ float ff_pow2_scale(float m) {
-  return m > 0.f ? ldexpf(1.f, -ilogbf(m)) : 1.f;
-}
-__device__ __forceinline__ float2 ffc_abs(float4 v) {
-  const float sc = ff_pow2_scale(fmaxf(fabsf(v.x), fabsf(v.z)));
-  const float2 re = ff_scale2(re_of(v), sc), im = ff_scale2(im_of(v), sc);
-  return ff_scale2(ff_sqrt_n(ff_add(ff_mul(re, re), ff_mul(im, im))), 1.f / sc);
-}
-
-// The breakdown test and the scale of the next basis vector from ||w||^2 after (hn2) and
-// before (wn2) the orthogonalisation: *inv = 1 / h_{k+1,k}, or 0 when h_{k+1,k} <= brk ||w||
-// (the test of givens_column).  Every caller gets the same bits from the same sums.
-__device__ __forceinline__ bool ff_step_inv(float2 hn2, float2 wn2, float brk, float2* hn,
-                                            float2* inv) {
-  *hn = ff_sqrt_n(hn2);
-  const float2 wn = ff_sqrt_n(wn2);
-  const bool brk_now = ff_le(*hn, ff_mul(make_float2(brk, 0.f), wn));
-  *inv = brk_now ? make_float2(0.f, 0.f) : ff_div_n(make_float2(1.f, 0.f), *hn);
-  return brk_now;
-}
-
-// Givens step for column k of rhs r in float pairs (the float-pair outer Arnoldi form), called
-// by every thread of one block; warp 0 works.  col[0..k] is the new Hessenberg column h1 + h2
-// (shared memory, float pairs), hn2 / wn2 as for ff_step_inv.  The sweep over the previous
-// rotations is the prefix scan of givens_column, here on the float32 pipes (a float64
-// instruction issues at 1/64 of their rate).  The rotations are kept as float pairs in the
-// storage of gs.cc / gs.ss (a float2 per cosine, a float4 per sine); R, g and the scalars are
-// written in float64.
-__device__ void givens_column_ff(const GmresDev& gs, int r, int k, double brk, const float4* col,
-                                 float2 hn2, float2 wn2) {
-  __syncthreads();  // col, and the caller's stores, come first
-  if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
-  const int M = gs.mmax;
-  float2* ccf = reinterpret_cast<float2*>(gs.cc + (long long)r * M);
-  float4* ssf = reinterpret_cast<float4*>(gs.ss + (long long)r * M);
-  double2* R = gs.R + (long long)r * (M + 1) * M + (long long)k * (M + 1);
-  const float4 one = make_float4(1.f, 0.f, 0.f, 0.f), zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  const int q = (k + 31) / 32;
-  const int i0 = min(lane * q, k), i1 = min(i0 + q, k);
-  float4 A = one, B = zero4;
-  for (int i = i0; i < i1; ++i) {
-    const float2 c = ccf[i];
-    const float4 al = ffc_mconj(ssf[i]);
-    B = ffc_add_n(ffc_mul(al, B), ffc_rmul(c, col[i + 1]));
-    A = ffc_mul(al, A);
-  }
-#pragma unroll 1
-  for (int o = 1; o < 32; o <<= 1) {
-    const float4 Ap = shfl_up4(A, o), Bp = shfl_up4(B, o);
-    if (lane >= o) {
-      B = ffc_add_n(ffc_mul(A, Bp), B);
-      A = ffc_mul(A, Ap);
-    }
-  }
-  float4 Ax = shfl_up4(A, 1), Bx = shfl_up4(B, 1);
-  if (lane == 0) {
-    Ax = one;
-    Bx = zero4;
-  }
-  float4 t = ffc_add_n(ffc_mul(Ax, col[0]), Bx);  // t_{i0}
-  for (int i = i0; i < i1; ++i) {
-    const float2 c = ccf[i];
-    const float4 s = ssf[i], hn1 = col[i + 1];
-    R[i] = d_from_ffc(ffc_add_n(ffc_mul(s, hn1), ffc_rmul(c, t)));
-    t = ffc_add_n(ffc_mul(ffc_mconj(s), t), ffc_rmul(c, hn1));
-  }
-  const int last = k == 0 ? 0 : (k - 1) / q;
-  if (lane != last) return;
-  double* sc = gs.scal + (long long)r * SC_COUNT;
-  float2 hn, inv;
-  const bool brk_now = ff_step_inv(hn2, wn2, float(brk), &hn, &inv);
-  float2 c;
-  float4 s;
-  const float4 a = t;
-  if (hn.x == 0.f) {
-    c = make_float2(1.f, 0.f);
-    s = zero4;
-  } else if (a.x == 0.f && a.z == 0.f) {
-    c = make_float2(0.f, 0.f);
-    s = one;
-  } else {
-    // c = |a| / rho, s = (a / |a|) hn / rho, rho = sqrt(|a|^2 + hn^2), from values rescaled
-    // by a power of two (the ratios do not change)
-    const float sc2 = ff_pow2_scale(fmaxf(fmaxf(fabsf(a.x), fabsf(a.z)), hn.x));
-    const float2 ar = ff_scale2(re_of(a), sc2), ai = ff_scale2(im_of(a), sc2);
-    const float2 hs = ff_scale2(hn, sc2);
-    const float2 ra2 = ff_add(ff_mul(ar, ar), ff_mul(ai, ai));
-    const float2 ra = ff_sqrt_n(ra2);
-    const float2 rho = ff_sqrt_n(ff_add(ra2, ff_mul(hs, hs)));
-    c = ff_div_n(ra, rho);
-    const float2 f = ff_div_n(hs, ff_mul(ra, rho));
-    s = ffc(ff_mul(ar, f), ff_mul(ai, f));
-  }
-  // R_kk = c a + s hn
-  const float4 rkk = ffc_add_n(ffc_rmul(c, a), ffc(ff_mul(re_of(s), hn), ff_mul(im_of(s), hn)));
-  ccf[k] = c;
-  ssf[k] = s;
-  double2* gg = gs.g + (long long)r * (M + 1);
-  const float4 gk = ffc_from_d(gg[k]);
-  const float4 gk1 = ffc_mul(ffc_mconj(s), gk);
-  const float2 est = ffc_abs(gk1);
-  R[k] = d_from_ffc(rkk);
-  R[k + 1] = make_double2(0.0, 0.0);
-  gg[k] = d_from_ffc(ffc_rmul(c, gk));
-  gg[k + 1] = d_from_ffc(gk1);
-  const double estd = d_from_ff(est);
-  sc[SC_EST] = estd;
-  sc[SC_HN] = d_from_ff(hn);
-  sc[SC_INV] = d_from_ff(inv);
-  gs.kend[r] = k + 1;
-  if (brk_now || estd <= sc[SC_TOL]) gs.stopped[r] = 1;
-}
 
 }  // namespace
 }  // namespace hz

@@ -6,8 +6,8 @@
 // (hi + lo, about 48 significant bits): a complex element is a float4 (re.hi, re.lo, im.hi,
 // im.lo), 16 bytes like a double2.  Products are error-free float32 transformations (FMA),
 // sums are two-sum chains, so the CGS2 passes run on the float32 pipes.  Dots are accumulated
-// across warps and blocks as float pairs too and stored in float64 once per value; the Givens
-// step (givens_column_ff) also runs in float pairs and stores R, g and the scalars in float64.
+// across warps and blocks as float pairs too and converted to float64 once per value; the
+// Hessenberg/Givens least squares stays float64, as in the float64 form.
 #include <cuda_runtime.h>
 
 #include "hz_device.cuh"
@@ -159,25 +159,13 @@ k_cgs_ff(const float4* __restrict__ V, long long vis, long long vrs, int nb, flo
   if (!last_block(counters + r)) return;
   double2* out = MODE == 0 ? gs.h1 + (long long)r * (M + 2)
                : MODE == 1 ? gs.h2 + (long long)r * (M + 2) : gs.nrm + 2 * r;
-  __shared__ float2 s_hn2;
   for (int sidx = warp; sidx < nslots; sidx += F_WARPS) {
     const float4 t = warp_sum_partials_ff(part, sidx, (int)gridDim.x, lane);
-    if (lane == 0) {
-      out[sidx] = d_from_ffc(t);
-      if (MODE == 2) s_hn2 = make_float2(t.x, t.y);
-    }
+    if (lane == 0) out[sidx] = d_from_ffc(t);
   }
   __syncthreads();
   if (threadIdx.x == 0) counters[r] = 0;
-  if (MODE == 2) {
-    // the Hessenberg column h1 + h2 as float pairs (the float64 copies convert back exactly)
-    const double2* h1 = gs.h1 + (long long)r * (M + 2);
-    const double2* h2 = gs.h2 + (long long)r * (M + 2);
-    float4* col = sm4;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x)
-      col[i] = ffc_add(ffc_from_d(h1[i]), ffc_from_d(h2[i]));
-    givens_column_ff(gs, r, nb - 1, brk, col, s_hn2, ff_from_d(h1[nb].x));  // whole block
-  }
+  if (MODE == 2) givens_column(gs, r, nb - 1, brk);  // whole block; float64 least squares
 }
 
 // v = w * (1 / h_{k+1,k}) in place on float pairs; the float64 scale is split once per block.
