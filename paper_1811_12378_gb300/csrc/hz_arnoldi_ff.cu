@@ -306,26 +306,43 @@ __global__ void __launch_bounds__(AT, 1) k_arnoldi_ff(Arn a, int ppt) {
     }
   }
   __syncthreads();
-  float2 hn2;
-  update(a, P, sw, hf);  // w -= V h2
+  const float2 wn2 = re_of(h1f[nb]);
+  // v_{k+1} = w / h_{k+1,k} (zero at a breakdown): the float64 test and scale of the Givens
+  // step (givens_column), from the same float64 values it reads
+  auto set_inv = [&](float2 hn2) {
+    const double hn = sqrt(d_from_ff(hn2)), wn = sqrt(d_from_ff(wn2));
+    s_inv = ff_from_d(hn <= a.brk * wn ? 0.0 : 1.0 / hn);
+  };
+  // block 0: the Hessenberg column and the norms in float64 for the Givens step
+  auto store_column = [&](float2 hn2) {
+    for (int i = threadIdx.x; i <= nb; i += AT) {
+      a.gs.h1[i] = d_from_ffc(h1f[i]);
+      if (i < nb) a.gs.h2[i] = d_from_ffc(h2f[i]);
+    }
+    if (threadIdx.x == 0) a.gs.nrm[0] = make_double2(d_from_ff(hn2), 0.0);
+  };
+  bool givens_done = false;
   if (s_fast) {
-    hn2 = s_hn2;
+    // h_{k+1,k} is known: block 0's first warp runs the Givens step (serial float64, about
+    // 14 us) while the other warps start the last pass, and does its own points after it
+    const float2 hn2 = s_hn2;
+    if (threadIdx.x == 0) set_inv(hn2);
+    if (blockIdx.x == 0) store_column(hn2);
+    __syncthreads();  // uniform: s_fast is the same in every thread
+    if (blockIdx.x == 0 && threadIdx.x < 32) givens_column_warp(a.gs, 0, nb - 1, a.brk);
+    givens_done = true;
+    update(a, P, sw, hf);  // w -= V h2
   } else {
+    update(a, P, sw, hf);
     warp_norm(P, sw, wp, ldw, 0);
     block_partial(arn_part(a, 2), wp, ldw, 1);
     if (!grid_sync(a.bar, G, a.err)) return;
     grid_reduce(arn_part(a, 2), 1, wp, hf, 0);  // ||w||^2 to wp[0]
-    hn2 = re_of(wp[0]);
+    const float2 hn2 = re_of(wp[0]);
+    if (threadIdx.x == 0) set_inv(hn2);
+    if (blockIdx.x == 0) store_column(hn2);
+    __syncthreads();
   }
-  const float2 wn2 = re_of(h1f[nb]);
-
-  // ---- v_{k+1} = w / h_{k+1,k} (zero at a breakdown): the float64 test and scale of the
-  // Givens step (givens_column), from the same float64 values it reads
-  if (threadIdx.x == 0) {
-    const double hn = sqrt(d_from_ff(hn2)), wn = sqrt(d_from_ff(wn2));
-    s_inv = ff_from_d(hn <= a.brk * wn ? 0.0 : 1.0 / hn);
-  }
-  __syncthreads();
   {
     const float2 s = s_inv;
 #pragma unroll 1
@@ -343,15 +360,8 @@ __global__ void __launch_bounds__(AT, 1) k_arnoldi_ff(Arn a, int ppt) {
       }
     }
   }
-  if (blockIdx.x == 0) {
-    // the Hessenberg column and the norms in float64 for the Givens step (float64 least squares)
-    for (int i = threadIdx.x; i <= nb; i += AT) {
-      a.gs.h1[i] = d_from_ffc(h1f[i]);
-      if (i < nb) a.gs.h2[i] = d_from_ffc(h2f[i]);
-    }
-    if (threadIdx.x == 0) a.gs.nrm[0] = make_double2(d_from_ff(hn2), 0.0);
-    givens_column(a.gs, 0, nb - 1, a.brk);  // starts with a block barrier
-  }
+  if (blockIdx.x == 0 && !givens_done && threadIdx.x < 32)
+    givens_column_warp(a.gs, 0, nb - 1, a.brk);
 }
 
 constexpr int ARN_PPT_MAX = 16;

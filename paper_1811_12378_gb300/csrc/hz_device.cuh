@@ -426,10 +426,10 @@ __device__ __forceinline__ double2 shfl_up2(double2 v, int o) {
   return make_double2(__shfl_up_sync(0xffffffffu, v.x, o), __shfl_up_sync(0xffffffffu, v.y, o));
 }
 
-__device__ void givens_column(const GmresDev& gs, int r, int k, double brk) {
-  __syncthreads();  // the caller's stores of h1, h2 and the norm come first
-  if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
+// The step itself, run by one whole warp (lane = threadIdx.x & 31) once h1, h2 and the norm of
+// column k are in memory and visible to it.
+__device__ void givens_column_warp(const GmresDev& gs, int r, int k, double brk) {
+  const int lane = threadIdx.x & 31;
   const int M = gs.mmax;
   const double2* h1 = gs.h1 + (long long)r * (M + 2);
   const double2* h2 = gs.h2 + (long long)r * (M + 2);
@@ -506,6 +506,11 @@ __device__ void givens_column(const GmresDev& gs, int r, int k, double brk) {
   sc[SC_INV] = brk_now ? 0.0 : 1.0 / hn;
   gs.kend[r] = k + 1;
   if (brk_now || est <= sc[SC_TOL]) gs.stopped[r] = 1;
+}
+
+__device__ void givens_column(const GmresDev& gs, int r, int k, double brk) {
+  __syncthreads();  // the caller's stores of h1, h2 and the norm come first
+  if (threadIdx.x < 32) givens_column_warp(gs, r, k, brk);
 }
 
 // ---------------------------------------------------------------- float-pair products
