@@ -9,13 +9,14 @@
 // k_cgs_ff<0..2>, k_scale_ff): the same float-pair products in the same order, the same
 // float64 coefficients rounded to float pairs.  Only the grouping of the global sums differs.
 // The five launches of that form spend much of their time in ramps, in a partial second wave
-// and in the serial finish of each reduction by its last block; here the grid stays resident
-// (one block of 512 threads on every SM), each block owns a contiguous range of points and keeps its part of
-// w in shared memory through every pass, and the passes are separated by two grid barriers
-// (three where the Pythagorean norm of the last pass would cancel, see below).  After each barrier every
-// block adds all blocks' float-pair partials in the same fixed order, so every block holds the
-// same float64 coefficients without a broadcast.  Block 0 alone writes the Hessenberg column
-// and runs the Givens step.
+// and in the serial finish of each reduction by its last block.  Here the grid stays resident
+// (one block of 512 threads on every SM), each block owns a contiguous range of points and
+// keeps its part of w in shared memory through every pass, and the passes are separated by two
+// grid barriers (three where the Pythagorean norm of the last pass would cancel, see below).
+// After each barrier every block adds all blocks' float-pair partials in the same fixed order,
+// so every block holds the same coefficients without a broadcast.  Block 0 alone writes the
+// Hessenberg column, and its first warp runs the Givens step while the other warps, and every
+// other block, run the last pass.
 //
 // The barrier spins with a bound (about a second); a block that gives up sets the error flag
 // and returns, the others then skip their waits, and the host reports the flag after the solve.
