@@ -1,6 +1,7 @@
 """Parity at the benchmark's full sizes, in the configuration bench.py times, checked with
 properties the oracle computes cheaply at any size: the float64 true residual of every GPU
-solution (one oracle matvec each) and the stencil itself on 256^3 fields.
+solution (one oracle matvec each) and the stencil itself on 256^3 fields, and the 256^3
+sixteen-source configuration through a fixed number of outer steps.
 
 Tolerances: the solver's own 1e-8 relative residual (plus 1e-12 for the difference between the
 library's and numpy's float64 residual sums); stencil float64 1e-14, complex64 2e-6 relative L2.
@@ -79,3 +80,36 @@ def test_stencil_256():
         assert np.linalg.norm(y - ref) <= 1e-14 * np.linalg.norm(ref)
         y32 = P.apply_shifted(xd.to(torch.complex64), z).cpu().numpy().reshape(op.shape)
         assert np.linalg.norm(y32 - ref) <= 2e-6 * np.linalg.norm(ref)
+
+
+def test_large_256_sixteen_sources_fixed_steps():
+    """The large configuration at full size (256^3, c in [1, 3], 12-cell sponge, 8 ppw, J = 8,
+    16 point sources), chosen form, two calls of 8 right-hand sides (the workspace of 16 at
+    once, with the restart storage, would not fit in the device memory): one cycle of a fixed
+    10 outer steps per call.  Properties: every reported float64 true residual has dropped
+    below 1, and for one sampled right-hand side of each call it equals the oracle's matvec
+    residual of the returned solution."""
+    wl, idx = W.large_bumps_256()
+    N = wl.nx
+    n = N ** 3
+    amp = 1.0 / wl.h ** 3
+    op = O.make_operator(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max)
+    with hzpkg.Problem(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, wl.J, wl.t, wl.eps,
+                       nrhs_max=8, restart_max=10, inner_k_max=wl.k_in) as P:
+        for half in range(2):
+            srcs = idx[8 * half: 8 * half + 8]
+            f = torch.zeros((8, n), dtype=torch.complex128, device=DEV)
+            for r, (i, j, k) in enumerate(srcs):
+                f[r, i + N * (j + N * k)] = amp
+            u, st = P.solve(f, restart=10, inner_k=wl.k_in, rtol=wl.rtol, max_cycles=1,
+                            fixed_its=10, precision=hzpkg.HZ_MIXED_C64_FF, check=False)
+            assert [s.its for s in st] == [10] * 8
+            assert all(0.0 < s.rel_res_true < 1.0 for s in st)
+            r = 3 + half
+            i, j, k = srcs[r]
+            fr = np.zeros(op.shape, dtype=np.complex128)
+            fr[k, j, i] = amp
+            ur = u[r].cpu().numpy().reshape(op.shape)
+            del u, f
+            res = _residual(op, fr, ur)
+            assert abs(res - st[r].rel_res_true) <= 1e-12 + 1e-9 * res

@@ -168,6 +168,23 @@ def gaussian_bumps_64(seed: int = 1) -> Workload:
                     8, 1.0, default_eps(n, n, n), 30, 4, 1e-8, c, f)
 
 
+def large_bumps_256(seed: int = 5, nsrc: int = 16):
+    """256^3 (h = 1/257), c = 1 + 16 Gaussian bumps (width 0.1, amplitudes U[0, 2]) clipped to
+    [1, 3], 8 ppw at c_min, 12-cell sponge, J = 8 contour nodes, FGMRES(40) with k_in = 4 to
+    1e-8, nsrc unit point sources (value 1/h^3) at seeded core points.  The right-hand sides are
+    returned as grid indices (nsrc fields of 256^3 complex128 values would be 4.3 GB on the
+    host): (Workload with an empty f, [(i, j, k), ...])."""
+    n = 256
+    h = 1.0 / (n + 1)
+    c = medium_gaussian_bumps(seed, n, n, n, h, nbumps=16, width=0.1, amp_hi=2.0, c_lo=1.0,
+                              c_hi=3.0)
+    g = _rng(seed + 1000)
+    idx = [random_core_index(g, n, n, n, 12) for _ in range(nsrc)]
+    f = np.zeros((0, 1, 1, 1), dtype=np.complex128)
+    return (Workload("large_bumps_256", n, n, n, h, omega_for_ppw(c, h, 8.0), 12, 1.0, 8, 1.0,
+                     default_eps(n, n, n), 40, 4, 1e-8, c, f), idx)
+
+
 def small_case(seed: int, nx: int, ny: int, nz: int, nrhs: int = 1, ppw: float = 8.0,
                layer: int = 2, J: int = 4, restart: int = 10, k_in: int = 3,
                medium: str = "bumps") -> Workload:
