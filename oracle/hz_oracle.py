@@ -14,6 +14,8 @@ Everything is complex128 / float64 numpy, written step by step in the paper's or
 * poly solve    fixed-point scheme                           (§4.2 eq:fix-pt-exp)
 * FCI           quadrature, step d, inner GMRES              (§2 Algorithm 1)
 * FGMRES        flexible GMRES with FCI as right precond.    (§2, after Algorithm 1)
+* Case Two      iC - I on (iu; u), its spectrum rectangle    (§3 eq:mat-2x2, Theorem
+                and Algorithm 1 / FGMRES on it                thm:spectrum-2x2 and Remark)
 
 Readings of points the paper leaves open (sign of the damping, normalisation, sponge
 profile, delta search, stopping by a fixed sweep count, CGS2, Givens) are stated at each
@@ -510,3 +512,75 @@ def solve(op: Operator, f: np.ndarray, nodes: list, m: int, k_in: int, rtol: flo
           max_cycles: int, fixed_its: int = 0) -> SolveResult:
     """A u = f by FGMRES(m) preconditioned with FCI (Algorithm 1)."""
     return fgmres(op, f, lambda v: fci(op, v, nodes, k_in), m, rtol, max_cycles, fixed_its)
+
+
+# ---------------------------------------------------------------------------------------
+# Case Two (§3, eq:mat-2x2, Theorem thm:spectrum-2x2): the double-size system
+# ---------------------------------------------------------------------------------------
+
+@dataclass
+class Operator2x2:
+    """Case Two's coefficient matrix iC - I on stacked fields x = (x1; x2) of shape
+    (2, nz, ny, nx), with C = [[0, I], [-(A1 + I), -A2]] (eq:mat-2x2) and A = A1 - i A2 the
+    Case One operator split as in spectrum_box: A1 = s L_h - diag(m) Hermitian, A2 =
+    diag(a) positive semi-definite.  (iC - I)(iu; u) = (0; f) holds exactly when A u = f.
+    It exposes the ``apply`` / ``shape`` interface the polynomial scheme, Algorithm 1 and
+    FGMRES use, so those run on it unchanged.
+    """
+    base: Operator
+
+    @property
+    def shape(self):
+        return (2,) + self.base.shape
+
+    @property
+    def n(self):
+        return 2 * self.base.n
+
+    def apply_c(self, x: np.ndarray):
+        """C x = (x2; -(A1 + I) x1 - A2 x2)."""
+        x = np.asarray(x, dtype=np.complex128).reshape(self.shape)
+        x1, x2 = x[0], x[1]
+        a1x1 = self.base.apply(x1) + 1j * self.base.a * x1  # A1 x1 = A x1 + i A2 x1
+        return np.stack([x2, -(a1x1 + x1) - self.base.a * x2])
+
+    def apply(self, x: np.ndarray, z: complex = 0.0) -> np.ndarray:
+        """((iC - I) - z I) x."""
+        x = np.asarray(x, dtype=np.complex128).reshape(self.shape)
+        return 1j * self.apply_c(x) - x - z * x
+
+
+def spectrum_box_2x2(op: Operator):
+    """A rectangle [b1, b2] x [-rho2, 0] containing the spectrum of iC - I.
+
+    The Remark after Theorem thm:spectrum-2x2 puts it in |mu + 1| <= R, -rho2 <= Im mu <= 0,
+    R = rho2/2 + sqrt(rho2^2/4 + rho1), with rho1 = rho(A1 + I) and rho2 = rho(A2) as in
+    Lemma lem:spectrum-1x1.  Reading: rho1 from Weyl's inequality as in spectrum_box,
+    rho(A1 + I) <= s*lmax - min m + 1 (A1 + I is positive semi-definite since m <= 1), and
+    [b1, b2] = [-1 - R, -1 + R].  Returns (b1, b2, rho2, rho1, R).
+    """
+    _, hi = laplacian_extremes(op.nx, op.ny, op.nz, op.h)
+    rho1 = op.s * hi - float(op.m.min()) + 1.0
+    rho2 = float(op.a.max())
+    R = rho2 / 2.0 + math.sqrt(rho2 * rho2 / 4.0 + rho1)
+    return -1.0 - R, -1.0 + R, rho2, rho1, R
+
+
+def setup_nodes_2x2(op: Operator, J: int, t: float, eps: float, qmax: int = 5,
+                    reduction: float = 5.0):
+    """Contour and per-node parameters of Algorithm 1 for iC - I: the nodes of eq:quad-points
+    depend on rho2 and eps only, the polynomial scheme's rate on the rectangle above."""
+    b1, b2, rho2, _, _ = spectrum_box_2x2(op)
+    z, sigma = contour_nodes(J, t, eps, rho2)
+    nodes = [node_parameters(zj, sj, b1, b2, rho2, qmax, reduction) for zj, sj in zip(z, sigma)]
+    return (b1, b2, rho2), nodes
+
+
+def solve_2x2(op: Operator, f: np.ndarray, nodes: list, m: int, k_in: int, rtol: float,
+              max_cycles: int, fixed_its: int = 0) -> SolveResult:
+    """Case Two: (iC - I) Y = (0; f) by FGMRES(m) with FCI on iC - I; the solution of
+    A u = f is u = Y[1] (eq:mat-2x2).  rel_res_true is the 2x2 system's residual."""
+    op2 = Operator2x2(op)
+    F = np.stack([np.zeros(op.shape, dtype=np.complex128),
+                  np.asarray(f, dtype=np.complex128).reshape(op.shape)])
+    return fgmres(op2, F, lambda v: fci(op2, v, nodes, k_in), m, rtol, max_cycles, fixed_its)

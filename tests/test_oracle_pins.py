@@ -505,3 +505,135 @@ def test_precond_identity_gives_gmres():
     res = O.fgmres(op, f, lambda v: v, m=5, rtol=1e-30, max_cycles=1)
     x, _ = O.gmres_cycle(op.apply, f, 5)
     assert np.linalg.norm(res.u - x) <= 1e-12 * np.linalg.norm(x)
+
+
+# ---------------------------------------------------------------------------------------
+# Case Two (§3, eq:mat-2x2, Theorem thm:spectrum-2x2, eq:shifted-2x2)
+# ---------------------------------------------------------------------------------------
+
+def dense_2x2(A):
+    """iC - I from a dense A alone: A1 and A2 are its Hermitian part and i times its
+    skew-Hermitian part (A = A1 - i A2), C = [[0, I], [-(A1 + I), -A2]] (eq:mat-2x2)."""
+    n = A.shape[0]
+    A1 = 0.5 * (A + A.conj().T)
+    A2 = 0.5j * (A - A.conj().T)
+    I = np.eye(n)
+    C = np.block([[np.zeros((n, n)), I], [-(A1 + I), -A2]])
+    return C, 1j * C - np.eye(2 * n)
+
+
+def dense_of(apply, n):
+    """The dense matrix of a linear map on n-vectors (columns = images of unit vectors)."""
+    cols = []
+    for k in range(n):
+        e = np.zeros(n, dtype=np.complex128)
+        e[k] = 1.0
+        cols.append(np.asarray(apply(e)).ravel())
+    return np.stack(cols, axis=1)
+
+
+def test_case_two_operator_is_the_block_matrix():
+    """Operator2x2 and its C equal the blocks of eq:mat-2x2 built from the dense A's
+    Hermitian and skew-Hermitian parts (damped medium, so A2 != 0)."""
+    op, _ = tiny_operator(seed=7, nx=4, ny=3, nz=5, layer=1)
+    op2 = O.Operator2x2(op)
+    C, B = dense_2x2(dense_operator(op))
+    assert np.allclose(dense_of(op2.apply_c, op2.n), C, rtol=0, atol=1e-12 * np.abs(C).max())
+    assert np.allclose(dense_of(op2.apply, op2.n), B, rtol=0, atol=1e-12 * np.abs(B).max())
+    # the shifted form subtracts z I
+    z = 0.3 - 0.7j
+    Bz = dense_of(lambda x: op2.apply(x, z), op2.n)
+    assert np.allclose(Bz, B - z * np.eye(op2.n), rtol=0, atol=1e-12 * np.abs(B).max())
+
+
+def test_case_two_solution_is_case_one():
+    """eq:mat-2x2: the solution of (iC - I) Y = (0; f) is Y = (iu; u) with A u = f."""
+    op, wl = tiny_operator(seed=8, nx=5, ny=3, nz=4, layer=1)
+    A = dense_operator(op)
+    _, B = dense_2x2(A)
+    f = W.random_field(3, 1, op.nx, op.ny, op.nz)[0].ravel()
+    u = np.linalg.solve(A, f)
+    Y = np.linalg.solve(B, np.concatenate([np.zeros_like(f), f]))
+    n = op.n
+    assert np.linalg.norm(Y[n:] - u) <= 1e-10 * np.linalg.norm(u)
+    assert np.linalg.norm(Y[:n] - 1j * u) <= 1e-10 * np.linalg.norm(u)
+
+
+def test_case_two_spectrum_undamped_closed_form():
+    """Theorem thm:spectrum-2x2 with rho2 = 0 (constant medium, no sponge): the eigenvalues of
+    C are +-i sqrt(lambda) over the eigenvalues lambda of A1 + I, here s*(the closed-form
+    sine-mode eigenvalues of -Delta_h), since m = 1."""
+    nx, ny, nz = 3, 4, 2
+    h = 1.0 / 6
+    op = constant_operator(nx, ny, nz, h, 2 * math.pi / (6 * h))
+    op2 = O.Operator2x2(op)
+    ev = np.linalg.eigvals(dense_of(op2.apply_c, op2.n))
+    lam = [op.s * (sine_eig(nx, kx, h) + sine_eig(ny, ky, h) + sine_eig(nz, kz, h))
+           for kx in range(1, nx + 1) for ky in range(1, ny + 1) for kz in range(1, nz + 1)]
+    expect = np.concatenate([1j * np.sqrt(lam), -1j * np.sqrt(lam)])
+    key = lambda v: (round(v.imag, 9), round(v.real, 9))
+    got = np.array(sorted(ev, key=key))
+    exp = np.array(sorted(expect, key=key))
+    assert np.max(np.abs(got - exp)) <= 1e-10 * np.max(np.abs(exp))
+
+
+@pytest.mark.parametrize("seed,shape,layer", [(9, (4, 3, 5), 1), (10, (5, 5, 3), 2)])
+def test_case_two_spectrum_bound(seed, shape, layer):
+    """Theorem thm:spectrum-2x2 with damping: every eigenvalue mu of C has |mu| <= R and
+    Re mu in [-rho2, 0], R = rho2/2 + sqrt(rho2^2/4 + rho1) with the exact rho1 = rho(A1 + I);
+    the oracle's rectangle (Weyl bound for rho1) contains the spectrum of iC - I (Remark)."""
+    op, _ = tiny_operator(seed=seed, nx=shape[0], ny=shape[1], nz=shape[2], layer=layer)
+    A = dense_operator(op)
+    C, B = dense_2x2(A)
+    A1 = 0.5 * (A + A.conj().T)
+    rho1 = float(np.max(np.linalg.eigvalsh(A1 + np.eye(op.n))))
+    rho2 = float(op.a.max())
+    R = rho2 / 2 + math.sqrt(rho2 ** 2 / 4 + rho1)
+    ev = np.linalg.eigvals(C)
+    tol = 1e-9 * R
+    assert np.all(np.abs(ev) <= R + tol)
+    assert np.all(ev.real <= tol) and np.all(ev.real >= -rho2 - tol)
+    assert ev.real.min() < -1e-6  # damping moves some eigenvalue off the imaginary axis
+    b1, b2, rho2o, rho1o, Ro = O.spectrum_box_2x2(op)
+    assert rho2o == rho2 and rho1o >= rho1 - 1e-9 * rho1 and Ro >= R - tol
+    mu = np.linalg.eigvals(B)
+    assert np.all(mu.real >= b1 - tol) and np.all(mu.real <= b2 + tol)
+    assert np.all(mu.imag <= tol) and np.all(mu.imag >= -rho2 - tol)
+    assert np.all(np.abs(mu + 1) <= Ro + tol)
+
+
+def test_shifted_2x2_equivalence():
+    """eq:shifted-2x2 (A Hermitian): with z + 1 = (s+1)^2, ((iC - I) - sI) Y = (0; f) has
+    Y = (iy; (s+1) y) where (A - zI) y = f."""
+    nx, ny, nz = 4, 3, 3
+    h = 1.0 / 5
+    op = constant_operator(nx, ny, nz, h, 2 * math.pi / (5 * h))
+    op2 = O.Operator2x2(op)
+    f = W.random_field(4, 1, nx, ny, nz)[0].ravel()
+    A = dense_operator(op)
+    for z in (1j, 0.5j, 0.2 + 0.25j):
+        s = np.sqrt(z + 1) - 1
+        y = np.linalg.solve(A - z * np.eye(op.n), f)
+        Y = np.linalg.solve(dense_of(lambda x: op2.apply(x, s), op2.n),
+                            np.concatenate([np.zeros_like(f), f]))
+        n = op.n
+        assert np.linalg.norm(Y[:n] - 1j * y) <= 1e-10 * np.linalg.norm(y)
+        assert np.linalg.norm(Y[n:] - (s + 1) * y) <= 1e-10 * np.linalg.norm((s + 1) * y)
+
+
+def test_case_two_fgmres_matches_dense_lu():
+    """Algorithm 1 and FGMRES applied to iC - I (Case Two) on a damped grid: the 2x2 true
+    residual reaches 1e-8, and the two blocks of the iterate are i u and u for the dense LU
+    solution u of A u = f, within the residual bound times the condition number."""
+    op, wl = tiny_operator(seed=11, nx=5, ny=4, nz=4, layer=1)
+    _, nodes = O.setup_nodes_2x2(op, 8, 1.0, 0.5)
+    f = W.random_field(6, 1, op.nx, op.ny, op.nz)[0]
+    res = O.solve_2x2(op, f, nodes, 30, 4, 1e-8, 20)
+    assert res.converged and res.rel_res_true <= 1e-8
+    _, B = dense_2x2(dense_operator(op))
+    kappa = np.linalg.cond(B)
+    u = np.linalg.solve(dense_operator(op), f.ravel())
+    Y = res.u.reshape(2, -1)
+    bound = kappa * 1e-8 * math.sqrt(2.0)
+    assert np.linalg.norm(Y[1] - u) <= bound * np.linalg.norm(u)
+    assert np.linalg.norm(Y[0] - 1j * u) <= bound * np.linalg.norm(u)
