@@ -182,6 +182,16 @@ hz_status hz_problem_set_nodes(hz_problem* p, int J, const double* z_ri, const d
 hz_status hz_apply_shifted(hz_problem* p, double zr, double zi, const void* x, void* y,
                            int nvec, int precision, void* stream);
 
+/* Case Two of Section 3 (eq:mat-2x2): y = ((iC - I) - z I) x for the double-size matrix with
+ * C = [[0, I], [-(A1 + I), -A2]], where A = A1 - i A2 is the normalised operator split into its
+ * Hermitian part A1 = s L_h - diag(m) and A2 = diag(a).  Each of the nvec vectors is two
+ * fields stored one after the other, x = (x1; x2) (2*nx*ny*nz values), so (iC - I)(iu; u) =
+ * (0; f) exactly when A u = f, and with z = s the shifted form eq:shifted-2x2.  x and y must
+ * not overlap.  precision HZ_C128: double complex; HZ_MIXED_C64: float complex, computed in
+ * float32.  HZ_ERR_INVALID for nvec > 65535 or grids of 2^31 points or more. */
+hz_status hz_apply_2x2(hz_problem* p, double zr, double zi, const void* x, void* y, int nvec,
+                       int precision, void* stream);
+
 /* y ~ (A - z_node I)^{-1} f for nvec fields by sweeps_node steps of eq:fix-pt-exp from
  * y = 0 (Section 4.2).  Field type as in hz_apply_shifted.  nvec <= nrhs_max. */
 hz_status hz_shifted_solve(hz_problem* p, int node, const void* f, void* y, int nvec,

@@ -1187,6 +1187,27 @@ hz_status hz_apply_shifted(hz_problem* p, double zr, double zi, const void* x, v
   return HZ_OK;
 }
 
+hz_status hz_apply_2x2(hz_problem* p, double zr, double zi, const void* x, void* y, int nvec,
+                       int precision, void* stream) {
+  HZ_TRY(check_problem(p));
+  if (nvec < 0) return fail(HZ_ERR_INVALID, "nvec < 0");
+  if (nvec == 0) return HZ_OK;
+  if (!x || !y) return fail(HZ_ERR_INVALID, "null field");
+  if (nvec > 65535) return fail(HZ_ERR_INVALID, "nvec > 65535");
+  if (p->g.n > 0x7fffffffLL) return fail(HZ_ERR_INVALID, "grid of 2^31 points or more");
+  HZ_TRY(set_device(p));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == HZ_C128) {
+    HZ_CUDA(hz::launch_apply_2x2(p->g, p->d64, (const double2*)x, (double2*)y, nvec, zr, zi, st));
+  } else if (precision == HZ_MIXED_C64) {
+    HZ_CUDA(hz::launch_apply_2x2_32(p->g, p->d32, (const float2*)x, (float2*)y, nvec, float(zr),
+                                    float(zi), st));
+  } else {
+    return fail(HZ_ERR_INVALID, "unknown precision");
+  }
+  return HZ_OK;
+}
+
 hz_status hz_shifted_solve(hz_problem* p, int node, const void* f, void* y, int nvec,
                            int precision, void* stream) {
   HZ_TRY(check_problem(p));

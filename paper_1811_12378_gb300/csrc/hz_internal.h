@@ -192,6 +192,12 @@ cudaError_t launch_fci_tail32(const Geom& g, const float2* dg, const float2* w32
                               double2* out,
                               double2* partial, unsigned* bar, int* err, long long n, int kin,
                               double brk, int pyth, int ppt, int blocks, cudaStream_t st);
+// ---- Case Two (hz_case_two.cu): y = ((iC - I) - zI) x on stacked fields (x1; x2) per vector,
+// C = [[0, I], [-(A1 + I), -A2]] (eq:mat-2x2), from the diagonal dg of A = A1 - i A2 ----
+cudaError_t launch_apply_2x2(const Geom& g, const double2* dg, const double2* x, double2* y,
+                             int nvec, double zr, double zi, cudaStream_t st);
+cudaError_t launch_apply_2x2_32(const Geom& g, const float2* dg, const float2* x, float2* y,
+                                int nvec, float zr, float zi, cudaStream_t st);
 // ---- one outer float-pair Arnoldi step as one cooperative kernel (hz_arnoldi_ff.cu) ----
 // Points per thread and grid size for n points and restart length mmax; *ppt = 0 where the
 // grid cannot be co-resident or cooperative launch is unavailable.

@@ -24,7 +24,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory",
 
 # every exported symbol declared in include/hz.h
 EXPORTS = ["hz_problem_create", "hz_plan", "hz_problem_destroy", "hz_problem_get_info",
-           "hz_problem_nodes", "hz_problem_set_nodes", "hz_apply_shifted", "hz_shifted_solve",
+           "hz_problem_nodes", "hz_problem_set_nodes", "hz_apply_shifted", "hz_apply_2x2",
+           "hz_shifted_solve",
            "hz_fci", "hz_solve", "hz_solve_batched", "hz_profile_enable", "hz_profile_read",
            "hz_problem_fused_tail", "hz_problem_fused_arnoldi", "hz_residual_noalloc",
            "hz_status_string", "hz_last_error", "hz_launch_count"]
@@ -100,6 +101,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.hz_problem_nodes.argtypes = [P, dp, dp, dp, dp, ip, dp, ip]
     lib.hz_problem_set_nodes.argtypes = [P, C.c_int, dp, dp, dp, dp, ip, ip]
     lib.hz_apply_shifted.argtypes = [P, C.c_double, C.c_double, P, P, C.c_int, C.c_int, P]
+    lib.hz_apply_2x2.argtypes = [P, C.c_double, C.c_double, P, P, C.c_int, C.c_int, P]
     lib.hz_shifted_solve.argtypes = [P, C.c_int, P, P, C.c_int, C.c_int, P]
     lib.hz_fci.argtypes = [P, P, P, C.c_int, C.c_int, C.c_int, P]
     lib.hz_solve.argtypes = [P, P, P, C.c_int, C.POINTER(HzSolveOpts), C.POINTER(HzSolveStats), P]
@@ -314,6 +316,20 @@ class Problem:
         z = complex(z)
         _check(self._lib.hz_apply_shifted(self._h, z.real, z.imag, xp, yp, nvec, prec,
                                           _stream(stream)), self._lib)
+        return y
+
+    def apply_2x2(self, x, z=0.0, out=None, precision=None, stream=None):
+        """Case Two: ((iC - I) - zI) x on vectors of two stacked fields (x1; x2)."""
+        import torch
+        prec = precision if precision is not None else (
+            HZ_MIXED_C64 if x.dtype == torch.complex64 else HZ_C128)
+        dt = torch.complex64 if prec == HZ_MIXED_C64 else torch.complex128
+        xp, nvec = _dev_ptr(x, dt, 2 * self.n)
+        y = torch.empty_like(x) if out is None else out
+        yp, _ = _dev_ptr(y, dt, 2 * self.n)
+        z = complex(z)
+        _check(self._lib.hz_apply_2x2(self._h, z.real, z.imag, xp, yp, nvec, prec,
+                                      _stream(stream)), self._lib)
         return y
 
     def shifted_solve(self, node, f, out=None, precision=None, stream=None):

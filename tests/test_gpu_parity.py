@@ -72,6 +72,25 @@ def test_stencil_parity(shape, layer):
             assert rel(y32, ref) <= 2e-6
 
 
+@pytest.mark.parametrize("shape,layer", [((37, 19, 11), 3), ((2, 7, 1), 1), ((1, 1, 1), 0)],
+                         ids=lambda v: str(v))
+def test_case_two_operator_parity(shape, layer):
+    """Case Two (§3 eq:mat-2x2): ((iC - I) - zI) x on 2 vectors of two stacked fields each,
+    against the oracle's Operator2x2 (pinned on CPU by the dense block matrix and Theorem
+    thm:spectrum-2x2), float64 and float32 paths, the unshifted and two shifted forms."""
+    nx, ny, nz = shape
+    wl = W.small_case(12, nx, ny, nz, layer=layer, medium="bumps" if nx > 1 else "const")
+    op2 = O.Operator2x2(O.make_operator(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max))
+    x = W.random_field(13, 4, nx, ny, nz).reshape(2, 2, nz, ny, nx)
+    with hzpkg.Problem(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, 4, 1.0, 1.0) as P:
+        for z in (0.0, 0.3 - 0.7j, -1.5 + 0.2j):
+            ref = np.stack([op2.apply(x[v], z) for v in range(2)])
+            y = to_np(P.apply_2x2(to_dev(x.reshape(2, -1)), z))
+            assert rel(y, ref) <= 1e-14
+            y32 = to_np(P.apply_2x2(to_dev(x.reshape(2, -1), torch.complex64), z))
+            assert rel(y32, ref) <= 2e-6
+
+
 def test_stencil_sine_modes_gpu():
     """P1 on the GPU: sine modes are eigenvectors of the stencil with c = 1, no sponge."""
     nx, ny, nz = 40, 21, 9
