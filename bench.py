@@ -4,8 +4,11 @@
 Metric: right-hand sides per second solved to a relative residual of 1e-8 (float64 true
 residual), for the 64^3 Gaussian-bump workload (8 bumps, c in [1, 2], 8 points per wavelength
 at c_min, 8-cell sponge, one Gaussian source, J = 8 contour nodes, FGMRES(30) with FCI and 4
-inner GMRES steps).  One step = one full solve of that right-hand side.  `value` is the chosen
-(mixed-precision) form; the plain all-float64 form is reported beside it.
+inner GMRES steps).  One step = one full solve of that right-hand side.  `value` is the mixed
+form HZ_MIXED_C64 (complex64 polynomial sweeps; quadrature sum, step d, inner and outer CGS2,
+Givens and true residual in float64); the plain all-float64 form and two faster forms that
+depart from that precision split are reported beside it, each with its solution error against
+the float64 oracle.  `large` solves the 256^3 configuration (8 of its 16 sources).
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -48,6 +51,8 @@ def parse():
     ap.add_argument("--ncu-large", action="store_true",
                     help="run only the 256^3 stencil / polynomial-stage bandwidth measurement, "
                          "bracketed with cudaProfilerStart/Stop")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 256^3 sixteen-source configuration's solve")
     return ap.parse_args()
 
 
@@ -112,64 +117,91 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle
+# The oracle is timed in processes of its own (spawned before this process touches the GPU),
+# one numpy thread each: a full solve to 1e-8 on one core, the float64 reference solution that
+# the GPU solutions are compared with (rtol 1e-12), and afterwards one bounded sample per host
+# core at the same time (the all-core throughput).
+
+def _single_thread_env():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
+def oracle_job(name: str, rtol: float, fixed_its: int = 0, want_u: bool = False):
+    """One oracle FGMRES solve of a workload (runs in a worker process).  Returns its step
+    count, true residual, wall-clock start/end of the solve and, if asked, the solution."""
+    import numpy as np  # noqa: F401  (imported here, after the thread settings)
+    import workloads as W
+    from oracle import hz_oracle as O
+    wl = getattr(W, name)()
+    op = O.make_operator(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max)
+    _, nodes = O.setup_nodes(op, wl.J, wl.t, wl.eps)
+    t0 = time.time()
+    res = O.solve(op, op.s * wl.f[0], nodes, wl.restart, wl.k_in, rtol, 60, fixed_its=fixed_its)
+    t1 = time.time()
+    return {"its": res.its, "rel_res_true": res.rel_res_true, "t0": t0, "t1": t1,
+            "u": res.u.ravel() if want_u else None}
+
+
+def oracle_pool(workers: int):
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    _single_thread_env()
+    return ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+
+
 def oracle_counts():
+    """The oracle's own step counts to 1e-8 (oracle/reference_counts.json, written by
+    oracle/reference_counts.py, which calls only the oracle)."""
     with open(os.path.join(ROOT, "oracle", "reference_counts.json")) as fh:
         return json.load(fh)
 
 
-def time_oracle_sample(wl, outer_steps: int):
-    """Seconds for `outer_steps` outer FGMRES steps of the oracle on this workload (plus the
-    time per step), with the thread count numpy's BLAS uses."""
-    from oracle import hz_oracle as O
-    op = O.make_operator(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max)
-    _, nodes = O.setup_nodes(op, wl.J, wl.t, wl.eps)
-    t0 = time.perf_counter()
-    O.solve(op, op.s * wl.f[0], nodes, wl.restart, wl.k_in, 1e-30, 1, fixed_its=outer_steps)
-    return time.perf_counter() - t0
-
-
-def cpu_threads():
+def host_cores() -> int:
     try:
-        from threadpoolctl import threadpool_info
-        n = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
-        return int(n)
-    except Exception:
-        return 1
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def run_reference(args):
+    """--impl reference: the oracle (complex128 numpy, one thread) on the benchmark workload.
+    Each timed step is a bounded sample: 4 outer FGMRES steps of the solve, scaled by the
+    oracle's own step count to 1e-8."""
     rank, _, world = dist_env()
     if rank != 0:
         return
-    import workloads as W
-    wl = W.gaussian_bumps_64()
-    its = oracle_counts()[wl.name]["its"]
-    per = 1  # outer FGMRES steps per timed sample
+    _single_thread_env()
+    counts = oracle_counts()["gaussian_bumps_64"]
+    per = 4
     for _ in range(args.warmup):
-        time_oracle_sample(wl, per)
-    tt = [time_oracle_sample(wl, per) for _ in range(args.steps)]
+        oracle_job("gaussian_bumps_64", 1e-30, fixed_its=per)
+    tt = []
+    for _ in range(args.steps):
+        r = oracle_job("gaussian_bumps_64", 1e-30, fixed_its=per)
+        tt.append(r["t1"] - r["t0"])
     step_s = sum(tt) / len(tt)
+    its = counts["its"]
     value = 1.0 / (step_s / per * its)
-    sample = (f"{per} outer FGMRES step (FCI with {oracle_counts()[wl.name]['poly_matvecs_per_fci']}"
-              f" polynomial-sweep matvecs + inner GMRES + CGS2) of the oracle per timed step, "
-              f"scaled by the oracle's {its} steps to 1e-8")
-    cores = cpu_threads()
+    sample = (f"{per} outer FGMRES steps of the oracle per timed step (FCI with "
+              f"{counts['poly_matvecs_per_fci']} polynomial-sweep matvecs, 4 inner GMRES steps, "
+              f"CGS2), scaled by the oracle's {its} steps to 1e-8; one numpy thread")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
         "data": "synthetic", "config": {"workload": WORKLOAD, "form": "oracle complex128"},
-        "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}), flush=True)
 
 
 # ----------------------------------------------------------------------------- GPU arm
-def traffic_from_profile(kernel_src_hash: str):
-    """DRAM bytes per launch of the polynomial-stage kernel from the committed ncu summary,
-    or None if the summary is missing or was taken on a different kernel source."""
-    path = os.path.join(ROOT, "profiles", "poly_stage_gaussian_bumps_64.txt")
+def traffic_from_profile(name: str, kernel_src_hash: str):
+    """DRAM bytes per launch of a kernel from a committed ncu summary under profiles/, or None
+    if the summary is missing or was taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     vals = {}
@@ -194,13 +226,40 @@ def kernel_hash():
     return h.hexdigest()
 
 
-def measured_peak_hbm():
+def measured_peaks():
+    """(HBM copy GB/s, kind) from MEASURED_PEAKS.json, else the fallback figure."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as fh:
             return float(json.load(fh)["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+# Float64 peak of a GB300 from its unit counts: 152 SMs x 2 float64 FMA per clock x 2 flops at
+# the 2070 MHz maximum SM clock = 1.259 TFLOP/s (the part's published 1.25 TFLOP/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def l2_copy_bandwidth(torch, dev, mib=32, reps=200):
+    """Copy bandwidth of a buffer pair that stays in the 126 MB L2 (read + write bytes / time,
+    best of several event-timed bursts): the roof of kernels whose fields are L2-resident."""
+    n = (mib << 20) // 4
+    a = torch.ones(n, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    for _ in range(10):
+        b.copy_(a)
+    best = None
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            b.copy_(a)
+        e1.record()
+        e1.synchronize()
+        gbs = 2.0 * a.numel() * 4 * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+        best = gbs if best is None else max(best, gbs)
+    return best
 
 
 def large_grid_bandwidth(hz, torch, dev, N=256, profile_region=False):
@@ -236,7 +295,7 @@ def large_grid_bandwidth(hz, torch, dev, N=256, profile_region=False):
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
     P.close()
-    peak, kind = measured_peak_hbm()
+    peak, kind = measured_peaks()
     st_gbs = 24.0 * n / t_st / 1e9
     poly_gbs = by / (ms / 1e3) / 1e9
     return {"grid": f"{N}^3", "peak": peak, "peak_kind": f"{kind} copy bandwidth",
@@ -244,6 +303,71 @@ def large_grid_bandwidth(hz, torch, dev, N=256, profile_region=False):
                             "bytes_per_point": 24},
             "poly_stage_c64_one_node": {"GB/s": poly_gbs, "frac": poly_gbs / peak,
                                         "us_per_launch": ms / nl * 1e3, "launches": nl}}
+
+
+def large_solve(hz, torch, dev, nrhs=8, profile_region=False):
+    """The large configuration (256^3, 16 Gaussian bumps with c in [1, 3], 12-cell sponge,
+    8 ppw, J = 8, FGMRES(40), 4 inner steps): the first nrhs of its 16 point sources solved to
+    1e-8 in one call of the float64-outer mixed form (complex64 sweeps and stored directions),
+    with per-kernel-class CUDA events (at this size a stage is milliseconds long, so the events
+    cost nothing measurable).  The roofline is the batched polynomial stage's (J nodes x nrhs
+    right-hand sides per launch, fields far beyond L2) against HBM."""
+    import workloads as W
+    wl, idx = W.large_bumps_256()
+    N = wl.nx
+    n = N ** 3
+    P = hz.Problem(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, wl.J, wl.t, wl.eps,
+                   nrhs_max=nrhs, restart_max=wl.restart, inner_k_max=wl.k_in,
+                   flags=hz.HZ_LIMIT_SWEEPS_C64 | hz.HZ_LIMIT_Z_C64)
+    f = torch.zeros((nrhs, n), dtype=torch.complex128, device=dev)
+    for r, (i, j, k) in enumerate(idx[:nrhs]):
+        f[r, i + N * (j + N * k)] = 1.0 / wl.h ** 3
+    u = torch.empty_like(f)
+    torch.cuda.synchronize()
+    if profile_region:
+        torch.cuda.profiler.start()
+    P.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    _, st = P.solve(f, out=u, restart=wl.restart, inner_k=wl.k_in, rtol=wl.rtol, max_cycles=12,
+                    precision=hz.HZ_MIXED_C64, check=False)
+    e1.record()
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    poly = P.profile_read(hz.PROF_POLY, flops=True)
+    sten = P.profile_read(hz.PROF_STENCIL, flops=True)
+    kryl = P.profile_read(hz.PROF_KRYLOV, flops=True)
+    P.profile(False)
+    if profile_region:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+    info = P.info
+    P.close()
+    del f, u
+    peak, kind = measured_peaks()
+    gbs = poly[2] / (poly[1] / 1e3) / 1e9
+    return {"workload": f"large_bumps_256: {N}^3 (h=1/{N + 1}), c = 1 + 16 seeded Gaussian bumps "
+                        f"(width 0.1, amplitudes U[0,2]) clipped to [1,3], 8 ppw, 12-cell sponge, "
+                        f"J=8, FGMRES(40) + FCI with 4 inner steps, point sources 1..{nrhs} of 16",
+            "form": "HZ_MIXED_C64 (complex64 sweeps; float64 quadrature sum, step d, inner and "
+                    "outer CGS2, Givens, true residual), sweep workspace and FGMRES directions "
+                    "stored in complex64",
+            "rhs": nrhs, "seconds": t, "RHS_per_s": nrhs / t,
+            "converged": sum(1 for x in st if x.converged),
+            "max_rel_res_true": max(x.rel_res_true for x in st),
+            "its": [x.its for x in st], "stages_per_fci": info["stages"],
+            "kernel_classes": {
+                "poly_stage": {"launches": poly[0], "ms": poly[1], "GB": poly[2] / 1e9},
+                "stencil": {"launches": sten[0], "ms": sten[1], "GB": sten[2] / 1e9,
+                            "fp64_TFLOP": sten[3] / 1e12},
+                "krylov": {"launches": kryl[0], "ms": kryl[1], "GB": kryl[2] / 1e9,
+                           "fp64_TFLOP": kryl[3] / 1e12}},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak, "traffic": None,
+                         "kernel": f"k_poly_stage<float2> ({wl.J} nodes x {nrhs} right-hand "
+                                   f"sides per launch, 256^3 fields)",
+                         "launches": poly[0], "avg_launch_us": poly[1] / poly[0] * 1e3,
+                         "peak_kind": f"{kind} copy bandwidth"}}
 
 
 def batched_uneven(hz, torch, dev, precision):
@@ -275,6 +399,7 @@ def batched_uneven(hz, torch, dev, precision):
     nr = len(flat)
     return {"workload": "12 instances: 4 x 48^3, 4 x 64^3, 4 x 96^3, layered media (5 layers, "
                         "c ~ U[1.5,4.5]), 8 ppw, J=8, 4 point sources each, FGMRES(30)",
+            "form": "HZ_MIXED_C64",
             "rhs": nr, "converged": sum(x.converged for x in flat),
             "max_rel_res_true": max(x.rel_res_true for x in flat),
             "its_range": [min(x.its for x in flat), max(x.its for x in flat)],
@@ -293,7 +418,30 @@ def max_over_ranks_of(x: float, world: int, device) -> float:
     return float(t.item())
 
 
+FORMS = {  # key: (precision constant name, description)
+    "mixed_f64": ("HZ_MIXED_C64", "complex64 stencil sweeps of the polynomial iteration; the "
+                  "quadrature-weighted sum, step d, inner and outer CGS2 Arnoldi, Givens least "
+                  "squares, solution update and true residual in float64"),
+    "plain": ("HZ_C128", "everything complex128 / float64"),
+    "fci32_f64_outer": ("HZ_MIXED_C64_FCI32", "departure: the whole FCI preconditioner in "
+                        "complex64 (inner GMRES with float32 scalars, quadrature sum in float "
+                        "pairs); outer FGMRES CGS2, Givens and true residual in float64"),
+    "ff": ("HZ_MIXED_C64_FF", "departure: as fci32_f64_outer with the outer Arnoldi basis and "
+           "CGS2 in float pairs (~48 bits); Hessenberg, Givens, update and residual float64"),
+}
+HEADLINE = "mixed_f64"
+
+
 def run_ours(args):
+    rank, local, world = dist_env()
+    cpu_leg = rank == 0 and world == 1 and not args.no_cpu_baseline and not args.ncu_region
+    pool = futs = None
+    if cpu_leg:
+        # the oracle's processes are spawned before this process touches the GPU
+        pool = oracle_pool(2)
+        futs = {"single": pool.submit(oracle_job, "gaussian_bumps_64", 1e-8),
+                "ref": pool.submit(oracle_job, "gaussian_bumps_64", 1e-12, 0, True)}
+
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -301,7 +449,6 @@ def run_ours(args):
     import paper_1811_12378_gb300 as hz
     import workloads as W
 
-    rank, local, world = dist_env()
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
@@ -317,6 +464,8 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     kw = dict(restart=wl.restart, inner_k=wl.k_in, rtol=wl.rtol, max_cycles=20)
+    prec = {k: getattr(hz, v[0]) for k, v in FORMS.items()}
+    sols = {}
 
     def barrier():
         torch.cuda.synchronize()
@@ -333,142 +482,182 @@ def run_ours(args):
             e0.record(stream)
             if e2e:
                 f_dev.copy_(f_host, non_blocking=True)
-            _, stats = P.solve(f_dev, out=u_dev, precision=form, **kw)
+            _, stats = P.solve(f_dev, out=u_dev, precision=prec[form], **kw)
             if e2e:
                 u_host.copy_(u_dev, non_blocking=True)
             e1.record(stream)
             e1.synchronize()
             total += e0.elapsed_time(e1) / 1e3
+        if not e2e:
+            sols[form] = u_dev.cpu().numpy()[0].copy()
         return total, stats[0]
 
     def max_over_ranks(x):
         return max_over_ranks_of(x, world, dev)
 
-    chosen = hz.HZ_MIXED_C64_FF
     # warm-up (all forms)
     for _ in range(max(args.warmup, 3)):
-        P.solve(f_dev, out=u_dev, precision=chosen, **kw)
-    P.solve(f_dev, out=u_dev, precision=hz.HZ_MIXED_C64_FCI32, **kw)
-    P.solve(f_dev, out=u_dev, precision=hz.HZ_MIXED_C64, **kw)
-    P.solve(f_dev, out=u_dev, precision=hz.HZ_C128, **kw)
+        P.solve(f_dev, out=u_dev, precision=prec[HEADLINE], **kw)
+    for form in FORMS:
+        P.solve(f_dev, out=u_dev, precision=prec[form], **kw)
     barrier()
 
     if args.ncu_region:
         torch.cuda.profiler.start()
-        timed(chosen, args.steps)
+        timed(HEADLINE, args.steps)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         P.close()
         return
 
-    # timed region: chosen form
+    # timed region: the headline form
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = hz.launch_count()
     barrier()
-    t_mixed, st_mixed = timed(chosen, args.steps)
+    t_head, st_head = timed(HEADLINE, args.steps)
     barrier()
     launches = hz.launch_count() - launches0
     clk = clocks.stop()
-    t_mixed = max_over_ranks(t_mixed)
+    t_head = max_over_ranks(t_head)
 
     # the same steps again with CUDA events around every launch of each kernel class, on the
     # launching stream (the events cost host time, so the headline value above is taken
     # without them)
     P.profile(True)
     barrier()
-    timed(chosen, args.steps)
+    timed(HEADLINE, args.steps)
     barrier()
-    poly = P.profile_read(hz.PROF_POLY)
-    sten = P.profile_read(hz.PROF_STENCIL)
-    kryl = P.profile_read(hz.PROF_KRYLOV)
+    cls = {"poly_stage": P.profile_read(hz.PROF_POLY, flops=True),
+           "stencil": P.profile_read(hz.PROF_STENCIL, flops=True),
+           "krylov": P.profile_read(hz.PROF_KRYLOV, flops=True)}
     P.profile(False)
 
-    # plain float64 form and the form with float64 FCI internals, same steps
-    barrier()
-    t_plain, st_plain = timed(hz.HZ_C128, args.steps)
-    t_plain = max_over_ranks(t_plain)
-    barrier()
-    t_m64, st_m64 = timed(hz.HZ_MIXED_C64, args.steps)
-    t_m64 = max_over_ranks(t_m64)
-    barrier()
-    t_f32, st_f32 = timed(hz.HZ_MIXED_C64_FCI32, args.steps)
-    t_f32 = max_over_ranks(t_f32)
+    # the other forms, same steps
+    others = {}
+    for form in FORMS:
+        if form == HEADLINE:
+            continue
+        barrier()
+        t_f, st_f = timed(form, args.steps)
+        others[form] = (max_over_ranks(t_f), st_f)
 
     # end to end through the public API: pinned host f -> device, solve, u -> pinned host
     barrier()
-    t_e2e, _ = timed(chosen, args.steps, e2e=True)
+    t_e2e, _ = timed(HEADLINE, args.steps, e2e=True)
     t_e2e = max_over_ranks(t_e2e)
 
-    # residual check of the last chosen-form solution with an independent float64 stencil
+    # residual check of the headline solution with an independent float64 stencil
     s = P.info["s"]
+    u_dev.copy_(torch.from_numpy(sols[HEADLINE][None]).to(dev))
     Au = P.apply_shifted(u_dev)
     res = float(torch.linalg.vector_norm(s * f_dev - Au) / torch.linalg.vector_norm(s * f_dev))
 
+    # the precision floor of every form: solves to a true residual of 1e-11 (untimed)
+    sols11 = {}
+    for form in FORMS:
+        u11, st11 = P.solve(f_dev, restart=wl.restart, inner_k=wl.k_in, rtol=1e-11,
+                            max_cycles=40, precision=prec[form], check=False)
+        sols11[form] = (u11.cpu().numpy()[0].copy(), st11[0].rel_res_true)
+    P.close()
+
+    l2_peak = l2_copy_bandwidth(torch, dev)
     # stencil and polynomial-stage HBM bandwidth on a grid larger than L2 (256^3: every
     # complex64 field is 134 MB), the configuration the HBM figures are meaningful on
     hbm = large_grid_bandwidth(hz, torch, dev)
-    uneven = batched_uneven(hz, torch, dev, chosen) if world == 1 else None
+    large = large_solve(hz, torch, dev) if world == 1 and not args.no_large else None
+    uneven = batched_uneven(hz, torch, dev, prec[HEADLINE]) if world == 1 else None
 
     rhs_total = args.steps * world
-    value = rhs_total / t_mixed
-    peak, peak_kind = measured_peak_hbm()
-    nl, ms, by = poly
-    achieved = (by / nl) / ((ms / nl) / 1e3) / 1e9 if nl else None
-    traffic = traffic_from_profile(kernel_hash())
+    value = rhs_total / t_head
+    peak_hbm, peak_kind = measured_peaks()
+
+    # roofline of the dominant kernel class of the headline solve
+    dom = max(cls, key=lambda k: cls[k][1])
+    nl, ms, by, fl = cls[dom]
+    if dom == "poly_stage":
+        achieved = (by / nl) / ((ms / nl) / 1e3) / 1e9
+        roof = {"bound": "l2", "achieved": achieved, "peak": l2_peak, "unit": "GB/s",
+                "frac": achieved / l2_peak,
+                "traffic": traffic_from_profile("poly_stage_gaussian_bumps_64.txt", kernel_hash()),
+                "kernel": "k_poly_stage<float2> (batched sweeps of all active contour nodes)",
+                "peak_kind": "measured L2-resident copy bandwidth (32 MiB buffers, this run); "
+                             "the 64^3 fields stay in L2, so HBM is not the roof here"}
+    else:
+        achieved = (fl / nl) / ((ms / nl) / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": f"{dom} class (float64 Krylov kernels: CGS2 passes, step d)"
+                          if dom == "krylov" else "k_stencil_diag (float64 stencil)",
+                "peak_kind": "float64 FMA rate from unit counts (152 SMs x 2 FMA/clk x 2 flops "
+                             "x 2.07 GHz)"}
+    roof.update({"class": dom, "launches": nl, "avg_launch_us": ms / nl * 1e3})
+
     line = {
         "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_mixed / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f32pair+f64",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_head / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": "mixed, FCI in complex64: polynomial sweeps, "
-                   "step d and inner GMRES in complex64, quadrature sum accumulated in float pairs "
-                   "(~48 bits) and returned in float64; "
-                   "outer FGMRES Arnoldi basis and CGS2 in float pairs (two float32, ~48 bits); "
-                   "Hessenberg, Givens, solution update and true residual in float64",
+        "config": {"workload": WORKLOAD, "form": f"{FORMS[HEADLINE][0]}: {FORMS[HEADLINE][1]}",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"replicas x{world}"},
-        "its": st_mixed.its, "matvecs": st_mixed.matvecs,
-        "rel_res_true": st_mixed.rel_res_true, "rel_res_check": res,
-        "plain": {"value": rhs_total / t_plain, "unit": "RHS/s",
-                  "ms_per_step": t_plain / args.steps * 1e3, "dtype": "c128",
-                  "its": st_plain.its, "rel_res_true": st_plain.rel_res_true},
-        "fci32_f64_outer": {"value": rhs_total / t_f32, "unit": "RHS/s",
-                            "ms_per_step": t_f32 / args.steps * 1e3,
-                            "form": "FCI in complex64, outer Arnoldi in float64",
-                            "its": st_f32.its, "rel_res_true": st_f32.rel_res_true},
-        "mixed_f64_fci": {"value": rhs_total / t_m64, "unit": "RHS/s",
-                          "ms_per_step": t_m64 / args.steps * 1e3,
-                          "form": "complex64 sweeps only; step d, inner GMRES float64",
-                          "its": st_m64.its, "rel_res_true": st_m64.rel_res_true},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None,
-                     "traffic": traffic, "kernel": "k_poly_stage<float2> (batched sweeps)",
-                     "launches": nl, "avg_launch_us": (ms / nl * 1e3) if nl else None,
-                     "peak_kind": f"{peak_kind} copy bandwidth"},
-        "kernel_classes": {
-            "poly_stage": {"launches": poly[0], "ms": poly[1], "GB": poly[2] / 1e9},
-            "stencil_f64": {"launches": sten[0], "ms": sten[1], "GB": sten[2] / 1e9},
-            "krylov_f64": {"launches": kryl[0], "ms": kryl[1], "GB": kryl[2] / 1e9}},
+        "its": st_head.its, "matvecs": st_head.matvecs,
+        "rel_res_true": st_head.rel_res_true, "rel_res_check": res,
+        "roofline": roof,
+        "kernel_classes": {k: {"launches": v[0], "ms": v[1], "GB": v[2] / 1e9,
+                               "fp64_TFLOP": v[3] / 1e12} for k, v in cls.items()},
         "e2e": {"value": rhs_total / t_e2e, "unit": "RHS/s", "h2d_bytes_per_step": n * 16,
                 "d2h_bytes_per_step": n * 16},
+        "l2_copy_GBps": l2_peak,
         "stencil_hbm": hbm,
+        "large": large,
         "batched_uneven": uneven,
         "gpu_launches": launches,
         "clocks": clk,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        counts = oracle_counts()[wl.name]
-        per = 1
-        t_cpu = time_oracle_sample(wl, per)
+    for form, (t_f, st_f) in others.items():
+        line[form] = {"value": rhs_total / t_f, "unit": "RHS/s",
+                      "ms_per_step": t_f / args.steps * 1e3, "form": FORMS[form][1],
+                      "its": st_f.its, "rel_res_true": st_f.rel_res_true}
+    if cpu_leg:
+        ref = futs["ref"].result()
+        single = futs["single"].result()
+        pool.shutdown()
+        uref = ref["u"]
+        nref = float(np.linalg.norm(uref))
+        errs = {}
+        for form in FORMS:
+            errs[form] = {
+                "at_rtol_1e-8": float(np.linalg.norm(sols[form] - uref) / nref),
+                "at_rtol_1e-11": float(np.linalg.norm(sols11[form][0] - uref) / nref),
+                "rel_res_true_1e-11_solve": sols11[form][1]}
+        line["err_vs_oracle"] = {
+            "reference": f"oracle float64 solution at a true residual of "
+                         f"{ref['rel_res_true']:.2e} ({ref['its']} steps)",
+            "forms": errs}
+        # all-core sample: one bounded sample per host core at the same time
+        cores = host_cores()
+        per = 6
+        allp = oracle_pool(cores)
+        jobs = [allp.submit(oracle_job, "gaussian_bumps_64", 1e-30, per) for _ in range(cores)]
+        rs = [j.result() for j in jobs]
+        allp.shutdown()
+        wall = max(r["t1"] for r in rs) - min(r["t0"] for r in rs)
+        its8 = single["its"]
         line["cpu_baseline"] = {
-            "value": 1.0 / (t_cpu / per * counts["its"]), "unit": "RHS/s",
-            "cores": cpu_threads(), "kind": "oracle",
-            "sample": f"{per} outer FGMRES step of the complex128 oracle on this workload "
-                      f"({t_cpu:.2f} s), scaled by the oracle's {counts['its']} steps to 1e-8"}
+            "value": cores * per / its8 / wall, "unit": "RHS/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{cores} processes (one numpy thread each) each timing {per} outer FGMRES "
+                      f"steps of the oracle on this workload at the same time ({wall:.1f} s "
+                      f"wall), scaled by the oracle's {its8} steps to 1e-8 measured below"}
+        line["cpu_baseline_single_core"] = {
+            "value": 1.0 / (single["t1"] - single["t0"]), "unit": "RHS/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"one full oracle solve of this workload to 1e-8 ({single['its']} steps, "
+                      f"{single['t1'] - single['t0']:.1f} s, true residual "
+                      f"{single['rel_res_true']:.2e}), one numpy thread, run beside the GPU part"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    P.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -51,16 +51,19 @@ typedef enum {
   HZ_ERR_NOT_CONVERGED = 4,  /* hz_solve: max_cycles reached above rtol; u is the last iterate */
   HZ_ERR_BREAKDOWN = 5,      /* reserved */
   HZ_ERR_DIVERGED = 6,       /* hz_solve: a residual became NaN or Inf */
-  HZ_ERR_SETUP = 7           /* no polynomial order <= qmax converges at some node */
+  HZ_ERR_SETUP = 7,          /* no polynomial order <= qmax converges at some node */
+  HZ_ERR_TIMEOUT = 8         /* a grid-wide barrier of a cooperative kernel gave up waiting
+                                (hz_problem_set_spin_limit); the solve stopped at that step */
 } hz_status;
 
 typedef enum {
   HZ_C128 = 0,        /* everything complex128 / float64 ("plain" form) */
-  HZ_MIXED_C64 = 1,   /* polynomial sweeps in complex64; quadrature sum (float-pair
-                         accumulation, about 48 bits, returned as float64), step d, inner and
-                         outer Arnoldi, Givens and true residual in float64 */
+  HZ_MIXED_C64 = 1,   /* polynomial sweeps in complex64; the quadrature-weighted sum of their
+                         results accumulated in float64; step d, the inner and outer Arnoldi
+                         (CGS2), Givens least squares and the true residual in float64 */
   HZ_MIXED_C64_FCI32 = 2, /* the whole FCI preconditioner in complex64 (sweeps, step d, inner
-                         GMRES), except its quadrature sum, accumulated as in HZ_MIXED_C64; the outer
+                         GMRES with float32 scalars), except its quadrature sum, accumulated in
+                         float pairs (about 48 bits) and returned as float64; the outer
                          FGMRES (CGS2 Arnoldi, Givens, updates) and the true residual in
                          float64.  FGMRES admits a variable preconditioner, so the solution
                          still reaches the float64 residual target. */
@@ -99,13 +102,28 @@ typedef struct {
  * outer restart length (1..128), inner GMRES steps (0..128).  autotune != 0 times the
  * candidate tile shapes of the polynomial-stage and complex64 stencil kernels on this grid
  * at creation (a few milliseconds) and keeps the fastest; 0 keeps fixed defaults.  Tiling
- * changes no result: every candidate performs the same arithmetic per point. */
+ * changes no result: every candidate performs the same arithmetic per point.  flags: an OR of
+ * hz_limit_flags (0 for none), which trade precision forms for device memory. */
 typedef struct {
   int nrhs_max;
   int restart_max;
   int inner_k_max;
   int autotune;
+  int flags;
 } hz_limits;
+
+typedef enum {
+  /* the polynomial workspace (4 J fields per right-hand side) sized for complex64 sweeps only:
+     half the memory; HZ_C128 in hz_solve, hz_fci and hz_shifted_solve returns HZ_ERR_INVALID */
+  HZ_LIMIT_SWEEPS_C64 = 1,
+  /* FGMRES stores its directions z_k = FCI(v_k) rounded to complex64 (half the memory of the
+     m direction fields).  The outer matvec A z_k is taken in float64 from the stored value, so
+     the Arnoldi relation holds for the directions as stored and the solution update u += Z y
+     (float64) stays consistent with the Krylov residual; this is FGMRES with a preconditioner
+     whose output is rounded (Section 2, after Algorithm 1: any right preconditioner may vary
+     from step to step).  hz_solve accepts only HZ_MIXED_C64 and HZ_MIXED_C64_FCI32 then. */
+  HZ_LIMIT_Z_C64 = 2
+} hz_limit_flags;
 
 /* hz_solve settings.  restart_m <= restart_max, inner_k <= inner_k_max.  precision is an
  * hz_precision.  fixed_its > 0 takes exactly that many outer Arnoldi steps (cycles of
@@ -186,7 +204,9 @@ hz_status hz_apply_shifted(hz_problem* p, double zr, double zi, const void* x, v
  * C = [[0, I], [-(A1 + I), -A2]], where A = A1 - i A2 is the normalised operator split into its
  * Hermitian part A1 = s L_h - diag(m) and A2 = diag(a).  Each of the nvec vectors is two
  * fields stored one after the other, x = (x1; x2) (2*nx*ny*nz values), so (iC - I)(iu; u) =
- * (0; f) exactly when A u = f, and with z = s the shifted form eq:shifted-2x2.  x and y must
+ * (0; f) exactly when A u = f.  For Hermitian A (layer_cells = 0 or sigma_max = 0) the shift
+ * z = s gives the shifted form eq:shifted-2x2; with a sponge the lower blocks are -i(A1 + I)
+ * and -i A2 - (s + 1) I instead.  x and y must
  * not overlap.  precision HZ_C128: double complex; HZ_MIXED_C64: float complex, computed in
  * float32.  HZ_ERR_INVALID for nvec > 65535 or grids of 2^31 points or more. */
 hz_status hz_apply_2x2(hz_problem* p, double zr, double zi, const void* x, void* y, int nvec,
@@ -229,9 +249,19 @@ hz_status hz_solve_batched(hz_problem* const* probs, int nprob, const void* cons
  * 0 = batched polynomial stage (eq:fix-pt-exp sweeps + quadrature; timed as whole stage
  * sequences, so its time includes the short gaps between stages), 1 = shifted stencil,
  * 2 = Krylov reductions (CGS2, norms, step d).  hz_profile_read synchronises the recorded
- * events and returns, per class, launches, total milliseconds and total algorithmic bytes
- * since the last enable; any output pointer may be null. */
+ * events and returns, per class, launches, total milliseconds, total algorithmic bytes and
+ * the algorithmic float64 flops of the float64 kernels among them (an FMA counts 2; float32
+ * kernels add none) since the last enable; any output pointer may be null. */
 hz_status hz_profile_enable(hz_problem* p, int on);
+
+/* Poll limit of the grid-wide barriers inside the cooperative kernels (hz_problem_fused_tail,
+ * hz_problem_fused_arnoldi): a block polls the barrier at most `polls` times (back to back,
+ * then about 32 ns apart) before it gives up; polls < 0 restores the default (2^23, about a
+ * second).  A barrier that gives up makes its kernel return early, hz_solve stops after that
+ * outer step and returns HZ_ERR_TIMEOUT (u is then not a solution), and the next call starts
+ * clean.  With polls = 0 every barrier wait that is not already satisfied gives up at once.
+ * Waits for the problem's queued work first.  Not in the paper: a guard for shared devices. */
+hz_status hz_problem_set_spin_limit(hz_problem* p, long long polls);
 
 /* Selects how the complex64 forms run steps 3-5 of Algorithm 1 (step d, the inner GMRES,
  * v + d w) for a single right-hand side.  mode = 1 (the default): one cooperative kernel whose
@@ -257,7 +287,7 @@ hz_status hz_problem_fused_tail(hz_problem* p, int mode);
  * barrier timeout is reported as for hz_problem_fused_tail. */
 hz_status hz_problem_fused_arnoldi(hz_problem* p, int mode);
 hz_status hz_profile_read(hz_problem* p, int cls, long long* launches, double* ms,
-                          double* bytes);
+                          double* bytes, double* flops);
 
 /* Residual without any device allocation, for callers that cannot call cudaMalloc (code
  * running while their stream is being captured into a CUDA graph, allocators that own a

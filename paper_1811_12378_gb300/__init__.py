@@ -2,9 +2,11 @@
 the shifted 7-point stencil, the polynomial fixed-point scheme at every contour node, the
 FCI preconditioner (Algorithm 1) and flexible GMRES, as CUDA kernels behind the C ABI of
 include/hz.h.  ``hz`` is the Python binding (argument marshalling only)."""
-from .hz import (HZ_C128, HZ_MIXED_C64, HZ_MIXED_C64_FCI32, HZ_MIXED_C64_FF, EXPORTS, PROF_KRYLOV, PROF_POLY, PROF_STENCIL, HzError,
+from .hz import (HZ_C128, HZ_MIXED_C64, HZ_MIXED_C64_FCI32, HZ_MIXED_C64_FF, HZ_LIMIT_SWEEPS_C64,
+                 HZ_LIMIT_Z_C64, EXPORTS, PROF_KRYLOV, PROF_POLY, PROF_STENCIL, HzError,
                  Problem, SolveStats, launch_count, library_path, load, plan, solve_batched)
 
-__all__ = ["HZ_C128", "HZ_MIXED_C64", "HZ_MIXED_C64_FCI32", "HZ_MIXED_C64_FF", "EXPORTS", "PROF_KRYLOV", "PROF_POLY", "PROF_STENCIL",
+__all__ = ["HZ_C128", "HZ_MIXED_C64", "HZ_MIXED_C64_FCI32", "HZ_MIXED_C64_FF",
+           "HZ_LIMIT_SWEEPS_C64", "HZ_LIMIT_Z_C64", "EXPORTS", "PROF_KRYLOV", "PROF_POLY", "PROF_STENCIL",
            "HzError", "Problem", "SolveStats",
            "launch_count", "library_path", "load", "plan", "solve_batched"]

@@ -1,6 +1,7 @@
 """Compile libhz (the CUDA kernels, the solver and its C ABI) for sm_103a, in-tree."""
 from __future__ import annotations
 
+import hashlib
 import os
 import shutil
 import subprocess
@@ -25,15 +26,39 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: libhz needs the CUDA toolkit to build")
 
 
+STAMP = LIB + ".sha256"
+
+
+def _fingerprint(nvcc: str, deps) -> str:
+    """sha256 over the compiler path, the flags and the content of every source and header."""
+    h = hashlib.sha256()
+    h.update(" ".join([nvcc, *ARCH, *FLAGS, *SOURCES]).encode())
+    for d in deps:
+        h.update(os.path.basename(d).encode())
+        with open(d, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def build(verbose: bool = False, force: bool = False) -> str:
-    """Build _build/libhz.so if any source is newer than it; returns its path."""
+    """Build _build/libhz.so unless the library there was built from exactly these sources and
+    flags (a content hash kept beside it; file times are not trusted); returns its path."""
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, "hz_internal.h"), os.path.join(CSRC, "hz_device.cuh"), os.path.join(INCLUDE, "hz.h")]
-    if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps)):
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+    headers = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC)
+                     if f.endswith((".h", ".cuh")))
+    deps = srcs + headers + [os.path.join(INCLUDE, "hz.h")]
     nvcc = _nvcc()
+    fp = _fingerprint(nvcc, deps)
+    if not force and os.path.exists(LIB) and os.path.exists(STAMP):
+        with open(STAMP) as fh:
+            if fh.read().strip() == fp:
+                return LIB
+    os.makedirs(OUT_DIR, exist_ok=True)
+    # objects of sources that are no longer part of the library
+    keep = {os.path.basename(s) + ".o" for s in SOURCES}
+    for f in os.listdir(OUT_DIR):
+        if f.endswith(".o") and f not in keep:
+            os.remove(os.path.join(OUT_DIR, f))
     objs = []
 
     def compile_one(src):
@@ -54,6 +79,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(fp + "\n")
     return LIB
 
 

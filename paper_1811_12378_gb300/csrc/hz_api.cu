@@ -56,7 +56,7 @@ struct ProfClass {
   std::vector<cudaEvent_t> ev;  // 2 * kProfPool
   int used = 0;
   long long launches = 0;
-  double ms = 0.0, bytes = 0.0;
+  double ms = 0.0, bytes = 0.0, flops = 0.0;
 };
 
 }  // namespace
@@ -84,7 +84,10 @@ struct hz_problem {
   float2* w32 = nullptr;     // [nrhs][n] quadrature sum rounded to complex64
   float2* Aw32 = nullptr;    // [nrhs][n]
   double2* V = nullptr;      // [nrhs][m+1][n] outer basis
-  double2* Z = nullptr;      // [nrhs][m][n] preconditioned directions
+  double2* Z = nullptr;      // [nrhs][m][n] preconditioned directions (float64)
+  float2* Z32 = nullptr;     // [nrhs][m][n] the same stored in complex64 (HZ_LIMIT_Z_C64)
+  bool z32 = false;          // HZ_LIMIT_Z_C64
+  bool sweeps32 = false;     // HZ_LIMIT_SWEEPS_C64
   double2* partial = nullptr;
   unsigned* counters = nullptr;
   void* gmem = nullptr;      // all GmresDev arrays
@@ -116,7 +119,8 @@ struct hz_problem {
   bool tail_solo = true;     // false while several problems run concurrently (batched solve)
   bool tail_used = false;
   int tail_ppt[2] = {0, 0}, tail_blocks[2] = {0, 0};
-  unsigned* tail_bar = nullptr;  // [0] arrivals, [1] generation, [2] error flag
+  unsigned* tail_bar = nullptr;  // [0] arrivals, [1] generation, [2] error flag, [3] poll limit
+  unsigned* h_bar = nullptr;     // pinned copy of the error flag, read after each outer step
   // the outer float-pair Arnoldi step as one cooperative kernel (hz_arnoldi_ff.cu), sharing
   // the barrier words and the error flag of the FCI tail (the two never run concurrently)
   int arn_mode = 1;  // hz_problem_fused_arnoldi: 0 five kernels, 1 cooperative, 2 summed norm
@@ -141,6 +145,7 @@ struct hz_problem {
     if (h_scal) cudaFreeHost(h_scal);
     if (h_stopped) cudaFreeHost(h_stopped);
     if (h_tol) cudaFreeHost(h_tol);
+    if (h_bar) cudaFreeHost(h_bar);
   }
 };
 
@@ -216,6 +221,7 @@ struct ProfScope {
   int cls, slot = -1;
   cudaStream_t st;
   double bytes;
+  double flops = 0.0;
   hz_status begin() {
     if (!p->prof_on) return HZ_OK;
     ProfClass& c = p->prof[cls];
@@ -230,6 +236,7 @@ struct ProfScope {
     HZ_CUDA(cudaEventRecord(c.ev[2 * slot + 1], st));
     c.launches++;
     c.bytes += bytes;
+    c.flops += flops;
     return HZ_OK;
   }
 };
@@ -240,6 +247,15 @@ struct ProfScope {
     HZ_TRY(ps_.begin());                         \
     HZ_CUDA(CALL);                               \
     HZ_TRY(ps_.end());                           \
+  } while (0)
+
+// The same for a float64 kernel, also adding its algorithmic float64 flops (an FMA counts 2).
+#define HZ_TIMED_F(P, CLS, ST, BYTES, FLOPS, CALL)            \
+  do {                                                        \
+    ProfScope ps_{(P), (CLS), -1, (ST), (BYTES), (FLOPS)};    \
+    HZ_TRY(ps_.begin());                                      \
+    HZ_CUDA(CALL);                                            \
+    HZ_TRY(ps_.end());                                        \
   } while (0)
 
 // Algorithmic bytes of one stencil launch: x read and y written once per field, m once.
@@ -254,6 +270,18 @@ double cgs_bytes(int mode, long long n, int nb, int nvec) {
   const double fld = 16.0 * double(n) * nvec;
   return mode == 0 ? fld * (nb + 1) : fld * (nb + 2);
 }
+
+// Float64 flops of one Gram-Schmidt launch per point and field: a complex dot or update term
+// is 4 FMA (8 flops), a squared norm 2 FMA.  Mode 0: nb dots + the norm; mode 1: nb updates
+// and nb dots; mode 2: nb updates + the norm.
+double cgs_flops(int mode, long long n, int nb, int nvec) {
+  const double pts = double(n) * nvec;
+  return mode == 1 ? pts * 16.0 * nb : pts * (8.0 * nb + 4.0);
+}
+
+// Float64 flops of the float64 stencil per point: 10 neighbour additions, the shifted diagonal
+// (2), and two complex multiply-adds with the Laplacian weight (10).
+constexpr double kStencil64Flops = 22.0;
 
 // ------------------------------------------------------------------ polynomial solves
 
@@ -375,7 +403,7 @@ template <typename T, typename R>
 hz_status run_poly(hz_problem* p, const T* dg, Buf<const T> f, int nvec,
                    const std::vector<int>& which, bool quad, Buf<double2> wbuf,
                    std::vector<long long>* yfinal, cudaStream_t st,
-                   Buf<float2> w32buf = Buf<float2>{nullptr, 0}) {
+                   Buf<float2> w32buf = Buf<float2>{nullptr, 0}, bool quad64 = false) {
   const long long n = p->g.n;
   T* ws = (T*)p->poly;
   const long long wrs = 4LL * p->J * n;  // elements of T per rhs
@@ -383,6 +411,7 @@ hz_status run_poly(hz_problem* p, const T* dg, Buf<const T> f, int nvec,
   std::vector<long long> ycur;
   build_schedule<R>(p, which, quad, sched, ycur);
   const int T_total = (int)sched.size();
+  if (quad && T_total > 0) sched.back().quad64 = quad64 ? 1 : 0;
   // one event pair around the whole stage sequence (per-launch events would cost more than
   // a 64^3 stage); launches and bytes are added per stage
   ProfScope seq{p, 0, -1, st, 0.0};
@@ -399,17 +428,18 @@ hz_status run_poly(hz_problem* p, const T* dg, Buf<const T> f, int nvec,
   return HZ_OK;
 }
 
-// FCI (Algorithm 1) on nvec double-complex fields r -> out.
-// After a synchronisation: a grid barrier of the cooperative FCI tail that gave up leaves its
-// flag set; report it once and reset the barrier words for the next launch.
+// After a synchronisation: a grid barrier of a cooperative kernel that gave up leaves its
+// flag set; report it once and reset the barrier words (not the poll limit) for the next launch.
 hz_status check_tail_fault(hz_problem* p) {
   if (!p->tail_used) return HZ_OK;
   unsigned w[3] = {0, 0, 0};
   HZ_CUDA(cudaMemcpy(w, p->tail_bar, sizeof(w), cudaMemcpyDeviceToHost));
   if (w[2] == 0) return HZ_OK;
-  HZ_CUDA(cudaMemset(p->tail_bar, 0, sizeof(unsigned) * 4));
-  return fail(HZ_ERR_CUDA, "a grid barrier of a cooperative kernel timed out");
+  HZ_CUDA(cudaMemset(p->tail_bar, 0, sizeof(unsigned) * 3));
+  return fail(HZ_ERR_TIMEOUT, "a grid barrier of a cooperative kernel gave up waiting");
 }
+
+// FCI (Algorithm 1) on nvec double-complex fields r -> out.
 
 bool tail_fits(const hz_problem* p, int nvec, int kin) {
   const int c = kin <= 4 ? 0 : 1;
@@ -435,8 +465,10 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
     const Buf<float2> w32b{fci32 ? p->w32 : nullptr, n};
     // (float-pair input: the normalisation that made r already wrote its complex64 rounding)
     if (!r_ff) HZ_CUDA(hz::launch_convert_c128_c64(r, Buf<float2>{p->f32, n}, n, nvec, st));
+    // HZ_MIXED_C64 keeps the quadrature accumulation in float64; the complex64-FCI forms sum
+    // the terms in float pairs
     HZ_TRY((run_poly<float2, float>(p, p->d32, Buf<const float2>{p->f32, n}, nvec, all, true,
-                                    wb, nullptr, st, w32b)));
+                                    wb, nullptr, st, w32b, precision == HZ_MIXED_C64)));
   } else {
     HZ_TRY((run_poly<double2, double>(p, p->d64, r, nvec, all, true, wb, nullptr, st)));
   }
@@ -485,25 +517,26 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
     return HZ_OK;
   }
   // Aw, step d, inner start v0 = (r - d Aw)/||r - d Aw||
-  HZ_TIMED(p, 1, st, (stencil_bytes<double2, double2>(n, nvec)),
-           (hz::launch_stencil_diag(p->g, p->d64, Buf<const double2>{p->w, n},
-                                    Buf<double2>{p->Aw, n}, nvec, 0.0, 0.0, st)));
+  HZ_TIMED_F(p, 1, st, (stencil_bytes<double2, double2>(n, nvec)), kStencil64Flops * n * nvec,
+             (hz::launch_stencil_diag(p->g, p->d64, Buf<const double2>{p->w, n},
+                                      Buf<double2>{p->Aw, n}, nvec, 0.0, 0.0, st)));
   const long long vrs = (long long)(p->lim.inner_k_max + 1) * n;
-  HZ_TIMED(p, 2, st, 16.0 * n * nvec * 5,
-           hz::launch_fci_step(Buf<const double2>{p->Aw, n}, r, Buf<double2>{p->Vin, vrs}, p->gin,
-                               p->partial, p->counters, n, nvec, st));
+  // two launches: d (reads Aw, r) and v0 = r - d Aw with its norm (reads Aw, r; writes v0)
+  HZ_TIMED_F(p, 2, st, 16.0 * n * nvec * 5, 24.0 * n * nvec,
+             hz::launch_fci_step(Buf<const double2>{p->Aw, n}, r, Buf<double2>{p->Vin, vrs},
+                                 p->gin, p->partial, p->counters, n, nvec, st));
   HZ_CUDA(hz::launch_scale(Buf<double2>{p->Vin, vrs}, Buf<const double2>{p->Vin, vrs}, n, p->gin,
                            nvec, st));
   for (int j = 0; j < kin; ++j) {
     Buf<double2> wj{p->Vin + (long long)(j + 1) * n, vrs};
-    HZ_TIMED(p, 1, st, (stencil_bytes<double2, double2>(n, nvec)),
-             (hz::launch_stencil_diag(p->g, p->d64,
-                                      Buf<const double2>{p->Vin + (long long)j * n, vrs}, wj, nvec,
-                                      0.0, 0.0, st)));
+    HZ_TIMED_F(p, 1, st, (stencil_bytes<double2, double2>(n, nvec)), kStencil64Flops * n * nvec,
+               (hz::launch_stencil_diag(p->g, p->d64,
+                                        Buf<const double2>{p->Vin + (long long)j * n, vrs}, wj,
+                                        nvec, 0.0, 0.0, st)));
     for (int mode = 0; mode < 3; ++mode)
-      HZ_TIMED(p, 2, st, cgs_bytes(mode, n, j + 1, nvec),
-               hz::launch_cgs(mode, p->Vin, n, vrs, j + 1, wj, n, p->gin, p->partial, p->counters,
-                              nvec, kBreakdown, st));
+      HZ_TIMED_F(p, 2, st, cgs_bytes(mode, n, j + 1, nvec), cgs_flops(mode, n, j + 1, nvec),
+                 hz::launch_cgs(mode, p->Vin, n, vrs, j + 1, wj, n, p->gin, p->partial,
+                                p->counters, nvec, kBreakdown, st));
     HZ_CUDA(hz::launch_scale(wj, Buf<const double2>{wj.p, vrs}, n, p->gin, nvec, st));
   }
   HZ_CUDA(hz::launch_backsolve(p->gin, nvec, st));
@@ -521,8 +554,25 @@ hz_status outer_step_launches(hz_problem* p, int k, int nrhs, int K, int precisi
   const long long zrs = (long long)p->lim.restart_max * n;
   GmresDev& go = p->gout;
   Buf<const double2> vk{p->V + (long long)k * n, vrs};
-  Buf<double2> zk{p->Z + (long long)k * n, zrs};
   const bool ff = precision == HZ_MIXED_C64_FF;
+  if (p->z32) {
+    // z_k = FCI(v_k) into a float64 scratch field (Aw is free once FCI has returned), stored
+    // rounded to complex64; the matvec then reads the stored value
+    HZ_TRY(run_fci(p, vk, Buf<double2>{p->Aw, n}, nrhs, K, precision, st, false));
+    Buf<float2> z32k{p->Z32 + (long long)k * n, zrs};
+    HZ_CUDA(hz::launch_convert_c128_c64(Buf<const double2>{p->Aw, n}, z32k, n, nrhs, st));
+    Buf<double2> wk{p->V + (long long)(k + 1) * n, vrs};
+    HZ_TIMED_F(p, 1, st, double(n) * nrhs * (8.0 + 16.0 + 16.0), kStencil64Flops * n * nrhs,
+               (hz::launch_stencil_diag_x32(p->g, p->d64, Buf<const float2>{z32k.p, zrs}, wk,
+                                            nrhs, st)));
+    for (int mode = 0; mode < 3; ++mode)
+      HZ_TIMED_F(p, 2, st, cgs_bytes(mode, n, k + 1, nrhs), cgs_flops(mode, n, k + 1, nrhs),
+                 hz::launch_cgs(mode, p->V, n, vrs, k + 1, wk, n, go, p->partial, p->counters,
+                                nrhs, kBreakdown, st));
+    HZ_CUDA(hz::launch_scale(wk, Buf<const double2>{wk.p, vrs}, n, go, nrhs, st));
+    return HZ_OK;
+  }
+  Buf<double2> zk{p->Z + (long long)k * n, zrs};
   HZ_TRY(run_fci(p, vk, zk, nrhs, K, precision, st, ff));
   if (ff) {
     // the float-pair Arnoldi: w = A z_k stored as float pairs in v_{k+1}'s slot
@@ -549,13 +599,13 @@ hz_status outer_step_launches(hz_problem* p, int k, int nrhs, int K, int precisi
     return HZ_OK;
   }
   Buf<double2> wk{p->V + (long long)(k + 1) * n, vrs};
-  HZ_TIMED(p, 1, st, (stencil_bytes<double2, double2>(n, nrhs)),
-           (hz::launch_stencil_diag(p->g, p->d64, Buf<const double2>{zk.p, zrs}, wk, nrhs, 0.0,
-                                    0.0, st)));
+  HZ_TIMED_F(p, 1, st, (stencil_bytes<double2, double2>(n, nrhs)), kStencil64Flops * n * nrhs,
+             (hz::launch_stencil_diag(p->g, p->d64, Buf<const double2>{zk.p, zrs}, wk, nrhs, 0.0,
+                                      0.0, st)));
   for (int mode = 0; mode < 3; ++mode)
-    HZ_TIMED(p, 2, st, cgs_bytes(mode, n, k + 1, nrhs),
-             hz::launch_cgs(mode, p->V, n, vrs, k + 1, wk, n, go, p->partial, p->counters, nrhs,
-                            kBreakdown, st));
+    HZ_TIMED_F(p, 2, st, cgs_bytes(mode, n, k + 1, nrhs), cgs_flops(mode, n, k + 1, nrhs),
+               hz::launch_cgs(mode, p->V, n, vrs, k + 1, wk, n, go, p->partial, p->counters, nrhs,
+                              kBreakdown, st));
   HZ_CUDA(hz::launch_scale(wk, Buf<const double2>{wk.p, vrs}, n, go, nrhs, st));
   return HZ_OK;
 }
@@ -782,6 +832,11 @@ hz_status check_solve_args(const hz_problem* p, int nrhs, const hz_solve_opts* o
   if (opts->precision != HZ_C128 && opts->precision != HZ_MIXED_C64 &&
       opts->precision != HZ_MIXED_C64_FCI32 && opts->precision != HZ_MIXED_C64_FF)
     return fail(HZ_ERR_INVALID, "unknown precision");
+  if (p->sweeps32 && opts->precision == HZ_C128)
+    return fail(HZ_ERR_INVALID, "HZ_C128 needs a problem created without HZ_LIMIT_SWEEPS_C64");
+  if (p->z32 && opts->precision != HZ_MIXED_C64 && opts->precision != HZ_MIXED_C64_FCI32)
+    return fail(HZ_ERR_INVALID, "a problem created with HZ_LIMIT_Z_C64 solves in HZ_MIXED_C64 or "
+                                "HZ_MIXED_C64_FCI32 only");
   return HZ_OK;
 }
 }  // namespace
@@ -798,6 +853,7 @@ const char* hz_status_string(hz_status s) {
     case HZ_ERR_BREAKDOWN: return "breakdown";
     case HZ_ERR_DIVERGED: return "diverged";
     case HZ_ERR_SETUP: return "set-up failed";
+    case HZ_ERR_TIMEOUT: return "timeout";
   }
   return "unknown status";
 }
@@ -819,8 +875,10 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
     return fail(HZ_ERR_INVALID, "invalid contour options (1 <= J <= 16, t > 0, eps > 0, "
                                 "1 <= qmax <= 12, reduction > 1)");
   if (!limits || limits->nrhs_max < 1 || limits->restart_max < 1 || limits->inner_k_max < 0 ||
-      limits->restart_max > 128 || limits->inner_k_max > 128)
-    return fail(HZ_ERR_INVALID, "invalid limits (1 <= restart_max <= 128, 0 <= inner_k_max <= 128)");
+      limits->restart_max > 128 || limits->inner_k_max > 128 ||
+      (limits->flags & ~(HZ_LIMIT_SWEEPS_C64 | HZ_LIMIT_Z_C64)) != 0)
+    return fail(HZ_ERR_INVALID, "invalid limits (1 <= restart_max <= 128, 0 <= inner_k_max <= 128, "
+                                "known flags only)");
   const long long n = (long long)grid->nx * grid->ny * grid->nz;
   for (long long i = 0; i < n; ++i)
     if (!(c_host[i] > 0) || !std::isfinite(c_host[i]))
@@ -868,7 +926,10 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   if ((s = dalloc(p, (void**)&p->m64, sizeof(double) * n)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->d64, sizeof(double2) * n)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->d32, sizeof(float2) * n)) != HZ_OK) return bail(s);
-  if ((s = dalloc(p, &p->poly, sizeof(double2) * 4 * (size_t)p->J * n * R)) != HZ_OK) return bail(s);
+  p->sweeps32 = (limits->flags & HZ_LIMIT_SWEEPS_C64) != 0;
+  p->z32 = (limits->flags & HZ_LIMIT_Z_C64) != 0;
+  const size_t poly_es = p->sweeps32 ? sizeof(float2) : sizeof(double2);
+  if ((s = dalloc(p, &p->poly, poly_es * 4 * (size_t)p->J * n * R)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->f32, sizeof(float2) * (size_t)n * R)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->w, sizeof(double2) * (size_t)n * R)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->Aw, sizeof(double2) * (size_t)n * R)) != HZ_OK) return bail(s);
@@ -880,7 +941,11 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   if ((s = dalloc(p, (void**)&p->Aw32, sizeof(float2) * (size_t)n * R)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->V, sizeof(double2) * (size_t)n * (M + 1) * R)) != HZ_OK)
     return bail(s);
-  if ((s = dalloc(p, (void**)&p->Z, sizeof(double2) * (size_t)n * M * R)) != HZ_OK) return bail(s);
+  if (p->z32) {
+    if ((s = dalloc(p, (void**)&p->Z32, sizeof(float2) * (size_t)n * M * R)) != HZ_OK) return bail(s);
+  } else {
+    if ((s = dalloc(p, (void**)&p->Z, sizeof(double2) * (size_t)n * M * R)) != HZ_OK) return bail(s);
+  }
   // grids of the cooperative kernels (whole numbers of blocks per SM)
   {
     cudaError_t pe = hz::fci_tail32_plan(n, std::min(K, 4), &p->tail_ppt[0], &p->tail_blocks[0]);
@@ -914,18 +979,20 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   gmres_layout(p->gin, cur, R, K);
   e = cudaMemset(p->gmem, 0, gb);
   if (e == cudaSuccess) e = cudaMemset(p->counters, 0, sizeof(unsigned) * R);
-  if (e == cudaSuccess) e = cudaMemset(p->poly, 0, sizeof(double2) * 4 * (size_t)p->J * n * R);
+  if (e == cudaSuccess) e = cudaMemset(p->poly, 0, poly_es * 4 * (size_t)p->J * n * R);
   if (e != cudaSuccess) {
     delete p;
     return cuda_fail(e, "cudaMemset");
   }
   if (cudaMallocHost(&p->h_scal, sizeof(double) * hz::SC_COUNT * R) != cudaSuccess ||
       cudaMallocHost(&p->h_stopped, sizeof(int) * R) != cudaSuccess ||
-      cudaMallocHost(&p->h_tol, sizeof(double) * R) != cudaSuccess) {
+      cudaMallocHost(&p->h_tol, sizeof(double) * R) != cudaSuccess ||
+      cudaMallocHost(&p->h_bar, sizeof(unsigned) * 4) != cudaSuccess) {
     cudaGetLastError();
     delete p;
     return fail(HZ_ERR_OOM, "pinned host allocation failed");
   }
+  std::memset(p->h_bar, 0, sizeof(unsigned) * 4);
   // the inner GMRES of FCI never stops on a tolerance (SC_TOL < 0), fixed once here
   {
     std::vector<double> sc(hz::SC_COUNT * (size_t)R, 0.0);
@@ -979,7 +1046,11 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
     delete p;
     return cuda_fail(e, "cudaMemcpy of coefficients");
   }
-  e = cudaMemset(p->tail_bar, 0, sizeof(unsigned) * 4);
+  e = cudaMemset(p->tail_bar, 0, sizeof(unsigned) * 3);
+  if (e == cudaSuccess) {
+    const unsigned lim = hz::GRID_SPINS_DEFAULT;
+    e = cudaMemcpy(p->tail_bar + 3, &lim, sizeof(unsigned), cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     delete p;
     return cuda_fail(e, "cooperative FCI tail set-up");
@@ -1053,6 +1124,17 @@ hz_status hz_problem_fused_arnoldi(hz_problem* p, int mode) {
   return HZ_OK;
 }
 
+hz_status hz_problem_set_spin_limit(hz_problem* p, long long polls) {
+  HZ_TRY(check_problem(p));
+  HZ_TRY(set_device(p));
+  if (polls > 0xffffffffLL) return fail(HZ_ERR_INVALID, "poll limit above 2^32 - 1");
+  const unsigned lim = polls < 0 ? hz::GRID_SPINS_DEFAULT : (unsigned)polls;
+  // the problem's kernels run on its own stream: let them finish before the word changes
+  HZ_CUDA(cudaStreamSynchronize(p->own));
+  HZ_CUDA(cudaMemcpy(p->tail_bar + 3, &lim, sizeof(unsigned), cudaMemcpyHostToDevice));
+  return HZ_OK;
+}
+
 hz_status hz_profile_enable(hz_problem* p, int on) {
   HZ_TRY(check_problem(p));
   HZ_TRY(set_device(p));
@@ -1065,13 +1147,14 @@ hz_status hz_profile_enable(hz_problem* p, int on) {
     c.launches = 0;
     c.ms = 0.0;
     c.bytes = 0.0;
+    c.flops = 0.0;
   }
   p->prof_on = on != 0;
   return HZ_OK;
 }
 
 hz_status hz_profile_read(hz_problem* p, int cls, long long* launches, double* ms,
-                          double* bytes) {
+                          double* bytes, double* flops) {
   HZ_TRY(check_problem(p));
   if (cls < 0 || cls > 2) return fail(HZ_ERR_INVALID, "kernel class must be 0, 1 or 2");
   ProfClass& c = p->prof[cls];
@@ -1079,6 +1162,7 @@ hz_status hz_profile_read(hz_problem* p, int cls, long long* launches, double* m
   if (launches) *launches = c.launches;
   if (ms) *ms = c.ms;
   if (bytes) *bytes = c.bytes;
+  if (flops) *flops = c.flops;
   return HZ_OK;
 }
 
@@ -1222,6 +1306,8 @@ hz_status hz_shifted_solve(hz_problem* p, int node, const void* f, void* y, int 
   std::vector<long long> yfin;
   Buf<double2> nob{nullptr, 0};
   size_t es;
+  if (precision == HZ_C128 && p->sweeps32)
+    return fail(HZ_ERR_INVALID, "HZ_C128 needs a problem created without HZ_LIMIT_SWEEPS_C64");
   if (precision == HZ_C128) {
     HZ_TRY((run_poly<double2, double>(p, p->d64, Buf<const double2>{(const double2*)f, n}, nvec,
                                       which, false, nob, &yfin, st)));
@@ -1248,6 +1334,8 @@ hz_status hz_fci(hz_problem* p, const void* r, void* out, int nvec, int inner_k,
   if (precision != HZ_C128 && precision != HZ_MIXED_C64 && precision != HZ_MIXED_C64_FCI32 &&
       precision != HZ_MIXED_C64_FF)
     return fail(HZ_ERR_INVALID, "unknown precision");
+  if (p->sweeps32 && precision == HZ_C128)
+    return fail(HZ_ERR_INVALID, "HZ_C128 needs a problem created without HZ_LIMIT_SWEEPS_C64");
   if (nvec == 0) return HZ_OK;
   if (!r || !out) return fail(HZ_ERR_INVALID, "null field");
   HZ_TRY(set_device(p));
@@ -1351,7 +1439,19 @@ struct SolveState {
                             cudaMemcpyDeviceToHost, st));
     HZ_CUDA(cudaMemcpyAsync(p->h_stopped, go.stopped, sizeof(int) * nrhs, cudaMemcpyDeviceToHost,
                             st));
+    if (p->tail_used)
+      HZ_CUDA(cudaMemcpyAsync(p->h_bar, p->tail_bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                              st));
     return HZ_OK;
+  }
+
+  // after the stream synchronised: a cooperative kernel's barrier gave up during this step
+  // (the solve stops; drive() reports HZ_ERR_TIMEOUT)
+  bool barrier_gave_up() {
+    if (!p->tail_used || p->h_bar[0] == 0) return false;
+    finished = true;
+    in_cycle = false;
+    return true;
   }
 
   // true residual r = s f - A u, v0 = r / ||r||
@@ -1377,6 +1477,7 @@ struct SolveState {
   // after the stream synchronised: convergence per rhs; start the next cycle or finish
   hz_status after_cycle_start() {
     GmresDev& go = p->gout;
+    if (barrier_gave_up()) return HZ_OK;
     bool all_done = true;
     for (int r = 0; r < nrhs; ++r) {
       const double beta = p->h_scal[r * hz::SC_COUNT + hz::SC_BETA];
@@ -1427,6 +1528,7 @@ struct SolveState {
   // after the stream synchronised: stop flags; end the cycle when no rhs is left or m steps
   hz_status after_step() {
     GmresDev& go = p->gout;
+    if (barrier_gave_up()) return HZ_OK;
     bool any_active = false, push = false;
     for (int r = 0; r < nrhs; ++r) {
       if (!active[r]) continue;
@@ -1455,8 +1557,12 @@ struct SolveState {
       // u += Z y (rhs done at the cycle start have kend = 0)
       in_cycle = false;
       HZ_CUDA(hz::launch_backsolve(go, nrhs, st));
-      HZ_CUDA(hz::launch_combine(Buf<double2>{(double2*)u, n}, p->Z, n, zrs, go,
-                                 Buf<const double2>{nullptr, 0}, -1, 1, n, nrhs, M, st));
+      if (p->z32)
+        HZ_CUDA(hz::launch_combine_b32(Buf<double2>{(double2*)u, n}, p->Z32, n, zrs, go, 1, n,
+                                       nrhs, st));
+      else
+        HZ_CUDA(hz::launch_combine(Buf<double2>{(double2*)u, n}, p->Z, n, zrs, go,
+                                   Buf<const double2>{nullptr, 0}, -1, 1, n, nrhs, M, st));
       if (diverged) finished = true;
     }
     return HZ_OK;

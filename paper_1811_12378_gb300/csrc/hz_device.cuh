@@ -283,19 +283,19 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // ---------------------------------------------------------------- grid barrier
-constexpr long long kGridSpins = 1LL << 23;  // about a second of polling
-
-// Grid barrier over nblocks resident blocks: bar[0] counts arrivals, bar[1] is the generation.
-// Arrival is an acquire-release atomic (it publishes the block's writes, ordered before it by
-// the block barrier, and the last arriver sees everyone's); the last arriver resets the count
-// and releases the next generation; the others poll the generation with acquire loads, first
-// back to back, then with a short sleep.  false if this block gave up (or another already
-// had): the caller returns.
+// Grid barrier over nblocks resident blocks: bar[0] counts arrivals, bar[1] is the generation,
+// bar[3] the poll limit (set by the host; GRID_SPINS_DEFAULT unless changed).  Arrival is an
+// acquire-release atomic (it publishes the block's writes, ordered before it by the block
+// barrier, and the last arriver sees everyone's); the last arriver resets the count and
+// releases the next generation; the others poll the generation with acquire loads, first back
+// to back, then with a short sleep, at most bar[3] times.  false if this block gave up (or
+// another already had): the caller returns.
 __device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* err) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned gen, old;
+    unsigned gen, old, spins;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(spins) : "l"(bar + 3) : "memory");
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(bar + 1) : "memory");
     asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
     if (old == nblocks - 1) {
@@ -304,7 +304,7 @@ __device__ bool grid_sync(unsigned* bar, unsigned nblocks, int* err) {
       ok = 1;
     } else {
       ok = 0;
-      for (long long it = 0; it < kGridSpins; ++it) {
+      for (unsigned it = 0; it < spins; ++it) {
         unsigned now;
         asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(now) : "l"(bar + 1) : "memory");
         if (now != gen) {

@@ -16,6 +16,7 @@ constexpr int MAXJ = 16;          // contour nodes per problem
 constexpr int RED_THREADS = 256;  // threads of a reduction block
 constexpr int RED_PPT = 4;        // points per thread in a reduction block
 constexpr int RED_CHUNK = RED_THREADS * RED_PPT;
+constexpr unsigned GRID_SPINS_DEFAULT = 1u << 23;  // grid-barrier poll limit: about a second
 constexpr int RED_MIN_CHUNK = 256;  // smallest points per block of any reduction kernel
                                     // (sizes the per-block partial sums)
 
@@ -81,6 +82,7 @@ struct StageArgs {
   StageNode<R> nd[MAXJ];
   int nnodes;
   int final_quad;
+  int quad64;  // complex64 sweeps: form the quadrature sum in float64 (0: float pairs)
 };
 
 // Per-right-hand-side state of one GMRES / FGMRES cycle on the device.
@@ -122,6 +124,11 @@ cudaError_t launch_stencil32(const Geom& g, const float2* dg, Buf<const float2> 
 cudaError_t launch_stencil_diag(const Geom& g, const double2* dg, Buf<const double2> x,
                                 Buf<double2> y, int nvec, double zr, double zi, cudaStream_t st);
 
+// The same with complex64 input (FGMRES directions stored in complex64), float64 arithmetic,
+// z = 0.
+cudaError_t launch_stencil_diag_x32(const Geom& g, const double2* dg, Buf<const float2> x,
+                                    Buf<double2> y, int nvec, cudaStream_t st);
+
 cudaError_t launch_convert_c128_c64(Buf<const double2> x, Buf<float2> y, long long n, int nvec,
                                     cudaStream_t st);
 cudaError_t launch_convert_c64_c128(Buf<const float2> x, Buf<double2> y, long long n, int nvec,
@@ -143,6 +150,11 @@ cudaError_t launch_scale(Buf<double2> dst, Buf<const double2> src, long long n, 
 cudaError_t launch_combine(Buf<double2> out, const double2* B, long long bis, long long brs,
                            const GmresDev& gs, Buf<const double2> E, int e_slot, int accumulate,
                            long long n, int nvec, int kmax, cudaStream_t st);
+
+// out[r] = (accumulate ? out[r] : 0) + sum_{i<kend[r]} y[r][i] B_i with complex64 fields B.
+cudaError_t launch_combine_b32(Buf<double2> out, const float2* B, long long bis, long long brs,
+                               const GmresDev& gs, int accumulate, long long n, int nvec,
+                               cudaStream_t st);
 
 // y = R^{-1} g over kend[r] columns (one block per rhs)
 cudaError_t launch_backsolve(const GmresDev& gs, int nvec, cudaStream_t st);

@@ -137,9 +137,9 @@ k_poly_stage(Geom g, const T* __restrict__ dg, const T* __restrict__ f, long lon
     T* wsr = ws + r * wrs;
     const T* __restrict__ fr = f + r * frs;
     const T* __restrict__ in = wsr + nd.in;
-    const T* __restrict__ accin = wsr + nd.acc;
+    const T* accin = wsr + nd.acc;  // accin and accout alias: no __restrict__ on either
     T* __restrict__ kout = wsr + nd.kout;
-    T* __restrict__ accout = wsr + nd.acc;
+    T* accout = wsr + nd.acc;
     T* __restrict__ yout = wsr + nd.yout;
     const bool first = kind == SK_FIRST || kind == SK_FIRST_LAST;
     const bool stencil = !(first && nd.yzero);
@@ -199,7 +199,31 @@ k_poly_stage(Geom g, const T* __restrict__ dg, const T* __restrict__ f, long lon
     }
   }
   if (a.final_quad) {  // uniform over the launch; every node is LAST or FIRST_LAST here
-    if constexpr (sizeof(T) == 8) {
+    if (sizeof(T) == 8 && a.quad64) {
+      // complex64 y, float64 sum: each y_j is exact in float64, so the terms and their sum
+      // carry only float64 rounding (the quadrature accumulation of the float64-outer form)
+      double2* qr = qs + (size_t)threadIdx.z * a.nnodes * ZC * 32;
+#pragma unroll
+      for (int t = 0; t < ZC; ++t) {
+        const double yr = double(yn[t].x), yi = double(yn[t].y);
+        qr[(q * ZC + t) * 32 + threadIdx.x] =
+            make_double2(fma(nd.wqr, yr, -nd.wqi * yi), fma(nd.wqr, yi, nd.wqi * yr));
+      }
+      __syncthreads();
+      if (inside) {
+        for (int t = q; t < ZC; t += a.nnodes) {
+          if (k0 + t >= g.nz) break;
+          double sx = 0.0, sy = 0.0;
+          for (int u = 0; u < a.nnodes; ++u) {
+            const double2 v = qr[(u * ZC + t) * 32 + threadIdx.x];
+            sx += v.x;
+            sy += v.y;
+          }
+          w[r * wwrs + p0 + sxy * t] = make_double2(sx, sy);
+          if (w32) w32[r * w32rs + p0 + sxy * t] = make_float2(float(sx), float(sy));
+        }
+      }
+    } else if constexpr (sizeof(T) == 8) {
       // complex64 y: each node's term (sigma_j / z_j) y_j as float pairs (hi + lo) from
       // error-free products and sums, then a float-pair sum over the nodes (about 48 bits,
       // no float64 instruction until the final conversion)
@@ -418,14 +442,19 @@ k_cgs(const double2* __restrict__ V, long long vis, long long vrs, int nb, doubl
   if (MODE == 2) givens_column(gs, r, nb - 1, brk);  // whole block
 }
 
+// A field value as float64 (complex64 input converts exactly).
+__device__ __forceinline__ double2 as_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 as_d2(float2 v) { return make_double2(double(v.x), double(v.y)); }
+
 // Float64 shifted stencil from the precomputed complex diagonal d = 6 s/h^2 - m - i a:
 //     (A - zI) x = (d - z) x - (s/h^2) * (sum of the 6 neighbours).
 // About 16 float64 operations a point (the float64 pipe is the scarce unit on GB300).
 // FF: the result is stored as float pairs (float4 per complex point) for the float-pair
-// Arnoldi of HZ_MIXED_C64_FF.
-template <bool FF>
+// Arnoldi of HZ_MIXED_C64_FF.  TX: the input field's type (double2, or float2 for FGMRES
+// directions stored in complex64; the arithmetic is float64 either way).
+template <bool FF, typename TX>
 __global__ void __launch_bounds__(BX * BY)
-k_stencil_diag(Geom g, const double2* __restrict__ dg, const double2* __restrict__ x,
+k_stencil_diag(Geom g, const double2* __restrict__ dg, const TX* __restrict__ x,
                long long xrs, double2* __restrict__ y, long long yrs, double zr, double zi) {
   pdl_enter();
   const int i = blockIdx.x * BX + threadIdx.x;
@@ -435,12 +464,12 @@ k_stencil_diag(Geom g, const double2* __restrict__ dg, const double2* __restrict
   if (i >= g.nx || j >= g.ny) return;
   const long long sy = g.nx, sz = (long long)g.nx * g.ny;
   const long long p = i + sy * j + sz * k;
-  const double2* xr = x + r * xrs;
+  const TX* xr = x + r * xrs;
   const double2 z0 = make_double2(0.0, 0.0);
-  const double2 xm = i > 0 ? xr[p - 1] : z0, xp = i < g.nx - 1 ? xr[p + 1] : z0;
-  const double2 ym = j > 0 ? xr[p - sy] : z0, yp = j < g.ny - 1 ? xr[p + sy] : z0;
-  const double2 zm = k > 0 ? xr[p - sz] : z0, zp = k < g.nz - 1 ? xr[p + sz] : z0;
-  const double2 xc = xr[p];
+  const double2 xm = i > 0 ? as_d2(xr[p - 1]) : z0, xp = i < g.nx - 1 ? as_d2(xr[p + 1]) : z0;
+  const double2 ym = j > 0 ? as_d2(xr[p - sy]) : z0, yp = j < g.ny - 1 ? as_d2(xr[p + sy]) : z0;
+  const double2 zm = k > 0 ? as_d2(xr[p - sz]) : z0, zp = k < g.nz - 1 ? as_d2(xr[p + sz]) : z0;
+  const double2 xc = as_d2(xr[p]);
   const double2 d = dg[p];
   const double nbx = ((xm.x + xp.x) + (ym.x + yp.x)) + (zm.x + zp.x);
   const double nby = ((xm.y + xp.y) + (ym.y + yp.y)) + (zm.y + zp.y);
@@ -468,7 +497,8 @@ __global__ void k_scale(double2* __restrict__ dst, long long drs, const double2*
   }
 }
 
-__global__ void k_combine(double2* out, long long ors, const double2* __restrict__ B, long long bis,
+template <typename TB>
+__global__ void k_combine(double2* out, long long ors, const TB* __restrict__ B, long long bis,
                           long long brs, GmresDev gs, const double2* __restrict__ E, long long ers,
                           int use_e, int accumulate, long long n) {
   pdl_enter();
@@ -480,7 +510,7 @@ __global__ void k_combine(double2* out, long long ors, const double2* __restrict
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
     double2 acc = accumulate ? out[r * ors + p] : make_double2(0.0, 0.0);
-    for (int b = 0; b < kk; ++b) acc = cadd(acc, cmul(y[b], B[r * brs + b * bis + p]));
+    for (int b = 0; b < kk; ++b) acc = cadd(acc, cmul(y[b], as_d2(B[r * brs + b * bis + p])));
     if (use_e) acc = cadd(acc, cmul(d, E[r * ers + p]));
     out[r * ors + p] = acc;
   }
@@ -792,7 +822,17 @@ cudaError_t launch_stencil_diag(const Geom& g, const double2* dg, Buf<const doub
   dim3 blk(BX, BY, 1);
   dim3 grd((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz * nvec);
   count_launch();
-  return launch_pdl(k_stencil_diag<false>, grd, blk, 0, st, g, dg, x.p, x.rs, y.p, y.rs, zr, zi);
+  return launch_pdl(k_stencil_diag<false, double2>, grd, blk, 0, st, g, dg, x.p, x.rs, y.p, y.rs,
+                    zr, zi);
+}
+
+cudaError_t launch_stencil_diag_x32(const Geom& g, const double2* dg, Buf<const float2> x,
+                                    Buf<double2> y, int nvec, cudaStream_t st) {
+  dim3 blk(BX, BY, 1);
+  dim3 grd((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz * nvec);
+  count_launch();
+  return launch_pdl(k_stencil_diag<false, float2>, grd, blk, 0, st, g, dg, x.p, x.rs, y.p, y.rs,
+                    0.0, 0.0);
 }
 
 cudaError_t launch_stencil_diag_ff(const Geom& g, const double2* dg, Buf<const double2> x,
@@ -800,7 +840,7 @@ cudaError_t launch_stencil_diag_ff(const Geom& g, const double2* dg, Buf<const d
   dim3 blk(BX, BY, 1);
   dim3 grd((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz * nvec);
   count_launch();
-  return launch_pdl(k_stencil_diag<true>, grd, blk, 0, st, g, dg, x.p, x.rs,
+  return launch_pdl(k_stencil_diag<true, double2>, grd, blk, 0, st, g, dg, x.p, x.rs,
                     reinterpret_cast<double2*>(y.p), y.rs, 0.0, 0.0);
 }
 
@@ -816,8 +856,16 @@ cudaError_t launch_combine(Buf<double2> out, const double2* B, long long bis, lo
                            long long n, int nvec, int kmax, cudaStream_t st) {
   (void)kmax;
   count_launch();
-  return launch_pdl(k_combine, dim3(ew_blocks(n), nvec), 256, 0, st, out.p, out.rs, B, bis, brs, gs,
-                    E.p, E.rs, e_slot >= 0 ? 1 : 0, accumulate, n);
+  return launch_pdl(k_combine<double2>, dim3(ew_blocks(n), nvec), 256, 0, st, out.p, out.rs, B, bis,
+                    brs, gs, E.p, E.rs, e_slot >= 0 ? 1 : 0, accumulate, n);
+}
+
+cudaError_t launch_combine_b32(Buf<double2> out, const float2* B, long long bis, long long brs,
+                               const GmresDev& gs, int accumulate, long long n, int nvec,
+                               cudaStream_t st) {
+  count_launch();
+  return launch_pdl(k_combine<float2>, dim3(ew_blocks(n), nvec), 256, 0, st, out.p, out.rs, B, bis,
+                    brs, gs, (const double2*)nullptr, 0LL, 0, accumulate, n);
 }
 
 cudaError_t prepare_kernels(int mmax) {

@@ -20,14 +20,15 @@ HZ_MIXED_C64_FCI32 = 2
 HZ_MIXED_C64_FF = 3
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory",
-          4: "not converged", 5: "breakdown", 6: "diverged", 7: "set-up failed"}
+          4: "not converged", 5: "breakdown", 6: "diverged", 7: "set-up failed", 8: "timeout"}
 
 # every exported symbol declared in include/hz.h
 EXPORTS = ["hz_problem_create", "hz_plan", "hz_problem_destroy", "hz_problem_get_info",
            "hz_problem_nodes", "hz_problem_set_nodes", "hz_apply_shifted", "hz_apply_2x2",
            "hz_shifted_solve",
            "hz_fci", "hz_solve", "hz_solve_batched", "hz_profile_enable", "hz_profile_read",
-           "hz_problem_fused_tail", "hz_problem_fused_arnoldi", "hz_residual_noalloc",
+           "hz_problem_fused_tail", "hz_problem_fused_arnoldi", "hz_problem_set_spin_limit",
+           "hz_residual_noalloc",
            "hz_status_string", "hz_last_error", "hz_launch_count"]
 
 # kernel classes of hz_profile_read
@@ -46,7 +47,12 @@ class HzContour(C.Structure):
 
 class HzLimits(C.Structure):
     _fields_ = [("nrhs_max", C.c_int), ("restart_max", C.c_int), ("inner_k_max", C.c_int),
-                ("autotune", C.c_int)]
+                ("autotune", C.c_int), ("flags", C.c_int)]
+
+
+# hz_limits.flags bits
+HZ_LIMIT_SWEEPS_C64 = 1
+HZ_LIMIT_Z_C64 = 2
 
 
 class HzSolveOpts(C.Structure):
@@ -111,7 +117,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.hz_profile_enable.argtypes = [P, C.c_int]
     lib.hz_problem_fused_tail.argtypes = [P, C.c_int]
     lib.hz_problem_fused_arnoldi.argtypes = [P, C.c_int]
-    lib.hz_profile_read.argtypes = [P, C.c_int, C.POINTER(C.c_longlong), dp, dp]
+    lib.hz_problem_set_spin_limit.argtypes = [P, C.c_longlong]
+    lib.hz_profile_read.argtypes = [P, C.c_int, C.POINTER(C.c_longlong), dp, dp, dp]
     lib.hz_residual_noalloc.argtypes = [C.POINTER(HzGrid), P, C.c_double, P, C.c_double, P, P, P,
                                         C.c_int, P]
     lib.hz_status_string.argtypes = [C.c_int]
@@ -224,7 +231,7 @@ class Problem:
     """
 
     def __init__(self, c, h, omega, layer_cells, sigma_max, J, t, eps, qmax=5, reduction=5.0,
-                 nrhs_max=1, restart_max=30, inner_k_max=8, autotune=True):
+                 nrhs_max=1, restart_max=30, inner_k_max=8, autotune=True, flags=0):
         self._lib = load()
         c = np.ascontiguousarray(c, dtype=np.float64)
         self.shape = c.shape
@@ -232,7 +239,8 @@ class Problem:
         self.n = nx * ny * nz
         g = _grid(nx, ny, nz, h, omega, layer_cells, sigma_max)
         co = HzContour(int(J), float(t), float(eps), int(qmax), float(reduction))
-        lim = HzLimits(int(nrhs_max), int(restart_max), int(inner_k_max), 1 if autotune else 0)
+        lim = HzLimits(int(nrhs_max), int(restart_max), int(inner_k_max), 1 if autotune else 0,
+                       int(flags))
         handle = C.c_void_p()
         _check(self._lib.hz_problem_create(C.byref(g), _dp(c), C.byref(co), C.byref(lim),
                                            C.byref(handle)), self._lib)
@@ -273,15 +281,22 @@ class Problem:
         the last norm always summed, 0 (or False) five kernels."""
         _check(self._lib.hz_problem_fused_arnoldi(self._h, int(mode)), self._lib)
 
+    def set_spin_limit(self, polls: int = -1):
+        """Poll limit of the cooperative kernels' grid barriers (-1: the default, ~1 s)."""
+        _check(self._lib.hz_problem_set_spin_limit(self._h, int(polls)), self._lib)
+
     def profile(self, on: bool = True):
         """Start (and zero) or stop per-kernel-class CUDA-event timing."""
         _check(self._lib.hz_profile_enable(self._h, 1 if on else 0), self._lib)
 
-    def profile_read(self, cls: int):
-        """(launches, milliseconds, algorithmic bytes) of a kernel class since profile()."""
-        nl, ms, by = C.c_longlong(), C.c_double(), C.c_double()
+    def profile_read(self, cls: int, flops: bool = False):
+        """(launches, milliseconds, algorithmic bytes[, float64 flops]) of a kernel class since
+        profile()."""
+        nl, ms, by, fl = C.c_longlong(), C.c_double(), C.c_double(), C.c_double()
         _check(self._lib.hz_profile_read(self._h, int(cls), C.byref(nl), C.byref(ms),
-                                         C.byref(by)), self._lib)
+                                         C.byref(by), C.byref(fl)), self._lib)
+        if flops:
+            return int(nl.value), float(ms.value), float(by.value), float(fl.value)
         return int(nl.value), float(ms.value), float(by.value)
 
     def nodes(self):

@@ -448,6 +448,56 @@ def test_failure_statuses():
         assert st[0].converged and st[0].its == 1 and st[0].rel_res_true <= 1e-12
 
 
+def test_barrier_timeout_status_and_recovery():
+    """A grid barrier that gives up is reported as HZ_ERR_TIMEOUT, and the problem recovers.
+    The wait is made to run out on purpose by a poll limit of 0 (every barrier wait that is
+    not already satisfied gives up at once: the kernel returns, nothing hangs); the next solve
+    with the default limit must reproduce the first solve bit for bit."""
+    wl = W.point_source_32()
+    with problem_of(wl, None, nrhs_max=1, restart_max=wl.restart, inner_k_max=wl.k_in) as P:
+        f = to_dev(wl.f)
+        kw = dict(restart=wl.restart, inner_k=wl.k_in, rtol=1e-8, max_cycles=10,
+                  precision=hzpkg.HZ_MIXED_C64_FF)
+        u0, st0 = P.solve(f, **kw)
+        assert st0[0].converged
+        u0 = to_np(u0)
+        P.set_spin_limit(0)
+        with pytest.raises(hzpkg.HzError) as ei:
+            P.solve(f, **kw)
+        assert ei.value.status == 8, ei.value
+        P.set_spin_limit(-1)
+        u1, st1 = P.solve(f, **kw)
+        assert st1[0].converged and st1[0].its == st0[0].its
+        assert np.array_equal(to_np(u1), u0)
+
+
+def test_limit_flags_restrict_forms_and_keep_results():
+    """HZ_LIMIT_SWEEPS_C64 refuses float64 sweeps; HZ_LIMIT_Z_C64 refuses the forms whose
+    directions must stay float64 or float pairs; both problems solve the mixed form to 1e-8."""
+    wl = W.point_source_32()
+    fl = hzpkg.HZ_LIMIT_SWEEPS_C64 | hzpkg.HZ_LIMIT_Z_C64
+    P = hzpkg.Problem(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, wl.J, wl.t, wl.eps,
+                      nrhs_max=2, restart_max=wl.restart, inner_k_max=wl.k_in, flags=fl)
+    with P:
+        f = to_dev(np.concatenate([wl.f, wl.f[:, ::-1]]).reshape(2, -1))
+        for prec in (hzpkg.HZ_C128, hzpkg.HZ_MIXED_C64_FF):
+            with pytest.raises(hzpkg.HzError) as ei:
+                P.solve(f, precision=prec)
+            assert ei.value.status == 1
+        with pytest.raises(hzpkg.HzError) as ei:
+            P.fci(f, inner_k=2, precision=hzpkg.HZ_C128)
+        assert ei.value.status == 1
+        for prec in (hzpkg.HZ_MIXED_C64, hzpkg.HZ_MIXED_C64_FCI32):
+            u, st = P.solve(f, restart=wl.restart, inner_k=wl.k_in, rtol=1e-8, max_cycles=10,
+                            precision=prec)
+            assert all(s.converged for s in st)
+            op, _ = oracle_of(wl)
+            for r in range(2):
+                fr = to_np(f)[r].reshape(op.shape) * op.s
+                ur = to_np(u)[r].reshape(op.shape)
+                assert np.linalg.norm(fr - op.apply(ur)) / np.linalg.norm(fr) <= 1e-8
+
+
 def test_native_kernels_launch():
     before = hzpkg.launch_count()
     wl = W.small_case(1, 8, 8, 8, layer=1, J=2)
