@@ -307,6 +307,76 @@ hz_status hz_residual_noalloc(const hz_grid* grid, const double* c, double c_min
                               double fscale, const void* u, void* r, double* norm2, int nvec,
                               void* stream);
 
+/* ---- The learned right preconditioner ----
+ * The paper has no network: flexible GMRES admits a right preconditioner that changes from
+ * step to step (Section 2, the remark after Algorithm 1), so a learned map from a residual to
+ * an approximate error can serve as one, alone or combined with FCI, while the float64 true
+ * residual still decides convergence.  The network is a 4-level 3D U-Net with 16 base channels
+ * and 3x3x3 kernels; its convolutions run on the tensor cores in BF16 with FP32 accumulation,
+ * its training (forward, backward, Adam) on the GPU.  Input per voxel: 8 channels (Re r, Im r,
+ * the medium m = c_min^2/c^2, five zeros) with r scaled to unit RMS; output: 2 channels
+ * (Re e, Im e), scaled back.  Volumes are multiples of 8 in each direction.
+ * Parameters: one flat float32 array of hz_net_param_count() values: for each of the 14
+ * convolutions in the order e1a (8->16), e1b (16->16), e2a (16->32), e2b, e3a (32->64), e3b,
+ * ba (64->128), bb, d3a (192->64), d3b, d2a (96->32), d2b, d1a (48->16), d1b, the weights
+ * w[Cout][27][Cin] (tap t = 9 dz + 3 dy + dx for offsets dz - 1, dy - 1, dx - 1) then the bias
+ * b[Cout]; then the head's w[2][16] and b[2].  The decoder's inputs are the upsampled map
+ * followed by the skip map. */
+typedef struct hz_net hz_net;
+
+long long hz_net_param_count(void);
+
+/* Allocate a network (parameters zero) with activation and gradient storage for up to
+ * batch_max volumes of D x H x W voxels (multiples of 8, >= 8) on the current device. */
+hz_status hz_net_create(int D, int H, int W, int batch_max, hz_net** out);
+hz_status hz_net_destroy(hz_net* net);
+
+/* Copy the parameters in from host memory (and reset Adam's moments) or out to host memory. */
+hz_status hz_net_set_params(hz_net* net, const float* host);
+hz_status hz_net_get_params(const hz_net* net, float* host);
+
+/* y = N(x): x device float32 [batch][D][H][W][8] (rounded to bf16 on entry), y device float32
+ * [batch][D][H][W][2].  Synchronises the stream.  HZ_ERR_TIMEOUT if a bounded wait inside a
+ * tensor-core kernel gave up. */
+hz_status hz_net_forward(hz_net* net, const float* x, float* y, int batch, int D, int H, int W,
+                         void* stream);
+
+/* One training step on device float32 inputs x [batch][D][H][W][8] and targets
+ * [batch][D][H][W][2]: forward, loss L = sum over samples of sum |y - t|^2 / (2 D H W) into
+ * *loss (host), every parameter gradient (into grads, device float32, the parameter layout, if
+ * not null), and an Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr (none
+ * for lr = 0).  Synchronises the stream. */
+hz_status hz_net_train_step(hz_net* net, const float* x, const float* target, int batch, int D,
+                            int H, int W, float lr, float* grads, double* loss, void* stream);
+
+/* The same on nvec pairs of complex128 device fields (residual r, error e with A e = r) of
+ * problem p's grid: the input is built from r / rms(r) and p's medium, the target is
+ * e / rms(r). */
+hz_status hz_net_train_fields(hz_net* net, hz_problem* p, const void* r, const void* e, int nvec,
+                              float lr, double* loss, void* stream);
+
+/* Right preconditioner of hz_solve: mode 0 FCI (Algorithm 1, the default; net may be null);
+ * 1 the network alone, z = N(v); 2 z = N(v) + FCI(v - A N(v)); 3 z = FCI(v) + N(v - A FCI(v)).
+ * The network must hold the grid (multiples of 8) and nrhs_max volumes; allocates two float64
+ * fields per right-hand side on first use.  HZ_MIXED_C64_FF is refused with a network. */
+hz_status hz_problem_set_preconditioner(hz_problem* p, hz_net* net, int mode);
+
+/* Single 3x3x3 convolutions on the tensor cores, for checking the network's kernels.
+ * hz_conv3d: y = conv3(x, w) + bias (ReLU if relu), x device bf16 [B][D][H][W][Cin] (Cin a
+ * multiple of 8), w device float32 [Cout][27][Cin] (Cout a multiple of 16, <= 256), bias
+ * float32 [Cout] or null, y device float32 [B][D][H][W][Cout].  hz_conv3d_backward: for the
+ * output gradient g (device bf16 [B][D][H][W][Cout], Cout <= 128) dw = sum over voxels of
+ * g (x) shifted x (device float32 [Cout][27][Cin]) and, if dx is not null, dx = the input
+ * gradient (device float32 [B][D][H][W][Cin], Cin a multiple of 16).  workspace: device,
+ * hz_conv3d_workspace_bytes(Cin, Cout) bytes, 16-byte aligned.  Both synchronise the stream. */
+hz_status hz_conv3d(const void* x, int B, int D, int H, int W, int Cin, const float* w,
+                    const float* bias, int Cout, int relu, float* y, void* workspace,
+                    void* stream);
+hz_status hz_conv3d_backward(const void* x, const void* g, int B, int D, int H, int W, int Cin,
+                             const float* w, int Cout, float* dx, float* dw, void* workspace,
+                             void* stream);
+long long hz_conv3d_workspace_bytes(int Cin, int Cout);
+
 /* Name of a status code. */
 const char* hz_status_string(hz_status s);
 

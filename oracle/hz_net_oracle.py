@@ -151,21 +151,29 @@ def init_params(seed: int) -> dict:
     return p
 
 
-def forward(p: dict, x0: np.ndarray, keep: bool = False):
+def _identity(x):
+    return x
+
+
+def forward(p: dict, x0: np.ndarray, keep: bool = False, bf16: bool = False):
     """Network output y[D, H, W, 2] for the input map x0[D, H, W, 8] (D, H, W multiples of 8).
-    keep: also return every intermediate map, for the backward pass."""
-    cache = {"x0": x0}
+    keep: also return every intermediate map, for the backward pass.  bf16: round the input,
+    the 3x3x3 weights and every stored feature map (ReLU and pooling outputs) to bfloat16, the
+    storage format of a reduced-precision implementation; the arithmetic stays float64."""
+    q = bf16_round if bf16 else _identity
+    x0 = q(x0)
+    cache = {"x0": x0, "bf16": bf16}
 
     def cr(name, x):  # conv + relu, keeping the input and the output
         cache[name + ".in"] = x
-        y = relu(conv3(x, p[name + ".w"], p[name + ".b"]))
+        y = q(relu(conv3(x, q(p[name + ".w"]), p[name + ".b"])))
         cache[name + ".out"] = y
         return y
 
     s1 = cr("e1b", cr("e1a", x0))
-    s2 = cr("e2b", cr("e2a", avgpool2(s1)))
-    s3 = cr("e3b", cr("e3a", avgpool2(s2)))
-    b = cr("bb", cr("ba", avgpool2(s3)))
+    s2 = cr("e2b", cr("e2a", q(avgpool2(s1))))
+    s3 = cr("e3b", cr("e3a", q(avgpool2(s2))))
+    b = cr("bb", cr("ba", q(avgpool2(s3))))
     d3 = cr("d3b", cr("d3a", np.concatenate([up2(b), s3], axis=3)))
     d2 = cr("d2b", cr("d2a", np.concatenate([up2(d3), s2], axis=3)))
     d1 = cr("d1b", cr("d1a", np.concatenate([up2(d2), s1], axis=3)))
@@ -175,14 +183,20 @@ def forward(p: dict, x0: np.ndarray, keep: bool = False):
 
 
 def backward(p: dict, cache: dict, dy: np.ndarray) -> dict:
-    """Gradients of a loss with respect to every parameter, given d(loss)/dy."""
+    """Gradients of a loss with respect to every parameter, given d(loss)/dy.  After a bf16
+    forward pass, the gradient through each ReLU and the weights of each data gradient are
+    rounded to bfloat16 as well (the operands of a reduced-precision backward pass); the bias
+    gradient is the sum of the unrounded values."""
+    q = bf16_round if cache.get("bf16") else _identity
     grads = {}
     dd1, grads["head.w"], grads["head.b"] = conv1_backward(cache["head.in"], p["head.w"], dy)
 
     def cr_back(name, dout):  # through relu, then the convolution
         dpre = dout * (cache[name + ".out"] > 0)
-        dx, grads[name + ".w"], grads[name + ".b"] = conv3_backward(cache[name + ".in"],
-                                                                    p[name + ".w"], dpre)
+        db = dpre.reshape(-1, dpre.shape[3]).sum(axis=0)
+        dx, grads[name + ".w"], _ = conv3_backward(cache[name + ".in"], q(p[name + ".w"]),
+                                                   q(dpre))
+        grads[name + ".b"] = db
         return dx
 
     c1, c2, c3, c4 = LEVELS

@@ -17,6 +17,7 @@
 
 #include "hz.h"
 #include "hz_internal.h"
+#include "hz_net_internal.h"
 
 using hz::Buf;
 using hz::GmresDev;
@@ -125,6 +126,13 @@ struct hz_problem {
   // the barrier words and the error flag of the FCI tail (the two never run concurrently)
   int arn_mode = 1;  // hz_problem_fused_arnoldi: 0 five kernels, 1 cooperative, 2 summed norm
   int arn_ppt = 0, arn_blocks = 0;
+
+  // the learned right preconditioner (hz_problem_set_preconditioner): the network, how it
+  // combines with FCI, and two float64 fields per right-hand side for the combinations
+  hz_net* net = nullptr;
+  int net_mode = 0;
+  double2* pre_t = nullptr;
+  double2* pre_z = nullptr;
 
   void drop_graphs() {
     for (cudaGraphExec_t g : step_graphs)
@@ -545,8 +553,42 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
   return HZ_OK;
 }
 
-// One outer FGMRES step k on all right-hand sides: z_k = FCI(v_k), w = A z_k, CGS2 against
-// v_0..v_k with the Givens update of column k, v_{k+1} = w / h_{k+1,k}.
+// The right preconditioner z = M(v) of one outer step (v field r at v.p + r v.rs, z likewise).
+// net_mode 0: FCI (Algorithm 1); 1: the network alone; 2: z = N(v) + FCI(v - A N(v)); 3: z =
+// FCI(v) + N(v - A FCI(v)).  The corrections use the float64 stencil for the residual.
+hz_status run_precond(hz_problem* p, Buf<const double2> v, Buf<double2> z, int nrhs, int K,
+                      int precision, cudaStream_t st, bool r_ff) {
+  if (p->net_mode == 0 || !p->net) return run_fci(p, v, z, nrhs, K, precision, st, r_ff);
+  const long long n = p->g.n;
+  const int nx = p->g.nx, ny = p->g.ny, nz = p->g.nz;
+  auto net = [&](Buf<const double2> in, Buf<double2> out, int acc) {
+    return hz::net_apply_field(p->net, in.p, in.rs, p->m64, out.p, out.rs, nrhs, nx, ny, nz, acc,
+                               st);
+  };
+  // t = v - A z (A z into pre_z as scratch)
+  auto residual = [&]() -> hz_status {
+    HZ_TIMED_F(p, 1, st, (stencil_bytes<double2, double2>(n, nrhs)), kStencil64Flops * n * nrhs,
+               (hz::launch_stencil_diag(p->g, p->d64, Buf<const double2>{z.p, z.rs},
+                                        Buf<double2>{p->pre_z, n}, nrhs, 0.0, 0.0, st)));
+    HZ_CUDA(hz::launch_field_sub(v.p, v.rs, p->pre_z, n, p->pre_t, n, n, nrhs, st));
+    return HZ_OK;
+  };
+  if (p->net_mode == 1) return net(v, z, 0);
+  if (p->net_mode == 2) {
+    HZ_TRY(net(v, z, 0));
+    HZ_TRY(residual());
+    HZ_TRY(run_fci(p, Buf<const double2>{p->pre_t, n}, Buf<double2>{p->pre_z, n}, nrhs, K,
+                   precision, st, false));
+    HZ_CUDA(hz::launch_field_add(z.p, z.rs, p->pre_z, n, n, nrhs, st));
+    return HZ_OK;
+  }
+  HZ_TRY(run_fci(p, v, z, nrhs, K, precision, st, r_ff));
+  HZ_TRY(residual());
+  return net(Buf<const double2>{p->pre_t, n}, z, 1);
+}
+
+// One outer FGMRES step k on all right-hand sides: z_k = M(v_k) (FCI, or the network), w = A z_k,
+// CGS2 against v_0..v_k with the Givens update of column k, v_{k+1} = w / h_{k+1,k}.
 hz_status outer_step_launches(hz_problem* p, int k, int nrhs, int K, int precision,
                               cudaStream_t st) {
   const long long n = p->g.n;
@@ -558,7 +600,7 @@ hz_status outer_step_launches(hz_problem* p, int k, int nrhs, int K, int precisi
   if (p->z32) {
     // z_k = FCI(v_k) into a float64 scratch field (Aw is free once FCI has returned), stored
     // rounded to complex64; the matvec then reads the stored value
-    HZ_TRY(run_fci(p, vk, Buf<double2>{p->Aw, n}, nrhs, K, precision, st, false));
+    HZ_TRY(run_precond(p, vk, Buf<double2>{p->Aw, n}, nrhs, K, precision, st, false));
     Buf<float2> z32k{p->Z32 + (long long)k * n, zrs};
     HZ_CUDA(hz::launch_convert_c128_c64(Buf<const double2>{p->Aw, n}, z32k, n, nrhs, st));
     Buf<double2> wk{p->V + (long long)(k + 1) * n, vrs};
@@ -573,7 +615,7 @@ hz_status outer_step_launches(hz_problem* p, int k, int nrhs, int K, int precisi
     return HZ_OK;
   }
   Buf<double2> zk{p->Z + (long long)k * n, zrs};
-  HZ_TRY(run_fci(p, vk, zk, nrhs, K, precision, st, ff));
+  HZ_TRY(run_precond(p, vk, zk, nrhs, K, precision, st, ff));
   if (ff) {
     // the float-pair Arnoldi: w = A z_k stored as float pairs in v_{k+1}'s slot
     Buf<float4> wf{(float4*)(p->V + (long long)(k + 1) * n), vrs};
@@ -617,7 +659,7 @@ hz_status outer_step(hz_problem* p, int k, int nrhs, int K, int precision, cudaS
   const long long key =
       ((((long long)nrhs * 4 + precision) * 1024 + K) * 2 + (tail_fits(p, nrhs, K) ? 1 : 0)) * 2 +
       (arnoldi_fits(p, nrhs) ? 1 : 0) + 2 * (p->arn_mode == 2 ? 1 : 0) +
-      4 * (p->tail_mode == 2 ? 1 : 0);
+      4 * (p->tail_mode == 2 ? 1 : 0) + 8 * p->net_mode;
   if (p->graph_key != key) {
     p->drop_graphs();
     p->graph_key = key;
@@ -837,6 +879,10 @@ hz_status check_solve_args(const hz_problem* p, int nrhs, const hz_solve_opts* o
   if (p->z32 && opts->precision != HZ_MIXED_C64 && opts->precision != HZ_MIXED_C64_FCI32)
     return fail(HZ_ERR_INVALID, "a problem created with HZ_LIMIT_Z_C64 solves in HZ_MIXED_C64 or "
                                 "HZ_MIXED_C64_FCI32 only");
+  if (p->net_mode != 0 && opts->precision == HZ_MIXED_C64_FF)
+    return fail(HZ_ERR_INVALID, "the learned preconditioner needs a float64 outer basis");
+  if (p->net_mode != 0 && !hz::net_fits(p->net, nrhs, p->g.nx, p->g.ny, p->g.nz))
+    return fail(HZ_ERR_INVALID, "right-hand sides or grid beyond the network's capacity");
   return HZ_OK;
 }
 }  // namespace
@@ -1133,6 +1179,34 @@ hz_status hz_problem_set_spin_limit(hz_problem* p, long long polls) {
   HZ_CUDA(cudaStreamSynchronize(p->own));
   HZ_CUDA(cudaMemcpy(p->tail_bar + 3, &lim, sizeof(unsigned), cudaMemcpyHostToDevice));
   return HZ_OK;
+}
+
+hz_status hz_problem_set_preconditioner(hz_problem* p, hz_net* net, int mode) {
+  HZ_TRY(check_problem(p));
+  if (mode < 0 || mode > 3) return fail(HZ_ERR_INVALID, "preconditioner mode 0..3");
+  if (mode != 0 && !net) return fail(HZ_ERR_INVALID, "modes 1..3 need a network");
+  if (mode != 0 && !hz::net_fits(net, 1, p->g.nx, p->g.ny, p->g.nz))
+    return fail(HZ_ERR_INVALID, "grid sizes must be multiples of 8 within the network's volume");
+  HZ_TRY(set_device(p));
+  if (mode != 0 && !p->pre_t) {
+    const size_t bytes = sizeof(double2) * (size_t)p->g.n * p->lim.nrhs_max;
+    HZ_TRY(dalloc(p, (void**)&p->pre_t, bytes));
+    HZ_TRY(dalloc(p, (void**)&p->pre_z, bytes));
+  }
+  if (mode != p->net_mode || net != p->net) p->drop_graphs();
+  p->net = mode != 0 ? net : nullptr;
+  p->net_mode = mode;
+  return HZ_OK;
+}
+
+hz_status hz_net_train_fields(hz_net* net, hz_problem* p, const void* r, const void* e, int nvec,
+                              float lr, double* loss, void* stream) {
+  HZ_TRY(check_problem(p));
+  if (!net || !r || !e) return fail(HZ_ERR_INVALID, "null argument");
+  if (nvec < 1) return fail(HZ_ERR_INVALID, "nvec < 1");
+  HZ_TRY(set_device(p));
+  return hz::net_train_fields(net, (const double2*)r, p->m64, (const double2*)e, nvec, p->g.nx,
+                              p->g.ny, p->g.nz, lr, loss, (cudaStream_t)stream);
 }
 
 hz_status hz_profile_enable(hz_problem* p, int on) {
@@ -1620,6 +1694,8 @@ hz_status drive(std::vector<SolveState>& ss) {
   // the loop ends right after a residual evaluation, so rel[] is the final true residual
   for (auto& s : ss) HZ_CUDA(cudaStreamSynchronize(s.st));
   for (auto& s : ss) HZ_TRY(check_tail_fault(s.p));
+  for (auto& s : ss)
+    if (s.p->net_mode != 0 && s.p->net) HZ_TRY(hz::net_check(s.p->net));
   hz_status ret = HZ_OK;
   for (auto& s : ss) {
     const hz_status r = s.result();

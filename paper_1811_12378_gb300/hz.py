@@ -28,7 +28,10 @@ EXPORTS = ["hz_problem_create", "hz_plan", "hz_problem_destroy", "hz_problem_get
            "hz_shifted_solve",
            "hz_fci", "hz_solve", "hz_solve_batched", "hz_profile_enable", "hz_profile_read",
            "hz_problem_fused_tail", "hz_problem_fused_arnoldi", "hz_problem_set_spin_limit",
-           "hz_residual_noalloc",
+           "hz_residual_noalloc", "hz_net_param_count", "hz_net_create", "hz_net_destroy",
+           "hz_net_set_params", "hz_net_get_params", "hz_net_forward", "hz_net_train_step",
+           "hz_net_train_fields", "hz_problem_set_preconditioner", "hz_conv3d",
+           "hz_conv3d_backward", "hz_conv3d_workspace_bytes",
            "hz_status_string", "hz_last_error", "hz_launch_count"]
 
 # kernel classes of hz_profile_read
@@ -121,6 +124,24 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.hz_profile_read.argtypes = [P, C.c_int, C.POINTER(C.c_longlong), dp, dp, dp]
     lib.hz_residual_noalloc.argtypes = [C.POINTER(HzGrid), P, C.c_double, P, C.c_double, P, P, P,
                                         C.c_int, P]
+    fp = C.POINTER(C.c_float)
+    lib.hz_net_param_count.argtypes = []
+    lib.hz_net_param_count.restype = C.c_longlong
+    lib.hz_net_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(P)]
+    lib.hz_net_destroy.argtypes = [P]
+    lib.hz_net_set_params.argtypes = [P, fp]
+    lib.hz_net_get_params.argtypes = [P, fp]
+    lib.hz_net_forward.argtypes = [P, P, P, C.c_int, C.c_int, C.c_int, C.c_int, P]
+    lib.hz_net_train_step.argtypes = [P, P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, P,
+                                      dp, P]
+    lib.hz_net_train_fields.argtypes = [P, P, P, P, C.c_int, C.c_float, dp, P]
+    lib.hz_problem_set_preconditioner.argtypes = [P, P, C.c_int]
+    lib.hz_conv3d.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P, C.c_int,
+                              C.c_int, P, P, P]
+    lib.hz_conv3d_backward.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P,
+                                       C.c_int, P, P, P, P]
+    lib.hz_conv3d_workspace_bytes.argtypes = [C.c_int, C.c_int]
+    lib.hz_conv3d_workspace_bytes.restype = C.c_longlong
     lib.hz_status_string.argtypes = [C.c_int]
     lib.hz_status_string.restype = C.c_char_p
     lib.hz_last_error.argtypes = []
@@ -129,7 +150,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.hz_launch_count.restype = C.c_ulonglong
     for name in EXPORTS:
         fn = getattr(lib, name)
-        if name not in ("hz_status_string", "hz_last_error", "hz_launch_count"):
+        if name not in ("hz_status_string", "hz_last_error", "hz_launch_count",
+                        "hz_net_param_count", "hz_conv3d_workspace_bytes"):
             fn.restype = C.c_int
     _lib = lib
     return lib
@@ -281,6 +303,12 @@ class Problem:
         the last norm always summed, 0 (or False) five kernels."""
         _check(self._lib.hz_problem_fused_arnoldi(self._h, int(mode)), self._lib)
 
+    def set_preconditioner(self, net=None, mode: int = 0):
+        """Right preconditioner of solve(): 0 FCI; 1 the network; 2 network then FCI on its
+        residual; 3 FCI then the network on its residual (hz_problem_set_preconditioner)."""
+        _check(self._lib.hz_problem_set_preconditioner(
+            self._h, net._h if net is not None else None, int(mode)), self._lib)
+
     def set_spin_limit(self, polls: int = -1):
         """Poll limit of the cooperative kernels' grid barriers (-1: the default, ~1 s)."""
         _check(self._lib.hz_problem_set_spin_limit(self._h, int(polls)), self._lib)
@@ -413,3 +441,150 @@ def solve_batched(problems, fs, restart=30, inner_k=4, rtol=1e-8, max_cycles=50,
                     for s in st[off:off + nr[i]]])
         off += nr[i]
     return us, out
+
+
+# ---------------------------------------------------------------------------- learned part
+# The network's 3x3x3 convolutions in parameter order: (name, input channels, output channels)
+NET_CONVS = [("e1a", 8, 16), ("e1b", 16, 16), ("e2a", 16, 32), ("e2b", 32, 32),
+             ("e3a", 32, 64), ("e3b", 64, 64), ("ba", 64, 128), ("bb", 128, 128),
+             ("d3a", 192, 64), ("d3b", 64, 64), ("d2a", 96, 32), ("d2b", 32, 32),
+             ("d1a", 48, 16), ("d1b", 16, 16)]
+
+
+def flatten_params(params: dict) -> np.ndarray:
+    """The flat float32 parameter array of include/hz.h from {name.w, name.b, head.w, head.b}."""
+    parts = []
+    for name, _, _ in NET_CONVS:
+        parts += [np.ravel(params[name + ".w"]), np.ravel(params[name + ".b"])]
+    parts += [np.ravel(params["head.w"]), np.ravel(params["head.b"])]
+    return np.ascontiguousarray(np.concatenate(parts), dtype=np.float32)
+
+
+def unflatten_params(flat: np.ndarray) -> dict:
+    out, off = {}, 0
+    for name, ci, co in NET_CONVS:
+        out[name + ".w"] = flat[off:off + co * 27 * ci].reshape(co, 27, ci)
+        off += co * 27 * ci
+        out[name + ".b"] = flat[off:off + co]
+        off += co
+    out["head.w"] = flat[off:off + 32].reshape(2, 16)
+    out["head.b"] = flat[off + 32:off + 34]
+    return out
+
+
+class Net:
+    """The learned right preconditioner's network on the current CUDA device (hz_net_create):
+    activation storage for up to batch_max volumes of D x H x W voxels."""
+
+    def __init__(self, D, H, W, batch_max=1):
+        self._lib = load()
+        h = C.c_void_p()
+        _check(self._lib.hz_net_create(int(D), int(H), int(W), int(batch_max), C.byref(h)),
+               self._lib)
+        self._h = h
+        self.n_params = int(self._lib.hz_net_param_count())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hz_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        if a.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {a.size}")
+        _check(self._lib.hz_net_set_params(self._h, a.ctypes.data_as(C.POINTER(C.c_float))),
+               self._lib)
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.n_params, dtype=np.float32)
+        _check(self._lib.hz_net_get_params(self._h, a.ctypes.data_as(C.POINTER(C.c_float))),
+               self._lib)
+        return a
+
+    def forward(self, x, stream=None):
+        """y = N(x) for a float32 CUDA tensor x of shape (B, D, H, W, 8)."""
+        import torch
+        B, D, H, W, c = x.shape
+        if c != 8 or x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x: contiguous float32 CUDA tensor (B, D, H, W, 8)")
+        y = torch.empty((B, D, H, W, 2), dtype=torch.float32, device=x.device)
+        _check(self._lib.hz_net_forward(self._h, C.c_void_p(x.data_ptr()),
+                                        C.c_void_p(y.data_ptr()), B, D, H, W, _stream(stream)),
+               self._lib)
+        return y
+
+    def train_step(self, x, target, lr=0.0, want_grads=False, stream=None):
+        """One step (loss, gradients, Adam with lr) on float32 CUDA tensors x (B, D, H, W, 8)
+        and target (B, D, H, W, 2).  Returns (loss, flat gradient tensor or None)."""
+        import torch
+        B, D, H, W, _ = x.shape
+        g = torch.empty(self.n_params, dtype=torch.float32, device=x.device) if want_grads else None
+        loss = C.c_double()
+        _check(self._lib.hz_net_train_step(self._h, C.c_void_p(x.data_ptr()),
+                                           C.c_void_p(target.data_ptr()), B, D, H, W,
+                                           float(lr), C.c_void_p(g.data_ptr()) if g is not None
+                                           else None, C.byref(loss), _stream(stream)), self._lib)
+        return float(loss.value), g
+
+    def train_fields(self, problem, r, e, lr, stream=None):
+        """One training step on complex128 field pairs (r, e) of a Problem's grid."""
+        import torch
+        rp, nv = _dev_ptr(r, torch.complex128, problem.n)
+        ep, _ = _dev_ptr(e, torch.complex128, problem.n)
+        loss = C.c_double()
+        _check(self._lib.hz_net_train_fields(self._h, problem._h, rp, ep, nv, float(lr),
+                                             C.byref(loss), _stream(stream)), self._lib)
+        return float(loss.value)
+
+
+def _ws(lib, cin, cout, device):
+    import torch
+    nbytes = int(lib.hz_conv3d_workspace_bytes(int(cin), int(cout)))
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def conv3d(x, w, bias=None, relu=False, stream=None):
+    """y = conv3(x, w) + bias on the tensor cores: x bf16 CUDA (B, D, H, W, Cin), w float32
+    (Cout, 27, Cin); returns float32 (B, D, H, W, Cout)."""
+    import torch
+    lib = load()
+    B, D, H, W, cin = x.shape
+    cout = w.shape[0]
+    y = torch.empty((B, D, H, W, cout), dtype=torch.float32, device=x.device)
+    ws = _ws(lib, cin, cout, x.device)
+    _check(lib.hz_conv3d(C.c_void_p(x.data_ptr()), B, D, H, W, cin, C.c_void_p(w.data_ptr()),
+                         C.c_void_p(bias.data_ptr()) if bias is not None else None, cout,
+                         1 if relu else 0, C.c_void_p(y.data_ptr()), C.c_void_p(ws.data_ptr()),
+                         _stream(stream)), lib)
+    return y
+
+
+def conv3d_backward(x, g, w, want_dx=True, stream=None):
+    """(dx, dw) of conv3 for bf16 CUDA x (B, D, H, W, Cin), bf16 g (B, D, H, W, Cout) and
+    float32 w (Cout, 27, Cin)."""
+    import torch
+    lib = load()
+    B, D, H, W, cin = x.shape
+    cout = g.shape[-1]
+    dw = torch.empty((cout, 27, cin), dtype=torch.float32, device=x.device)
+    dx = torch.empty((B, D, H, W, cin), dtype=torch.float32, device=x.device) if want_dx else None
+    ws = _ws(lib, cin, cout, x.device)
+    _check(lib.hz_conv3d_backward(C.c_void_p(x.data_ptr()), C.c_void_p(g.data_ptr()), B, D, H, W,
+                                  cin, C.c_void_p(w.data_ptr()), cout,
+                                  C.c_void_p(dx.data_ptr()) if dx is not None else None,
+                                  C.c_void_p(dw.data_ptr()), C.c_void_p(ws.data_ptr()),
+                                  _stream(stream)), lib)
+    return dx, dw
