@@ -7,9 +7,15 @@ sums of up to 27 * 192 products: relative L2 <= 1e-5, each element within 1e-4 o
 largest magnitude.  The weight gradient sums up to 16^3 * 2 products per entry, split over
 blocks and added with float atomics: relative L2 <= 1e-4.  The whole network stores every
 feature map in bf16; the oracle's bf16 mode rounds at the same points, so the remaining
-difference is fp32-versus-float64 summation that occasionally moves a value across a bf16
-rounding boundary (one bf16 ulp, 2^-8 relative, on that element): relative L2 <= 2e-3 for the
-output and 5e-3 for each parameter gradient.
+difference is fp32-versus-float64 summation that moves some values across a bf16 rounding
+boundary: a sum of K products carries an fp32 error of about sqrt(K) 2^-24 relative, against
+a bf16 spacing of 2^-8, so about sqrt(K) 2^-16 (0.1% at K = 27 * 192) of each layer's stored
+values flip by one bf16 ulp (2^-8 relative), and the flips compound over the network's ~30
+rounding points.  Bounds: relative L2 <= 5e-3 for the output; for the gradients <= 1e-2 over
+all parameters together and <= 5e-2 for each parameter tensor (the bottleneck's weight
+gradient sums over only D^3/512 voxels per sample at the end of nine rounded backward levels,
+so a few flipped values move it by percents; a structural mistake -- a wrong tap, transposed
+channels, a dropped skip path -- gives errors of order one).
 """
 import numpy as np
 import pytest
@@ -107,27 +113,46 @@ def test_network_forward_and_gradients_match_oracle(B, D):
         assert np.array_equal(net.get_params(), hzpkg.flatten_params(p))
     ref_loss = 0.0
     ref_g = {k: 0.0 for k in p}
+    yerr = []
     for s in range(B):
         ys, cache = N.forward(p, x[s].astype(np.float64), keep=True, bf16=True)
-        assert rel(y[s], ys) <= 2e-3
+        yerr.append(rel(y[s], ys))
+        assert yerr[-1] <= 5e-3, yerr
         ls, dy = N.loss_mse(ys, t[s])
         ref_loss += ls
         gs = N.backward(p, cache, dy)
         for k in p:
             ref_g[k] = ref_g[k] + gs[k]
-    assert abs(loss - ref_loss) <= 2e-3 * ref_loss
-    for k in p:
-        assert rel(grads[k], ref_g[k]) <= 5e-3, (k, rel(grads[k], ref_g[k]))
+    assert abs(loss - ref_loss) <= 5e-3 * ref_loss
+    errs = {k: rel(grads[k], ref_g[k]) for k in p}
+    worst = max(errs, key=errs.get)
+    gall = np.concatenate([np.ravel(grads[k]) for k in p])
+    rall = np.concatenate([np.ravel(ref_g[k]) for k in p])
+    print(f"{B} x {D}^3: output rel. L2 vs oracle {max(yerr):.1e}; gradients: all "
+          f"{rel(gall, rall):.1e}, median tensor {np.median(list(errs.values())):.1e}, worst "
+          f"{worst} {errs[worst]:.1e}")
+    assert rel(gall, rall) <= 1e-2
+    assert errs[worst] <= 5e-2, errs
 
 
 def test_training_lowers_the_loss():
-    """Adam steps on a fixed batch (the oracle's own update rule is pinned on the CPU)."""
-    p, x, t = _net_case(41, 2, 16)
+    """Adam steps on a fixed batch with a learnable target (a pointwise mixing of the input's
+    two field channels); the oracle's own update rule is pinned on the CPU."""
+    p, x, _ = _net_case(41, 2, 16)
+    t = np.stack([0.5 * (x[..., 0] + x[..., 1]), 0.5 * (x[..., 0] - x[..., 1])], axis=-1)
     with hzpkg.Net(16, 16, 16, batch_max=2) as net:
         net.set_params(hzpkg.flatten_params(p))
-        xd, td = torch.from_numpy(x).to(DEV), torch.from_numpy(t).to(DEV)
-        losses = [net.train_step(xd, td, lr=1e-3)[0] for _ in range(30)]
-    assert losses[-1] < 0.8 * losses[0], losses
+        xd = torch.from_numpy(x).to(DEV)
+        td = torch.from_numpy(np.ascontiguousarray(t, dtype=np.float32)).to(DEV)
+        # the first step's update equals the oracle's Adam step on the library's own gradients
+        p0 = net.get_params().astype(np.float64)
+        l0, g0 = net.train_step(xd, td, lr=1e-3, want_grads=True)
+        ref = {"a": p0.copy()}
+        N.adam_step(ref, {"a": g0.cpu().numpy().astype(np.float64)}, {}, lr=1e-3)
+        p1 = net.get_params()
+        assert np.max(np.abs(p1 - ref["a"])) <= 1e-6 * (1.0 + np.max(np.abs(p0)))
+        losses = [l0] + [net.train_step(xd, td, lr=1e-3)[0] for _ in range(39)]
+    assert losses[-1] < 0.7 * losses[0], losses
 
 
 def _training_pairs(P, wl, k, seed):
