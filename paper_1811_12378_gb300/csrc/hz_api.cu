@@ -126,6 +126,9 @@ struct hz_problem {
   // the barrier words and the error flag of the FCI tail (the two never run concurrently)
   int arn_mode = 1;  // hz_problem_fused_arnoldi: 0 five kernels, 1 cooperative, 2 summed norm
   int arn_ppt = 0, arn_blocks = 0;
+  // the float64 cooperative FCI tail and outer step (hz_coop64.cu), same modes and barrier
+  int t64_ppt = 0, t64_blocks = 0;
+  int a64_ppt = 0, a64_blocks = 0;
 
   // the learned right preconditioner (hz_problem_set_preconditioner): the network, how it
   // combines with FCI, and two float64 fields per right-hand side for the combinations
@@ -459,6 +462,31 @@ bool arnoldi_fits(const hz_problem* p, int nvec) {
   return p->arn_mode != 0 && p->tail_solo && nvec == 1 && p->arn_ppt > 0;
 }
 
+bool tail64_fits(const hz_problem* p, int nvec, int kin) {
+  return p->tail_mode != 0 && p->tail_solo && nvec == 1 && kin <= hz::TAIL64_KMAX &&
+         p->t64_ppt > 0;
+}
+
+bool arnoldi64_fits(const hz_problem* p, int nvec) {
+  return p->arn_mode != 0 && p->tail_solo && nvec == 1 && p->a64_ppt > 0;
+}
+
+// Algorithmic bytes and float64 flops per point of the float64 FCI tail (step d, kin CGS2
+// steps, v + d w) and of one float64 outer Arnoldi step with nb basis fields: every field read
+// or written once per pass, 8 flops per complex multiply-add, 22 per stencil point.
+double tail64_bytes(long long n, int kin) {
+  double f = 3.0 + 2.0;  // step d: w, r, diagonal; W and v_0 written
+  for (int nb = 1; nb <= kin; ++nb) f += 2.0 + 3.0 * nb + 2.0;
+  return 16.0 * n * (f + kin + 1.0);
+}
+double tail64_flops(long long n, int kin) {
+  double f = 22.0 + 12.0 + 12.0;
+  for (int nb = 1; nb <= kin; ++nb) f += 24.0 + 32.0 * nb + 8.0;
+  return double(n) * (f + 8.0 * kin + 8.0);
+}
+double arn64_bytes(long long n, int nb) { return 16.0 * n * (3.0 + 3.0 * nb + 1.0); }
+double arn64_flops(long long n, int nb) { return double(n) * (22.0 + 32.0 * nb + 10.0); }
+
 // r_ff: r holds float pairs (the outer basis of HZ_MIXED_C64_FF) whose complex64 rounding the
 // normalisation kernel already wrote into p->f32; otherwise r is complex128.
 hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nvec, int kin,
@@ -479,6 +507,15 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
                                     wb, nullptr, st, w32b, precision == HZ_MIXED_C64)));
   } else {
     HZ_TRY((run_poly<double2, double>(p, p->d64, r, nvec, all, true, wb, nullptr, st)));
+  }
+  if (!fci32 && tail64_fits(p, nvec, kin)) {
+    // steps 3-5 in float64 as one cooperative launch (Aw serves as its scratch field)
+    HZ_TIMED_F(p, 2, st, tail64_bytes(n, kin), tail64_flops(n, kin),
+               hz::launch_fci_tail64(p->g, p->d64, p->w, r.p, p->Vin, p->Aw, out.p, p->partial,
+                                     p->tail_bar, (int*)(p->tail_bar + 2), n, kin, kBreakdown,
+                                     p->tail_mode == 1 ? 1 : 0, p->t64_ppt, p->t64_blocks, st));
+    p->tail_used = true;
+    return HZ_OK;
   }
   if (fci32 && tail_fits(p, nvec, kin)) {
     // steps 3-5 in one cooperative launch
@@ -604,6 +641,14 @@ hz_status outer_step_launches(hz_problem* p, int k, int nrhs, int K, int precisi
     Buf<float2> z32k{p->Z32 + (long long)k * n, zrs};
     HZ_CUDA(hz::launch_convert_c128_c64(Buf<const double2>{p->Aw, n}, z32k, n, nrhs, st));
     Buf<double2> wk{p->V + (long long)(k + 1) * n, vrs};
+    if (arnoldi64_fits(p, nrhs)) {
+      HZ_TIMED_F(p, 2, st, arn64_bytes(n, k + 1) - 8.0 * n, arn64_flops(n, k + 1),
+                 hz::launch_arnoldi64(p->g, p->d64, z32k.p, 1, p->V, wk.p, go, p->partial,
+                                      p->tail_bar, (int*)(p->tail_bar + 2), n, k + 1, kBreakdown,
+                                      p->arn_mode == 1 ? 1 : 0, p->a64_ppt, p->a64_blocks, st));
+      p->tail_used = true;
+      return HZ_OK;
+    }
     HZ_TIMED_F(p, 1, st, double(n) * nrhs * (8.0 + 16.0 + 16.0), kStencil64Flops * n * nrhs,
                (hz::launch_stencil_diag_x32(p->g, p->d64, Buf<const float2>{z32k.p, zrs}, wk,
                                             nrhs, st)));
@@ -641,6 +686,14 @@ hz_status outer_step_launches(hz_problem* p, int k, int nrhs, int K, int precisi
     return HZ_OK;
   }
   Buf<double2> wk{p->V + (long long)(k + 1) * n, vrs};
+  if (arnoldi64_fits(p, nrhs)) {
+    HZ_TIMED_F(p, 2, st, arn64_bytes(n, k + 1), arn64_flops(n, k + 1),
+               hz::launch_arnoldi64(p->g, p->d64, zk.p, 0, p->V, wk.p, go, p->partial,
+                                    p->tail_bar, (int*)(p->tail_bar + 2), n, k + 1, kBreakdown,
+                                    p->arn_mode == 1 ? 1 : 0, p->a64_ppt, p->a64_blocks, st));
+    p->tail_used = true;
+    return HZ_OK;
+  }
   HZ_TIMED_F(p, 1, st, (stencil_bytes<double2, double2>(n, nrhs)), kStencil64Flops * n * nrhs,
              (hz::launch_stencil_diag(p->g, p->d64, Buf<const double2>{zk.p, zrs}, wk, nrhs, 0.0,
                                       0.0, st)));
@@ -659,7 +712,8 @@ hz_status outer_step(hz_problem* p, int k, int nrhs, int K, int precision, cudaS
   const long long key =
       ((((long long)nrhs * 4 + precision) * 1024 + K) * 2 + (tail_fits(p, nrhs, K) ? 1 : 0)) * 2 +
       (arnoldi_fits(p, nrhs) ? 1 : 0) + 2 * (p->arn_mode == 2 ? 1 : 0) +
-      4 * (p->tail_mode == 2 ? 1 : 0) + 8 * p->net_mode;
+      4 * (p->tail_mode == 2 ? 1 : 0) + 8 * p->net_mode + 32 * (tail64_fits(p, nrhs, K) ? 1 : 0) +
+      64 * (arnoldi64_fits(p, nrhs) ? 1 : 0);
   if (p->graph_key != key) {
     p->drop_graphs();
     p->graph_key = key;
@@ -998,6 +1052,8 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
     if (pe == cudaSuccess && K > 4)
       pe = hz::fci_tail32_plan(n, hz::TAIL_KMAX, &p->tail_ppt[1], &p->tail_blocks[1]);
     if (pe == cudaSuccess) pe = hz::arnoldi_ff_plan(n, M, &p->arn_ppt, &p->arn_blocks);
+    if (pe == cudaSuccess) pe = hz::arnoldi64_plan(n, M, &p->a64_ppt, &p->a64_blocks);
+    if (pe == cudaSuccess) pe = hz::fci_tail64_plan(n, &p->t64_ppt, &p->t64_blocks);
     if (pe != cudaSuccess) {
       delete p;
       return cuda_fail(pe, "cooperative kernel plans");
@@ -1013,7 +1069,8 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   const long long npart = std::max(
       {nblk * slots * R,
        2LL * (hz::TAIL_KMAX + 2) * std::max(p->tail_blocks[0], p->tail_blocks[1]),
-       2LL * (M + 2) * p->arn_blocks});
+       2LL * (M + 2) * p->arn_blocks, 2LL * (M + 2) * p->a64_blocks,
+       2LL * (hz::TAIL64_KMAX + 2) * p->t64_blocks});
   if ((s = dalloc(p, (void**)&p->partial, sizeof(double2) * (size_t)npart)) != HZ_OK)
     return bail(s);
   if ((s = dalloc(p, (void**)&p->counters, sizeof(unsigned) * R)) != HZ_OK) return bail(s);

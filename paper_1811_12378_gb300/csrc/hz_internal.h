@@ -224,6 +224,24 @@ cudaError_t launch_arnoldi_ff(const Geom& g, const double2* dg, const double2* z
                               const float4* V, float4* vnext, float2* y32, const GmresDev& gs,
                               double2* partial, unsigned* bar, int* err, long long n, int nb,
                               double brk, int pyth, int ppt, int blocks, cudaStream_t st);
+// ---- float64 cooperative kernels of the float64-outer forms (hz_coop64.cu), one right-hand side
+// Grid plans (ppt 0: the multi-kernel forms serve).
+cudaError_t arnoldi64_plan(long long n, int mmax, int* ppt, int* blocks);
+cudaError_t fci_tail64_plan(long long n, int* ppt, int* blocks);
+constexpr int TAIL64_KMAX = 4;
+// One outer Arnoldi step in float64: w = A z (z double2, or float2 if z32), CGS2 against the nb
+// fields V, the Givens step of column nb - 1 and vnext = w / h; partial: 2 (mmax + 2) blocks.
+cudaError_t launch_arnoldi64(const Geom& g, const double2* dg, const void* z, int z32,
+                             const double2* V, double2* vnext, const GmresDev& gs,
+                             double2* partial, unsigned* bar, int* err, long long n, int nb,
+                             double brk, int pyth, int ppt, int blocks, cudaStream_t st);
+// Algorithm 1 steps 3-5 in float64 (kin <= 4): w the quadrature sum, r the FCI input, V kin + 1
+// fields, W one scratch field; partial: 2 (TAIL64_KMAX + 2) blocks.
+cudaError_t launch_fci_tail64(const Geom& g, const double2* dg, const double2* w,
+                              const double2* r, double2* V, double2* W, double2* out,
+                              double2* partial, unsigned* bar, int* err, long long n, int kin,
+                              double brk, int pyth, int ppt, int blocks, cudaStream_t st);
+
 // y = R^{-1} g in float32 for the complex64 FCI form's inner GMRES (GmresDev storage float64).
 cudaError_t launch_backsolve32(const GmresDev& gs, int nvec, cudaStream_t st);
 

@@ -302,39 +302,6 @@ __global__ void k_c64_to_c128(const float2* __restrict__ x, long long xrs, doubl
   }
 }
 
-// Butterfly reduction of 8 per-lane complex partials over a warp: after the three exchange
-// steps each lane holds one vector's partial (vector index bits = lane bits 4, 3, 2), and two
-// more xor steps finish it.  18 float64 adds reduce 8 vectors, against 80 for 8 separate
-// shuffle trees -- float64 is the scarce pipe.  Lane l with (l & 3) == 0 ends with the sum
-// of vector ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 + ((l >> 2) & 1).
-__device__ __forceinline__ double2 warp_reduce8(double2 (&a)[8], int lane) {
-  double2 b4[4], b2[2];
-  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    const double2 keep = h16 ? a[4 + t] : a[t];
-    const double2 give = h16 ? a[t] : a[4 + t];
-    b4[t] = make_double2(keep.x + __shfl_xor_sync(0xffffffffu, give.x, 16),
-                         keep.y + __shfl_xor_sync(0xffffffffu, give.y, 16));
-  }
-#pragma unroll
-  for (int t = 0; t < 2; ++t) {
-    const double2 keep = h8 ? b4[2 + t] : b4[t];
-    const double2 give = h8 ? b4[t] : b4[2 + t];
-    b2[t] = make_double2(keep.x + __shfl_xor_sync(0xffffffffu, give.x, 8),
-                         keep.y + __shfl_xor_sync(0xffffffffu, give.y, 8));
-  }
-  const double2 keep = h4 ? b2[1] : b2[0];
-  const double2 give = h4 ? b2[0] : b2[1];
-  double x = keep.x + __shfl_xor_sync(0xffffffffu, give.x, 4);
-  double y = keep.y + __shfl_xor_sync(0xffffffffu, give.y, 4);
-  x += __shfl_xor_sync(0xffffffffu, x, 2);
-  y += __shfl_xor_sync(0xffffffffu, y, 2);
-  x += __shfl_xor_sync(0xffffffffu, x, 1);
-  y += __shfl_xor_sync(0xffffffffu, y, 1);
-  return make_double2(x, y);
-}
-
 // Classical Gram-Schmidt pieces in float64.  A block of CG_WARPS warps owns 256 PPL points;
 // lane l of warp w owns the PPL points seg + l + 32 e, kept in registers, so every basis
 // field is read with coalesced 512-byte warp loads.  Dots are formed 8 basis fields at a time

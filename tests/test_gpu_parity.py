@@ -469,6 +469,39 @@ def test_barrier_timeout_status_and_recovery():
         u1, st1 = P.solve(f, **kw)
         assert st1[0].converged and st1[0].its == st0[0].its
         assert np.array_equal(to_np(u1), u0)
+        # the same through the float64 cooperative kernels of the float64-outer form
+        kw64 = dict(kw, precision=hzpkg.HZ_MIXED_C64)
+        u2, st2 = P.solve(f, **kw64)
+        P.set_spin_limit(0)
+        with pytest.raises(hzpkg.HzError) as ei:
+            P.solve(f, **kw64)
+        assert ei.value.status == 8, ei.value
+        P.set_spin_limit(-1)
+        u3, st3 = P.solve(f, **kw64)
+        assert st3[0].converged and np.array_equal(to_np(u3), to_np(u2))
+
+
+@pytest.mark.parametrize("prec", [hzpkg.HZ_C128, hzpkg.HZ_MIXED_C64])
+@pytest.mark.parametrize("name", ["point_source_32", "gaussian_bumps_64"])
+def test_float64_cooperative_steps_match_multi_kernel_form(prec, name):
+    """The float64 cooperative outer Arnoldi step and FCI tail (one right-hand side) against
+    the multi-kernel float64 form at a fixed step count across a restart: the same float64
+    arithmetic per point, only the grouping of the global sums differs, so the iterates agree
+    to a few rounding errors amplified by the iteration (1e-10 relative)."""
+    wl = getattr(W, name)()
+    f = to_dev(wl.f)
+    kw = dict(restart=12, inner_k=4, rtol=1e-8, max_cycles=5, precision=prec, fixed_its=20)
+    with problem_of(wl, None, nrhs_max=1, restart_max=12, inner_k_max=4) as P:
+        u_fused, st_f = P.solve(f, **kw)
+        P.fused_tail(0)
+        P.fused_arnoldi(0)
+        u_multi, st_m = P.solve(f, **kw)
+        P.fused_tail(2)  # the summed last norm instead of the Pythagorean difference
+        P.fused_arnoldi(2)
+        u_sum, _ = P.solve(f, **kw)
+    assert st_f[0].its == st_m[0].its == 20
+    assert rel(to_np(u_fused), to_np(u_multi)) <= 1e-10
+    assert rel(to_np(u_sum), to_np(u_multi)) <= 1e-10
 
 
 def test_limit_flags_restrict_forms_and_keep_results():
