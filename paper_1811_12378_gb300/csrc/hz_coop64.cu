@@ -153,7 +153,8 @@ __device__ __forceinline__ void dots64(const Arn64& a, const Pts& P, const doubl
       for (int t = 0; t < 8; ++t)
         v[t] = b0 + t < nb ? __ldg(a.V + (long long)(b0 + t) * a.n + p) : cz();
 #pragma unroll
-      for (int t = 0; t < 8; ++t) dot_acc(acc[t], v[t], w);
+      for (int t = 0; t < 8; ++t)
+        if (b0 + t < nb) dot_acc(acc[t], v[t], w);  // uniform: nb is the same in every thread
     }
     const double2 red = warp_reduce8(acc, lane);
     if ((lane & 3) == 0) {
@@ -345,9 +346,23 @@ __global__ void __launch_bounds__(TT) k_fci_tail64(Tail64 a) {
     const long long p = t0 + (long long)e * TT;
     coords_of(g, p < pend ? p : 0, ci[e], cj[e], ck[e]);
   }
-  // partial sums of ns slots v[0..ns) of this thread -> part(q)
+  // partial sums of ns slots v[0..ns) of this thread -> part(q): one or two slots by
+  // shuffle trees, more by the butterfly of warp_reduce8 (18 float64 adds for up to 8 slots
+  // against 10 per slot: float64 adds are the scarce instructions here)
   auto partial = [&](double2* v, int ns, int q) {
-    for (int s = 0; s < ns; ++s) warp_store(v[s], wsum, LDW, s);
+    if (ns <= 2) {
+      for (int s = 0; s < ns; ++s) warp_store(v[s], wsum, LDW, s);
+    } else {
+      const int lane = threadIdx.x & 31;
+      double2 acc[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) acc[t] = t < ns ? v[t] : cz();
+      const double2 red = warp_reduce8(acc, lane);
+      if ((lane & 3) == 0) {
+        const int t = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        if (t < ns) wsum[(threadIdx.x >> 5) * LDW + t] = red;
+      }
+    }
     block_partial64(part(q), wsum, LDW, ns, TW);
   };
 
@@ -668,11 +683,21 @@ cudaError_t fci_tail64_plan(long long n, int* ppt, int* blocks) {
       default: e = tail64_occ<8>(&per_sm); break;
     }
     if (e != cudaSuccess) return e;
-    // at most two blocks per SM (more blocks lengthen every barrier and all-blocks sum)
+    // at most two blocks per SM (more blocks lengthen every barrier and all-blocks sum), and
+    // the same number on every SM (float64-bound: the busiest SM sets the time)
     const long long need = (n + (long long)TT * p - 1) / ((long long)TT * p);
-    if (need <= (long long)std::min(per_sm, 2) * sms) {
+    const long long cap = (long long)std::min(per_sm, 2) * sms;
+    if (need <= cap) {
       *ppt = p;
-      *blocks = (int)need;
+      *blocks = (int)std::min<long long>(need <= sms ? need : cap, (n + TT - 1) / TT);
+      // points per thread for that grid
+      *ppt = (int)((n + (long long)(*blocks) * TT - 1) / ((long long)(*blocks) * TT));
+      if (*ppt > 8) {
+        *ppt = 0;
+        *blocks = 0;
+        continue;
+      }
+      *ppt = *ppt <= 1 ? 1 : (*ppt <= 2 ? 2 : (*ppt <= 4 ? 4 : 8));
       return cudaSuccess;
     }
   }

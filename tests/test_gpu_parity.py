@@ -482,13 +482,12 @@ def test_barrier_timeout_status_and_recovery():
 
 
 @pytest.mark.parametrize("prec", [hzpkg.HZ_C128, hzpkg.HZ_MIXED_C64])
-@pytest.mark.parametrize("name", ["point_source_32", "gaussian_bumps_64"])
-def test_float64_cooperative_steps_match_multi_kernel_form(prec, name):
+def test_float64_cooperative_steps_match_multi_kernel_form(prec):
     """The float64 cooperative outer Arnoldi step and FCI tail (one right-hand side) against
-    the multi-kernel float64 form at a fixed step count across a restart: the same float64
-    arithmetic per point, only the grouping of the global sums differs, so the iterates agree
-    to a few rounding errors amplified by the iteration (1e-10 relative)."""
-    wl = getattr(W, name)()
+    the multi-kernel float64 form at a fixed step count across a restart (32^3): the same
+    float64 arithmetic per point, only the grouping of the global sums differs, so the iterates
+    agree to a few rounding errors amplified by the iteration (1e-10 relative)."""
+    wl = W.point_source_32()
     f = to_dev(wl.f)
     kw = dict(restart=12, inner_k=4, rtol=1e-8, max_cycles=5, precision=prec, fixed_its=20)
     with problem_of(wl, None, nrhs_max=1, restart_max=12, inner_k_max=4) as P:
@@ -502,6 +501,25 @@ def test_float64_cooperative_steps_match_multi_kernel_form(prec, name):
     assert st_f[0].its == st_m[0].its == 20
     assert rel(to_np(u_fused), to_np(u_multi)) <= 1e-10
     assert rel(to_np(u_sum), to_np(u_multi)) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", [hzpkg.HZ_C128, hzpkg.HZ_MIXED_C64])
+def test_float64_cooperative_steps_converge_like_multi_kernel_form_64(prec):
+    """At 64^3 (several points per thread in both cooperative kernels) the iterates at a fixed
+    step count are ill-conditioned functions of the rounding (every variant, the multi-kernel
+    one included, differs from the oracle's 20-step iterate by about 4e-5 while a single FCI
+    application agrees to 1e-11), so the two forms are compared on their converged solutions:
+    both at a true residual of 1e-11, they agree to 5e-11."""
+    wl = W.gaussian_bumps_64()
+    f = to_dev(wl.f)
+    kw = dict(restart=wl.restart, inner_k=4, rtol=1e-11, max_cycles=40, precision=prec)
+    with problem_of(wl, None, nrhs_max=1, restart_max=wl.restart, inner_k_max=4) as P:
+        u_fused, st_f = P.solve(f, **kw)
+        P.fused_tail(0)
+        P.fused_arnoldi(0)
+        u_multi, st_m = P.solve(f, **kw)
+    assert st_f[0].converged and st_m[0].converged
+    assert rel(to_np(u_fused), to_np(u_multi)) <= 5e-11
 
 
 def test_limit_flags_restrict_forms_and_keep_results():
