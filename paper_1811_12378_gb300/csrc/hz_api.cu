@@ -462,13 +462,21 @@ bool arnoldi_fits(const hz_problem* p, int nvec) {
   return p->arn_mode != 0 && p->tail_solo && nvec == 1 && p->arn_ppt > 0;
 }
 
+// The float64 cooperative kernels pay off where the float64 Krylov work is latency-bound, not
+// where it is float64-throughput-bound (measured on GB300, HZ_MIXED_C64, one right-hand side:
+// 32^3 10.9 ms per solve against 13.7 ms for the multi-kernel form; 64^3 60.6 against 54.0 ms,
+// where the multi-kernel Gram-Schmidt kernels, sized so the busiest SM has the least work, keep
+// the float64 pipes busier than one resident grid with barriers and serial Givens steps).
+constexpr long long kCoop64MaxPoints = 1LL << 17;
+
 bool tail64_fits(const hz_problem* p, int nvec, int kin) {
   return p->tail_mode != 0 && p->tail_solo && nvec == 1 && kin <= hz::TAIL64_KMAX &&
-         p->t64_ppt > 0;
+         p->t64_ppt > 0 && p->g.n <= kCoop64MaxPoints;
 }
 
 bool arnoldi64_fits(const hz_problem* p, int nvec) {
-  return p->arn_mode != 0 && p->tail_solo && nvec == 1 && p->a64_ppt > 0;
+  return p->arn_mode != 0 && p->tail_solo && nvec == 1 && p->a64_ppt > 0 &&
+         p->g.n <= kCoop64MaxPoints;
 }
 
 // Algorithmic bytes and float64 flops per point of the float64 FCI tail (step d, kin CGS2

@@ -504,11 +504,11 @@ def test_float64_cooperative_steps_match_multi_kernel_form(prec):
 
 
 @pytest.mark.parametrize("prec", [hzpkg.HZ_C128, hzpkg.HZ_MIXED_C64])
-def test_float64_cooperative_steps_converge_like_multi_kernel_form_64(prec):
-    """At 64^3 (several points per thread in both cooperative kernels) the iterates at a fixed
-    step count are ill-conditioned functions of the rounding (every variant, the multi-kernel
-    one included, differs from the oracle's 20-step iterate by about 4e-5 while a single FCI
-    application agrees to 1e-11), so the two forms are compared on their converged solutions:
+def test_float64_forms_converge_alike_at_64(prec):
+    """At 64^3 (where the solver picks the multi-kernel float64 steps by default) the iterates
+    at a fixed step count are ill-conditioned functions of the rounding (every variant differs
+    from the oracle's 20-step iterate by about 4e-5 while a single FCI application agrees to
+    1e-11), so the default and the modes-0 forms are compared on their converged solutions:
     both at a true residual of 1e-11, they agree to 5e-11."""
     wl = W.gaussian_bumps_64()
     f = to_dev(wl.f)
