@@ -122,7 +122,18 @@ typedef enum {
      (float64) stays consistent with the Krylov residual; this is FGMRES with a preconditioner
      whose output is rounded (Section 2, after Algorithm 1: any right preconditioner may vary
      from step to step).  hz_solve accepts only HZ_MIXED_C64 and HZ_MIXED_C64_FCI32 then. */
-  HZ_LIMIT_Z_C64 = 2
+  HZ_LIMIT_Z_C64 = 2,
+  /* Case Two of Section 3: the solver runs on the double-size matrix iC - I of eq:mat-2x2
+     (float64, HZ_C128 only; not combined with the other flags).  The contour and the
+     polynomial parameters come from the rectangle of the Remark after Theorem
+     thm:spectrum-2x2: Re mu in [-1 - R, -1 + R], Im mu in [-rho2, 0], R = rho2/2 +
+     sqrt(rho2^2/4 + rho1), rho1 = rho(A1 + I) bounded by Weyl's inequality.  Fields of the
+     solver are 2n points (x1; x2): hz_fci takes and returns such fields, hz_shifted_solve
+     returns them, and hz_solve takes the physical f (n points per right-hand side) and
+     returns Y = (i u; u) (2n points per right-hand side; u is its second half), solving
+     (iC - I) Y = (0; s f); its stats report the residual of that system.  The workspace is
+     twice that of a Case One problem. */
+  HZ_LIMIT_CASE_TWO = 4
 } hz_limit_flags;
 
 /* hz_solve settings.  restart_m <= restart_max, inner_k <= inner_k_max.  precision is an

@@ -87,6 +87,8 @@ struct hz_problem {
   double2* V = nullptr;      // [nrhs][m+1][n] outer basis
   double2* Z = nullptr;      // [nrhs][m][n] preconditioned directions (float64)
   float2* Z32 = nullptr;     // [nrhs][m][n] the same stored in complex64 (HZ_LIMIT_Z_C64)
+  bool case2 = false;        // HZ_LIMIT_CASE_TWO: the solver runs on iC - I (eq:mat-2x2)
+  long long nf = 0;          // points of a solver field: n, or 2n for Case Two
   bool z32 = false;          // HZ_LIMIT_Z_C64
   bool sweeps32 = false;     // HZ_LIMIT_SWEEPS_C64
   double2* partial = nullptr;
@@ -314,7 +316,7 @@ Slots slots_of(int s, long long n) {
 template <typename R>
 void build_schedule(const hz_problem* p, const std::vector<int>& which, bool quad,
                     std::vector<hz::StageArgs<R>>& out, std::vector<long long>& ycur) {
-  const long long n = p->g.n;
+  const long long n = p->nf;
   const int nn = (int)which.size();
   int T_total = 0;
   for (int node : which) T_total = std::max(T_total, p->nodes[node].q * p->nodes[node].sweeps);
@@ -415,11 +417,39 @@ hz_status run_poly(hz_problem* p, const T* dg, Buf<const T> f, int nvec,
                    const std::vector<int>& which, bool quad, Buf<double2> wbuf,
                    std::vector<long long>* yfinal, cudaStream_t st,
                    Buf<float2> w32buf = Buf<float2>{nullptr, 0}, bool quad64 = false) {
-  const long long n = p->g.n;
+  const long long n = p->nf;
   T* ws = (T*)p->poly;
   const long long wrs = 4LL * p->J * n;  // elements of T per rhs
   std::vector<hz::StageArgs<R>> sched;
   std::vector<long long> ycur;
+  if constexpr (sizeof(T) == sizeof(double2)) {
+    if (p->case2) {
+      // Case Two: the scheme on iC - I, every node's y stored, then the quadrature sum
+      build_schedule<R>(p, which, false, sched, ycur);
+      ProfScope seq{p, 0, -1, st, 0.0};
+      HZ_TRY(seq.begin());
+      for (const auto& a : sched)
+        HZ_CUDA(hz::launch_poly_stage_2x2(p->g, p->d64, Buf<const double2>{f.p, f.rs},
+                                          (double2*)ws, wrs, nvec, a, st));
+      if (quad) {
+        std::vector<double> wr(which.size()), wi(which.size());
+        for (size_t s = 0; s < which.size(); ++s) {
+          const NodeParams& np = p->nodes[which[s]];
+          const std::complex<double> wq = std::complex<double>(np.sr, np.si) /
+                                          std::complex<double>(np.zr, np.zi);
+          wr[s] = wq.real();
+          wi[s] = wq.imag();
+        }
+        HZ_CUDA(hz::launch_quad_2x2((const double2*)ws, wrs, wbuf, n, nvec, ycur.data(),
+                                    wr.data(), wi.data(), (int)which.size(), st));
+      }
+      seq.bytes = 0.0;
+      HZ_TRY(seq.end());
+      if (seq.slot >= 0) p->prof[0].launches += (long long)sched.size() - 1;
+      if (yfinal) *yfinal = ycur;
+      return HZ_OK;
+    }
+  }
   build_schedule<R>(p, which, quad, sched, ycur);
   const int T_total = (int)sched.size();
   if (quad && T_total > 0) sched.back().quad64 = quad64 ? 1 : 0;
@@ -495,11 +525,19 @@ double tail64_flops(long long n, int kin) {
 double arn64_bytes(long long n, int nb) { return 16.0 * n * (3.0 + 3.0 * nb + 1.0); }
 double arn64_flops(long long n, int nb) { return double(n) * (22.0 + 32.0 * nb + 10.0); }
 
+// y = (B - 0 I) x in float64 for solver fields: B = A (Case One) or iC - I (Case Two).
+cudaError_t apply_op64(const hz_problem* p, Buf<const double2> x, Buf<double2> y, int nvec,
+                       cudaStream_t st) {
+  if (p->case2)
+    return hz::launch_apply_2x2_strided(p->g, p->d64, x.p, x.rs, y.p, y.rs, nvec, 0.0, 0.0, st);
+  return hz::launch_stencil_diag(p->g, p->d64, x, y, nvec, 0.0, 0.0, st);
+}
+
 // r_ff: r holds float pairs (the outer basis of HZ_MIXED_C64_FF) whose complex64 rounding the
 // normalisation kernel already wrote into p->f32; otherwise r is complex128.
 hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nvec, int kin,
                   int precision, cudaStream_t st, bool r_ff = false) {
-  const long long n = p->g.n;
+  const long long n = p->nf;
   const bool fci32 = precision == HZ_MIXED_C64_FCI32 || precision == HZ_MIXED_C64_FF;
   std::vector<int> all(p->J);
   for (int j = 0; j < p->J; ++j) all[j] = j;
@@ -571,8 +609,7 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
   }
   // Aw, step d, inner start v0 = (r - d Aw)/||r - d Aw||
   HZ_TIMED_F(p, 1, st, (stencil_bytes<double2, double2>(n, nvec)), kStencil64Flops * n * nvec,
-             (hz::launch_stencil_diag(p->g, p->d64, Buf<const double2>{p->w, n},
-                                      Buf<double2>{p->Aw, n}, nvec, 0.0, 0.0, st)));
+             apply_op64(p, Buf<const double2>{p->w, n}, Buf<double2>{p->Aw, n}, nvec, st));
   const long long vrs = (long long)(p->lim.inner_k_max + 1) * n;
   // two launches: d (reads Aw, r) and v0 = r - d Aw with its norm (reads Aw, r; writes v0)
   HZ_TIMED_F(p, 2, st, 16.0 * n * nvec * 5, 24.0 * n * nvec,
@@ -583,9 +620,7 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
   for (int j = 0; j < kin; ++j) {
     Buf<double2> wj{p->Vin + (long long)(j + 1) * n, vrs};
     HZ_TIMED_F(p, 1, st, (stencil_bytes<double2, double2>(n, nvec)), kStencil64Flops * n * nvec,
-               (hz::launch_stencil_diag(p->g, p->d64,
-                                        Buf<const double2>{p->Vin + (long long)j * n, vrs}, wj,
-                                        nvec, 0.0, 0.0, st)));
+               apply_op64(p, Buf<const double2>{p->Vin + (long long)j * n, vrs}, wj, nvec, st));
     for (int mode = 0; mode < 3; ++mode)
       HZ_TIMED_F(p, 2, st, cgs_bytes(mode, n, j + 1, nvec), cgs_flops(mode, n, j + 1, nvec),
                  hz::launch_cgs(mode, p->Vin, n, vrs, j + 1, wj, n, p->gin, p->partial,
@@ -636,7 +671,7 @@ hz_status run_precond(hz_problem* p, Buf<const double2> v, Buf<double2> z, int n
 // CGS2 against v_0..v_k with the Givens update of column k, v_{k+1} = w / h_{k+1,k}.
 hz_status outer_step_launches(hz_problem* p, int k, int nrhs, int K, int precision,
                               cudaStream_t st) {
-  const long long n = p->g.n;
+  const long long n = p->nf;
   const long long vrs = (long long)(p->lim.restart_max + 1) * n;
   const long long zrs = (long long)p->lim.restart_max * n;
   GmresDev& go = p->gout;
@@ -703,8 +738,7 @@ hz_status outer_step_launches(hz_problem* p, int k, int nrhs, int K, int precisi
     return HZ_OK;
   }
   HZ_TIMED_F(p, 1, st, (stencil_bytes<double2, double2>(n, nrhs)), kStencil64Flops * n * nrhs,
-             (hz::launch_stencil_diag(p->g, p->d64, Buf<const double2>{zk.p, zrs}, wk, nrhs, 0.0,
-                                      0.0, st)));
+             apply_op64(p, Buf<const double2>{zk.p, zrs}, wk, nrhs, st));
   for (int mode = 0; mode < 3; ++mode)
     HZ_TIMED_F(p, 2, st, cgs_bytes(mode, n, k + 1, nrhs), cgs_flops(mode, n, k + 1, nrhs),
                hz::launch_cgs(mode, p->V, n, vrs, k + 1, wk, n, go, p->partial, p->counters, nrhs,
@@ -941,6 +975,8 @@ hz_status check_solve_args(const hz_problem* p, int nrhs, const hz_solve_opts* o
   if (p->z32 && opts->precision != HZ_MIXED_C64 && opts->precision != HZ_MIXED_C64_FCI32)
     return fail(HZ_ERR_INVALID, "a problem created with HZ_LIMIT_Z_C64 solves in HZ_MIXED_C64 or "
                                 "HZ_MIXED_C64_FCI32 only");
+  if (p->case2 && opts->precision != HZ_C128)
+    return fail(HZ_ERR_INVALID, "Case Two problems solve in HZ_C128");
   if (p->net_mode != 0 && opts->precision == HZ_MIXED_C64_FF)
     return fail(HZ_ERR_INVALID, "the learned preconditioner needs a float64 outer basis");
   if (p->net_mode != 0 && !hz::net_fits(p->net, nrhs, p->g.nx, p->g.ny, p->g.nz))
@@ -984,9 +1020,11 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
                                 "1 <= qmax <= 12, reduction > 1)");
   if (!limits || limits->nrhs_max < 1 || limits->restart_max < 1 || limits->inner_k_max < 0 ||
       limits->restart_max > 128 || limits->inner_k_max > 128 ||
-      (limits->flags & ~(HZ_LIMIT_SWEEPS_C64 | HZ_LIMIT_Z_C64)) != 0)
+      (limits->flags & ~(HZ_LIMIT_SWEEPS_C64 | HZ_LIMIT_Z_C64 | HZ_LIMIT_CASE_TWO)) != 0 ||
+      ((limits->flags & HZ_LIMIT_CASE_TWO) &&
+       (limits->flags & (HZ_LIMIT_SWEEPS_C64 | HZ_LIMIT_Z_C64))))
     return fail(HZ_ERR_INVALID, "invalid limits (1 <= restart_max <= 128, 0 <= inner_k_max <= 128, "
-                                "known flags only)");
+                                "known flags only; HZ_LIMIT_CASE_TWO alone)");
   const long long n = (long long)grid->nx * grid->ny * grid->nz;
   for (long long i = 0; i < n; ++i)
     if (!(c_host[i] > 0) || !std::isfinite(c_host[i]))
@@ -1024,10 +1062,26 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   p->g.szc = 4;
   p->g.srows = 4;
   std::string err;
-  if (!hz::setup_nodes(p->su, *contour, p->nodes, err)) {
+  p->case2 = (limits->flags & HZ_LIMIT_CASE_TWO) != 0;
+  p->nf = p->case2 ? 2 * n : n;
+  bool nodes_ok;
+  if (p->case2) {
+    // Case Two: the rectangle of the Remark after Theorem thm:spectrum-2x2 for iC - I,
+    // |mu + 1| <= R = rho2/2 + sqrt(rho2^2/4 + rho1), rho1 = rho(A1 + I) <= b2 + 1 (Weyl)
+    hz::Setup s2 = p->su;
+    const double rho1 = p->su.b2 + 1.0, rho2 = p->su.rho2;
+    const double Rr = 0.5 * rho2 + std::sqrt(0.25 * rho2 * rho2 + rho1);
+    s2.b1 = -1.0 - Rr;
+    s2.b2 = -1.0 + Rr;
+    nodes_ok = hz::setup_nodes(s2, *contour, p->nodes, err);
+  } else {
+    nodes_ok = hz::setup_nodes(p->su, *contour, p->nodes, err);
+  }
+  if (!nodes_ok) {
     delete p;
     return fail(HZ_ERR_SETUP, err);
   }
+  const long long nf = p->nf;
 
   const int R = limits->nrhs_max, M = limits->restart_max, K = limits->inner_k_max;
   hz_status s;
@@ -1037,22 +1091,22 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   p->sweeps32 = (limits->flags & HZ_LIMIT_SWEEPS_C64) != 0;
   p->z32 = (limits->flags & HZ_LIMIT_Z_C64) != 0;
   const size_t poly_es = p->sweeps32 ? sizeof(float2) : sizeof(double2);
-  if ((s = dalloc(p, &p->poly, poly_es * 4 * (size_t)p->J * n * R)) != HZ_OK) return bail(s);
+  if ((s = dalloc(p, &p->poly, poly_es * 4 * (size_t)p->J * nf * R)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->f32, sizeof(float2) * (size_t)n * R)) != HZ_OK) return bail(s);
-  if ((s = dalloc(p, (void**)&p->w, sizeof(double2) * (size_t)n * R)) != HZ_OK) return bail(s);
-  if ((s = dalloc(p, (void**)&p->Aw, sizeof(double2) * (size_t)n * R)) != HZ_OK) return bail(s);
-  if ((s = dalloc(p, (void**)&p->Vin, sizeof(double2) * (size_t)n * (K + 1) * R)) != HZ_OK)
+  if ((s = dalloc(p, (void**)&p->w, sizeof(double2) * (size_t)nf * R)) != HZ_OK) return bail(s);
+  if ((s = dalloc(p, (void**)&p->Aw, sizeof(double2) * (size_t)nf * R)) != HZ_OK) return bail(s);
+  if ((s = dalloc(p, (void**)&p->Vin, sizeof(double2) * (size_t)nf * (K + 1) * R)) != HZ_OK)
     return bail(s);
   if ((s = dalloc(p, (void**)&p->Vin32, sizeof(float2) * (size_t)n * (K + 1) * R)) != HZ_OK)
     return bail(s);
   if ((s = dalloc(p, (void**)&p->w32, sizeof(float2) * (size_t)n * R)) != HZ_OK) return bail(s);
   if ((s = dalloc(p, (void**)&p->Aw32, sizeof(float2) * (size_t)n * R)) != HZ_OK) return bail(s);
-  if ((s = dalloc(p, (void**)&p->V, sizeof(double2) * (size_t)n * (M + 1) * R)) != HZ_OK)
+  if ((s = dalloc(p, (void**)&p->V, sizeof(double2) * (size_t)nf * (M + 1) * R)) != HZ_OK)
     return bail(s);
   if (p->z32) {
     if ((s = dalloc(p, (void**)&p->Z32, sizeof(float2) * (size_t)n * M * R)) != HZ_OK) return bail(s);
   } else {
-    if ((s = dalloc(p, (void**)&p->Z, sizeof(double2) * (size_t)n * M * R)) != HZ_OK) return bail(s);
+    if ((s = dalloc(p, (void**)&p->Z, sizeof(double2) * (size_t)nf * M * R)) != HZ_OK) return bail(s);
   }
   // grids of the cooperative kernels (whole numbers of blocks per SM)
   {
@@ -1066,12 +1120,15 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
       delete p;
       return cuda_fail(pe, "cooperative kernel plans");
     }
+    if (p->case2) {  // the cooperative kernels apply Case One's operator: not for Case Two
+      p->tail_ppt[0] = p->tail_ppt[1] = p->arn_ppt = p->a64_ppt = p->t64_ppt = 0;
+    }
   }
   // block partial sums (16 bytes each): linear reduction kernels (>= 256 points a block) and
   // the fused stencil reductions (32 x 4 x 4 tiles, ragged at the edges), (slots x blocks) per
   // rhs; the cooperative kernels, two alternating areas of their slots x blocks
   const long long nblk = std::max<long long>(
-      (n + hz::RED_MIN_CHUNK - 1) / hz::RED_MIN_CHUNK,
+      (nf + hz::RED_MIN_CHUNK - 1) / hz::RED_MIN_CHUNK,
       (long long)((grid->nx + 31) / 32) * ((grid->ny + 3) / 4) * ((grid->nz + 3) / 4));
   const int slots = std::max(M, K) + 2;
   const long long npart = std::max(
@@ -1090,7 +1147,7 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   gmres_layout(p->gin, cur, R, K);
   e = cudaMemset(p->gmem, 0, gb);
   if (e == cudaSuccess) e = cudaMemset(p->counters, 0, sizeof(unsigned) * R);
-  if (e == cudaSuccess) e = cudaMemset(p->poly, 0, poly_es * 4 * (size_t)p->J * n * R);
+  if (e == cudaSuccess) e = cudaMemset(p->poly, 0, poly_es * 4 * (size_t)p->J * nf * R);
   if (e != cudaSuccess) {
     delete p;
     return cuda_fail(e, "cudaMemset");
@@ -1166,7 +1223,7 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
     delete p;
     return cuda_fail(e, "cooperative FCI tail set-up");
   }
-  if (limits->autotune) {
+  if (limits->autotune && !p->case2) {
     const hz_status ts = autotune(p);
     if (ts != HZ_OK) {
       delete p;
@@ -1250,6 +1307,8 @@ hz_status hz_problem_set_preconditioner(hz_problem* p, hz_net* net, int mode) {
   HZ_TRY(check_problem(p));
   if (mode < 0 || mode > 3) return fail(HZ_ERR_INVALID, "preconditioner mode 0..3");
   if (mode != 0 && !net) return fail(HZ_ERR_INVALID, "modes 1..3 need a network");
+  if (mode != 0 && p->case2)
+    return fail(HZ_ERR_INVALID, "the network preconditions Case One problems only");
   if (mode != 0 && !hz::net_fits(net, 1, p->g.nx, p->g.ny, p->g.nz))
     return fail(HZ_ERR_INVALID, "grid sizes must be multiples of 8 within the network's volume");
   HZ_TRY(set_device(p));
@@ -1440,11 +1499,13 @@ hz_status hz_shifted_solve(hz_problem* p, int node, const void* f, void* y, int 
   if (!f || !y) return fail(HZ_ERR_INVALID, "null field");
   HZ_TRY(set_device(p));
   cudaStream_t st = (cudaStream_t)stream;
-  const long long n = p->g.n;
+  const long long n = p->nf;
   std::vector<int> which{node};
   std::vector<long long> yfin;
   Buf<double2> nob{nullptr, 0};
   size_t es;
+  if (p->case2 && precision != HZ_C128)
+    return fail(HZ_ERR_INVALID, "Case Two problems solve in HZ_C128");
   if (precision == HZ_C128 && p->sweeps32)
     return fail(HZ_ERR_INVALID, "HZ_C128 needs a problem created without HZ_LIMIT_SWEEPS_C64");
   if (precision == HZ_C128) {
@@ -1475,11 +1536,13 @@ hz_status hz_fci(hz_problem* p, const void* r, void* out, int nvec, int inner_k,
     return fail(HZ_ERR_INVALID, "unknown precision");
   if (p->sweeps32 && precision == HZ_C128)
     return fail(HZ_ERR_INVALID, "HZ_C128 needs a problem created without HZ_LIMIT_SWEEPS_C64");
+  if (p->case2 && precision != HZ_C128)
+    return fail(HZ_ERR_INVALID, "Case Two problems solve in HZ_C128");
   if (nvec == 0) return HZ_OK;
   if (!r || !out) return fail(HZ_ERR_INVALID, "null field");
   HZ_TRY(set_device(p));
   cudaStream_t st = (cudaStream_t)stream;
-  const long long n = p->g.n;
+  const long long n = p->nf;
   return run_fci(p, Buf<const double2>{(const double2*)r, n}, Buf<double2>{(double2*)out, n}, nvec,
                  inner_k, precision, st);
 }
@@ -1555,7 +1618,7 @@ struct SolveState {
   hz_status init() {
     M = o->restart_m;
     K = o->inner_k;
-    n = p->g.n;
+    n = p->nf;
     vrs = (long long)(p->lim.restart_max + 1) * n;
     zrs = (long long)p->lim.restart_max * n;
     fixed = o->fixed_its > 0;
@@ -1596,6 +1659,21 @@ struct SolveState {
   // true residual r = s f - A u, v0 = r / ||r||
   hz_status enqueue_cycle_start() {
     GmresDev& go = p->gout;
+    if (p->case2) {
+      // Case Two: r = (0; s f) - (iC - I) U, U = (iu; u) the 2n-point iterate
+      if (cycle > 0)
+        HZ_CUDA(apply_op64(p, Buf<const double2>{(const double2*)u, n}, Buf<double2>{p->Aw, n},
+                           nrhs, st));
+      HZ_CUDA(hz::launch_residual_2x2((const double2*)f, p->g.n, p->su.s,
+                                      cycle == 0 ? Buf<const double2>{nullptr, 0}
+                                                 : Buf<const double2>{p->Aw, n},
+                                      Buf<double2>{p->V, vrs}, p->g.n, go, p->partial,
+                                      p->counters, nrhs, st));
+      for (int r = 0; r < nrhs; ++r) mvs[r] += cycle == 0 ? 0 : 1;
+      HZ_CUDA(hz::launch_scale(Buf<double2>{p->V, vrs}, Buf<const double2>{p->V, vrs}, n, go,
+                               nrhs, st));
+      return enqueue_flags();
+    }
     HZ_CUDA(hz::launch_residual_start(p->g, p->m64, Buf<const double2>{(const double2*)f, n},
                                       p->su.s,
                                       cycle == 0 ? Buf<const double2>{nullptr, 0}

@@ -210,6 +210,24 @@ cudaError_t launch_apply_2x2(const Geom& g, const double2* dg, const double2* x,
                              int nvec, double zr, double zi, cudaStream_t st);
 cudaError_t launch_apply_2x2_32(const Geom& g, const float2* dg, const float2* x, float2* y,
                                 int nvec, float zr, float zi, cudaStream_t st);
+// the same (float64) with per-vector strides (fields of 2n points at x + r xrs)
+cudaError_t launch_apply_2x2_strided(const Geom& g, const double2* dg, const double2* x,
+                                     long long xrs, double2* y, long long yrs, int nvec,
+                                     double zr, double zi, cudaStream_t st);
+// One sweep of eq:fix-pt-exp on iC - I for the active nodes of a stage (float64); f holds
+// (f1; f2) per right-hand side, workspace slots are 2n-point fields; every node's final y is
+// stored (no fused quadrature).
+cudaError_t launch_poly_stage_2x2(const Geom& g, const double2* dg, Buf<const double2> f,
+                                  double2* ws, long long wrs, int nvec, const StageArgs<double>& a,
+                                  cudaStream_t st);
+// w = sum_s (wr_s + i wi_s) y_s with y_s at ws + r wrs + off[s] (nf values per field).
+cudaError_t launch_quad_2x2(const double2* ws, long long wrs, Buf<double2> w, long long nf,
+                            int nvec, const long long* off, const double* wr, const double* wi,
+                            int nn, cudaStream_t st);
+// Case Two cycle start: v0 = (0; fs f) - t (t = (iC - I) U, or null for U = 0), beta.
+cudaError_t launch_residual_2x2(const double2* f, long long frs, double fs, Buf<const double2> t,
+                                Buf<double2> v0, long long n, const GmresDev& gs,
+                                double2* partial, unsigned* counters, int nvec, cudaStream_t st);
 // ---- one outer float-pair Arnoldi step as one cooperative kernel (hz_arnoldi_ff.cu) ----
 // Points per thread and grid size for n points and restart length mmax; *ppt = 0 where the
 // grid cannot be co-resident or cooperative launch is unavailable.

@@ -56,6 +56,7 @@ class HzLimits(C.Structure):
 # hz_limits.flags bits
 HZ_LIMIT_SWEEPS_C64 = 1
 HZ_LIMIT_Z_C64 = 2
+HZ_LIMIT_CASE_TWO = 4
 
 
 class HzSolveOpts(C.Structure):
@@ -268,6 +269,7 @@ class Problem:
                                            C.byref(handle)), self._lib)
         self._h = handle
         self.nrhs_max = nrhs_max
+        self.case_two = bool(int(flags) & HZ_LIMIT_CASE_TWO)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -380,18 +382,20 @@ class Problem:
         prec = precision if precision is not None else (
             HZ_MIXED_C64 if f.dtype == torch.complex64 else HZ_C128)
         dt = torch.complex64 if prec == HZ_MIXED_C64 else torch.complex128
-        fp, nvec = _dev_ptr(f, dt, self.n)
+        nf = self.n * (2 if self.case_two else 1)
+        fp, nvec = _dev_ptr(f, dt, nf)
         y = torch.empty_like(f) if out is None else out
-        yp, _ = _dev_ptr(y, dt, self.n)
+        yp, _ = _dev_ptr(y, dt, nf)
         _check(self._lib.hz_shifted_solve(self._h, int(node), fp, yp, nvec, prec,
                                           _stream(stream)), self._lib)
         return y
 
     def fci(self, r, inner_k=4, precision=HZ_C128, out=None, stream=None):
         import torch
-        rp, nvec = _dev_ptr(r, torch.complex128, self.n)
+        nf = self.n * (2 if self.case_two else 1)
+        rp, nvec = _dev_ptr(r, torch.complex128, nf)
         y = torch.empty_like(r) if out is None else out
-        yp, _ = _dev_ptr(y, torch.complex128, self.n)
+        yp, _ = _dev_ptr(y, torch.complex128, nf)
         _check(self._lib.hz_fci(self._h, rp, yp, nvec, int(inner_k), int(precision),
                                 _stream(stream)), self._lib)
         return y
@@ -401,8 +405,12 @@ class Problem:
         """FGMRES(restart) with FCI; f in physical units.  Returns (u, [SolveStats])."""
         import torch
         fp, nrhs = _dev_ptr(f, torch.complex128, self.n)
-        u = torch.empty_like(f) if out is None else out
-        up, _ = _dev_ptr(u, torch.complex128, self.n)
+        if self.case_two:  # Y = (i u; u): two fields per right-hand side
+            u = torch.empty((nrhs, 2 * self.n), dtype=torch.complex128,
+                            device=f.device) if out is None else out
+        else:
+            u = torch.empty_like(f) if out is None else out
+        up, _ = _dev_ptr(u, torch.complex128, self.n * (2 if self.case_two else 1))
         opts = HzSolveOpts(int(restart), int(inner_k), float(rtol), int(max_cycles),
                            int(precision), int(fixed_its))
         st = (HzSolveStats * max(nrhs, 1))()

@@ -556,3 +556,70 @@ def test_native_kernels_launch():
         P.apply_shifted(torch.ones(1, P.n, dtype=torch.complex128, device=DEV))
         torch.cuda.synchronize()
     assert hzpkg.launch_count() > before
+
+
+# ---------------------------------------------------------------------------------- Case Two
+def case_two_problem(wl, nrhs_max=1, restart_max=10, inner_k_max=3):
+    return hzpkg.Problem(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, wl.J, wl.t, wl.eps,
+                         nrhs_max=nrhs_max, restart_max=restart_max, inner_k_max=inner_k_max,
+                         flags=hzpkg.HZ_LIMIT_CASE_TWO)
+
+
+@pytest.mark.parametrize("shape,layer", [((13, 9, 7), 2), ((32, 32, 32), 8)])
+def test_case_two_nodes_and_fci_match_oracle(shape, layer):
+    """Case Two (eq:mat-2x2): the contour and polynomial parameters from the rectangle of the
+    Remark after Theorem thm:spectrum-2x2 equal the oracle's setup_nodes_2x2, and FCI on iC - I
+    (Algorithm 1 with the scheme eq:fix-pt-exp on the 2n-point fields) equals the oracle's on
+    the same input: 1e-11 relative (float64)."""
+    wl = W.small_case(11, *shape, layer=layer, J=4) if shape[0] != 32 else W.point_source_32()
+    op = O.make_operator(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max)
+    _, nodes = O.setup_nodes_2x2(op, wl.J, wl.t, wl.eps)
+    with case_two_problem(wl, nrhs_max=2, inner_k_max=4) as P:
+        tb = P.nodes()
+        assert list(tb["q"]) == [nd.q for nd in nodes]
+        assert list(tb["sweeps"]) == [nd.sweeps for nd in nodes]
+        assert np.allclose(tb["z"], [nd.z for nd in nodes], rtol=1e-12, atol=1e-14)
+        assert np.allclose(tb["delta"], [nd.delta for nd in nodes], rtol=1e-7)
+        r = W.random_field(13, 2, wl.nx, wl.ny, 2 * wl.nz)  # two stacked fields per vector
+        out = to_np(P.fci(to_dev(r.reshape(2, -1)), inner_k=4)).reshape(2, -1)
+    op2 = O.Operator2x2(op)
+    for v in range(2):
+        ref = O.fci(op2, r[v].reshape(op2.shape), nodes, 4)
+        assert rel(out[v], ref) <= 1e-11
+
+
+def test_case_two_solve_fixed_steps_match_oracle():
+    """FGMRES(5) with FCI on iC - I across two restarts equals the oracle's solve_2x2 at a
+    fixed step count (iterates Y, float64)."""
+    wl = W.small_case(3, 13, 9, 7, layer=2, J=4)
+    op = O.make_operator(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max)
+    _, nodes = O.setup_nodes_2x2(op, wl.J, wl.t, wl.eps)
+    res = O.solve_2x2(op, op.s * wl.f[0], nodes, m=5, k_in=3, rtol=1e-30, max_cycles=100,
+                      fixed_its=12)
+    with case_two_problem(wl, restart_max=5) as P:
+        Y, st = P.solve(to_dev(wl.f.reshape(1, -1)), restart=5, inner_k=3, rtol=1e-30,
+                        max_cycles=100, fixed_its=12)
+    assert st[0].its == 12 and st[0].cycles == res.cycles
+    assert rel(to_np(Y)[0], res.u) <= 1e-9
+    assert st[0].rel_res_true == pytest.approx(res.rel_res_true, rel=1e-6)
+
+
+def test_case_two_solves_point_source_32():
+    """Case Two on the 32^3 point source to 1e-8: the 2x2 residual of the returned Y, from the
+    oracle's Operator2x2, equals the reported one; Y's halves satisfy Y1 = i Y2 and Case One's
+    residual of u = Y2 is reported (it is bounded by the 2x2 residual times the coupling)."""
+    wl = W.point_source_32()
+    op = O.make_operator(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max)
+    op2 = O.Operator2x2(op)
+    with case_two_problem(wl, restart_max=wl.restart, inner_k_max=wl.k_in) as P:
+        Y, st = P.solve(to_dev(wl.f.reshape(1, -1)), restart=wl.restart, inner_k=wl.k_in,
+                        rtol=1e-8, max_cycles=40)
+    assert st[0].converged
+    Yn = to_np(Y)[0].reshape(op2.shape)
+    F = np.stack([np.zeros(op.shape, dtype=np.complex128), op.s * wl.f[0]])
+    res2 = np.linalg.norm(F - op2.apply(Yn)) / np.linalg.norm(F)
+    assert res2 <= 1e-8 + 1e-12 and abs(res2 - st[0].rel_res_true) <= 1e-10
+    res1 = np.linalg.norm(op.s * wl.f[0] - op.apply(Yn[1])) / np.linalg.norm(op.s * wl.f[0])
+    print(f"Case Two 32^3: {st[0].its} steps, 2x2 residual {res2:.2e}, Case One residual of "
+          f"u = Y2 {res1:.2e}")
+    assert res1 <= 1e-6
