@@ -411,17 +411,85 @@ def gmres_cycle(apply, b: np.ndarray, k: int, breakdown: float = 1e-14):
 
 
 # ---------------------------------------------------------------------------------------
+# ILU(0) of the 7-point Laplacian: the inner preconditioner of §6.3 (used for the finite-
+# difference runs of §7.3)
+# ---------------------------------------------------------------------------------------
+
+def ilu0_pivots(nx: int, ny: int, nz: int, cs: float) -> np.ndarray:
+    """Pivots d of the incomplete LU factorisation without fill of K = cs * (7-point stencil:
+    6 on the diagonal, -1 for each neighbour inside the grid), natural order (x fastest).
+
+    For the 7-point pattern the product of the factors only adds entries outside the pattern
+    besides the diagonal, so ILU(0) is M = (D + L) D^{-1} (D + U) with L, U the strict lower
+    and upper parts of K and d_p = K_pp - sum over the lower neighbours q of K_pq K_qp / d_q.
+    The recursion runs point by point in natural order (plain loops)."""
+    d = np.zeros((nz, ny, nx))
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                v = 6.0 * cs
+                if i > 0:
+                    v -= cs * cs / d[k, j, i - 1]
+                if j > 0:
+                    v -= cs * cs / d[k, j - 1, i]
+                if k > 0:
+                    v -= cs * cs / d[k - 1, j, i]
+                d[k, j, i] = v
+    return d
+
+
+def ilu0_apply(d: np.ndarray, cs: float, t: np.ndarray) -> np.ndarray:
+    """z = M^{-1} t for M = (D + L) D^{-1} (D + U) of ilu0_pivots: (D + L) u = t forward, then
+    (D + U) z = D u backward, i.e. u_p = (t_p + cs * sum of u over the lower neighbours) / d_p
+    and z_p = u_p + (cs / d_p) * sum of z over the upper neighbours.  Each value depends only
+    on earlier (later) points, so the sweeps take the hyperplanes i + j + k = const in turn,
+    vectorised over each plane, which gives the same values as the point-by-point order."""
+    nz, ny, nx = d.shape
+    t = np.asarray(t, dtype=np.complex128).reshape(nz, ny, nx)
+    K, J, I = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    S = I + J + K
+    planes = [np.nonzero(S.ravel() == w)[0] for w in range(nx + ny + nz - 2)]
+    u = np.zeros(nz * ny * nx, dtype=np.complex128)
+    z = np.zeros_like(u)
+    tf, df = t.ravel(), d.ravel()
+    Ii, Jj, Kk = I.ravel(), J.ravel(), K.ravel()
+    sy, sz = nx, nx * ny
+    for pts in planes:
+        acc = tf[pts].copy()
+        for off, ok in ((1, Ii[pts] > 0), (sy, Jj[pts] > 0), (sz, Kk[pts] > 0)):
+            q = pts[ok]
+            acc[ok] += cs * u[q - off]
+        u[pts] = acc / df[pts]
+    for pts in reversed(planes):
+        acc = np.zeros(len(pts), dtype=np.complex128)
+        for off, ok in ((1, Ii[pts] < nx - 1), (sy, Jj[pts] < ny - 1), (sz, Kk[pts] < nz - 1)):
+            q = pts[ok]
+            acc[ok] += z[q + off]
+        z[pts] = u[pts] + (cs / df[pts]) * acc
+    return z.reshape(nz, ny, nx)
+
+
+def ilu0_preconditioner(op: Operator):
+    """M^{-1} for the normalised operator's Laplacian part s L_h (weight cs = s / h^2)."""
+    cs = op.s / (op.h * op.h)
+    d = ilu0_pivots(op.nx, op.ny, op.nz, cs)
+    return lambda t: ilu0_apply(d, cs, t)
+
+
+# ---------------------------------------------------------------------------------------
 # FCI (§2, Algorithm 1) and flexible GMRES around it
 # ---------------------------------------------------------------------------------------
 
-def fci(op: Operator, r: np.ndarray, nodes: list, k_in: int, shifted_solve=None):
+def fci(op: Operator, r: np.ndarray, nodes: list, k_in: int, shifted_solve=None,
+        inner_precond=None):
     """Algorithm 1 applied to r:
 
     1. y_j = (A - z_j I)^{-1} r, here by the polynomial scheme with the node's sweeps
        (``shifted_solve(node, r)`` may replace it, e.g. by an exact solve in tests);
     2. w = sum_j sigma_j / z_j y_j;
     3. d = argmin_d ||r - d A w|| = (Aw)^H r / ||Aw||^2;
-    4. v from k_in GMRES steps on A v = r - d A w (x0 = 0);
+    4. v from k_in GMRES steps on A v = r - d A w (x0 = 0); with ``inner_precond`` (a map t ->
+       M^{-1} t, §6.3) the GMRES runs right-preconditioned on A M^{-1} and v = M^{-1} x;
     5. return v + d w.
     """
     r = np.asarray(r, dtype=np.complex128).reshape(op.shape)
@@ -433,7 +501,11 @@ def fci(op: Operator, r: np.ndarray, nodes: list, k_in: int, shifted_solve=None)
     den = np.vdot(Aw, Aw)
     d = np.vdot(Aw, r) / den if den != 0 else 0.0
     g = r - d * Aw
-    v, _ = gmres_cycle(op.apply, g, k_in)
+    if inner_precond is None:
+        v, _ = gmres_cycle(op.apply, g, k_in)
+    else:
+        x, _ = gmres_cycle(lambda q: op.apply(inner_precond(q)), g, k_in)
+        v = inner_precond(x)
     return v + d * w
 
 
@@ -509,9 +581,10 @@ def fgmres(op: Operator, f: np.ndarray, precond, m: int, rtol: float, max_cycles
 
 
 def solve(op: Operator, f: np.ndarray, nodes: list, m: int, k_in: int, rtol: float,
-          max_cycles: int, fixed_its: int = 0) -> SolveResult:
+          max_cycles: int, fixed_its: int = 0, inner_precond=None) -> SolveResult:
     """A u = f by FGMRES(m) preconditioned with FCI (Algorithm 1)."""
-    return fgmres(op, f, lambda v: fci(op, v, nodes, k_in), m, rtol, max_cycles, fixed_its)
+    return fgmres(op, f, lambda v: fci(op, v, nodes, k_in, inner_precond=inner_precond), m,
+                  rtol, max_cycles, fixed_its)
 
 
 # ---------------------------------------------------------------------------------------

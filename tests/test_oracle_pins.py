@@ -637,3 +637,69 @@ def test_case_two_fgmres_matches_dense_lu():
     bound = kappa * 1e-8 * math.sqrt(2.0)
     assert np.linalg.norm(Y[1] - u) <= bound * np.linalg.norm(u)
     assert np.linalg.norm(Y[0] - 1j * u) <= bound * np.linalg.norm(u)
+
+
+# ------------------------------------------------------------------ ILU(0) (§6.3, §7.3)
+def _laplacian_dense(nx, ny, nz, cs):
+    """cs * (6 on the diagonal, -1 per neighbour) as a dense matrix, by its definition."""
+    n = nx * ny * nz
+    K = np.zeros((n, n))
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                p = i + nx * (j + ny * k)
+                K[p, p] = 6.0 * cs
+                for di, dj, dk in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1),
+                                   (0, 0, -1)):
+                    ii, jj, kk = i + di, j + dj, k + dk
+                    if 0 <= ii < nx and 0 <= jj < ny and 0 <= kk < nz:
+                        K[p, ii + nx * (jj + ny * kk)] = -cs
+    return K
+
+
+def test_ilu0_factors_reproduce_the_matrix_on_its_pattern():
+    """ILU(0)'s defining property: the product of the factors equals K at every entry of K's
+    sparsity pattern (diagonal included), and M^{-1} of ilu0_apply inverts that product."""
+    nx, ny, nz, cs = 4, 3, 5, 2.5
+    K = _laplacian_dense(nx, ny, nz, cs)
+    d = O.ilu0_pivots(nx, ny, nz, cs).ravel()
+    Lo, Up = np.tril(K, -1), np.triu(K, 1)
+    M = (np.diag(d) + Lo) @ np.diag(1.0 / d) @ (np.diag(d) + Up)
+    pattern = K != 0
+    assert np.allclose(M[pattern], K[pattern], rtol=1e-12, atol=1e-12)
+    assert np.any(np.abs(M[~pattern]) > 1e-3)  # the dropped fill is real
+    rng = np.random.Generator(np.random.PCG64(3))
+    t = rng.standard_normal(K.shape[0]) + 1j * rng.standard_normal(K.shape[0])
+    z = O.ilu0_apply(d.reshape(nz, ny, nx), cs, t).ravel()
+    assert np.allclose(M @ z, t, rtol=1e-12, atol=1e-12)
+
+
+def test_ilu0_preconditioned_inner_gmres_is_the_least_squares_minimiser():
+    """Algorithm 1 step 4 with the inner preconditioner: v = M^{-1} x, x minimising
+    ||g - A M^{-1} x|| over the Krylov space of A M^{-1} (brute force on a tiny grid)."""
+    wl = W.small_case(2, 5, 4, 3, layer=1, J=2)
+    op = O.make_operator(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max)
+    Minv = O.ilu0_preconditioner(op)
+    n = op.n
+    A = np.column_stack([op.apply(e.reshape(op.shape)).ravel() for e in np.eye(n)])
+    P = np.column_stack([Minv(e.reshape(op.shape)).ravel() for e in np.eye(n)])
+    g = wl.f[0].ravel()
+    k = 3
+    B = A @ P
+    Kr = np.column_stack([np.linalg.matrix_power(B, i) @ g for i in range(k)])
+    c, *_ = np.linalg.lstsq(B @ Kr, g, rcond=None)
+    x_ls = Kr @ c
+    x, _ = O.gmres_cycle(lambda q: op.apply(Minv(q)), g.reshape(op.shape), k)
+    assert np.linalg.norm(x.ravel() - x_ls) <= 1e-9 * np.linalg.norm(x_ls)
+    # fci with the preconditioner returns M^{-1} x + d w with x that minimiser for its own g
+    _, nodes = O.setup_nodes(op, 2, 1.0, 1.0)
+    r = wl.f[0].ravel()
+    w = sum((nd.sigma / nd.z) * O.poly_solve(op, r.reshape(op.shape), nd).ravel() for nd in nodes)
+    Aw = A @ w
+    d = np.vdot(Aw, r) / np.vdot(Aw, Aw)
+    gg = r - d * Aw
+    Kg = np.column_stack([np.linalg.matrix_power(B, i) @ gg for i in range(k)])
+    cg, *_ = np.linalg.lstsq(B @ Kg, gg, rcond=None)
+    expect = P @ (Kg @ cg) + d * w
+    out = O.fci(op, r.reshape(op.shape), nodes, k, inner_precond=Minv).ravel()
+    assert np.linalg.norm(out - expect) <= 1e-9 * np.linalg.norm(expect)
