@@ -265,6 +265,21 @@ hz_status hz_solve_batched(hz_problem* const* probs, int nprob, const void* cons
  * kernels add none) since the last enable; any output pointer may be null. */
 hz_status hz_profile_enable(hz_problem* p, int on);
 
+/* ILU(0) of the 7-point discrete Laplacian (Section 6.3, used for the finite-difference runs of
+ * Section 7.3) as the right preconditioner of the inner GMRES of FCI (Algorithm 1 step 4):
+ * the inner GMRES minimises ||g - A M^{-1} x|| and returns v = M^{-1} x.  M = (D + L) D^{-1}
+ * (D + U) is the incomplete factorisation without fill of the normalised operator's Laplacian
+ * part s L_h in natural order (x fastest): L, U its strict lower and upper parts, d_p =
+ * 6 s/h^2 - (s/h^2)^2 * (sum of 1/d_q over the lower neighbours q).  on != 0 enables it (the
+ * first time it computes the pivots on the host and allocates one float64 field per
+ * right-hand side); it applies to the float64 inner GMRES of HZ_C128 and HZ_MIXED_C64, and
+ * hz_solve / hz_fci refuse the complex64-FCI forms while it is on.  Case One problems only. */
+hz_status hz_problem_set_inner_ilu(hz_problem* p, int on);
+
+/* z = M^{-1} t with the ILU(0) factors above, for nvec double-complex fields of n points
+ * (device; t and z must not overlap).  Needs hz_problem_set_inner_ilu(p, 1).  Asynchronous. */
+hz_status hz_ilu0_apply(hz_problem* p, const void* t, void* z, int nvec, void* stream);
+
 /* Poll limit of the grid-wide barriers inside the cooperative kernels (hz_problem_fused_tail,
  * hz_problem_fused_arnoldi): a block polls the barrier at most `polls` times (back to back,
  * then about 32 ns apart) before it gives up; polls < 0 restores the default (2^23, about a

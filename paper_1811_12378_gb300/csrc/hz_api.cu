@@ -88,6 +88,9 @@ struct hz_problem {
   double2* Z = nullptr;      // [nrhs][m][n] preconditioned directions (float64)
   float2* Z32 = nullptr;     // [nrhs][m][n] the same stored in complex64 (HZ_LIMIT_Z_C64)
   bool case2 = false;        // HZ_LIMIT_CASE_TWO: the solver runs on iC - I (eq:mat-2x2)
+  bool ilu_on = false;       // hz_problem_set_inner_ilu: ILU(0) right-preconditions inner GMRES
+  double* invd = nullptr;    // [n] 1 / ILU(0) pivots
+  double2* ilu_t = nullptr;  // [nrhs][n] scratch field of the preconditioned inner GMRES
   long long nf = 0;          // points of a solver field: n, or 2n for Case Two
   bool z32 = false;          // HZ_LIMIT_Z_C64
   bool sweeps32 = false;     // HZ_LIMIT_SWEEPS_C64
@@ -501,7 +504,7 @@ constexpr long long kCoop64MaxPoints = 1LL << 17;
 
 bool tail64_fits(const hz_problem* p, int nvec, int kin) {
   return p->tail_mode != 0 && p->tail_solo && nvec == 1 && kin <= hz::TAIL64_KMAX &&
-         p->t64_ppt > 0 && p->g.n <= kCoop64MaxPoints;
+         p->t64_ppt > 0 && p->g.n <= kCoop64MaxPoints && !p->ilu_on;
 }
 
 bool arnoldi64_fits(const hz_problem* p, int nvec) {
@@ -617,10 +620,17 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
                                  p->gin, p->partial, p->counters, n, nvec, st));
   HZ_CUDA(hz::launch_scale(Buf<double2>{p->Vin, vrs}, Buf<const double2>{p->Vin, vrs}, n, p->gin,
                            nvec, st));
+  // with ILU(0) (Section 6.3) the inner GMRES runs right-preconditioned on A M^{-1}
+  const bool ilu = p->ilu_on;
   for (int j = 0; j < kin; ++j) {
     Buf<double2> wj{p->Vin + (long long)(j + 1) * n, vrs};
+    Buf<const double2> src{p->Vin + (long long)j * n, vrs};
+    if (ilu) {
+      HZ_CUDA(hz::launch_ilu0(p->g, p->invd, src, Buf<double2>{p->ilu_t, n}, nvec, st));
+      src = Buf<const double2>{p->ilu_t, n};
+    }
     HZ_TIMED_F(p, 1, st, (stencil_bytes<double2, double2>(n, nvec)), kStencil64Flops * n * nvec,
-               apply_op64(p, Buf<const double2>{p->Vin + (long long)j * n, vrs}, wj, nvec, st));
+               apply_op64(p, src, wj, nvec, st));
     for (int mode = 0; mode < 3; ++mode)
       HZ_TIMED_F(p, 2, st, cgs_bytes(mode, n, j + 1, nvec), cgs_flops(mode, n, j + 1, nvec),
                  hz::launch_cgs(mode, p->Vin, n, vrs, j + 1, wj, n, p->gin, p->partial,
@@ -628,6 +638,14 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
     HZ_CUDA(hz::launch_scale(wj, Buf<const double2>{wj.p, vrs}, n, p->gin, nvec, st));
   }
   HZ_CUDA(hz::launch_backsolve(p->gin, nvec, st));
+  if (ilu) {
+    // out = M^{-1} (V y) + d w
+    HZ_CUDA(hz::launch_combine(Buf<double2>{p->ilu_t, n}, p->Vin, n, vrs, p->gin,
+                               Buf<const double2>{nullptr, 0}, -1, 0, n, nvec, kin, st));
+    HZ_CUDA(hz::launch_ilu0(p->g, p->invd, Buf<const double2>{p->ilu_t, n}, out, nvec, st));
+    HZ_CUDA(hz::launch_add_dw(out, Buf<const double2>{p->w, n}, n, p->gin, nvec, st));
+    return HZ_OK;
+  }
   HZ_CUDA(hz::launch_combine(out, p->Vin, n, vrs, p->gin, Buf<const double2>{p->w, n}, 0, 0, n,
                              nvec, kin, st));
   return HZ_OK;
@@ -977,6 +995,9 @@ hz_status check_solve_args(const hz_problem* p, int nrhs, const hz_solve_opts* o
                                 "HZ_MIXED_C64_FCI32 only");
   if (p->case2 && opts->precision != HZ_C128)
     return fail(HZ_ERR_INVALID, "Case Two problems solve in HZ_C128");
+  if (p->ilu_on && opts->precision != HZ_C128 && opts->precision != HZ_MIXED_C64)
+    return fail(HZ_ERR_INVALID, "ILU(0) preconditions the float64 inner GMRES (HZ_C128, "
+                                "HZ_MIXED_C64)");
   if (p->net_mode != 0 && opts->precision == HZ_MIXED_C64_FF)
     return fail(HZ_ERR_INVALID, "the learned preconditioner needs a float64 outer basis");
   if (p->net_mode != 0 && !hz::net_fits(p->net, nrhs, p->g.nx, p->g.ny, p->g.nz))
@@ -1323,6 +1344,36 @@ hz_status hz_problem_set_preconditioner(hz_problem* p, hz_net* net, int mode) {
   return HZ_OK;
 }
 
+hz_status hz_problem_set_inner_ilu(hz_problem* p, int on) {
+  HZ_TRY(check_problem(p));
+  if (on && p->case2) return fail(HZ_ERR_INVALID, "ILU(0) applies to Case One problems");
+  HZ_TRY(set_device(p));
+  if (on && !p->invd) {
+    std::vector<double> invd;
+    hz::ilu0_inverse_pivots(p->g.nx, p->g.ny, p->g.nz, p->g.cs, invd);
+    HZ_TRY(dalloc(p, (void**)&p->invd, sizeof(double) * invd.size()));
+    HZ_TRY(dalloc(p, (void**)&p->ilu_t, sizeof(double2) * (size_t)p->nf * p->lim.nrhs_max));
+    HZ_CUDA(cudaMemcpy(p->invd, invd.data(), sizeof(double) * invd.size(),
+                       cudaMemcpyHostToDevice));
+  }
+  if ((on != 0) != p->ilu_on) p->drop_graphs();
+  p->ilu_on = on != 0;
+  return HZ_OK;
+}
+
+hz_status hz_ilu0_apply(hz_problem* p, const void* t, void* z, int nvec, void* stream) {
+  HZ_TRY(check_problem(p));
+  if (!p->ilu_on) return fail(HZ_ERR_INVALID, "enable ILU(0) with hz_problem_set_inner_ilu first");
+  if (nvec < 0 || nvec > 65535) return fail(HZ_ERR_INVALID, "nvec out of range");
+  if (nvec == 0) return HZ_OK;
+  if (!t || !z || t == z) return fail(HZ_ERR_INVALID, "null or overlapping fields");
+  HZ_TRY(set_device(p));
+  const long long n = p->g.n;
+  HZ_CUDA(hz::launch_ilu0(p->g, p->invd, Buf<const double2>{(const double2*)t, n},
+                          Buf<double2>{(double2*)z, n}, nvec, (cudaStream_t)stream));
+  return HZ_OK;
+}
+
 hz_status hz_net_train_fields(hz_net* net, hz_problem* p, const void* r, const void* e, int nvec,
                               float lr, double* loss, void* stream) {
   HZ_TRY(check_problem(p));
@@ -1538,6 +1589,9 @@ hz_status hz_fci(hz_problem* p, const void* r, void* out, int nvec, int inner_k,
     return fail(HZ_ERR_INVALID, "HZ_C128 needs a problem created without HZ_LIMIT_SWEEPS_C64");
   if (p->case2 && precision != HZ_C128)
     return fail(HZ_ERR_INVALID, "Case Two problems solve in HZ_C128");
+  if (p->ilu_on && precision != HZ_C128 && precision != HZ_MIXED_C64)
+    return fail(HZ_ERR_INVALID, "ILU(0) preconditions the float64 inner GMRES (HZ_C128, "
+                                "HZ_MIXED_C64)");
   if (nvec == 0) return HZ_OK;
   if (!r || !out) return fail(HZ_ERR_INVALID, "null field");
   HZ_TRY(set_device(p));

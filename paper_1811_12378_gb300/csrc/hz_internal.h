@@ -260,6 +260,16 @@ cudaError_t launch_fci_tail64(const Geom& g, const double2* dg, const double2* w
                               double2* partial, unsigned* bar, int* err, long long n, int kin,
                               double brk, int pyth, int ppt, int blocks, cudaStream_t st);
 
+// ---- ILU(0) of the 7-point Laplacian, the inner GMRES's right preconditioner (hz_ilu.cu)
+// 1 / d_p of M = (D + L) D^{-1} (D + U), K = cs * (7-point stencil), natural order (host).
+void ilu0_inverse_pivots(int nx, int ny, int nz, double cs, std::vector<double>& invd);
+// z = M^{-1} t for nvec fields (t and z must not overlap).
+cudaError_t launch_ilu0(const Geom& g, const double* invd, Buf<const double2> t, Buf<double2> z,
+                        int nvec, cudaStream_t st);
+// out += d w, d = the FCI step size of each right-hand side (gs.scal).
+cudaError_t launch_add_dw(Buf<double2> out, Buf<const double2> w, long long n, const GmresDev& gs,
+                          int nvec, cudaStream_t st);
+
 // y = R^{-1} g in float32 for the complex64 FCI form's inner GMRES (GmresDev storage float64).
 cudaError_t launch_backsolve32(const GmresDev& gs, int nvec, cudaStream_t st);
 

@@ -31,7 +31,8 @@ EXPORTS = ["hz_problem_create", "hz_plan", "hz_problem_destroy", "hz_problem_get
            "hz_residual_noalloc", "hz_net_param_count", "hz_net_create", "hz_net_destroy",
            "hz_net_set_params", "hz_net_get_params", "hz_net_forward", "hz_net_train_step",
            "hz_net_train_fields", "hz_problem_set_preconditioner", "hz_conv3d",
-           "hz_conv3d_backward", "hz_conv3d_workspace_bytes",
+           "hz_conv3d_backward", "hz_conv3d_workspace_bytes", "hz_problem_set_inner_ilu",
+           "hz_ilu0_apply",
            "hz_status_string", "hz_last_error", "hz_launch_count"]
 
 # kernel classes of hz_profile_read
@@ -137,6 +138,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                                       dp, P]
     lib.hz_net_train_fields.argtypes = [P, P, P, P, C.c_int, C.c_float, dp, P]
     lib.hz_problem_set_preconditioner.argtypes = [P, P, C.c_int]
+    lib.hz_problem_set_inner_ilu.argtypes = [P, C.c_int]
+    lib.hz_ilu0_apply.argtypes = [P, P, P, C.c_int, P]
     lib.hz_conv3d.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P, C.c_int,
                               C.c_int, P, P, P]
     lib.hz_conv3d_backward.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P,
@@ -310,6 +313,19 @@ class Problem:
         residual; 3 FCI then the network on its residual (hz_problem_set_preconditioner)."""
         _check(self._lib.hz_problem_set_preconditioner(
             self._h, net._h if net is not None else None, int(mode)), self._lib)
+
+    def set_inner_ilu(self, on: bool = True):
+        """ILU(0) of the 7-point Laplacian as the inner GMRES's right preconditioner."""
+        _check(self._lib.hz_problem_set_inner_ilu(self._h, 1 if on else 0), self._lib)
+
+    def ilu0_apply(self, t, out=None, stream=None):
+        """z = M^{-1} t with the ILU(0) factors (complex128 fields of the grid)."""
+        import torch
+        tp, nvec = _dev_ptr(t, torch.complex128, self.n)
+        z = torch.empty_like(t) if out is None else out
+        zp, _ = _dev_ptr(z, torch.complex128, self.n)
+        _check(self._lib.hz_ilu0_apply(self._h, tp, zp, nvec, _stream(stream)), self._lib)
+        return z
 
     def set_spin_limit(self, polls: int = -1):
         """Poll limit of the cooperative kernels' grid barriers (-1: the default, ~1 s)."""
