@@ -1349,6 +1349,7 @@ hz_status hz_problem_set_inner_ilu(hz_problem* p, int on) {
   if (on && p->case2) return fail(HZ_ERR_INVALID, "ILU(0) applies to Case One problems");
   HZ_TRY(set_device(p));
   if (on && !p->invd) {
+    HZ_CUDA(hz::ilu0_prepare());
     std::vector<double> invd;
     hz::ilu0_inverse_pivots(p->g.nx, p->g.ny, p->g.nz, p->g.cs, invd);
     HZ_TRY(dalloc(p, (void**)&p->invd, sizeof(double) * invd.size()));

@@ -68,6 +68,71 @@ __global__ void __launch_bounds__(IT) k_ilu0_apply(Geom g, const double* __restr
   }
 }
 
+// The same sweeps with each (j, k) line's latest value held in shared memory: the three
+// neighbours a point needs from the previous hyperplane are the previous values of its own
+// line and of lines (j - 1, k) and (j, k - 1) (upper sweep: j + 1, k + 1), so a hyperplane
+// step reads only shared memory besides its own t, 1/d (and u) values, which do not depend on
+// the recurrence and are loaded ahead.  Two buffers alternate by hyperplane parity, since a
+// line is overwritten in the same step in which its neighbour lines read its previous value.
+__global__ void __launch_bounds__(IT) k_ilu0_apply_smem(Geom g, const double* __restrict__ invd,
+                                                        double cs,
+                                                        const double2* __restrict__ t,
+                                                        long long trs, double2* z,
+                                                        long long zrs) {
+  pdl_enter();
+  extern __shared__ double2 lv[];  // [2][ny * nz]
+  const int r = blockIdx.x;
+  const double2* tr = t + r * trs;
+  double2* zr = z + r * zrs;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const long long sy = nx, sz = (long long)nx * ny;
+  const int W = nx + ny + nz - 2;
+  const int lines = ny * nz;
+  double2* buf[2] = {lv, lv + lines};
+  // forward: u_p = (t_p + cs (u_{i-1} + u_{j-1} + u_{k-1})) / d_p
+  for (int w = 0; w < W; ++w) {
+    const double2* old = buf[(w + 1) & 1];
+    double2* cur = buf[w & 1];
+    for (int l = threadIdx.x; l < lines; l += IT) {
+      const int j = l % ny, k = l / ny, i = w - j - k;
+      if (i < 0 || i >= nx) continue;
+      const long long p = i + sy * j + sz * k;
+      const double2 tv = tr[p];
+      const double iv = invd[p];
+      double2 acc = make_double2(0.0, 0.0);
+      if (i > 0) acc = cadd(acc, old[l]);
+      if (j > 0) acc = cadd(acc, old[l - 1]);
+      if (k > 0) acc = cadd(acc, old[l - ny]);
+      const double2 u = make_double2((tv.x + cs * acc.x) * iv, (tv.y + cs * acc.y) * iv);
+      cur[l] = u;
+      zr[p] = u;
+    }
+    __syncthreads();
+  }
+  // backward: z_p = u_p + cs / d_p (z_{i+1} + z_{j+1} + z_{k+1}), each thread on its own lines
+  for (int w = W - 1; w >= 0; --w) {
+    const double2* old = buf[(w + 1) & 1];
+    double2* cur = buf[w & 1];
+    for (int l = threadIdx.x; l < lines; l += IT) {
+      const int j = l % ny, k = l / ny, i = w - j - k;
+      if (i < 0 || i >= nx) continue;
+      const long long p = i + sy * j + sz * k;
+      const double2 u = zr[p];
+      const double f = cs * invd[p];
+      double2 acc = make_double2(0.0, 0.0);
+      if (i < nx - 1) acc = cadd(acc, old[l]);
+      if (j < ny - 1) acc = cadd(acc, old[l + 1]);
+      if (k < nz - 1) acc = cadd(acc, old[l + ny]);
+      const double2 zv = make_double2(u.x + f * acc.x, u.y + f * acc.y);
+      cur[l] = zv;
+      zr[p] = zv;
+    }
+    __syncthreads();
+  }
+}
+
+constexpr size_t kIluSmemMax = 200 * 1024;
+
 // out[r] += d[r] w[r], d the FCI step size in the inner GMRES state
 __global__ void k_add_dw(double2* __restrict__ out, long long ors, const double2* __restrict__ w,
                          long long wrs, long long n, GmresDev gs) {
@@ -81,6 +146,11 @@ __global__ void k_add_dw(double2* __restrict__ out, long long ors, const double2
 }
 
 }  // namespace
+
+cudaError_t ilu0_prepare() {
+  return cudaFuncSetAttribute(k_ilu0_apply_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kIluSmemMax);
+}
 
 void ilu0_inverse_pivots(int nx, int ny, int nz, double cs, std::vector<double>& invd) {
   const long long n = (long long)nx * ny * nz;
@@ -104,6 +174,11 @@ cudaError_t launch_ilu0(const Geom& g, const double* invd, Buf<const double2> t,
                         int nvec, cudaStream_t st) {
   if (nvec < 1 || nvec > 65535) return cudaErrorInvalidValue;
   count_launch();
+  const size_t smem = 2 * sizeof(double2) * (size_t)g.ny * g.nz;
+  if (smem <= kIluSmemMax) {
+    return launch_pdl(k_ilu0_apply_smem, dim3(nvec), dim3(IT), smem, st, g, invd, g.cs, t.p,
+                      t.rs, z.p, z.rs);
+  }
   return launch_pdl(k_ilu0_apply, dim3(nvec), dim3(IT), 0, st, g, invd, g.cs, t.p, t.rs, z.p,
                     z.rs);
 }

@@ -263,6 +263,8 @@ cudaError_t launch_fci_tail64(const Geom& g, const double2* dg, const double2* w
 // ---- ILU(0) of the 7-point Laplacian, the inner GMRES's right preconditioner (hz_ilu.cu)
 // 1 / d_p of M = (D + L) D^{-1} (D + U), K = cs * (7-point stencil), natural order (host).
 void ilu0_inverse_pivots(int nx, int ny, int nz, double cs, std::vector<double>& invd);
+// Kernel attributes of the sweeps (once, outside any stream capture).
+cudaError_t ilu0_prepare();
 // z = M^{-1} t for nvec fields (t and z must not overlap).
 cudaError_t launch_ilu0(const Geom& g, const double* invd, Buf<const double2> t, Buf<double2> z,
                         int nvec, cudaStream_t st);
