@@ -90,6 +90,8 @@ struct hz_problem {
   bool case2 = false;        // HZ_LIMIT_CASE_TWO: the solver runs on iC - I (eq:mat-2x2)
   bool ilu_on = false;       // hz_problem_set_inner_ilu: ILU(0) right-preconditions inner GMRES
   double* invd = nullptr;    // [n] 1 / ILU(0) pivots
+  float* invd32 = nullptr;   // [n] the same in float32 (the sweeps of HZ_MIXED_C64)
+  float2* ilu_u32 = nullptr; // [nrhs][n] complex64 scratch of those sweeps
   double2* ilu_t = nullptr;  // [nrhs][n] scratch field of the preconditioned inner GMRES
   long long nf = 0;          // points of a solver field: n, or 2n for Case Two
   bool z32 = false;          // HZ_LIMIT_Z_C64
@@ -620,13 +622,21 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
                                  p->gin, p->partial, p->counters, n, nvec, st));
   HZ_CUDA(hz::launch_scale(Buf<double2>{p->Vin, vrs}, Buf<const double2>{p->Vin, vrs}, n, p->gin,
                            nvec, st));
-  // with ILU(0) (Section 6.3) the inner GMRES runs right-preconditioned on A M^{-1}
+  // with ILU(0) (Section 6.3) the inner GMRES runs right-preconditioned on A M^{-1}; its sweeps
+  // in float32 arithmetic in the complex64-sweep form, float64 in the all-float64 form
   const bool ilu = p->ilu_on;
+  const bool ilu32 = ilu && precision == HZ_MIXED_C64 && hz::ilu0_fits32(p->g);
+  auto ilu_apply = [&](Buf<const double2> t, Buf<double2> z) -> cudaError_t {
+    if (ilu32)
+      return hz::launch_ilu0_32(p->g, p->invd32, t, Buf<float2>{p->ilu_u32, p->g.n}, z, nvec,
+                                st);
+    return hz::launch_ilu0(p->g, p->invd, t, z, nvec, st);
+  };
   for (int j = 0; j < kin; ++j) {
     Buf<double2> wj{p->Vin + (long long)(j + 1) * n, vrs};
     Buf<const double2> src{p->Vin + (long long)j * n, vrs};
     if (ilu) {
-      HZ_CUDA(hz::launch_ilu0(p->g, p->invd, src, Buf<double2>{p->ilu_t, n}, nvec, st));
+      HZ_CUDA(ilu_apply(src, Buf<double2>{p->ilu_t, n}));
       src = Buf<const double2>{p->ilu_t, n};
     }
     HZ_TIMED_F(p, 1, st, (stencil_bytes<double2, double2>(n, nvec)), kStencil64Flops * n * nvec,
@@ -642,7 +652,7 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
     // out = M^{-1} (V y) + d w
     HZ_CUDA(hz::launch_combine(Buf<double2>{p->ilu_t, n}, p->Vin, n, vrs, p->gin,
                                Buf<const double2>{nullptr, 0}, -1, 0, n, nvec, kin, st));
-    HZ_CUDA(hz::launch_ilu0(p->g, p->invd, Buf<const double2>{p->ilu_t, n}, out, nvec, st));
+    HZ_CUDA(ilu_apply(Buf<const double2>{p->ilu_t, n}, out));
     HZ_CUDA(hz::launch_add_dw(out, Buf<const double2>{p->w, n}, n, p->gin, nvec, st));
     return HZ_OK;
   }
@@ -1355,6 +1365,12 @@ hz_status hz_problem_set_inner_ilu(hz_problem* p, int on) {
     HZ_TRY(dalloc(p, (void**)&p->invd, sizeof(double) * invd.size()));
     HZ_TRY(dalloc(p, (void**)&p->ilu_t, sizeof(double2) * (size_t)p->nf * p->lim.nrhs_max));
     HZ_CUDA(cudaMemcpy(p->invd, invd.data(), sizeof(double) * invd.size(),
+                       cudaMemcpyHostToDevice));
+    std::vector<float> invd32(invd.size());
+    for (size_t q = 0; q < invd.size(); ++q) invd32[q] = float(invd[q]);
+    HZ_TRY(dalloc(p, (void**)&p->invd32, sizeof(float) * invd32.size()));
+    HZ_TRY(dalloc(p, (void**)&p->ilu_u32, sizeof(float2) * (size_t)p->g.n * p->lim.nrhs_max));
+    HZ_CUDA(cudaMemcpy(p->invd32, invd32.data(), sizeof(float) * invd32.size(),
                        cudaMemcpyHostToDevice));
   }
   if ((on != 0) != p->ilu_on) p->drop_graphs();

@@ -131,6 +131,69 @@ __global__ void __launch_bounds__(IT) k_ilu0_apply_smem(Geom g, const double* __
   }
 }
 
+// The sweeps in float32 arithmetic for the complex64-sweep form (HZ_MIXED_C64): the result is
+// a preconditioner application, like the complex64 polynomial sweeps, and one SM retires 64
+// times more float32 than float64 operations on GB300, which is what bounds a sweep run by a
+// single block.  t and z stay float64 fields (the inner basis is float64); the forward result
+// goes to a complex64 scratch field u.
+__global__ void __launch_bounds__(IT) k_ilu0_apply_smem32(Geom g, const float* __restrict__ invd,
+                                                          float cs,
+                                                          const double2* __restrict__ t,
+                                                          long long trs, float2* u32,
+                                                          long long urs, double2* z,
+                                                          long long zrs) {
+  pdl_enter();
+  extern __shared__ float2 lv32[];  // [2][ny * nz]
+  const int r = blockIdx.x;
+  const double2* tr = t + r * trs;
+  float2* ur = u32 + r * urs;
+  double2* zr = z + r * zrs;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const long long sy = nx, sz = (long long)nx * ny;
+  const int W = nx + ny + nz - 2;
+  const int lines = ny * nz;
+  float2* b0 = lv32;
+  float2* b1 = lv32 + lines;
+  for (int w = 0; w < W; ++w) {
+    const float2* old = (w & 1) ? b0 : b1;
+    float2* cur = (w & 1) ? b1 : b0;
+    for (int l = threadIdx.x; l < lines; l += IT) {
+      const int j = l % ny, k = l / ny, i = w - j - k;
+      if (i < 0 || i >= nx) continue;
+      const long long p = i + sy * j + sz * k;
+      const double2 tv = tr[p];
+      const float iv = invd[p];
+      float ax = 0.f, ay = 0.f;
+      if (i > 0) { ax += old[l].x; ay += old[l].y; }
+      if (j > 0) { ax += old[l - 1].x; ay += old[l - 1].y; }
+      if (k > 0) { ax += old[l - ny].x; ay += old[l - ny].y; }
+      const float2 u = make_float2((float(tv.x) + cs * ax) * iv, (float(tv.y) + cs * ay) * iv);
+      cur[l] = u;
+      ur[p] = u;
+    }
+    __syncthreads();
+  }
+  for (int w = W - 1; w >= 0; --w) {
+    const float2* old = (w & 1) ? b0 : b1;
+    float2* cur = (w & 1) ? b1 : b0;
+    for (int l = threadIdx.x; l < lines; l += IT) {
+      const int j = l % ny, k = l / ny, i = w - j - k;
+      if (i < 0 || i >= nx) continue;
+      const long long p = i + sy * j + sz * k;
+      const float2 u = ur[p];
+      const float f = cs * invd[p];
+      float ax = 0.f, ay = 0.f;
+      if (i < nx - 1) { ax += old[l].x; ay += old[l].y; }
+      if (j < ny - 1) { ax += old[l + 1].x; ay += old[l + 1].y; }
+      if (k < nz - 1) { ax += old[l + ny].x; ay += old[l + ny].y; }
+      const float2 zv = make_float2(u.x + f * ax, u.y + f * ay);
+      cur[l] = zv;
+      zr[p] = make_double2(double(zv.x), double(zv.y));
+    }
+    __syncthreads();
+  }
+}
+
 constexpr size_t kIluSmemMax = 200 * 1024;
 
 // out[r] += d[r] w[r], d the FCI step size in the inner GMRES state
@@ -148,8 +211,27 @@ __global__ void k_add_dw(double2* __restrict__ out, long long ors, const double2
 }  // namespace
 
 cudaError_t ilu0_prepare() {
-  return cudaFuncSetAttribute(k_ilu0_apply_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)kIluSmemMax);
+  cudaError_t e = cudaFuncSetAttribute(k_ilu0_apply_smem,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kIluSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ilu0_apply_smem32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kIluSmemMax);
+  return e;
+}
+
+cudaError_t launch_ilu0_32(const Geom& g, const float* invd32, Buf<const double2> t,
+                           Buf<float2> u32, Buf<double2> z, int nvec, cudaStream_t st) {
+  if (nvec < 1 || nvec > 65535) return cudaErrorInvalidValue;
+  const size_t smem = 2 * sizeof(float2) * (size_t)g.ny * g.nz;
+  if (smem > kIluSmemMax) return cudaErrorInvalidValue;
+  count_launch();
+  return launch_pdl(k_ilu0_apply_smem32, dim3(nvec), dim3(IT), smem, st, g, invd32,
+                    float(g.cs), t.p, t.rs, u32.p, u32.rs, z.p, z.rs);
+}
+
+bool ilu0_fits32(const Geom& g) {
+  return 2 * sizeof(float2) * (size_t)g.ny * g.nz <= kIluSmemMax;
 }
 
 void ilu0_inverse_pivots(int nx, int ny, int nz, double cs, std::vector<double>& invd) {

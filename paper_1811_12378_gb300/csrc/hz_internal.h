@@ -265,6 +265,11 @@ cudaError_t launch_fci_tail64(const Geom& g, const double2* dg, const double2* w
 void ilu0_inverse_pivots(int nx, int ny, int nz, double cs, std::vector<double>& invd);
 // Kernel attributes of the sweeps (once, outside any stream capture).
 cudaError_t ilu0_prepare();
+// The same in float32 arithmetic (float64 fields t and z, complex64 scratch u32), where the
+// y-z lines fit in shared memory (ilu0_fits32).
+cudaError_t launch_ilu0_32(const Geom& g, const float* invd32, Buf<const double2> t,
+                           Buf<float2> u32, Buf<double2> z, int nvec, cudaStream_t st);
+bool ilu0_fits32(const Geom& g);
 // z = M^{-1} t for nvec fields (t and z must not overlap).
 cudaError_t launch_ilu0(const Geom& g, const double* invd, Buf<const double2> t, Buf<double2> z,
                         int nvec, cudaStream_t st);

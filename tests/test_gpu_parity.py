@@ -645,7 +645,9 @@ def test_ilu0_apply_matches_oracle(shape, layer):
 @pytest.mark.parametrize("prec,tol", [(hzpkg.HZ_C128, 1e-11), (hzpkg.HZ_MIXED_C64, 1e-5)])
 def test_fci_with_ilu0_inner_preconditioner_matches_oracle(prec, tol):
     """Algorithm 1 with the inner GMRES right-preconditioned by ILU(0) (one and two right-hand
-    sides per call) against the oracle's fci(..., inner_precond)."""
+    sides per call) against the oracle's fci(..., inner_precond).  The mixed form takes its
+    complex64 polynomial sweeps and float32 ILU(0) sweeps (1e-5, as for its FCI without ILU);
+    the all-float64 form its float64 ones (1e-11)."""
     wl = W.small_case(3, 13, 9, 7, layer=2, J=4)
     op, nodes = oracle_of(wl)
     Minv = O.ilu0_preconditioner(op)
