@@ -135,16 +135,13 @@ __global__ void __launch_bounds__(IT) k_ilu0_apply_smem(Geom g, const double* __
 // a preconditioner application, like the complex64 polynomial sweeps, and one SM retires 64
 // times more float32 than float64 operations on GB300, which is what bounds a sweep run by a
 // single block.  t and z stay float64 fields (the inner basis is float64); the forward result
-// goes to a complex64 scratch field u.  Each thread keeps the (j, k) of its lines (at most
-// IL32 of them) in registers and loads the next hyperplane's inputs (t and 1/d, or u and 1/d)
-// while it computes the current one, so a hyperplane step waits only on shared memory.
-constexpr int IT32 = 512;
-constexpr int IL32 = 8;
-
-__global__ void __launch_bounds__(IT32, 1)
-k_ilu0_apply_smem32(Geom g, const float* __restrict__ invd, float cs,
-                    const double2* __restrict__ t, long long trs, float2* u32, long long urs,
-                    double2* z, long long zrs) {
+// goes to a complex64 scratch field u.
+__global__ void __launch_bounds__(IT) k_ilu0_apply_smem32(Geom g, const float* __restrict__ invd,
+                                                          float cs,
+                                                          const double2* __restrict__ t,
+                                                          long long trs, float2* u32,
+                                                          long long urs, double2* z,
+                                                          long long zrs) {
   pdl_enter();
   extern __shared__ float2 lv32[];  // [2][ny * nz]
   const int r = blockIdx.x;
@@ -157,94 +154,43 @@ k_ilu0_apply_smem32(Geom g, const float* __restrict__ invd, float cs,
   const int lines = ny * nz;
   float2* b0 = lv32;
   float2* b1 = lv32 + lines;
-  int jj[IL32], kk[IL32];
-#pragma unroll
-  for (int m = 0; m < IL32; ++m) {
-    const int l = threadIdx.x + m * IT32;
-    jj[m] = l < lines ? l % ny : 0;
-    kk[m] = l < lines ? l / ny : -(1 << 28);  // never on a hyperplane
-  }
-  // ---- forward: u_p = (t_p + cs (u_{i-1} + u_{j-1} + u_{k-1})) / d_p
-  float2 tv[IL32];
-  float iv[IL32];
-  auto load_f = [&](int w, float2 (&a)[IL32], float (&b)[IL32]) {
-#pragma unroll
-    for (int m = 0; m < IL32; ++m) {
-      const int i = w - jj[m] - kk[m];
-      if (i >= 0 && i < nx) {
-        const long long p = i + sy * jj[m] + sz * kk[m];
-        const double2 v = tr[p];
-        a[m] = make_float2(float(v.x), float(v.y));
-        b[m] = invd[p];
-      }
-    }
-  };
-  load_f(0, tv, iv);
   for (int w = 0; w < W; ++w) {
-    float2 tn[IL32];
-    float in[IL32];
-    if (w + 1 < W) load_f(w + 1, tn, in);
     const float2* old = (w & 1) ? b0 : b1;
     float2* cur = (w & 1) ? b1 : b0;
-#pragma unroll
-    for (int m = 0; m < IL32; ++m) {
-      const int l = threadIdx.x + m * IT32;
-      const int j = jj[m], k = kk[m], i = w - j - k;
+    for (int l = threadIdx.x; l < lines; l += IT) {
+      const int j = l % ny, k = l / ny, i = w - j - k;
       if (i < 0 || i >= nx) continue;
+      const long long p = i + sy * j + sz * k;
+      const double2 tv = tr[p];
+      const float iv = invd[p];
       float ax = 0.f, ay = 0.f;
       if (i > 0) { ax += old[l].x; ay += old[l].y; }
       if (j > 0) { ax += old[l - 1].x; ay += old[l - 1].y; }
       if (k > 0) { ax += old[l - ny].x; ay += old[l - ny].y; }
-      const float2 u = make_float2((tv[m].x + cs * ax) * iv[m], (tv[m].y + cs * ay) * iv[m]);
+      const float2 u = make_float2((float(tv.x) + cs * ax) * iv, (float(tv.y) + cs * ay) * iv);
       cur[l] = u;
-      ur[i + sy * j + sz * k] = u;
+      ur[p] = u;
     }
     __syncthreads();
-#pragma unroll
-    for (int m = 0; m < IL32; ++m) {
-      tv[m] = tn[m];
-      iv[m] = in[m];
-    }
   }
-  // ---- backward: z_p = u_p + cs / d_p (z_{i+1} + z_{j+1} + z_{k+1}); u written above by
-  // this same thread
-  auto load_b = [&](int w, float2 (&a)[IL32], float (&b)[IL32]) {
-#pragma unroll
-    for (int m = 0; m < IL32; ++m) {
-      const int i = w - jj[m] - kk[m];
-      if (i >= 0 && i < nx) {
-        const long long p = i + sy * jj[m] + sz * kk[m];
-        a[m] = ur[p];
-        b[m] = cs * invd[p];
-      }
-    }
-  };
-  load_b(W - 1, tv, iv);
   for (int w = W - 1; w >= 0; --w) {
-    float2 tn[IL32];
-    float in[IL32];
-    if (w > 0) load_b(w - 1, tn, in);
     const float2* old = (w & 1) ? b0 : b1;
     float2* cur = (w & 1) ? b1 : b0;
-#pragma unroll
-    for (int m = 0; m < IL32; ++m) {
-      const int l = threadIdx.x + m * IT32;
-      const int j = jj[m], k = kk[m], i = w - j - k;
+    for (int l = threadIdx.x; l < lines; l += IT) {
+      const int j = l % ny, k = l / ny, i = w - j - k;
       if (i < 0 || i >= nx) continue;
+      const long long p = i + sy * j + sz * k;
+      const float2 u = ur[p];
+      const float f = cs * invd[p];
       float ax = 0.f, ay = 0.f;
       if (i < nx - 1) { ax += old[l].x; ay += old[l].y; }
       if (j < ny - 1) { ax += old[l + 1].x; ay += old[l + 1].y; }
       if (k < nz - 1) { ax += old[l + ny].x; ay += old[l + ny].y; }
-      const float2 zv = make_float2(tv[m].x + iv[m] * ax, tv[m].y + iv[m] * ay);
+      const float2 zv = make_float2(u.x + f * ax, u.y + f * ay);
       cur[l] = zv;
-      zr[i + sy * j + sz * k] = make_double2(double(zv.x), double(zv.y));
+      zr[p] = make_double2(double(zv.x), double(zv.y));
     }
     __syncthreads();
-#pragma unroll
-    for (int m = 0; m < IL32; ++m) {
-      tv[m] = tn[m];
-      iv[m] = in[m];
-    }
   }
 }
 
@@ -279,15 +225,13 @@ cudaError_t launch_ilu0_32(const Geom& g, const float* invd32, Buf<const double2
   if (nvec < 1 || nvec > 65535) return cudaErrorInvalidValue;
   const size_t smem = 2 * sizeof(float2) * (size_t)g.ny * g.nz;
   if (smem > kIluSmemMax) return cudaErrorInvalidValue;
-  if ((long long)g.ny * g.nz > (long long)IT32 * IL32) return cudaErrorInvalidValue;
   count_launch();
-  return launch_pdl(k_ilu0_apply_smem32, dim3(nvec), dim3(IT32), smem, st, g, invd32,
+  return launch_pdl(k_ilu0_apply_smem32, dim3(nvec), dim3(IT), smem, st, g, invd32,
                     float(g.cs), t.p, t.rs, u32.p, u32.rs, z.p, z.rs);
 }
 
 bool ilu0_fits32(const Geom& g) {
-  return 2 * sizeof(float2) * (size_t)g.ny * g.nz <= kIluSmemMax &&
-         (long long)g.ny * g.nz <= (long long)IT32 * IL32;
+  return 2 * sizeof(float2) * (size_t)g.ny * g.nz <= kIluSmemMax;
 }
 
 void ilu0_inverse_pivots(int nx, int ny, int nz, double cs, std::vector<double>& invd) {
