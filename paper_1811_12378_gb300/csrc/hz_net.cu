@@ -71,16 +71,19 @@ __global__ void k_pool(const __nv_bfloat16* __restrict__ src, __nv_bfloat16* __r
   }
 }
 
-// dst [B][2D][2H][2W][C] = nearest-neighbour upsampling of src [B][D][H][W][C]
+// dst [B][2D][2H][2W][C] = nearest-neighbour upsampling of src [B][D][H][W][C]; a thread
+// moves 8 channels (16 bytes)
 __global__ void k_up(const __nv_bfloat16* __restrict__ src, __nv_bfloat16* __restrict__ dst,
                      int B, int D, int H, int W, int C) {
-  const int D2 = 2 * D, H2 = 2 * H, W2 = 2 * W;
-  GRID_STRIDE(i, (long long)B * D2 * H2 * W2 * C) {
-    const int c = (int)(i % C);
-    long long v = i / C;
+  const int D2 = 2 * D, H2 = 2 * H, W2 = 2 * W, C8 = C / 8;
+  const uint4* s8 = reinterpret_cast<const uint4*>(src);
+  uint4* d8 = reinterpret_cast<uint4*>(dst);
+  GRID_STRIDE(i, (long long)B * D2 * H2 * W2 * C8) {
+    const int c = (int)(i % C8);
+    long long v = i / C8;
     const int x = (int)(v % W2), y = (int)((v / W2) % H2), z = (int)((v / ((long long)W2 * H2)) % D2);
     const int b = (int)(v / ((long long)W2 * H2 * D2));
-    dst[i] = src[((((long long)b * D + z / 2) * H + y / 2) * W + x / 2) * C + c];
+    d8[i] = s8[((((long long)b * D + z / 2) * H + y / 2) * W + x / 2) * C8 + c];
   }
 }
 
@@ -179,8 +182,14 @@ __global__ void k_loss_head_back(const float* __restrict__ y, const float* __res
     pw[2 * HEAD_IN] += d0;
     pw[2 * HEAD_IN + 1] += dd1;
   }
-  for (int q = 0; q < OUT_CH * HEAD_IN + OUT_CH; ++q) atomicAdd(&sw[q], pw[q]);
-  atomicAdd(&sl, pl);
+  // per-warp sums first (shuffles), one shared atomic per warp and value
+  for (int q = 0; q < OUT_CH * HEAD_IN + OUT_CH; ++q) {
+    float v = pw[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&sw[q], v);
+  }
+  for (int o = 16; o > 0; o >>= 1) pl += __shfl_xor_sync(0xffffffffu, pl, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&sl, pl);
   __syncthreads();
   for (int q = threadIdx.x; q < OUT_CH * HEAD_IN; q += blockDim.x) atomicAdd(&dw[q], sw[q]);
   if (threadIdx.x < OUT_CH) atomicAdd(&dbias[threadIdx.x], sw[OUT_CH * HEAD_IN + threadIdx.x]);
@@ -418,7 +427,7 @@ hz_status net_forward(hz_net* n, const Dims& d, cudaStream_t st) {
   };
   auto up = [&](const __nv_bfloat16* s, __nv_bfloat16* o, int l, int C) -> hz_status {
     hz::count_launch();  // from level l to level l - 1
-    hz::k_up<<<hz::gs_blocks(d.vox(l - 1) * C), 256, 0, st>>>(s, o, B, d.D >> l, d.H >> l,
+    hz::k_up<<<hz::gs_blocks(d.vox(l - 1) * C / 8), 256, 0, st>>>(s, o, B, d.D >> l, d.H >> l,
                                                                 d.W >> l, C);
     NCHK(cudaGetLastError());
     return HZ_OK;
@@ -463,7 +472,8 @@ hz_status net_backward(hz_net* n, const Dims& d, cudaStream_t st) {
   };
   const long long per = (long long)(d.D) * d.H * d.W;
   hz::count_launch();
-  hz::k_loss_head_back<<<hz::gs_blocks(d.vox(0)), 256, 0, st>>>(
+  hz::k_loss_head_back<<<(int)std::min<long long>(hz::gs_blocks(d.vox(0)), 2 * n->sms), 256, 0,
+                          st>>>(
       n->y, n->tgt, n->act[hz::D1B], n->par + n->hw, n->gA, n->grad + n->hw, n->grad + n->hb,
       n->dscal, d.vox(0), 1.0f / (float)per);
   NCHK(cudaGetLastError());

@@ -168,6 +168,21 @@ def gaussian_bumps_64(seed: int = 1) -> Workload:
                     8, 1.0, default_eps(n, n, n), 30, 4, 1e-8, c, f)
 
 
+def gaussian_bumps(n: int, seed: int, ppw: float = 8.0, layer: int = 8, J: int = 8,
+                   restart: int = 30) -> Workload:
+    """The Gaussian-bump recipe of gaussian_bumps_64 at n^3 (h = 1/(n+1)): c = 1 + 8 bumps
+    (width 0.1, amplitudes U[0,0.4]) clipped to [1, 2], ppw points per wavelength at c_min, one
+    Gaussian source (sigma = 2h) at a seeded core point; media and sources for the learned
+    preconditioner's training (64^3) and application (128^3, 192^3) sizes."""
+    h = 1.0 / (n + 1)
+    c = medium_gaussian_bumps(seed, n, n, n, h)
+    g = _rng(seed + 1000)
+    i, j, k = random_core_index(g, n, n, n, layer)
+    f = source_gaussian(n, n, n, h, ((i + 1) * h, (j + 1) * h, (k + 1) * h), 2.0 * h)[None]
+    return Workload(f"gaussian_bumps_{n}_{seed}", n, n, n, h, omega_for_ppw(c, h, ppw), layer,
+                    1.0, J, 1.0, default_eps(n, n, n), restart, 4, 1e-8, c, f)
+
+
 def large_bumps_256(seed: int = 5, nsrc: int = 16):
     """256^3 (h = 1/257), c = 1 + 16 Gaussian bumps (width 0.1, amplitudes U[0, 2]) clipped to
     [1, 3], 8 ppw at c_min, 12-cell sponge, J = 8 contour nodes, FGMRES(40) with k_in = 4 to
