@@ -53,6 +53,8 @@ def parse():
                          "bracketed with cudaProfilerStart/Stop")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 256^3 sixteen-source configuration's solve")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip training and applying the learned preconditioner")
     return ap.parse_args()
 
 
@@ -370,6 +372,91 @@ def large_solve(hz, torch, dev, nrhs=8, profile_region=False):
                          "peak_kind": f"{kind} copy bandwidth"}}
 
 
+def learned_preconditioner(hz, torch, dev, n_media=4, batches=4, nb=8, epochs=40, lr=1e-3,
+                           sizes=(64, 128, 192)):
+    """The learned right preconditioner: train the U-Net on the GPU (its own BF16 tensor-core
+    kernels) from (residual, error) pairs of FCI on n_media random 64^3 Gaussian-bump media
+    (r = v - A FCI(v) for smooth random v, e = A^{-1} r by a plain-method solve to 1e-6), then
+    solve one fresh medium at each size to 1e-8 with FCI alone (mode 0) and with the network
+    followed by FCI on its residual (mode 2).  All on the GPU; the true residual decides."""
+    import numpy as np
+    import workloads as W
+    from oracle import hz_net_oracle as N  # noqa: F401  (only the initial weights' recipe)
+    g = np.random.Generator(np.random.PCG64(11))
+
+    def smooth(k, wl):
+        r = g.standard_normal((k, wl.nz, wl.ny, wl.nx)) + 1j * g.standard_normal(
+            (k, wl.nz, wl.ny, wl.nx))
+        for _ in range(2):
+            r = (r + np.roll(r, 1, 1) + np.roll(r, -1, 1) + np.roll(r, 1, 2) + np.roll(r, -1, 2)
+                 + np.roll(r, 1, 3) + np.roll(r, -1, 3)) / 7.0
+        return torch.from_numpy(r.reshape(k, -1)).to(dev)
+
+    net = hz.Net(64, 64, 64, batch_max=nb)
+    net.set_params(hz.flatten_params(N.init_params(5)))
+    data, probs = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for seed in range(1, 1 + n_media):
+        wl = W.gaussian_bumps(64, seed)
+        P = hz.Problem(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, wl.J, wl.t, wl.eps,
+                       nrhs_max=nb, restart_max=30, inner_k_max=4)
+        probs.append(P)
+        s = P.info["s"]
+        for _ in range(batches):
+            v = smooth(nb, wl)
+            z = P.fci(v, inner_k=4, precision=hz.HZ_MIXED_C64)
+            t = (v - P.apply_shifted(z)).contiguous()
+            e, _ = P.solve(t / s, restart=30, inner_k=4, rtol=1e-6, max_cycles=20,
+                           precision=hz.HZ_MIXED_C64, check=False)
+            data.append((P, t, e))
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = []
+    for ep in range(epochs):
+        tot = sum(net.train_fields(P, t, e, lr=lr) for (P, t, e) in data)
+        if ep in (0, epochs - 1):
+            losses.append(tot / len(data))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    params = net.get_params()
+    net.close()
+    del data
+    for P in probs:
+        P.close()
+    out = {"training": {"media": n_media, "pairs": n_media * batches * nb, "epochs": epochs,
+                        "adam_steps": epochs * n_media * batches, "batch": nb,
+                        "pairs_s": t_pairs, "train_s": t_train, "loss_first_last": losses},
+           "solves": []}
+    for n in sizes:
+        wl = W.gaussian_bumps(n, 100 + n)
+        P = hz.Problem(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, wl.J, wl.t, wl.eps,
+                       nrhs_max=1, restart_max=30, inner_k_max=4)
+        f = torch.from_numpy(wl.f.reshape(1, -1).copy()).to(dev)
+        netn = hz.Net(n, n, n, 1)
+        netn.set_params(params)
+        row = {"grid": f"{n}^3"}
+        for mode in (0, 2):
+            P.set_preconditioner(netn if mode else None, mode)
+            cyc = 40 if mode == 0 or n < 192 else 3
+            kw = dict(restart=30, inner_k=4, rtol=1e-8, max_cycles=cyc, precision=hz.HZ_MIXED_C64,
+                      check=False)
+            P.solve(f, **kw)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, st = P.solve(f, **kw)
+            e1.record()
+            e1.synchronize()
+            row[f"mode{mode}"] = {"its": st[0].its, "converged": st[0].converged,
+                                  "rel_res_true": st[0].rel_res_true,
+                                  "ms": e0.elapsed_time(e1)}
+        out["solves"].append(row)
+        P.close()
+        netn.close()
+    return out
+
+
 def batched_uneven(hz, torch, dev, precision):
     """12 instances (4 each of 48^3, 64^3, 96^3; layered media; 4 point sources each) solved
     together by hz_solve_batched, and one after another by hz_solve, to 1e-8."""
@@ -567,6 +654,8 @@ def run_ours(args):
     hbm = large_grid_bandwidth(hz, torch, dev)
     large = large_solve(hz, torch, dev) if world == 1 and not args.no_large else None
     uneven = batched_uneven(hz, torch, dev, prec[HEADLINE]) if world == 1 else None
+    learned = (learned_preconditioner(hz, torch, dev) if world == 1 and not args.no_learned
+               else None)
 
     rhs_total = args.steps * world
     value = rhs_total / t_head
@@ -612,6 +701,7 @@ def run_ours(args):
         "stencil_hbm": hbm,
         "large": large,
         "batched_uneven": uneven,
+        "learned_preconditioner": learned,
         "gpu_launches": launches,
         "clocks": clk,
     }
