@@ -51,6 +51,13 @@ def parse():
     ap.add_argument("--ncu-large", action="store_true",
                     help="run only the 256^3 stencil / polynomial-stage bandwidth measurement, "
                          "bracketed with cudaProfilerStart/Stop")
+    ap.add_argument("--ncu-case", choices=["ilu", "net", "batched128"], default=None,
+                    help="run only one profiling region, bracketed with cudaProfilerStart/Stop: "
+                         "ilu = one FCI application with the ILU(0) inner preconditioner on the "
+                         "64^3 workload (HZ_MIXED_C64); net = one forward pass and one training "
+                         "step of the network on one 64^3 sample; batched128 = one FCI "
+                         "application to 8 right-hand sides on a 128^3 Gaussian-bump medium "
+                         "(8 nodes x 8 right-hand sides per polynomial stage, fields beyond L2)")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 256^3 sixteen-source configuration's solve")
     ap.add_argument("--no-learned", action="store_true",
@@ -381,7 +388,6 @@ def learned_preconditioner(hz, torch, dev, n_media=4, batches=4, nb=8, epochs=40
     followed by FCI on its residual (mode 2).  All on the GPU; the true residual decides."""
     import numpy as np
     import workloads as W
-    from oracle import hz_net_oracle as N  # noqa: F401  (only the initial weights' recipe)
     g = np.random.Generator(np.random.PCG64(11))
 
     def smooth(k, wl):
@@ -393,7 +399,7 @@ def learned_preconditioner(hz, torch, dev, n_media=4, batches=4, nb=8, epochs=40
         return torch.from_numpy(r.reshape(k, -1)).to(dev)
 
     net = hz.Net(64, 64, 64, batch_max=nb)
-    net.set_params(hz.flatten_params(N.init_params(5)))
+    net.set_params(hz.flatten_params(hz.init_params(5)))
     data, probs = [], []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -752,8 +758,58 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def ncu_case(case: str):
+    """One small profiling region on the 64^3 workload (cudaProfilerStart/Stop around it, two
+    untimed repetitions before)."""
+    import torch
+    import paper_1811_12378_gb300 as hz
+    import workloads as W
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device="cpu").manual_seed(3)
+    if case == "ilu":
+        wl = W.gaussian_bumps_64()
+        P = hz.Problem(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, wl.J, wl.t, wl.eps,
+                       nrhs_max=1, restart_max=wl.restart, inner_k_max=wl.k_in)
+        P.set_inner_ilu(True)
+        r = torch.randn(1, P.n, dtype=torch.complex128, generator=g).to(dev)
+
+        def body():
+            P.fci(r, inner_k=wl.k_in, precision=hz.HZ_MIXED_C64)
+    elif case == "batched128":
+        wl = W.gaussian_bumps(128, 7)
+        P = hz.Problem(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, wl.J, wl.t, wl.eps,
+                       nrhs_max=8, restart_max=1, inner_k_max=wl.k_in,
+                       flags=hz.HZ_LIMIT_SWEEPS_C64)
+        r = torch.randn(8, P.n, dtype=torch.complex128, generator=g).to(dev)
+
+        def body():
+            P.fci(r, inner_k=wl.k_in, precision=hz.HZ_MIXED_C64)
+    else:
+        net = hz.Net(64, 64, 64, batch_max=1)
+        net.set_params(hz.flatten_params(hz.init_params(5)))
+        x = torch.randn(1, 64, 64, 64, 8, generator=g)
+        x[..., 3:] = 0
+        x = x.to(dev)
+        t = torch.randn(1, 64, 64, 64, 2, generator=g).to(dev)
+
+        def body():
+            net.forward(x)
+            net.train_step(x, t, lr=1e-4)
+    for _ in range(2):
+        body()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    body()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"ncu_case": case, "ok": True}))
+
+
 def main():
     args = parse()
+    if args.ncu_case:
+        ncu_case(args.ncu_case)
+        return
     if args.ncu_large:
         import torch
         import paper_1811_12378_gb300 as hz

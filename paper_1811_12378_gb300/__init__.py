@@ -5,10 +5,12 @@ include/hz.h.  ``hz`` is the Python binding (argument marshalling only)."""
 from .hz import (HZ_C128, HZ_MIXED_C64, HZ_MIXED_C64_FCI32, HZ_MIXED_C64_FF, HZ_LIMIT_SWEEPS_C64,
                  HZ_LIMIT_Z_C64, HZ_LIMIT_CASE_TWO, EXPORTS, PROF_KRYLOV, PROF_POLY, PROF_STENCIL, HzError,
                  Problem, SolveStats, launch_count, library_path, load, plan, solve_batched,
-                 Net, NET_CONVS, flatten_params, unflatten_params, conv3d, conv3d_backward)
+                 Net, NET_CONVS, flatten_params, unflatten_params, init_params, conv3d,
+                 conv3d_backward)
 
 __all__ = ["HZ_C128", "HZ_MIXED_C64", "HZ_MIXED_C64_FCI32", "HZ_MIXED_C64_FF",
            "HZ_LIMIT_SWEEPS_C64", "HZ_LIMIT_Z_C64", "HZ_LIMIT_CASE_TWO", "EXPORTS", "PROF_KRYLOV", "PROF_POLY", "PROF_STENCIL",
            "HzError", "Problem", "SolveStats",
            "launch_count", "library_path", "load", "plan", "solve_batched",
-           "Net", "NET_CONVS", "flatten_params", "unflatten_params", "conv3d", "conv3d_backward"]
+           "Net", "NET_CONVS", "flatten_params", "unflatten_params", "init_params", "conv3d",
+           "conv3d_backward"]

@@ -496,6 +496,19 @@ def unflatten_params(flat: np.ndarray) -> dict:
     return out
 
 
+def init_params(seed: int) -> dict:
+    """Seeded starting weights: He-normal 3x3x3 weights (std sqrt(2 / fan_in)), zero biases,
+    head weights of std 1/4 (fan-in 16)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    p = {}
+    for name, ci, co in NET_CONVS:
+        p[name + ".w"] = g.standard_normal((co, 27, ci)) * np.sqrt(2.0 / (27 * ci))
+        p[name + ".b"] = np.zeros(co)
+    p["head.w"] = g.standard_normal((2, 16)) / 4.0
+    p["head.b"] = np.zeros(2)
+    return p
+
+
 class Net:
     """The learned right preconditioner's network on the current CUDA device (hz_net_create):
     activation storage for up to batch_max volumes of D x H x W voxels."""
