@@ -7,13 +7,16 @@ GPU library and imports nothing from it; both sides are fed the same seeded inpu
 
 Everything is complex128 / float64 numpy, written step by step in the paper's order:
 
-* operator      A = s*L_h - diag(m) - i*diag(a)            (§7.1 eq:stiff-mass, Case One)
+* operator      A = s*L_h - diag(m) - i*diag(a)            (§7.1 eq:stiff-mass, Case One;
+                7-point or Fourier spectral L_h, eq:eig-Laplacian-spectral)
 * bounds        rectangle B = [b1, b2] x [-rho2, 0]          (§3 Lemma 3.1)
 * contour       nodes z_j and weights sigma_j                (§6.1, §6.2 eq:quad-points)
 * poly params   z0, delta, q, nu, sweeps                     (§4.2 eq:fix-pt-conv)
 * poly solve    fixed-point scheme                           (§4.2 eq:fix-pt-exp)
 * FCI           quadrature, step d, inner GMRES              (§2 Algorithm 1)
 * FGMRES        flexible GMRES with FCI as right precond.    (§2, after Algorithm 1)
+* inner precond ILU(0) of the 7-point Laplacian, regularised inverse spectral
+                Laplacian 1/max(lambda, 1)                   (§6.3, §7.3)
 * Case Two      iC - I on (iu; u), its spectrum rectangle    (§3 eq:mat-2x2, Theorem
                 and Algorithm 1 / FGMRES on it                thm:spectrum-2x2 and Remark)
 
@@ -69,6 +72,7 @@ class Operator:
     s: float
     m: np.ndarray   # (nz, ny, nx) float64
     a: np.ndarray   # (nz, ny, nx) float64
+    kind: str = "fd"  # "fd": 7-point, zero Dirichlet ghosts; "spectral": Fourier, periodic
 
     @property
     def shape(self):
@@ -79,8 +83,13 @@ class Operator:
         return self.nx * self.ny * self.nz
 
     def apply(self, x: np.ndarray, z: complex = 0.0) -> np.ndarray:
-        """(A - z I) x for one field x of shape (nz, ny, nx); zero Dirichlet ghosts."""
+        """(A - z I) x for one field x of shape (nz, ny, nx); zero Dirichlet ghosts (7-point)
+        or the periodic Fourier spectral Laplacian (§7.1, S = F^H Lambda F)."""
         x = np.asarray(x, dtype=np.complex128).reshape(self.shape)
+        if self.kind == "spectral":
+            lam = spectral_eigenvalues(self.nx, self.ny, self.nz, self.h)
+            lap = np.fft.ifftn(lam * np.fft.fftn(x))
+            return self.s * lap - self.m * x - 1j * self.a * x - z * x
         xp = np.pad(x, 1)
         nb = (xp[1:-1, 1:-1, 2:] + xp[1:-1, 1:-1, :-2]
               + xp[1:-1, 2:, 1:-1] + xp[1:-1, :-2, 1:-1]
@@ -89,9 +98,28 @@ class Operator:
         return self.s * lap - self.m * x - 1j * self.a * x - z * x
 
 
+def spectral_eigenvalues(nx: int, ny: int, nz: int, h: float) -> np.ndarray:
+    """Eigenvalues of -Delta under the Fourier spectral discretisation of the periodic box of
+    nx x ny x nz points with spacing h, shape (nz, ny, nx), in the order of numpy's FFT.
+
+    The mode with zero-based index i_d along an axis of n points is the plane wave
+    exp(2 pi i i_d x / (n h)), sampled; its wavenumber is taken as 2 pi min(i_d, n - i_d)/(n h),
+    the alias of smallest magnitude (§7.1 eq:eig-Laplacian-spectral uses min(i_d^2, (n-i_d)^2)).
+    -Delta has the sum over the axes of the squared wavenumbers.  Times s = c_min^2/omega^2
+    these are the paper's normalised (l_min/N)^2 sum min(i_d^2, (N - i_d)^2), since the
+    sampling rate at c_min is l_min = 2 pi c_min / (omega h)."""
+    def axis(n):
+        i = np.arange(n)
+        return (2.0 * math.pi * np.minimum(i, n - i) / (n * h)) ** 2
+    ex, ey, ez = axis(nx), axis(ny), axis(nz)
+    return ez[:, None, None] + ey[None, :, None] + ex[None, None, :]
+
+
 def make_operator(c: np.ndarray, h: float, omega: float, layer: int,
-                  sigma_max: float) -> Operator:
-    """Coefficients from the wavespeed c (shape (nz, ny, nx)): s, m = c_min^2/c^2, sponge a."""
+                  sigma_max: float, kind: str = "fd") -> Operator:
+    """Coefficients from the wavespeed c (shape (nz, ny, nx)): s, m = c_min^2/c^2, sponge a.
+    kind "spectral" takes the Fourier spectral Laplacian on the periodic box (§7.1) with the
+    same mass and sponge."""
     c = np.asarray(c, dtype=np.float64)
     nz, ny, nx = c.shape
     c_min = float(c.min())
@@ -102,7 +130,9 @@ def make_operator(c: np.ndarray, h: float, omega: float, layer: int,
         a = sigma_max * (d / layer) ** 2 * m
     else:
         a = np.zeros_like(m)
-    return Operator(nx, ny, nz, float(h), s, m, a)
+    if kind not in ("fd", "spectral"):
+        raise ValueError(kind)
+    return Operator(nx, ny, nz, float(h), s, m, a, kind)
 
 
 # ---------------------------------------------------------------------------------------
@@ -130,7 +160,11 @@ def spectrum_box(op: Operator):
     the Rayleigh quotient of A1 lies in [s*lmin - max m, s*lmax - min m] and that of A2 in
     [0, max a]; the Lemma's argument (lambda = v^H A v) then bounds every eigenvalue.
     """
-    lo, hi = laplacian_extremes(op.nx, op.ny, op.nz, op.h)
+    if op.kind == "spectral":
+        lam = spectral_eigenvalues(op.nx, op.ny, op.nz, op.h)
+        lo, hi = float(lam.min()), float(lam.max())
+    else:
+        lo, hi = laplacian_extremes(op.nx, op.ny, op.nz, op.h)
     b1 = op.s * lo - float(op.m.max())
     b2 = op.s * hi - float(op.m.min())
     rho2 = float(op.a.max())
@@ -474,6 +508,23 @@ def ilu0_preconditioner(op: Operator):
     cs = op.s / (op.h * op.h)
     d = ilu0_pivots(op.nx, op.ny, op.nz, cs)
     return lambda t: ilu0_apply(d, cs, t)
+
+
+# ---------------------------------------------------------------------------------------
+# Regularised inverse Laplacian: the inner preconditioner of the spectral runs (§7.3)
+# ---------------------------------------------------------------------------------------
+
+def invlap_preconditioner(op: Operator):
+    """M^{-1} = F^H diag(1 / max(lambda_i, 1)) F with lambda_i the normalised eigenvalues of
+    the spectral Laplacian, s times spectral_eigenvalues (eq:eig-Laplacian-spectral): the
+    inverse of the Laplacian on the modes above 1, the identity on the ones below."""
+    lam = op.s * spectral_eigenvalues(op.nx, op.ny, op.nz, op.h)
+    mult = 1.0 / np.maximum(lam, 1.0)
+
+    def apply(t):
+        t = np.asarray(t, dtype=np.complex128).reshape(op.shape)
+        return np.fft.ifftn(mult * np.fft.fftn(t))
+    return apply
 
 
 # ---------------------------------------------------------------------------------------

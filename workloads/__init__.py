@@ -78,13 +78,13 @@ def medium_constant(nx, ny, nz, c0=1.0):
 
 
 def medium_gaussian_bumps(seed, nx, ny, nz, h, nbumps=8, width=0.1, amp_hi=0.4,
-                          c_lo=1.0, c_hi=2.0):
+                          c_lo=1.0, c_hi=2.0, amp_lo=0.0):
     """c = clip(1 + sum_k a_k exp(-|x-x_k|^2 / (2 width^2)), c_lo, c_hi).
 
-    a_k ~ U[0, amp_hi], centres x_k ~ U[0, 1]^3 (unit cube), all drawn from PCG64(seed).
+    a_k ~ U[amp_lo, amp_hi], centres x_k ~ U[0, 1]^3 (unit cube), all drawn from PCG64(seed).
     """
     g = _rng(seed)
-    amps = g.uniform(0.0, amp_hi, size=nbumps)
+    amps = g.uniform(amp_lo, amp_hi, size=nbumps)
     ctrs = g.uniform(0.0, 1.0, size=(nbumps, 3))
     X, Y, Z = coords(nx, ny, nz, h)
     c = np.ones((nz, ny, nx))
@@ -180,6 +180,22 @@ def gaussian_bumps(n: int, seed: int, ppw: float = 8.0, layer: int = 8, J: int =
     i, j, k = random_core_index(g, n, n, n, layer)
     f = source_gaussian(n, n, n, h, ((i + 1) * h, (j + 1) * h, (k + 1) * h), 2.0 * h)[None]
     return Workload(f"gaussian_bumps_{n}_{seed}", n, n, n, h, omega_for_ppw(c, h, ppw), layer,
+                    1.0, J, 1.0, default_eps(n, n, n), restart, 4, 1e-8, c, f)
+
+
+def spectral_bumps(n: int, seed: int, ppw: float = 2.25, layer: int = 8, J: int = 8,
+                   restart: int = 30) -> Workload:
+    """A Fourier spectral workload on the periodic n^3 box of spacing h = 1/n: background c = 1
+    with 8 Gaussian bumps (width 0.1, amplitudes U[0.5, 1]) clipped to [1, 2], so the sampling
+    rate is ppw points per wavelength in the background and up to twice that in the anomalies
+    (the spectral runs sample 2.25 and 4.5), a layer-cell sponge at the box faces, one
+    Gaussian source (sigma = 2h) at a seeded core point."""
+    h = 1.0 / n
+    c = medium_gaussian_bumps(seed, n, n, n, h, nbumps=8, width=0.1, amp_lo=0.5, amp_hi=1.0)
+    g = _rng(seed + 1000)
+    i, j, k = random_core_index(g, n, n, n, layer)
+    f = source_gaussian(n, n, n, h, ((i + 1) * h, (j + 1) * h, (k + 1) * h), 2.0 * h)[None]
+    return Workload(f"spectral_bumps_{n}_{seed}", n, n, n, h, omega_for_ppw(c, h, ppw), layer,
                     1.0, J, 1.0, default_eps(n, n, n), restart, 4, 1e-8, c, f)
 
 
