@@ -75,15 +75,28 @@ typedef enum {
                          it; hz_fci treats it as HZ_MIXED_C64_FCI32. */
 } hz_precision;
 
+/* Discretisation of the Laplacian (Section 7.1). */
+typedef enum {
+  HZ_DISC_FD7 = 0,      /* 7-point finite differences, zero Dirichlet values outside the grid */
+  HZ_DISC_SPECTRAL = 1  /* Fourier spectral S = F^H Lambda F on the periodic box of nx*ny*nz
+                           points (eq:eig-Laplacian-spectral): Lambda_i = sum over the axes of
+                           (2 pi min(i_a, n_a - i_a) / (n_a h))^2.  Each n_a must be a product of
+                           2, 3 and 5 and at most 1024.  Spectral problems run HZ_C128 and
+                           HZ_MIXED_C64, Case One, without the network or ILU(0) (their inner
+                           preconditioner is hz_problem_set_inner_invlap). */
+} hz_discretization;
+
 /* Grid and medium.  Interior points nx*ny*nz with spacing h; omega the angular frequency;
  * layer_cells the sponge thickness in cells (0 = none); sigma_max its peak strength in
- * normalised units (Section 7.1: "positive diagonal entries for points near the boundary"). */
+ * normalised units (Section 7.1: "positive diagonal entries for points near the boundary");
+ * discretization an hz_discretization (0, the 7-point stencil, when zero-initialised). */
 typedef struct {
   int nx, ny, nz;
   double h;
   double omega;
   int layer_cells;
   double sigma_max;
+  int discretization;
 } hz_grid;
 
 /* Contour and polynomial-scheme settings (Sections 4.2, 6.1, 6.2).  J nodes on the ellipse
@@ -280,6 +293,20 @@ hz_status hz_problem_set_inner_ilu(hz_problem* p, int on);
  * (device; t and z must not overlap).  Needs hz_problem_set_inner_ilu(p, 1).  Asynchronous. */
 hz_status hz_ilu0_apply(hz_problem* p, const void* t, void* z, int nvec, void* stream);
 
+/* Spectral problems (HZ_DISC_SPECTRAL): right-precondition the inner GMRES of FCI (step 4 of
+ * Algorithm 1) with the regularised inverse Laplacian M^{-1} = F^H diag(1 / max(lambda_i, 1)) F,
+ * lambda_i = s Lambda_i the normalised eigenvalues of the spectral Laplacian (Section 7.3: the
+ * spectral runs' preconditioner; Section 6.3: an approximate Laplacian deflates the large
+ * eigenvalues).  The inner GMRES then runs on A M^{-1} and FCI returns M^{-1} x + d w.  on = 0
+ * turns it off.  HZ_ERR_INVALID for a 7-point problem.  Applies to HZ_C128 and HZ_MIXED_C64
+ * (the float64 inner GMRES). */
+hz_status hz_problem_set_inner_invlap(hz_problem* p, int on);
+
+/* z = M^{-1} t with the regularised inverse Laplacian above, for nvec double-complex fields
+ * of n points (device; t and z may be the same buffer).  nvec <= nrhs_max * J.  Any spectral
+ * problem (it need not be switched on).  Asynchronous on `stream`. */
+hz_status hz_invlap_apply(hz_problem* p, const void* t, void* z, int nvec, void* stream);
+
 /* Poll limit of the grid-wide barriers inside the cooperative kernels (hz_problem_fused_tail,
  * hz_problem_fused_arnoldi): a block polls the barrier at most `polls` times (back to back,
  * then about 32 ns apart) before it gives up; polls < 0 restores the default (2^23, about a
@@ -329,6 +356,7 @@ hz_status hz_profile_read(hz_problem* p, int cls, long long* launches, double* m
  * HZ_ERR_INVALID.  All calls share it: calls that overlap on the GPU race, so serialise
  * them (one stream).  The first call on a device looks up the array's device address (with
  * that device current); make it before any stream capture.  Asynchronous on `stream`. */
+/* (7-point grids only: HZ_ERR_INVALID for grid->discretization != HZ_DISC_FD7.) */
 hz_status hz_residual_noalloc(const hz_grid* grid, const double* c, double c_min, const void* f,
                               double fscale, const void* u, void* r, double* norm2, int nvec,
                               void* stream);

@@ -15,7 +15,7 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libhz.so")
 SOURCES = ["hz_kernels.cu", "hz_kernels32.cu", "hz_kernels_ff.cu", "hz_fci_tail32.cu",
            "hz_arnoldi_ff.cu", "hz_case_two.cu", "hz_api.cu", "hz_setup.cpp", "hz_noalloc.cu",
-           "hz_conv.cu", "hz_net.cu", "hz_coop64.cu", "hz_ilu.cu"]
+           "hz_conv.cu", "hz_net.cu", "hz_coop64.cu", "hz_ilu.cu", "hz_fft.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

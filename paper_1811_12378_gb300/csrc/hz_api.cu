@@ -88,6 +88,11 @@ struct hz_problem {
   double2* Z = nullptr;      // [nrhs][m][n] preconditioned directions (float64)
   float2* Z32 = nullptr;     // [nrhs][m][n] the same stored in complex64 (HZ_LIMIT_Z_C64)
   bool case2 = false;        // HZ_LIMIT_CASE_TWO: the solver runs on iC - I (eq:mat-2x2)
+  bool spectral = false;     // HZ_DISC_SPECTRAL: Fourier spectral Laplacian, periodic box
+  hz::SpecPlan spec{};       // its line-FFT tables
+  void* spec_tmp = nullptr;  // [J nrhs][n] double2: the FFT scratch and a stage's s S x batch
+  bool invlap_on = false;    // hz_problem_set_inner_invlap: 1/max(lambda, 1) right-preconditions
+                             // the inner GMRES (spectral problems)
   bool ilu_on = false;       // hz_problem_set_inner_ilu: ILU(0) right-preconditions inner GMRES
   double* invd = nullptr;    // [n] 1 / ILU(0) pivots
   float* invd32 = nullptr;   // [n] the same in float32 (the sweeps of HZ_MIXED_C64)
@@ -217,7 +222,8 @@ size_t gmres_carved_bytes(int nrhs, int M) {
 bool valid_grid(const hz_grid* g) {
   return g && g->nx >= 1 && g->ny >= 1 && g->nz >= 1 && g->h > 0 && std::isfinite(g->h) &&
          g->omega > 0 && std::isfinite(g->omega) && g->layer_cells >= 0 && g->sigma_max >= 0 &&
-         std::isfinite(g->sigma_max) && g->ny <= 65535 && g->nz <= 65535;
+         std::isfinite(g->sigma_max) && g->ny <= 65535 && g->nz <= 65535 &&
+         (g->discretization == HZ_DISC_FD7 || g->discretization == HZ_DISC_SPECTRAL);
 }
 
 // ------------------------------------------------------------------ kernel timing
@@ -458,6 +464,43 @@ hz_status run_poly(hz_problem* p, const T* dg, Buf<const T> f, int nvec,
   build_schedule<R>(p, which, quad, sched, ycur);
   const int T_total = (int)sched.size();
   if (quad && T_total > 0) sched.back().quad64 = quad64 ? 1 : 0;
+  if (p->spectral) {
+    // each stage: s S x of every node input it reads (line FFTs), then the pointwise stage
+    ProfScope seq{p, 0, -1, st, 0.0};
+    HZ_TRY(seq.begin());
+    double seq_bytes = 0.0;
+    int launches = 0;
+    for (int t = 0; t < T_total; ++t) {
+      hz::StageArgs<R>& a = sched[t];
+      hz::VecMap in = hz::vec_map(ws, wrs);
+      in.nq = 0;
+      for (int q = 0; q < a.nnodes; ++q) {
+        hz::StageNode<R>& nd = a.nd[q];
+        const bool first = nd.kind == hz::SK_FIRST || nd.kind == hz::SK_FIRST_LAST;
+        nd.lapi = -1;
+        if (first && nd.yzero) continue;
+        nd.lapi = in.nq;
+        in.off[in.nq++] = nd.in;
+      }
+      T* lap = (T*)p->spec_tmp;
+      if (in.nq > 0) {
+        HZ_CUDA(hz::launch_spectral<T>(p->spec, p->g, hz::SPEC_LAP, in, hz::vec_map(lap, n),
+                                       in.nq * nvec, dg, 0.0, 0.0, lap, st));
+        launches += 5;
+        seq_bytes += 10.0 * sizeof(T) * double(n) * in.nq * nvec;
+      }
+      HZ_CUDA((hz::launch_poly_stage_spec<T, R>(p->g, dg, f, ws, wrs, lap, in.nq, wbuf, w32buf,
+                                                nvec, a, st)));
+      ++launches;
+      seq_bytes += (stage_bytes_per_point<T, R>(a, nvec, w32buf.p != nullptr) +
+                    double(sizeof(T)) * in.nq) * double(n) * nvec;
+    }
+    seq.bytes = seq_bytes;
+    HZ_TRY(seq.end());
+    if (seq.slot >= 0) p->prof[0].launches += launches - 1;
+    if (yfinal) *yfinal = ycur;
+    return HZ_OK;
+  }
   // one event pair around the whole stage sequence (per-launch events would cost more than
   // a 64^3 stage); launches and bytes are added per stage
   ProfScope seq{p, 0, -1, st, 0.0};
@@ -530,11 +573,32 @@ double tail64_flops(long long n, int kin) {
 double arn64_bytes(long long n, int nb) { return 16.0 * n * (3.0 + 3.0 * nb + 1.0); }
 double arn64_flops(long long n, int nb) { return double(n) * (22.0 + 32.0 * nb + 10.0); }
 
+// Algorithmic bytes and float64 flops of apply_op64 on nvec fields: the 7-point stencil, or
+// the five line-FFT passes of the spectral operator (every field read and written once per
+// pass, the input and diagonal read again by the last; 5 log2(n_a) flops per point and
+// transform direction along each axis, 10 for the diagonal and the pointwise part).
+double op64_bytes(const hz_problem* p, int nvec) {
+  const double n = double(p->nf);
+  if (!p->spectral) return stencil_bytes<double2, double2>(p->nf, nvec);
+  return 16.0 * n * (11.0 * nvec + 1.0);
+}
+double op64_flops(const hz_problem* p, int nvec) {
+  const double n = double(p->nf);
+  if (!p->spectral) return kStencil64Flops * n * nvec;
+  double f = 10.0;
+  for (int a = 0; a < 3; ++a) f += 10.0 * std::log2(double(p->spec.ax[a].n));
+  return f * n * nvec;
+}
+
 // y = (B - 0 I) x in float64 for solver fields: B = A (Case One) or iC - I (Case Two).
 cudaError_t apply_op64(const hz_problem* p, Buf<const double2> x, Buf<double2> y, int nvec,
                        cudaStream_t st) {
   if (p->case2)
     return hz::launch_apply_2x2_strided(p->g, p->d64, x.p, x.rs, y.p, y.rs, nvec, 0.0, 0.0, st);
+  if (p->spectral)
+    return hz::launch_spectral<double2>(p->spec, p->g, hz::SPEC_APPLY, hz::vec_map(x.p, x.rs),
+                                        hz::vec_map(y.p, y.rs), nvec, p->d64, 0.0, 0.0,
+                                        (double2*)p->spec_tmp, st);
   return hz::launch_stencil_diag(p->g, p->d64, x, y, nvec, 0.0, 0.0, st);
 }
 
@@ -613,7 +677,7 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
     return HZ_OK;
   }
   // Aw, step d, inner start v0 = (r - d Aw)/||r - d Aw||
-  HZ_TIMED_F(p, 1, st, (stencil_bytes<double2, double2>(n, nvec)), kStencil64Flops * n * nvec,
+  HZ_TIMED_F(p, 1, st, op64_bytes(p, nvec), op64_flops(p, nvec),
              apply_op64(p, Buf<const double2>{p->w, n}, Buf<double2>{p->Aw, n}, nvec, st));
   const long long vrs = (long long)(p->lim.inner_k_max + 1) * n;
   // two launches: d (reads Aw, r) and v0 = r - d Aw with its norm (reads Aw, r; writes v0)
@@ -624,9 +688,13 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
                            nvec, st));
   // with ILU(0) (Section 6.3) the inner GMRES runs right-preconditioned on A M^{-1}; its sweeps
   // in float32 arithmetic in the complex64-sweep form, float64 in the all-float64 form
-  const bool ilu = p->ilu_on;
-  const bool ilu32 = ilu && precision == HZ_MIXED_C64 && hz::ilu0_fits32(p->g);
+  const bool ilu = p->ilu_on || p->invlap_on;
+  const bool ilu32 = p->ilu_on && precision == HZ_MIXED_C64 && hz::ilu0_fits32(p->g);
   auto ilu_apply = [&](Buf<const double2> t, Buf<double2> z) -> cudaError_t {
+    if (p->invlap_on)
+      return hz::launch_spectral<double2>(p->spec, p->g, hz::SPEC_INVLAP, hz::vec_map(t.p, t.rs),
+                                          hz::vec_map(z.p, z.rs), nvec, p->d64, 0.0, 0.0,
+                                          (double2*)p->spec_tmp, st);
     if (ilu32)
       return hz::launch_ilu0_32(p->g, p->invd32, t, Buf<float2>{p->ilu_u32, p->g.n}, z, nvec,
                                 st);
@@ -639,7 +707,7 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
       HZ_CUDA(ilu_apply(src, Buf<double2>{p->ilu_t, n}));
       src = Buf<const double2>{p->ilu_t, n};
     }
-    HZ_TIMED_F(p, 1, st, (stencil_bytes<double2, double2>(n, nvec)), kStencil64Flops * n * nvec,
+    HZ_TIMED_F(p, 1, st, op64_bytes(p, nvec), op64_flops(p, nvec),
                apply_op64(p, src, wj, nvec, st));
     for (int mode = 0; mode < 3; ++mode)
       HZ_TIMED_F(p, 2, st, cgs_bytes(mode, n, j + 1, nvec), cgs_flops(mode, n, j + 1, nvec),
@@ -765,7 +833,7 @@ hz_status outer_step_launches(hz_problem* p, int k, int nrhs, int K, int precisi
     p->tail_used = true;
     return HZ_OK;
   }
-  HZ_TIMED_F(p, 1, st, (stencil_bytes<double2, double2>(n, nrhs)), kStencil64Flops * n * nrhs,
+  HZ_TIMED_F(p, 1, st, op64_bytes(p, nrhs), op64_flops(p, nrhs),
              apply_op64(p, Buf<const double2>{zk.p, zrs}, wk, nrhs, st));
   for (int mode = 0; mode < 3; ++mode)
     HZ_TIMED_F(p, 2, st, cgs_bytes(mode, n, k + 1, nrhs), cgs_flops(mode, n, k + 1, nrhs),
@@ -1005,6 +1073,8 @@ hz_status check_solve_args(const hz_problem* p, int nrhs, const hz_solve_opts* o
                                 "HZ_MIXED_C64_FCI32 only");
   if (p->case2 && opts->precision != HZ_C128)
     return fail(HZ_ERR_INVALID, "Case Two problems solve in HZ_C128");
+  if (p->spectral && opts->precision != HZ_C128 && opts->precision != HZ_MIXED_C64)
+    return fail(HZ_ERR_INVALID, "spectral problems solve in HZ_C128 or HZ_MIXED_C64");
   if (p->ilu_on && opts->precision != HZ_C128 && opts->precision != HZ_MIXED_C64)
     return fail(HZ_ERR_INVALID, "ILU(0) preconditions the float64 inner GMRES (HZ_C128, "
                                 "HZ_MIXED_C64)");
@@ -1062,6 +1132,18 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
       return fail(HZ_ERR_INVALID, "wavespeed must be positive and finite");
   if ((long long)grid->nz * limits->nrhs_max > 65535)
     return fail(HZ_ERR_INVALID, "nz * nrhs_max must not exceed 65535");
+  hz::SpecPlan spec{};
+  if (grid->discretization == HZ_DISC_SPECTRAL) {
+    if (limits->flags & (HZ_LIMIT_CASE_TWO | HZ_LIMIT_Z_C64))
+      return fail(HZ_ERR_INVALID, "spectral problems: HZ_LIMIT_SWEEPS_C64 is the only flag");
+    const int dims[3] = {grid->nx, grid->ny, grid->nz};
+    for (int a = 0; a < 3; ++a) {
+      spec.ax[a].n = dims[a];
+      if (!hz::fft_factor(dims[a], spec.ax[a].rad, &spec.ax[a].nst))
+        return fail(HZ_ERR_INVALID, "spectral grid sizes must be products of 2, 3 and 5, at "
+                                    "most 1024");
+    }
+  }
 
   hz_problem* p = new hz_problem();
   auto bail = [&](hz_status s) {
@@ -1094,6 +1176,8 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
   p->g.srows = 4;
   std::string err;
   p->case2 = (limits->flags & HZ_LIMIT_CASE_TWO) != 0;
+  p->spectral = grid->discretization == HZ_DISC_SPECTRAL;
+  p->spec = spec;
   p->nf = p->case2 ? 2 * n : n;
   bool nodes_ok;
   if (p->case2) {
@@ -1151,7 +1235,8 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
       delete p;
       return cuda_fail(pe, "cooperative kernel plans");
     }
-    if (p->case2) {  // the cooperative kernels apply Case One's operator: not for Case Two
+    if (p->case2 || p->spectral) {
+      // the cooperative kernels apply the 7-point operator of Case One only
       p->tail_ppt[0] = p->tail_ppt[1] = p->arn_ppt = p->a64_ppt = p->t64_ppt = 0;
     }
   }
@@ -1232,7 +1317,7 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
             const double t = double(d) / double(L);
             ap = (grid->sigma_max * (t * t)) * mp;
           }
-          dg[q] = make_double2(6.0 * p->g.cs - mp, -ap);
+          dg[q] = make_double2((p->spectral ? 0.0 : 6.0 * p->g.cs) - mp, -ap);
         }
     e = cudaMemcpy(p->d64, dg.data(), sizeof(double2) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
@@ -1254,7 +1339,48 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
     delete p;
     return cuda_fail(e, "cooperative FCI tail set-up");
   }
-  if (limits->autotune && !p->case2) {
+  if (p->spectral) {
+    // line-FFT tables of every axis: twiddles exp(-2 pi i k / n) and the eigenvalue shares
+    // s (2 pi min(k, n - k) / (n h))^2, float64 on the host, rounded for the float32 kernels
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+      hz::FftAxis& ax = p->spec.ax[a];
+      const int na = ax.n;
+      std::vector<double2> tw(na);
+      std::vector<float2> tw32(na);
+      std::vector<double> ev(na);
+      std::vector<float> ev32(na);
+      for (int k = 0; k < na; ++k) {
+        const double ang = 2.0 * std::acos(-1.0) * double(k) / double(na);
+        tw[k] = make_double2(std::cos(ang), -std::sin(ang));
+        tw32[k] = make_float2(float(tw[k].x), float(tw[k].y));
+        const double kw = 2.0 * std::acos(-1.0) * double(std::min(k, na - k)) /
+                          (double(na) * grid->h);
+        ev[k] = p->su.s * kw * kw;
+        ev32[k] = float(ev[k]);
+      }
+      void* d[4];
+      const size_t sz[4] = {sizeof(double2) * na, sizeof(float2) * na, sizeof(double) * na,
+                            sizeof(float) * na};
+      const void* h[4] = {tw.data(), tw32.data(), ev.data(), ev32.data()};
+      for (int b = 0; b < 4; ++b) {
+        if ((s = dalloc(p, &d[b], sz[b])) != HZ_OK) return bail(s);
+        e = cudaMemcpy(d[b], h[b], sz[b], cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) break;
+      }
+      ax.tw64 = (const double2*)d[0];
+      ax.tw32 = (const float2*)d[1];
+      ax.e64 = (const double*)d[2];
+      ax.e32 = (const float*)d[3];
+    }
+    if (e != cudaSuccess) {
+      delete p;
+      return cuda_fail(e, "spectral tables");
+    }
+    // FFT scratch: a stage's batch of J x nrhs node inputs in double2 covers every use
+    if ((s = dalloc(p, &p->spec_tmp, sizeof(double2) * (size_t)p->J * R * n)) != HZ_OK)
+      return bail(s);
+  }
+  if (limits->autotune && !p->case2 && !p->spectral) {
     const hz_status ts = autotune(p);
     if (ts != HZ_OK) {
       delete p;
@@ -1338,6 +1464,8 @@ hz_status hz_problem_set_preconditioner(hz_problem* p, hz_net* net, int mode) {
   HZ_TRY(check_problem(p));
   if (mode < 0 || mode > 3) return fail(HZ_ERR_INVALID, "preconditioner mode 0..3");
   if (mode != 0 && !net) return fail(HZ_ERR_INVALID, "modes 1..3 need a network");
+  if (mode != 0 && p->spectral)
+    return fail(HZ_ERR_INVALID, "the network preconditions 7-point problems only");
   if (mode != 0 && p->case2)
     return fail(HZ_ERR_INVALID, "the network preconditions Case One problems only");
   if (mode != 0 && !hz::net_fits(net, 1, p->g.nx, p->g.ny, p->g.nz))
@@ -1357,6 +1485,9 @@ hz_status hz_problem_set_preconditioner(hz_problem* p, hz_net* net, int mode) {
 hz_status hz_problem_set_inner_ilu(hz_problem* p, int on) {
   HZ_TRY(check_problem(p));
   if (on && p->case2) return fail(HZ_ERR_INVALID, "ILU(0) applies to Case One problems");
+  if (on && p->spectral)
+    return fail(HZ_ERR_INVALID, "ILU(0) applies to 7-point problems (spectral problems: "
+                                "hz_problem_set_inner_invlap)");
   HZ_TRY(set_device(p));
   if (on && !p->invd) {
     HZ_CUDA(hz::ilu0_prepare());
@@ -1375,6 +1506,32 @@ hz_status hz_problem_set_inner_ilu(hz_problem* p, int on) {
   }
   if ((on != 0) != p->ilu_on) p->drop_graphs();
   p->ilu_on = on != 0;
+  return HZ_OK;
+}
+
+hz_status hz_problem_set_inner_invlap(hz_problem* p, int on) {
+  HZ_TRY(check_problem(p));
+  if (on && !p->spectral)
+    return fail(HZ_ERR_INVALID, "the inverse-Laplacian preconditioner needs a spectral problem");
+  HZ_TRY(set_device(p));
+  if (on && !p->ilu_t)  // the preconditioned inner GMRES's scratch field per right-hand side
+    HZ_TRY(dalloc(p, (void**)&p->ilu_t, sizeof(double2) * (size_t)p->nf * p->lim.nrhs_max));
+  if ((on != 0) != p->invlap_on) p->drop_graphs();
+  p->invlap_on = on != 0;
+  return HZ_OK;
+}
+
+hz_status hz_invlap_apply(hz_problem* p, const void* t, void* z, int nvec, void* stream) {
+  HZ_TRY(check_problem(p));
+  if (!p->spectral) return fail(HZ_ERR_INVALID, "hz_invlap_apply needs a spectral problem");
+  if (nvec < 0 || nvec > p->lim.nrhs_max * p->J) return fail(HZ_ERR_INVALID, "nvec out of range");
+  if (nvec == 0) return HZ_OK;
+  if (!t || !z) return fail(HZ_ERR_INVALID, "null field");
+  HZ_TRY(set_device(p));
+  const long long n = p->g.n;
+  HZ_CUDA(hz::launch_spectral<double2>(p->spec, p->g, hz::SPEC_INVLAP, hz::vec_map(t, n),
+                                       hz::vec_map(z, n), nvec, p->d64, 0.0, 0.0,
+                                       (double2*)p->spec_tmp, (cudaStream_t)stream));
   return HZ_OK;
 }
 
@@ -1521,6 +1678,24 @@ hz_status hz_apply_shifted(hz_problem* p, double zr, double zi, const void* x, v
   HZ_TRY(set_device(p));
   cudaStream_t st = (cudaStream_t)stream;
   const long long n = p->g.n;
+  if (p->spectral) {
+    if (nvec > p->lim.nrhs_max * p->J)
+      return fail(HZ_ERR_INVALID, "spectral problems: nvec <= nrhs_max * J");
+    if (precision == HZ_C128) {
+      HZ_TIMED(p, 1, st, op64_bytes(p, nvec),
+               (hz::launch_spectral<double2>(p->spec, p->g, hz::SPEC_APPLY,
+                                             hz::vec_map(x, n), hz::vec_map(y, n), nvec, p->d64,
+                                             zr, zi, (double2*)p->spec_tmp, st)));
+    } else if (precision == HZ_MIXED_C64) {
+      HZ_TIMED(p, 1, st, 0.5 * op64_bytes(p, nvec),
+               (hz::launch_spectral<float2>(p->spec, p->g, hz::SPEC_APPLY, hz::vec_map(x, n),
+                                            hz::vec_map(y, n), nvec, p->d32, zr, zi,
+                                            (float2*)p->spec_tmp, st)));
+    } else {
+      return fail(HZ_ERR_INVALID, "unknown precision");
+    }
+    return HZ_OK;
+  }
   if (precision == HZ_C128) {
     HZ_TIMED(p, 1, st, (stencil_bytes<double2, double2>(n, nvec)),
              (hz::launch_stencil_diag(p->g, p->d64,
@@ -1609,6 +1784,8 @@ hz_status hz_fci(hz_problem* p, const void* r, void* out, int nvec, int inner_k,
   if (p->ilu_on && precision != HZ_C128 && precision != HZ_MIXED_C64)
     return fail(HZ_ERR_INVALID, "ILU(0) preconditions the float64 inner GMRES (HZ_C128, "
                                 "HZ_MIXED_C64)");
+  if (p->spectral && precision != HZ_C128 && precision != HZ_MIXED_C64)
+    return fail(HZ_ERR_INVALID, "spectral problems run HZ_C128 or HZ_MIXED_C64");
   if (nvec == 0) return HZ_OK;
   if (!r || !out) return fail(HZ_ERR_INVALID, "null field");
   HZ_TRY(set_device(p));
@@ -1745,12 +1922,23 @@ struct SolveState {
                                nrhs, st));
       return enqueue_flags();
     }
-    HZ_CUDA(hz::launch_residual_start(p->g, p->m64, Buf<const double2>{(const double2*)f, n},
-                                      p->su.s,
-                                      cycle == 0 ? Buf<const double2>{nullptr, 0}
-                                                 : Buf<const double2>{(const double2*)u, n},
-                                      Buf<double2>{p->V, vrs}, go, p->partial, p->counters, nrhs,
-                                      st));
+    if (p->spectral && cycle > 0) {
+      // spectral: A u by the line FFTs, s f - A u in Aw, then the start from that field
+      HZ_CUDA(apply_op64(p, Buf<const double2>{(const double2*)u, n}, Buf<double2>{p->Aw, n},
+                         nrhs, st));
+      HZ_CUDA(hz::launch_scaled_sub((const double2*)f, n, p->su.s, p->Aw, n, p->Aw, n, n, nrhs,
+                                    st));
+      HZ_CUDA(hz::launch_residual_start(p->g, p->m64, Buf<const double2>{p->Aw, n}, 1.0,
+                                        Buf<const double2>{nullptr, 0}, Buf<double2>{p->V, vrs},
+                                        go, p->partial, p->counters, nrhs, st));
+    } else {
+      HZ_CUDA(hz::launch_residual_start(p->g, p->m64, Buf<const double2>{(const double2*)f, n},
+                                        p->su.s,
+                                        cycle == 0 ? Buf<const double2>{nullptr, 0}
+                                                   : Buf<const double2>{(const double2*)u, n},
+                                        Buf<double2>{p->V, vrs}, go, p->partial, p->counters,
+                                        nrhs, st));
+    }
     for (int r = 0; r < nrhs; ++r) mvs[r] += cycle == 0 ? 0 : 1;
     if (o->precision == HZ_MIXED_C64_FF)
       HZ_CUDA(hz::launch_scale_ff_from64(Buf<float4>{(float4*)p->V, vrs},

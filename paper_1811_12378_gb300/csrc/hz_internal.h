@@ -75,6 +75,7 @@ struct StageNode {
   float wrh, wrl, wih, wil;  // the same split into float pairs (hi + lo) for the complex64 sum
   int kind, yzero;
   long long in, kout, acc, yout;  // element offsets of the node's fields in the rhs workspace
+  int lapi;  // spectral problems: index of the node's input in the stage's Laplacian batch
 };
 
 template <typename R>
@@ -84,6 +85,64 @@ struct StageArgs {
   int final_quad;
   int quad64;  // complex64 sweeps: form the quadrature sum in float64 (0: float pairs)
 };
+
+// ---------------------------------------------------------------- Fourier spectral (hz_fft.cu)
+// The spectral Laplacian S = F^H Lambda F of the periodic box (Section 7.1,
+// eq:eig-Laplacian-spectral) and the regularised inverse Laplacian F^H diag(1/max(lambda, 1)) F
+// (Section 7.3), applied by line FFTs of the project's own (radices 2, 3, 4, 5).
+constexpr int FFT_MAXN = 1024;  // longest grid line of a spectral problem
+constexpr int FFT_MAXST = 10;   // radix stages of one line
+
+struct FftAxis {
+  int n, nst;
+  int rad[FFT_MAXST];
+  const double2* tw64;  // exp(-2 pi i k / n), k < n
+  const float2* tw32;
+  const double* e64;    // s (2 pi min(k, n - k) / (n h))^2, k < n: this axis's share of lambda
+  const float* e32;
+};
+
+struct SpecPlan {
+  FftAxis ax[3];  // x, y, z
+};
+
+// nvec fields: field v at (T*)base + (v / nq) * rs + off[v % nq] (elements).
+struct VecMap {
+  const void* base;
+  long long rs;
+  int nq;
+  long long off[MAXJ];
+};
+
+inline VecMap vec_map(const void* p, long long rs) {
+  VecMap m{};
+  m.base = p;
+  m.rs = rs;
+  m.nq = 1;
+  return m;
+}
+
+enum SpecMode { SPEC_APPLY = 0, SPEC_LAP = 1, SPEC_INVLAP = 2 };
+
+// Radices of an FFT of length n (false unless n = 2^a 3^b 5^c <= FFT_MAXN).
+bool fft_factor(int n, int* rad, int* nst);
+// out = (s S - diag(m) - i diag(a) - zI) in (SPEC_APPLY, dg = -m - i a), s S in (SPEC_LAP) or the
+// regularised inverse Laplacian of in (SPEC_INVLAP), for nvec fields; tmp holds nvec fields.
+template <typename T>
+cudaError_t launch_spectral(const SpecPlan& sp, const Geom& g, int mode, const VecMap& in,
+                            const VecMap& out, int nvec, const T* dg, double zr, double zi,
+                            T* tmp, cudaStream_t st);
+// t = sc f - a (nvec fields): the true residual from a precomputed A u.
+cudaError_t launch_scaled_sub(const double2* f, long long frs, double sc, const double2* a,
+                              long long ars, double2* t, long long trs, long long n, int nvec,
+                              cudaStream_t st);
+// One stage of the polynomial scheme on a spectral problem: the node inputs' s S x come
+// precomputed in lap (field l of right-hand side r at lap + (r * nlap + l) * n).
+template <typename T, typename R>
+cudaError_t launch_poly_stage_spec(const Geom& g, const T* dg, Buf<const T> f, T* ws,
+                                   long long wrs, const T* lap, int nlap, Buf<double2> w,
+                                   Buf<float2> w32, int nvec, const StageArgs<R>& a,
+                                   cudaStream_t st);
 
 // Per-right-hand-side state of one GMRES / FGMRES cycle on the device.
 struct GmresDev {

@@ -162,8 +162,9 @@ extern "C" hz_status hz_residual_noalloc(const hz_grid* grid, const double* c, d
                                          const void* f, double fscale, const void* u, void* r,
                                          double* norm2, int nvec, void* stream) {
   if (!grid || grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->h > 0) ||
-      !(grid->omega > 0) || grid->layer_cells < 0 || !(grid->sigma_max >= 0) || !(c_min > 0))
-    return fail(HZ_ERR_INVALID, "hz_residual_noalloc: invalid grid or c_min");
+      !(grid->omega > 0) || grid->layer_cells < 0 || !(grid->sigma_max >= 0) || !(c_min > 0) ||
+      grid->discretization != HZ_DISC_FD7)
+    return fail(HZ_ERR_INVALID, "hz_residual_noalloc: invalid grid or c_min (7-point grids only)");
   if (nvec < 0 || nvec > kMaxVec)
     return fail(HZ_ERR_INVALID, "hz_residual_noalloc: nvec must be in [0, 64]");
   if (nvec == 0) return HZ_OK;

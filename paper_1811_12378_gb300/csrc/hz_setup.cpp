@@ -4,7 +4,8 @@
 //
 // Readings used where the paper leaves the procedure open:
 //  * the rectangle is B = [b1, b2] x [-rho2, 0] with exact Weyl bounds of s L_h - diag(m)
-//    (the 7-point Dirichlet eigenvalues are known in closed form) and rho2 = max a;
+//    (the 7-point Dirichlet and the Fourier spectral eigenvalues are known in closed form)
+//    and rho2 = max a;
 //  * delta has the sign of Im z_j; |delta| is searched on 512 equal steps of
 //    (0, 4(q+1)/W], W = max |lambda - z0| over the sampled boundary of B, then refined by
 //    golden-section search on the bracket of the best grid point;
@@ -143,16 +144,23 @@ void setup_operator(const hz_grid& g, const double* c, Setup& out) {
           amax = std::max(amax, (g.sigma_max * (t * t)) * mp);
         }
       }
-  // extreme eigenvalues of the Dirichlet -Delta_h: sums over the axes of
-  // (4/h^2) sin^2(k pi / (2(n+1))) at k = 1 and k = n
   double lo = 0.0, hi = 0.0;
   const int dims[3] = {g.nx, g.ny, g.nz};
   for (int a = 0; a < 3; ++a) {
     const double nn = dims[a];
-    const double s1 = std::sin(kPi / (2.0 * (nn + 1.0)));
-    const double s2 = std::sin(nn * kPi / (2.0 * (nn + 1.0)));
-    lo += 4.0 / (g.h * g.h) * s1 * s1;
-    hi += 4.0 / (g.h * g.h) * s2 * s2;
+    if (g.discretization == HZ_DISC_SPECTRAL) {
+      // Fourier spectral -Delta (eq:eig-Laplacian-spectral): the constant mode gives 0, the
+      // largest wavenumber along an axis of n points is 2 pi floor(n/2) / (n h)
+      const double k = 2.0 * kPi * std::floor(nn / 2.0) / (nn * g.h);
+      hi += k * k;
+    } else {
+      // extreme eigenvalues of the Dirichlet -Delta_h: sums over the axes of
+      // (4/h^2) sin^2(k pi / (2(n+1))) at k = 1 and k = n
+      const double s1 = std::sin(kPi / (2.0 * (nn + 1.0)));
+      const double s2 = std::sin(nn * kPi / (2.0 * (nn + 1.0)));
+      lo += 4.0 / (g.h * g.h) * s1 * s1;
+      hi += 4.0 / (g.h * g.h) * s2 * s2;
+    }
   }
   out.b1 = out.s * lo - mmax;
   out.b2 = out.s * hi - mmin;

@@ -19,6 +19,10 @@ HZ_MIXED_C64 = 1
 HZ_MIXED_C64_FCI32 = 2
 HZ_MIXED_C64_FF = 3
 
+# discretisations of hz_grid.discretization
+HZ_DISC_FD7 = 0
+HZ_DISC_SPECTRAL = 1
+
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory",
           4: "not converged", 5: "breakdown", 6: "diverged", 7: "set-up failed", 8: "timeout"}
 
@@ -32,7 +36,7 @@ EXPORTS = ["hz_problem_create", "hz_plan", "hz_problem_destroy", "hz_problem_get
            "hz_net_set_params", "hz_net_get_params", "hz_net_forward", "hz_net_train_step",
            "hz_net_train_fields", "hz_problem_set_preconditioner", "hz_conv3d",
            "hz_conv3d_backward", "hz_conv3d_workspace_bytes", "hz_problem_set_inner_ilu",
-           "hz_ilu0_apply",
+           "hz_ilu0_apply", "hz_problem_set_inner_invlap", "hz_invlap_apply",
            "hz_status_string", "hz_last_error", "hz_launch_count"]
 
 # kernel classes of hz_profile_read
@@ -41,7 +45,8 @@ PROF_POLY, PROF_STENCIL, PROF_KRYLOV = 0, 1, 2
 
 class HzGrid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double),
-                ("omega", C.c_double), ("layer_cells", C.c_int), ("sigma_max", C.c_double)]
+                ("omega", C.c_double), ("layer_cells", C.c_int), ("sigma_max", C.c_double),
+                ("discretization", C.c_int)]
 
 
 class HzContour(C.Structure):
@@ -140,6 +145,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.hz_problem_set_preconditioner.argtypes = [P, P, C.c_int]
     lib.hz_problem_set_inner_ilu.argtypes = [P, C.c_int]
     lib.hz_ilu0_apply.argtypes = [P, P, P, C.c_int, P]
+    lib.hz_problem_set_inner_invlap.argtypes = [P, C.c_int]
+    lib.hz_invlap_apply.argtypes = [P, P, P, C.c_int, P]
     lib.hz_conv3d.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P, C.c_int,
                               C.c_int, P, P, P]
     lib.hz_conv3d_backward.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P,
@@ -180,9 +187,9 @@ def _ip(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_int))
 
 
-def _grid(nx, ny, nz, h, omega, layer_cells, sigma_max):
+def _grid(nx, ny, nz, h, omega, layer_cells, sigma_max, discretization=HZ_DISC_FD7):
     return HzGrid(int(nx), int(ny), int(nz), float(h), float(omega), int(layer_cells),
-                  float(sigma_max))
+                  float(sigma_max), int(discretization))
 
 
 def _tables_from(buf):
@@ -198,12 +205,13 @@ def _new_tables(J):
 
 
 def plan(c: np.ndarray, h: float, omega: float, layer_cells: int, sigma_max: float, J: int,
-         t: float, eps: float, qmax: int = 5, reduction: float = 5.0):
+         t: float, eps: float, qmax: int = 5, reduction: float = 5.0,
+         discretization: int = HZ_DISC_FD7):
     """Host-only set-up of libhz (no GPU): (info dict, node tables dict)."""
     lib = load()
     c = np.ascontiguousarray(c, dtype=np.float64)
     nz, ny, nx = c.shape
-    g = _grid(nx, ny, nz, h, omega, layer_cells, sigma_max)
+    g = _grid(nx, ny, nz, h, omega, layer_cells, sigma_max, discretization)
     co = HzContour(int(J), float(t), float(eps), int(qmax), float(reduction))
     info = HzInfo()
     tb = _new_tables(J)
@@ -257,13 +265,14 @@ class Problem:
     """
 
     def __init__(self, c, h, omega, layer_cells, sigma_max, J, t, eps, qmax=5, reduction=5.0,
-                 nrhs_max=1, restart_max=30, inner_k_max=8, autotune=True, flags=0):
+                 nrhs_max=1, restart_max=30, inner_k_max=8, autotune=True, flags=0,
+                 discretization=HZ_DISC_FD7):
         self._lib = load()
         c = np.ascontiguousarray(c, dtype=np.float64)
         self.shape = c.shape
         nz, ny, nx = c.shape
         self.n = nx * ny * nz
-        g = _grid(nx, ny, nz, h, omega, layer_cells, sigma_max)
+        g = _grid(nx, ny, nz, h, omega, layer_cells, sigma_max, discretization)
         co = HzContour(int(J), float(t), float(eps), int(qmax), float(reduction))
         lim = HzLimits(int(nrhs_max), int(restart_max), int(inner_k_max), 1 if autotune else 0,
                        int(flags))
@@ -325,6 +334,20 @@ class Problem:
         z = torch.empty_like(t) if out is None else out
         zp, _ = _dev_ptr(z, torch.complex128, self.n)
         _check(self._lib.hz_ilu0_apply(self._h, tp, zp, nvec, _stream(stream)), self._lib)
+        return z
+
+    def set_inner_invlap(self, on: bool = True):
+        """Spectral problems: the regularised inverse Laplacian 1/max(lambda, 1) as the inner
+        GMRES's right preconditioner (hz_problem_set_inner_invlap)."""
+        _check(self._lib.hz_problem_set_inner_invlap(self._h, 1 if on else 0), self._lib)
+
+    def invlap_apply(self, t, out=None, stream=None):
+        """z = M^{-1} t with the regularised inverse Laplacian (complex128 fields)."""
+        import torch
+        tp, nvec = _dev_ptr(t, torch.complex128, self.n)
+        z = torch.empty_like(t) if out is None else out
+        zp, _ = _dev_ptr(z, torch.complex128, self.n)
+        _check(self._lib.hz_invlap_apply(self._h, tp, zp, nvec, _stream(stream)), self._lib)
         return z
 
     def set_spin_limit(self, polls: int = -1):

@@ -38,6 +38,32 @@ def test_plan_matches_oracle(wl):
         assert tb["nu"][j] == pytest.approx(nd.nu, rel=1e-9)
 
 
+def spectral_cases():
+    return [W.small_case(3, 12, 10, 9, layer=2, J=4, ppw=2.5),
+            W.small_case(6, 7, 16, 5, layer=1, J=6, ppw=3.0),
+            W.spectral_bumps(24, 3),
+            W.spectral_bumps(64, 1)]
+
+
+@pytest.mark.parametrize("t", [1.0, 0.6])
+@pytest.mark.parametrize("wl", spectral_cases(), ids=lambda w: w.name)
+def test_spectral_plan_matches_oracle(wl, t):
+    """The same for the Fourier spectral Laplacian (its rectangle from the closed-form
+    wavenumbers, eq:eig-Laplacian-spectral), on circles and ellipses of ratio t = 0.6."""
+    info, tb = hzpkg.plan(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, wl.J, t, wl.eps,
+                          discretization=hzpkg.HZ_DISC_SPECTRAL)
+    op = O.make_operator(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, kind="spectral")
+    (b1, b2, rho2), nodes = O.setup_nodes(op, wl.J, t, wl.eps)
+    assert info["b1"] == pytest.approx(b1, rel=1e-13, abs=1e-13)
+    assert info["b2"] == pytest.approx(b2, rel=1e-13)
+    assert info["rho2"] == pytest.approx(rho2, rel=1e-14)
+    for j, nd in enumerate(nodes):
+        assert abs(tb["z"][j] - nd.z) <= 1e-13 * abs(nd.z)
+        assert abs(tb["sigma"][j] - nd.sigma) <= 1e-13 * abs(nd.sigma)
+        assert tb["q"][j] == nd.q and tb["sweeps"][j] == nd.sweeps
+        assert tb["delta"][j] == pytest.approx(nd.delta, rel=1e-7)
+
+
 def test_plan_rejects_bad_input():
     c = np.ones((4, 4, 4))
     with pytest.raises(hzpkg.HzError):
