@@ -45,7 +45,8 @@ bool fft_factor(int n, int* rad, int* nst) {
 
 namespace {
 
-constexpr int FT = 256;  // threads of a line-transform block
+constexpr int FT = 128;       // threads of a line-transform block
+constexpr int FT_XLINES = 64;  // most lines of an x-pass tile (their pointers sit in shared memory)
 
 enum PassKind { PASS_FWD = 0, PASS_MID = 1, PASS_INV = 2, PASS_LAST = 3 };
 
@@ -56,7 +57,8 @@ template <> struct RealT<double2> { using type = double; };
 struct PassArgs {
   VecMap src, dst, xin;
   int nx, ny, nz, nvec;
-  int tl;           // lines per tile
+  int tl;           // lines per tile (a power of two)
+  int tlsh;         // log2(tl)
   int kind;         // PassKind
   int invlap;       // PASS_MID: 1 / max(lambda, 1) instead of lambda
   int combine;      // PASS_LAST: add (dg - z) x
@@ -64,12 +66,26 @@ struct PassArgs {
   double zr, zi;
   const void* dg;
   int n, nst;       // this pass's line length and stages
+  int nsh;          // log2(n), or -1 when n is not a power of two
   int rad[FFT_MAXST];
+  int lsh[FFT_MAXST];   // log2 of the length L combined before stage s, or -1
+  int nbsh[FFT_MAXST];  // log2(n / radix of stage s), or -1
   const void* tw;   // this axis's twiddle table (T)
   const void* ex;   // per-axis eigenvalue shares (real type of T)
   const void* ey;
   const void* ez;
 };
+
+// q = x / d, r = x - q d, by a shift where d = 2^sh
+__device__ __forceinline__ void divmod(int x, int d, int sh, int& q, int& r) {
+  if (sh >= 0) {
+    q = x >> sh;
+    r = x & ((1 << sh) - 1);
+  } else {
+    q = x / d;
+    r = x - q * d;
+  }
+}
 
 template <typename T>
 __device__ __forceinline__ T cconj(T a) { return mk(a.x, -a.y); }
@@ -79,42 +95,43 @@ __device__ __forceinline__ T* field_ptr(const VecMap& m, int v) {
   return (T*)m.base + (long long)(v / m.nq) * m.rs + m.off[v % m.nq];
 }
 
-// One Stockham stage over all lines of the tile: X -> Y.
-template <typename T>
-__device__ __forceinline__ void fft_stage(const T* X, T* Y, int tl, int n, int ls, int L, int p,
-                                          const T* __restrict__ tw) {
-  const int nb = n / p;          // butterflies per line
-  const int r = n / (L * p);
-  const int ts = n / (L * p);    // twiddle index step: w_{Lp}^{jq} = tw[j q ts]
+// One Stockham stage of radix P over all lines of the tile: X -> Y.
+template <typename T, int P>
+__device__ __forceinline__ void fft_stage(const T* X, T* Y, int tl, int n, int ls, int L,
+                                          int lsh, int nbsh, const T* __restrict__ tw) {
+  const int nb = n / P;        // butterflies per line
+  const int r = n / (L * P);   // also the twiddle index step: w_{LP}^{jq} = tw[j q r]
   for (int b = threadIdx.x; b < tl * nb; b += FT) {
-    const int l = b / nb, u = b - l * nb;
-    const int j = u % L, m = u / L;
+    int l, u, m, j;
+    divmod(b, nb, nbsh, l, u);
+    divmod(u, L, lsh, m, j);
     const T* x = X + l * ls;
-    T* y = Y + l * ls;
-    T a[5];
+    T a[P];
     a[0] = x[m * L + j];
-    for (int q = 1; q < p; ++q) {
+#pragma unroll
+    for (int q = 1; q < P; ++q) {
       const T v = x[(m + r * q) * L + j];
-      a[q] = (j == 0) ? v : cmul(v, tw[j * q * ts]);
+      a[q] = (j == 0) ? v : cmul(v, tw[j * q * r]);
     }
-    T* o = y + m * L * p + j;
-    if (p == 2) {
+    T* o = Y + l * ls + m * L * P + j;
+    if constexpr (P == 2) {
       o[0] = cadd(a[0], a[1]);
       o[L] = csub(a[0], a[1]);
-    } else if (p == 4) {
+    } else if constexpr (P == 4) {
       const T s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
       const T s13 = cadd(a[1], a[3]), d13 = csub(a[1], a[3]);
-      // -i (a1 - a3) for output 1, +i for output 3
-      const T mi = mk(d13.y, -d13.x);
+      const T mi = mk(d13.y, -d13.x);  // -i (a1 - a3): output 1 adds it, output 3 subtracts
       o[0] = cadd(s02, s13);
       o[L] = cadd(d02, mi);
       o[2 * L] = csub(s02, s13);
       o[3 * L] = csub(d02, mi);
     } else {
-      const int wstep = n / p;  // w_p^m = tw[m n / p]
-      for (int k = 0; k < p; ++k) {
+      const int wstep = n / P;  // w_P^m = tw[m n / P]
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
         T acc = a[0];
-        for (int q = 1; q < p; ++q) acc = cadd(acc, cmul(a[q], tw[((k * q) % p) * wstep]));
+#pragma unroll
+        for (int q = 1; q < P; ++q) acc = cadd(acc, cmul(a[q], tw[((k * q) % P) * wstep]));
         o[k * L] = acc;
       }
     }
@@ -127,7 +144,10 @@ __device__ T* fft_lines(T* A, T* B, int tl, int ls, const PassArgs& a, const T* 
   int L = 1;
   for (int s = 0; s < a.nst; ++s) {
     const int p = a.rad[s];
-    fft_stage<T>(A, B, tl, a.n, ls, L, p, tw);
+    if (p == 4) fft_stage<T, 4>(A, B, tl, a.n, ls, L, a.lsh[s], a.nbsh[s], tw);
+    else if (p == 2) fft_stage<T, 2>(A, B, tl, a.n, ls, L, a.lsh[s], a.nbsh[s], tw);
+    else if (p == 3) fft_stage<T, 3>(A, B, tl, a.n, ls, L, a.lsh[s], a.nbsh[s], tw);
+    else fft_stage<T, 5>(A, B, tl, a.n, ls, L, a.lsh[s], a.nbsh[s], tw);
     __syncthreads();
     T* t = A;
     A = B;
@@ -141,41 +161,57 @@ template <typename T, int AXIS>
 __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
   pdl_enter();
   using R = typename RealT<T>::type;
-  extern __shared__ unsigned char fft_smem[];
+  extern __shared__ __align__(16) unsigned char fft_smem[];
+  __shared__ const T* s_src[FT_XLINES];  // x pass: each line's first point, per buffer
+  __shared__ T* s_dst[FT_XLINES];
+  __shared__ const T* s_xin[FT_XLINES];
+  __shared__ long long s_off[FT_XLINES];  // x pass: each line's first point within its field
   const int n = a.n, tl = a.tl;
   const int ls = n | 1;  // odd line stride in shared memory
   T* A = reinterpret_cast<T*>(fft_smem);
   T* B = A + (size_t)tl * ls;
   const long long sxy = (long long)a.nx * a.ny;
   const T* __restrict__ tw = (const T*)a.tw;
-  // line l of the tile: its field, the offset of its first point and its point stride
-  auto line = [&](int l, int& v, long long& off, long long& stride) -> bool {
-    if (AXIS == 0) {
-      const long long lg = (long long)blockIdx.x * tl + l;
-      const long long per = (long long)a.ny * a.nz;
-      if (lg >= per * a.nvec) return false;
-      v = (int)(lg / per);
-      off = (lg - (long long)v * per) * a.nx;
-      stride = 1;
-      return true;
+  // lines of the tile: x pass, pointers per line; y and z passes, one base per buffer and
+  // valid lines [0, nvalid), line l at base + l, point e at + e * stride
+  int nvalid = 0;
+  long long stride = 1;
+  const T* srcb = nullptr;
+  T* dstb = nullptr;
+  if (AXIS == 0) {
+    const long long per = (long long)a.ny * a.nz;
+    const long long total = per * a.nvec;
+    const long long l0 = (long long)blockIdx.x * tl;
+    nvalid = (int)(total - l0 < tl ? total - l0 : (long long)tl);
+    for (int l = threadIdx.x; l < nvalid; l += FT) {
+      const long long lg = l0 + l;
+      const int v = (int)(lg / per);
+      const long long off = (lg - (long long)v * per) * a.nx;
+      s_src[l] = field_ptr<const T>(a.src, v) + off;
+      s_dst[l] = field_ptr<T>(a.dst, v) + off;
+      s_xin[l] = a.combine ? field_ptr<const T>(a.xin, v) + off : nullptr;
+      s_off[l] = off;
     }
-    const int i = blockIdx.x * tl + l;
-    if (i >= a.nx) return false;
-    v = blockIdx.z;
-    off = (AXIS == 1 ? (long long)blockIdx.y * sxy : (long long)blockIdx.y * a.nx) + i;
+    __syncthreads();
+  } else {
+    const int i0 = blockIdx.x * tl;
+    nvalid = min(tl, a.nx - i0);
+    const int v = blockIdx.z;
+    const long long off = (AXIS == 1 ? (long long)blockIdx.y * sxy : (long long)blockIdx.y * a.nx)
+                          + i0;
     stride = AXIS == 1 ? a.nx : sxy;
-    return true;
-  };
+    srcb = field_ptr<const T>(a.src, v) + off;
+    dstb = field_ptr<T>(a.dst, v) + off;
+  }
   const bool conj_in = a.kind == PASS_INV || a.kind == PASS_LAST;
-  // load
+  // load (x pass: consecutive threads walk a line; y, z: consecutive threads the x positions)
   for (int t = threadIdx.x; t < tl * n; t += FT) {
-    const int l = AXIS == 0 ? t / n : t % tl;
-    const int e = AXIS == 0 ? t % n : t / tl;
-    int v;
-    long long off, stride;
+    int l, e;
+    if (AXIS == 0) divmod(t, n, a.nsh, l, e);
+    else divmod(t, tl, a.tlsh, e, l);
     T val = czero<T>();
-    if (line(l, v, off, stride)) {
-      val = field_ptr<const T>(a.src, v)[off + (long long)e * stride];
+    if (l < nvalid) {
+      val = AXIS == 0 ? s_src[l][e] : srcb[l + (long long)e * stride];
       if (conj_in) val = cconj(val);
     }
     A[l * ls + e] = val;
@@ -183,16 +219,16 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
   __syncthreads();
   T* X = fft_lines<T>(A, B, tl, ls, a, tw);
   if (a.kind == PASS_MID) {
-    // z lines after the x and y transforms: point (l, e) holds wave numbers (i, j, e)
+    // z lines after the x and y transforms: point (l, e) holds wave numbers (i0 + l, j, e)
     const R* ex = (const R*)a.ex;
-    const R* ey = (const R*)a.ey;
     const R* ez = (const R*)a.ez;
     const R sc = R(a.scale);
-    const R lj = ey[blockIdx.y];
+    const R lj = ((const R*)a.ey)[blockIdx.y];
+    const int i0 = blockIdx.x * tl;
     for (int t = threadIdx.x; t < tl * n; t += FT) {
-      const int l = t % tl, e = t / tl;
-      const int i = blockIdx.x * tl + l;
-      const R lam = (i < a.nx ? ex[i] : R(0)) + lj + ez[e];
+      int l, e;
+      divmod(t, tl, a.tlsh, e, l);
+      const R lam = (l < nvalid ? ex[i0 + l] : R(0)) + lj + ez[e];
       const R mlt = a.invlap ? sc / (lam > R(1) ? lam : R(1)) : sc * lam;
       const T x = X[l * ls + e];
       X[l * ls + e] = mk(mlt * x.x, -(mlt * x.y));  // conj: the inverse transform follows
@@ -204,30 +240,39 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
   const bool conj_out = a.kind != PASS_FWD;
   const T* __restrict__ dg = (const T*)a.dg;
   const R zr = R(a.zr), zi = R(a.zi);
+  const bool comb = a.kind == PASS_LAST && a.combine;
   for (int t = threadIdx.x; t < tl * n; t += FT) {
-    const int l = AXIS == 0 ? t / n : t % tl;
-    const int e = AXIS == 0 ? t % n : t / tl;
-    int v;
-    long long off, stride;
-    if (!line(l, v, off, stride)) continue;
-    const long long pp = off + (long long)e * stride;
+    int l, e;
+    if (AXIS == 0) divmod(t, n, a.nsh, l, e);
+    else divmod(t, tl, a.tlsh, e, l);
+    if (l >= nvalid) continue;
     T val = X[l * ls + e];
     if (conj_out) val = cconj(val);
-    if (a.kind == PASS_LAST && a.combine) {
-      const T x = field_ptr<const T>(a.xin, v)[pp];
-      const T d = dg[pp];
+    if (AXIS == 0 && comb) {  // the last pass runs along x: add (dg - z) x at the point
+      const T x = s_xin[l][e];
+      const T d = dg[s_off[l] + e];
       const R dr = d.x - zr, di = d.y - zi;
       val = mk(val.x + dr * x.x - di * x.y, val.y + dr * x.y + di * x.x);
     }
-    field_ptr<T>(a.dst, v)[pp] = val;
+    if (AXIS == 0) s_dst[l][e] = val;
+    else dstb[l + (long long)e * stride] = val;
   }
 }
 
-template <typename T>
+inline int ilog2_exact(long long v) {  // log2(v) for a power of two, else -1
+  if (v <= 0 || (v & (v - 1)) != 0) return -1;
+  int k = 0;
+  while ((1LL << k) < v) ++k;
+  return k;
+}
+
+// Lines per tile: x passes about 512 points (at most FT_XLINES lines), y and z passes about
+// 1024 points and at most 16 lines (16 adjacent x positions: 128-256 byte rows); powers of two.
 int tile_lines(int n, int axis) {
-  const int target = sizeof(T) == 16 ? 1024 : 2048;  // points per tile: 32 KB of shared memory
-  int tl = std::max(1, target / n);
-  if (axis != 0) tl = std::min(tl, 32);
+  const int target = axis == 0 ? 512 : 1024;
+  const int cap = axis == 0 ? FT_XLINES : 16;
+  int tl = 1;
+  while (tl * 2 <= cap && tl * 2 * n <= target) tl *= 2;
   return tl;
 }
 
@@ -249,9 +294,18 @@ cudaError_t run_pass(int axis, PassArgs a, const SpecPlan& sp, cudaStream_t st) 
   const FftAxis& ax = sp.ax[axis];
   a.n = ax.n;
   a.nst = ax.nst;
-  for (int s = 0; s < FFT_MAXST; ++s) a.rad[s] = s < ax.nst ? ax.rad[s] : 1;
+  a.nsh = ilog2_exact(ax.n);
+  int L = 1;
+  for (int s = 0; s < FFT_MAXST; ++s) {
+    const int p = s < ax.nst ? ax.rad[s] : 1;
+    a.rad[s] = p;
+    a.lsh[s] = ilog2_exact(L);
+    a.nbsh[s] = ilog2_exact(ax.n / p);
+    L *= p;
+  }
   a.tw = tw_of<T>(ax);
-  a.tl = tile_lines<T>(ax.n, axis);
+  a.tl = tile_lines(ax.n, axis);
+  a.tlsh = ilog2_exact(a.tl);
   const size_t smem = 2 * sizeof(T) * (size_t)a.tl * (size_t)(ax.n | 1);
   count_launch();
   if (axis == 0) {
