@@ -557,6 +557,18 @@ bool arnoldi64_fits(const hz_problem* p, int nvec) {
          p->g.n <= kCoop64MaxPoints;
 }
 
+// Algorithmic bytes of the complex64 FCI tail (steps 3-5, one cooperative launch): step d
+// reads w, r and the diagonal and writes v_0; inner step j (basis of j fields) reads v_{j-1}
+// for A v, the basis twice per CGS2 pass pair (dot, update) with w read and written alongside,
+// and writes v_j: 4j + 7 fields; the combine reads the k_in + 1 basis fields and the float64 w
+// and writes the float64 result.  Every field counted once per pass, 8 bytes a point.
+double fci_tail32_bytes(long long n, int kin) {
+  double f = 4.0;
+  for (int j = 1; j <= kin; ++j) f += 4.0 * j + 7.0;
+  f += kin + 1.0;
+  return 8.0 * double(n) * f + 32.0 * double(n);
+}
+
 // Algorithmic bytes and float64 flops per point of the float64 FCI tail (step d, kin CGS2
 // steps, v + d w) and of one float64 outer Arnoldi step with nb basis fields: every field read
 // or written once per pass, 8 flops per complex multiply-add, 22 per stencil point.
@@ -635,7 +647,7 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
   if (fci32 && tail_fits(p, nvec, kin)) {
     // steps 3-5 in one cooperative launch
     const int c = kin <= 4 ? 0 : 1;
-    HZ_TIMED(p, 2, st, 8.0 * n * (6.0 + 4.0 * kin * (kin + 3)),
+    HZ_TIMED(p, 2, st, fci_tail32_bytes(n, kin),
              hz::launch_fci_tail32(p->g, p->d32, p->w32, p->f32, p->w, p->Vin32, p->Aw32, out.p,
                                    p->partial, p->tail_bar, (int*)(p->tail_bar + 2), n, kin,
                                    kBreakdown, p->tail_mode == 1 ? 1 : 0, p->tail_ppt[c],
