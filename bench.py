@@ -51,13 +51,16 @@ def parse():
     ap.add_argument("--ncu-large", action="store_true",
                     help="run only the 256^3 stencil / polynomial-stage bandwidth measurement, "
                          "bracketed with cudaProfilerStart/Stop")
-    ap.add_argument("--ncu-case", choices=["ilu", "net", "batched128"], default=None,
+    ap.add_argument("--ncu-case", choices=["ilu", "net", "batched128", "spectral128",
+                                           "spectral256"], default=None,
                     help="run only one profiling region, bracketed with cudaProfilerStart/Stop: "
                          "ilu = one FCI application with the ILU(0) inner preconditioner on the "
                          "64^3 workload (HZ_MIXED_C64); net = one forward pass and one training "
                          "step of the network on one 64^3 sample; batched128 = one FCI "
                          "application to 8 right-hand sides on a 128^3 Gaussian-bump medium "
-                         "(8 nodes x 8 right-hand sides per polynomial stage, fields beyond L2)")
+                         "(8 nodes x 8 right-hand sides per polynomial stage, fields beyond L2); "
+                         "spectral128 / spectral256 = one complex64 spectral operator "
+                         "application (five line-FFT passes) on a 128^3 / 256^3 field")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 256^3 sixteen-source configuration's solve")
     ap.add_argument("--no-learned", action="store_true",
@@ -469,6 +472,7 @@ def spectral_block(hz, torch, dev, n=64, n_bw=256):
     workload (2.25 points per wavelength in the background, J = 8, FGMRES(30), k_in = 4) per
     precision form, with and without the preconditioner; and the complex64 spectral operator
     (five line-FFT passes) on an n_bw^3 field, beyond L2, against the measured HBM copy rate."""
+    import numpy as np
     import workloads as W
     wl = W.spectral_bumps(n, 1)
     P = hz.Problem(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, wl.J, wl.t, wl.eps,
@@ -842,6 +846,18 @@ def ncu_case(case: str):
 
         def body():
             P.fci(r, inner_k=wl.k_in, precision=hz.HZ_MIXED_C64)
+    elif case in ("spectral128", "spectral256"):
+        import numpy as np
+        nb = 128 if case == "spectral128" else 256
+        h = 1.0 / nb
+        P = hz.Problem(np.ones((nb, nb, nb)), h, 2 * np.pi / (2.25 * h), 8, 1.0, 1, 1.0, 1.0,
+                       nrhs_max=1, restart_max=1, inner_k_max=0, flags=hz.HZ_LIMIT_SWEEPS_C64,
+                       discretization=hz.HZ_DISC_SPECTRAL)
+        x = torch.randn(1, P.n, dtype=torch.complex64, generator=g).to(dev)
+        y = torch.empty_like(x)
+
+        def body():
+            P.apply_shifted(x, 0.1, out=y, precision=hz.HZ_MIXED_C64)
     elif case == "batched128":
         wl = W.gaussian_bumps(128, 7)
         P = hz.Problem(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, wl.J, wl.t, wl.eps,

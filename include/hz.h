@@ -88,7 +88,7 @@ typedef enum {
 
 /* Grid and medium.  Interior points nx*ny*nz with spacing h; omega the angular frequency;
  * layer_cells the sponge thickness in cells (0 = none); sigma_max its peak strength in
- * normalised units (Section 7.1: "positive diagonal entries for points near the boundary");
+ * normalised units (Section 7.1: a diagonal damping, positive near the boundary, zero inside);
  * discretization an hz_discretization (0, the 7-point stencil, when zero-initialised). */
 typedef struct {
   int nx, ny, nz;
