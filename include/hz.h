@@ -410,7 +410,9 @@ hz_status hz_net_train_fields(hz_net* net, hz_problem* p, const void* r, const v
                               float lr, double* loss, void* stream);
 
 /* Right preconditioner of hz_solve: mode 0 FCI (Algorithm 1, the default; net may be null);
- * 1 the network alone, z = N(v); 2 z = N(v) + FCI(v - A N(v)); 3 z = FCI(v) + N(v - A FCI(v)).
+ * 1 the network alone, z = N(v); 2 z = d N(v) + FCI(v - d A N(v)) with the least-squares step
+ * d = (A N v)^H v / ||A N v||^2 (the step of Algorithm 1's step 3 applied to the network's
+ * output, so that v - d A N(v) is never larger than v); 3 z = FCI(v) + N(v - A FCI(v)).
  * The network must hold the grid (multiples of 8) and nrhs_max volumes; allocates two float64
  * fields per right-hand side on first use.  HZ_MIXED_C64_FF is refused with a network. */
 hz_status hz_problem_set_preconditioner(hz_problem* p, hz_net* net, int mode);

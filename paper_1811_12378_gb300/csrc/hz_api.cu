@@ -763,8 +763,16 @@ hz_status run_precond(hz_problem* p, Buf<const double2> v, Buf<double2> z, int n
   };
   if (p->net_mode == 1) return net(v, z, 0);
   if (p->net_mode == 2) {
+    // z = d N(v) + FCI(v - d A N(v)), d = (A N v)^H v / ||A N v||^2: the network's correction
+    // with the step that minimises the residual it leaves (as step d does for w in Algorithm 1),
+    // so a poor network output cannot raise the residual FCI then works on
     HZ_TRY(net(v, z, 0));
-    HZ_TRY(residual());
+    HZ_TIMED_F(p, 1, st, (stencil_bytes<double2, double2>(n, nrhs)), kStencil64Flops * n * nrhs,
+               (hz::launch_stencil_diag(p->g, p->d64, Buf<const double2>{z.p, z.rs},
+                                        Buf<double2>{p->pre_z, n}, nrhs, 0.0, 0.0, st)));
+    HZ_CUDA(hz::launch_fci_step(Buf<const double2>{p->pre_z, n}, v, Buf<double2>{p->pre_t, n},
+                                p->gin, p->partial, p->counters, n, nrhs, st));
+    HZ_CUDA(hz::launch_scale_by_step(z.p, z.rs, p->gin, n, nrhs, st));
     HZ_TRY(run_fci(p, Buf<const double2>{p->pre_t, n}, Buf<double2>{p->pre_z, n}, nrhs, K,
                    precision, st, false));
     HZ_CUDA(hz::launch_field_add(z.p, z.rs, p->pre_z, n, n, nrhs, st));

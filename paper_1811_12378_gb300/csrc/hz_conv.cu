@@ -75,7 +75,56 @@ struct FwdArgs {
   float* outb;              //                    channels [na, N) -> outb [vox][N - na]
   int na, acc_a, acc_b;
   int* err;
+  // split over K (layers with few voxel tiles): blockIdx.z takes MMA steps [z ks, (z+1) ks) and
+  // adds its raw sums into acc (fp32 [vox][N], zeroed first); k_conv_finalize then applies
+  // the epilogue.  ks = 0: one block per tile does every step and the epilogue itself.
+  int ks;
+  float* acc;
 };
+
+// The epilogue of 16 output channels c0.. of voxel vox: bias, ReLU, then the stores asked for.
+__device__ __forceinline__ void conv_epilogue16(const FwdArgs& a, long long vox, int c0,
+                                                float* v) {
+  const int N = a.N;
+  if (a.bias) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] += a.bias[c0 + j];
+  }
+  if (a.relu) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
+  }
+  if (a.out16) {
+    uint4 pk[2];
+    uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+      pw[j] = *reinterpret_cast<const uint32_t*>(&h2);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(a.out16 + vox * N + c0);
+    dst[0] = pk[0];
+    dst[1] = pk[1];
+  }
+  if (a.out32) {
+    float4* dst = reinterpret_cast<float4*>(a.out32 + vox * N + c0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+  }
+  if (a.outa) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int n = c0 + j;
+      if (n < a.na) {
+        float* d = a.outa + vox * a.na + n;
+        *d = a.acc_a ? *d + v[j] : v[j];
+      } else {
+        float* d = a.outb + vox * (N - a.na) + (n - a.na);
+        *d = a.acc_b ? *d + v[j] : v[j];
+      }
+    }
+  }
+}
 
 __global__ void __launch_bounds__(CT) k_conv_fwd(const __grid_constant__ FwdArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -88,7 +137,9 @@ __global__ void __launch_bounds__(CT) k_conv_fwd(const __grid_constant__ FwdArgs
   const int z0 = (tile / (a.tx * a.ty)) * a.bz;
   const int N = a.N;
   const uint32_t ncols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
-  const int nsteps = (a.cm.nchunk + 1) / 2;
+  const int nsteps_all = (a.cm.nchunk + 1) / 2;
+  const int s_first = a.ks > 0 ? (int)blockIdx.z * a.ks : 0;
+  const int nsteps = a.ks > 0 ? min(a.ks, nsteps_all - s_first) : nsteps_all;
   if (warp == 0) tc::tmem_alloc(&tslot, ncols);
   if (threadIdx.x == 32) {
     for (int s = 0; s < FWD_STAGES; ++s) {
@@ -116,15 +167,16 @@ __global__ void __launch_bounds__(CT) k_conv_fwd(const __grid_constant__ FwdArgs
         break;
       }
       uint8_t* sa = smem + (size_t)st * a.stage_bytes;
+      const int gs = s_first + s;  // the step's place in the whole K loop
       tc::mbar_expect_tx(&full[st], 2u * 2048u + bbytes);
       for (int h = 0; h < 2; ++h) {
         // a padding chunk past the last re-reads the last one (its weights are zero)
-        const int kc = min(2 * s + h, a.cm.nchunk - 1);
+        const int kc = min(2 * gs + h, a.cm.nchunk - 1);
         int dz, dy, dx, src, coff;
         chunk_of(a.cm, kc, dz, dy, dx, src, coff);
         tc::tma_load5(sa + h * 2048, &a.src[src], &full[st], coff, x0 + dx, y0 + dy, z0 + dz, b);
       }
-      tc::bulk_load(sa + 4096, a.wp + (size_t)2 * s * N * 8, bbytes, &full[st]);
+      tc::bulk_load(sa + 4096, a.wp + (size_t)2 * gs * N * 8, bbytes, &full[st]);
       issued = s + 1;
     }
     // no copy may still be in flight when the block exits
@@ -161,47 +213,179 @@ __global__ void __launch_bounds__(CT) k_conv_fwd(const __grid_constant__ FwdArgs
       float v[16];
       tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
       if (!in) continue;
-      if (a.bias) {
+      if (a.ks > 0) {
+        float* d = a.acc + vox * N + c0;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] += a.bias[c0 + j];
-      }
-      if (a.relu) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
-      }
-      if (a.out16) {
-        uint4 pk[2];
-        uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-          pw[j] = *reinterpret_cast<const uint32_t*>(&h2);
-        }
-        uint4* dst = reinterpret_cast<uint4*>(a.out16 + vox * N + c0);
-        dst[0] = pk[0];
-        dst[1] = pk[1];
-      }
-      if (a.out32) {
-        float4* dst = reinterpret_cast<float4*>(a.out32 + vox * N + c0);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-      }
-      if (a.outa) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int n = c0 + j;
-          if (n < a.na) {
-            float* d = a.outa + vox * a.na + n;
-            *d = a.acc_a ? *d + v[j] : v[j];
-          } else {
-            float* d = a.outb + vox * (N - a.na) + (n - a.na);
-            *d = a.acc_b ? *d + v[j] : v[j];
-          }
-        }
+        for (int j = 0; j < 16; ++j) atomicAdd(d + j, v[j]);
+      } else {
+        conv_epilogue16(a, vox, c0, v);
       }
     }
   } else if (lane == 0) {
     atomicExch(a.err, 1);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+// The epilogue of a split convolution: acc holds the summed raw outputs.
+__global__ void __launch_bounds__(256) k_conv_finalize(const __grid_constant__ FwdArgs a,
+                                                       long long nvox) {
+  const int groups = a.N / 16;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nvox * groups) return;
+  const long long vox = i / groups;
+  const int c0 = (int)(i - vox * groups) * 16;
+  float v[16];
+  const float4* src = reinterpret_cast<const float4*>(a.acc + vox * a.N + c0);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float4 q = src[j];
+    v[4 * j] = q.x;
+    v[4 * j + 1] = q.y;
+    v[4 * j + 2] = q.z;
+    v[4 * j + 3] = q.w;
+  }
+  conv_epilogue16(a, vox, c0, v);
+}
+
+// ------------------------------------------------------------------ halo-tile forward kernel
+// The same convolution for N <= 64 output channels and W a multiple of 8, with the input read
+// once per tile instead of once per tap: the block's tile is 8 x 16 x 1 voxels (x, y, z), and
+// for each 8-channel chunk one TMA box {8 channels, 10, 18, 3} -- the tile with a one-voxel halo
+// on every side, 540 rows of 16 bytes in x-fastest order -- lands in shared memory.  The A
+// operand of tap (dx, dy, dz) is then a window of that box: core matrix k (output rows 8k..8k+7,
+// y = k, x = 0..7) starts at row (dz+1) 180 + (dy+1) 10 + (dx+1) + 10 k, so the descriptor takes
+// the tap's start address and SBO = 10 rows (160 bytes); the second K core matrix of an MMA is the
+// next chunk's box (LBO = the box spacing).  With 8 input channels (one chunk per tap) an MMA
+// pairs taps t and t+1 of the same box instead (LBO = their row distance; the 28th tap is the
+// zero-weight padding chunk).  Per chunk pair: two box loads, 27 bulk copies of the taps' weight
+// slices, 27 MMAs.
+constexpr int HX = 10, HY = 18, HZ = 3;
+constexpr int HALO_BYTES = 8704;  // 540 rows x 16 bytes = 8640, to a multiple of 128
+constexpr int HALO_STAGES = 2;
+
+struct HaloArgs {
+  CUtensorMap src[2];  // boxes {8, 10, 18, 3, 1}
+  ChunkMap cm;
+  const __nv_bfloat16* wp;  // [nchunk rounded up to even][N][8]
+  int N, D, H, W, tx, ty;   // tiles: tx = W / 8 along x, ty along y (16 rows), D along z
+  int ngroups;              // chunk pairs (cpt / 2), or 1 when cpt == 1
+  int nh;                   // boxes per group: 2, or 1
+  int nmma;                 // MMAs per group: 27, or 14
+  int bbytes;               // weight bytes per group
+  int stage_bytes;
+  FwdArgs epi;              // the epilogue's fields (bias, relu, outputs; ks = 0)
+};
+
+__device__ __forceinline__ int tap_row(int t) { return (t / 9) * HX * HY + ((t / 3) % 3) * HX + t % 3; }
+
+__global__ void __launch_bounds__(CT) k_conv_fwd_halo(const __grid_constant__ HaloArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t full[HALO_STAGES], empty[HALO_STAGES], done;
+  __shared__ uint32_t tslot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = blockIdx.x, b = blockIdx.y;
+  const int x0 = (tile % a.tx) * 8;
+  const int y0 = ((tile / a.tx) % a.ty) * 16;
+  const int z0 = tile / (a.tx * a.ty);
+  const int N = a.N;
+  const uint32_t ncols = N <= 32 ? 32 : 64;
+  int* err = a.epi.err;
+  if (warp == 0) tc::tmem_alloc(&tslot, ncols);
+  if (threadIdx.x == 32) {
+    for (int s = 0; s < HALO_STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(&done, 1);
+    tc::mbar_fence_init();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tslot;
+  const uint32_t sbase = tc::su32(smem);
+  const int cpt = a.cm.cpt;
+
+  if (threadIdx.x == 0) {
+    int issued = 0;
+    for (int g = 0; g < a.ngroups; ++g) {
+      const int st = g % HALO_STAGES;
+      const uint32_t ph = (uint32_t)(g / HALO_STAGES) & 1u;
+      if (g >= HALO_STAGES && !tc::mbar_wait(&empty[st], ph ^ 1u)) {
+        atomicExch(err, 1);
+        break;
+      }
+      uint8_t* sa = smem + (size_t)st * a.stage_bytes;
+      uint8_t* sb = sa + a.nh * HALO_BYTES;
+      tc::mbar_expect_tx(&full[st], (uint32_t)(a.nh * HX * HY * HZ * 16 + a.bbytes));
+      for (int h = 0; h < a.nh; ++h) {
+        const int c8 = a.nh == 2 ? 2 * g + h : 0;
+        const int src = c8 < a.cm.c0 ? 0 : 1;
+        const int coff = 8 * (src == 0 ? c8 : c8 - a.cm.c0);
+        tc::tma_load5(sa + h * HALO_BYTES, &a.src[src], &full[st], coff, x0 - 1, y0 - 1, z0 - 1,
+                      b);
+      }
+      if (a.nh == 2) {
+        const uint32_t piece = 2u * N * 16u;  // chunks t cpt + 2g and + 1 of tap t
+        for (int t = 0; t < 27; ++t)
+          tc::bulk_load(sb + t * piece, a.wp + ((size_t)t * cpt + 2 * g) * N * 8, piece, &full[st]);
+      } else {
+        tc::bulk_load(sb, a.wp, (uint32_t)a.bbytes, &full[st]);  // all 28 chunks
+      }
+      issued = g + 1;
+    }
+    for (int g = max(0, issued - HALO_STAGES); g < issued; ++g)
+      if (!tc::mbar_wait(&full[g % HALO_STAGES], (uint32_t)(g / HALO_STAGES) & 1u))
+        atomicExch(err, 1);
+  } else if (threadIdx.x == 32) {
+    const uint32_t idesc = tc::idesc_bf16(128, N, 0, 0);
+    for (int g = 0; g < a.ngroups; ++g) {
+      const int st = g % HALO_STAGES;
+      if (!tc::mbar_wait(&full[st], (uint32_t)(g / HALO_STAGES) & 1u)) {
+        atomicExch(err, 1);
+        break;
+      }
+      tc::fence_after();
+      const uint32_t sa = sbase + (uint32_t)st * a.stage_bytes;
+      const uint32_t sb = sa + (uint32_t)a.nh * HALO_BYTES;
+      for (int i = 0; i < a.nmma; ++i) {
+        uint32_t aaddr, lbo, baddr;
+        if (a.nh == 2) {
+          aaddr = sa + 16u * tap_row(i);
+          lbo = HALO_BYTES;
+          baddr = sb + (uint32_t)i * 2u * N * 16u;
+        } else {
+          const int t = 2 * i;
+          aaddr = sa + 16u * tap_row(t);
+          lbo = t + 1 < 27 ? 16u * (tap_row(t + 1) - tap_row(t)) : 16u;
+          baddr = sb + (uint32_t)t * N * 16u;
+        }
+        const uint64_t ad = tc::sdesc(aaddr, lbo, HX * 16);
+        const uint64_t bd = tc::sdesc(baddr, (uint32_t)N * 16u, 128);
+        tc::mma_bf16(tmem, ad, bd, idesc, (g > 0 || i > 0) ? 1u : 0u);
+      }
+      tc::mma_commit(&empty[st]);
+    }
+    tc::mma_commit(&done);
+  }
+  __syncwarp();
+  const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&done, 0));
+  tc::fence_after();
+  if (ok) {
+    const int r = warp * 32 + lane;
+    const int x = x0 + (r & 7), y = y0 + (r >> 3);
+    const bool in = y < a.H;
+    const long long vox = (((long long)b * a.D + z0) * a.H + y) * a.W + x;
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (in) conv_epilogue16(a.epi, vox, c0, v);
+    }
+  } else if (lane == 0) {
+    atomicExch(err, 1);
   }
   tc::fence_before();
   __syncthreads();
@@ -367,6 +551,10 @@ cudaError_t tma_encoder_init() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_conv_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              WG_STAGES * (16 * 1024 + 128 * 128));
+  if (e == cudaSuccess)  // N <= 64: two boxes and 27 x 2 x 64 x 16 bytes of weights per stage
+    e = cudaFuncSetAttribute(k_conv_fwd_halo, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             HALO_STAGES * ((2 * HALO_BYTES + 27 * 2 * 64 * 16 + 1023) / 1024 *
+                                            1024));
   if (e != cudaSuccess) return e;
   g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   return cudaSuccess;
@@ -419,7 +607,8 @@ cudaError_t launch_pack_weights(const float* w, __nv_bfloat16* wp, int Cin, int 
 cudaError_t launch_conv_fwd(const FMap& in0, const FMap* in1, const __nv_bfloat16* wp,
                             const float* bias, int N, int relu, __nv_bfloat16* out16,
                             float* out32, float* outa, float* outb, int na, int acc_a, int acc_b,
-                            int* err, cudaStream_t st) {
+                            int* err, cudaStream_t st, float* scratch, long long scratch_floats,
+                            int sms) {
   if (!map_ok(in0) || (in1 && (!map_ok(*in1) || in1->W != in0.W || in1->H != in0.H ||
                                in1->D != in0.D || in1->B != in0.B)))
     return cudaErrorInvalidValue;
@@ -430,12 +619,58 @@ cudaError_t launch_conv_fwd(const FMap& in0, const FMap* in1, const __nv_bfloat1
     return cudaErrorInvalidValue;
   FwdArgs a;
   std::memset(&a, 0, sizeof(a));
+  const int cin = in0.C + (in1 ? in1->C : 0);
+  {
+    // the halo-tile kernel where it applies: N <= 64 (two stages fit), W a multiple of 8, enough
+    // tiles for the device (or no scratch to split the per-tap kernel's K loop with)
+    const int cpt = cin / 8;
+    const long long htiles = (long long)(in0.W / 8) * ((in0.H + 15) / 16) * in0.D * in0.B;
+    const bool fits = N <= 64 && in0.W % 8 == 0 && (cpt == 1 || cpt % 2 == 0);
+    if (fits && (htiles >= sms || !scratch)) {
+      HaloArgs h;
+      std::memset(&h, 0, sizeof(h));
+      cudaError_t e = encode_map(&h.src[0], in0, HX, HY, HZ);
+      if (e != cudaSuccess) return e;
+      e = encode_map(&h.src[1], in1 ? *in1 : in0, HX, HY, HZ);
+      if (e != cudaSuccess) return e;
+      h.cm.cpt = cpt;
+      h.cm.c0 = in0.C / 8;
+      h.cm.nchunk = 27 * cpt;
+      h.wp = wp;
+      h.N = N;
+      h.D = in0.D;
+      h.H = in0.H;
+      h.W = in0.W;
+      h.tx = in0.W / 8;
+      h.ty = (in0.H + 15) / 16;
+      h.nh = cpt == 1 ? 1 : 2;
+      h.ngroups = cpt == 1 ? 1 : cpt / 2;
+      h.nmma = cpt == 1 ? 14 : 27;
+      h.bbytes = cpt == 1 ? conv_nchunk_pad(8) * N * 16 : 27 * 2 * N * 16;
+      h.stage_bytes = (h.nh * HALO_BYTES + h.bbytes + 1023) / 1024 * 1024;
+      h.epi.bias = bias;
+      h.epi.N = N;
+      h.epi.relu = relu;
+      h.epi.out16 = out16;
+      h.epi.out32 = out32;
+      h.epi.outa = outa;
+      h.epi.outb = outb;
+      h.epi.na = na;
+      h.epi.acc_a = acc_a;
+      h.epi.acc_b = acc_b;
+      h.epi.err = err;
+      const size_t smem = (size_t)HALO_STAGES * h.stage_bytes;
+      count_launch();
+      k_conv_fwd_halo<<<dim3((unsigned)(h.tx * h.ty * in0.D), (unsigned)in0.B), CT, smem, st>>>(
+          h);
+      return cudaGetLastError();
+    }
+  }
   box_for(128, in0.W, in0.H, a.bx, a.by, a.bz);
   cudaError_t e = encode_map(&a.src[0], in0, a.bx, a.by, a.bz);
   if (e != cudaSuccess) return e;
   e = encode_map(&a.src[1], in1 ? *in1 : in0, a.bx, a.by, a.bz);
   if (e != cudaSuccess) return e;
-  const int cin = in0.C + (in1 ? in1->C : 0);
   a.cm.cpt = cin / 8;
   a.cm.c0 = in0.C / 8;
   a.cm.nchunk = 27 * a.cm.cpt;
@@ -459,8 +694,34 @@ cudaError_t launch_conv_fwd(const FMap& in0, const FMap* in1, const __nv_bfloat1
   a.acc_b = acc_b;
   a.err = err;
   const size_t smem = (size_t)FWD_STAGES * a.stage_bytes;
+  // layers with fewer voxel tiles than about two per SM split their K loop over blocks (at
+  // least 4 MMA steps each) when a scratch of vox x N floats is given
+  const long long tiles = (long long)a.tx * a.ty * tz * in0.B;
+  const long long nvox = (long long)in0.W * in0.H * in0.D * in0.B;
+  const int nsteps = (a.cm.nchunk + 1) / 2;
+  int nsplit = 1;
+  if (scratch && scratch_floats >= nvox * N && tiles < 2LL * sms) {
+    nsplit = (int)std::min<long long>((2LL * sms + tiles - 1) / tiles, std::max(1, nsteps / 4));
+    if (nsplit > 1) {
+      a.ks = (nsteps + nsplit - 1) / nsplit;
+      nsplit = (nsteps + a.ks - 1) / a.ks;
+    }
+  }
+  if (nsplit > 1) {
+    a.acc = scratch;
+    cudaError_t me = cudaMemsetAsync(scratch, 0, sizeof(float) * (size_t)(nvox * N), st);
+    if (me != cudaSuccess) return me;
+  } else {
+    a.ks = 0;
+  }
   count_launch();
-  k_conv_fwd<<<dim3((unsigned)(a.tx * a.ty * tz), (unsigned)in0.B), CT, smem, st>>>(a);
+  k_conv_fwd<<<dim3((unsigned)(a.tx * a.ty * tz), (unsigned)in0.B, (unsigned)nsplit), CT, smem,
+               st>>>(a);
+  cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess || nsplit == 1) return le;
+  count_launch();
+  const long long items = nvox * (N / 16);
+  k_conv_finalize<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(a, nvox);
   return cudaGetLastError();
 }
 

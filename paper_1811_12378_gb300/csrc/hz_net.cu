@@ -296,6 +296,17 @@ __global__ void k_field_sub(const double2* __restrict__ v, long long vrs,
   }
 }
 
+__global__ void k_scale_by_step(double2* __restrict__ z, long long zrs, GmresDev gs, long long n) {
+  const int r = blockIdx.y;
+  const double* sc = gs.scal + (long long)r * SC_COUNT;
+  const double dr = sc[SC_DR], di = sc[SC_DI];
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const double2 v = z[r * zrs + p];
+    z[r * zrs + p] = make_double2(dr * v.x - di * v.y, dr * v.y + di * v.x);
+  }
+}
+
 __global__ void k_field_add(double2* __restrict__ dst, long long drs,
                             const double2* __restrict__ src, long long srs, long long n, int B) {
   GRID_STRIDE(i, (long long)B * n) {
@@ -340,6 +351,8 @@ struct hz_net {
   // gradients of activations (fp32)
   float *gA = nullptr, *gB = nullptr, *ds1 = nullptr, *ds2 = nullptr, *ds3 = nullptr;
   double* dscal = nullptr;  // [0] loss, [1..Bmax] per-sample sums of squares
+  float* ksplit = nullptr;  // fp32 sums of the convolutions that split their K loop (levels >= 1)
+  long long ksplit_floats = 0;
   int* err = nullptr;
   bool packed = false;
   std::vector<void*> allocs;
@@ -415,7 +428,8 @@ hz_status net_forward(hz_net* n, const Dims& d, cudaStream_t st) {
   };
   auto conv = [&](int l, const FMap& a, const FMap* b, __nv_bfloat16* out) -> hz_status {
     NCHK(hz::launch_conv_fwd(a, b, n->wp[l], n->par + n->boff[l], kConv[l].cout, 1, out, nullptr,
-                             nullptr, nullptr, 0, 0, 0, n->err, st));
+                             nullptr, nullptr, 0, 0, 0, n->err, st, n->ksplit, n->ksplit_floats,
+                             n->sms));
     return HZ_OK;
   };
   auto pool = [&](const __nv_bfloat16* s, __nv_bfloat16* o, int l, int C) -> hz_status {
@@ -493,7 +507,8 @@ hz_status net_backward(hz_net* n, const Dims& d, cudaStream_t st) {
     if (outa) {
       const int cin = kConv[l].cin0 + kConv[l].cin1;
       NCHK(hz::launch_conv_fwd(gm, nullptr, n->wt[l], nullptr, cin, 0, nullptr, nullptr, outa,
-                               outb, na, 0, acc_b, n->err, st));
+                               outb, na, 0, acc_b, n->err, st, n->ksplit, n->ksplit_floats,
+                               n->sms));
     }
     return HZ_OK;
   };
@@ -617,6 +632,13 @@ cudaError_t launch_field_sub(const double2* v, long long vrs, const double2* a, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_scale_by_step(double2* z, long long zrs, const GmresDev& gs, long long n,
+                                 int nvec, cudaStream_t st) {
+  count_launch();
+  k_scale_by_step<<<dim3(gs_blocks(n), nvec), 256, 0, st>>>(z, zrs, gs, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_field_add(double2* dst, long long drs, const double2* src, long long srs,
                              long long n, int nvec, cudaStream_t st) {
   count_launch();
@@ -682,6 +704,12 @@ hz_status hz_net_create(int D, int H, int W, int batch_max, hz_net** out) {
   if ((s = nalloc(n, &n->x0, v0 * 8))) return bail(s);
   for (int l = 0; l < NCONV; ++l)
     if ((s = nalloc(n, &n->act[l], lvox[lev[l]] * kConv[l].cout))) return bail(s);
+  for (int l = 0; l < NCONV; ++l)  // forward (cout) and data-gradient (cin) outputs
+    if (lev[l] >= 1)
+      n->ksplit_floats = std::max(n->ksplit_floats,
+                                  lvox[lev[l]] * std::max(kConv[l].cout,
+                                                          kConv[l].cin0 + kConv[l].cin1));
+  if ((s = nalloc(n, &n->ksplit, n->ksplit_floats))) return bail(s);
   if ((s = nalloc(n, &n->pool1, v1 * 16)) || (s = nalloc(n, &n->pool2, v2 * 32)) ||
       (s = nalloc(n, &n->pool3, v3 * 64)) || (s = nalloc(n, &n->up3, v2 * 128)) ||
       (s = nalloc(n, &n->up2, v1 * 64)) || (s = nalloc(n, &n->up1, v0 * 32)) ||

@@ -33,10 +33,13 @@ cudaError_t launch_pack_weights(const float* w, __nv_bfloat16* wp, int Cin, int 
 // out = conv3(in0 ++ in1, wp) (+ bias, relu): bf16 [vox][N] into out16, fp32 into out32, or
 // split fp32 outputs (channels [0, na) into outa, the rest into outb; acc_*: add instead of
 // store).  N a multiple of 16 in [16, 256].  err: set if a bounded wait gave up.
+// scratch (vox x N floats, may be null): lets layers with few voxel tiles split their K loop
+// over blocks (sms: the device's SM count).
 cudaError_t launch_conv_fwd(const FMap& in0, const FMap* in1, const __nv_bfloat16* wp,
                             const float* bias, int N, int relu, __nv_bfloat16* out16,
                             float* out32, float* outa, float* outb, int na, int acc_a, int acc_b,
-                            int* err, cudaStream_t st);
+                            int* err, cudaStream_t st, float* scratch = nullptr,
+                            long long scratch_floats = 0, int sms = 152);
 
 // dw[N][27][Cin] += sum over voxels of grad[v][n] (in0 ++ in1)[v + off_t][c]; N = grad.C a
 // multiple of 16 in [16, 128].
@@ -61,5 +64,8 @@ cudaError_t launch_field_sub(const double2* v, long long vrs, const double2* a, 
                              double2* t, long long trs, long long n, int nvec, cudaStream_t st);
 cudaError_t launch_field_add(double2* dst, long long drs, const double2* src, long long srs,
                              long long n, int nvec, cudaStream_t st);
+// z *= d per field, d the step of the last step-d reduction in gs (scal[SC_DR], scal[SC_DI]).
+cudaError_t launch_scale_by_step(double2* z, long long zrs, const GmresDev& gs, long long n,
+                                 int nvec, cudaStream_t st);
 
 }  // namespace hz
