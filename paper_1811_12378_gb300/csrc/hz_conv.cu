@@ -302,6 +302,15 @@ __global__ void __launch_bounds__(CT) k_conv_fwd_halo(const __grid_constant__ Ha
     tc::mbar_init(&done, 1);
     tc::mbar_fence_init();
   }
+  // the 64 bytes after each box are never loaded but read by the last tap pair of the 8-channel
+  // case (times zero weights): zero them, so that no stale NaN of an earlier kernel gets in
+  for (int i = threadIdx.x; i < HALO_STAGES * a.nh * 4; i += CT) {
+    const int box = i >> 2, row = i & 3;
+    uint8_t* p = smem + (size_t)(box / a.nh) * a.stage_bytes + (box % a.nh) * HALO_BYTES +
+                 HX * HY * HZ * 16 + row * 16;
+    *reinterpret_cast<uint4*>(p) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  tc::fence_proxy_async();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();

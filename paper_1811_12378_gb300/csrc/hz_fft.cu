@@ -157,7 +157,25 @@ __device__ T* fft_lines(T* A, T* B, int tl, int ls, const PassArgs& a, const T* 
   return A;
 }
 
-template <typename T, int AXIS>
+__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
+
+// The same for a line length N = 2^k known at compile time: radix 4 stages, then one of radix 2
+// where k is odd; every index computation is then shifts and masks of constants.
+template <typename T, int N, int L = 1>
+__device__ __forceinline__ T* fft_lines_ct(T* A, T* B, int tl, int ls, const T* __restrict__ tw) {
+  if constexpr (L >= N) {
+    return A;
+  } else {
+    constexpr int P = (N / L) % 4 == 0 ? 4 : 2;
+    fft_stage<T, P>(A, B, tl, N, ls, L, ilog2c(L), ilog2c(N / P), tw);
+    __syncthreads();
+    return fft_lines_ct<T, N, L * P>(B, A, tl, ls, tw);
+  }
+}
+
+// NC: the line length when it is one of the compiled power-of-two sizes, else 0 (any length
+// with the radix plan of the pass arguments).
+template <typename T, int AXIS, int NC>
 __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
   pdl_enter();
   using R = typename RealT<T>::type;
@@ -166,7 +184,8 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
   __shared__ T* s_dst[FT_XLINES];
   __shared__ const T* s_xin[FT_XLINES];
   __shared__ long long s_off[FT_XLINES];  // x pass: each line's first point within its field
-  const int n = a.n, tl = a.tl;
+  const int n = NC > 0 ? NC : a.n, tl = a.tl;
+  const int nsh = NC > 0 ? ilog2c(NC) : a.nsh;
   const int ls = n | 1;  // odd line stride in shared memory
   T* A = reinterpret_cast<T*>(fft_smem);
   T* B = A + (size_t)tl * ls;
@@ -207,7 +226,7 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
   // load (x pass: consecutive threads walk a line; y, z: consecutive threads the x positions)
   for (int t = threadIdx.x; t < tl * n; t += FT) {
     int l, e;
-    if (AXIS == 0) divmod(t, n, a.nsh, l, e);
+    if (AXIS == 0) divmod(t, n, nsh, l, e);
     else divmod(t, tl, a.tlsh, e, l);
     T val = czero<T>();
     if (l < nvalid) {
@@ -217,7 +236,9 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
     A[l * ls + e] = val;
   }
   __syncthreads();
-  T* X = fft_lines<T>(A, B, tl, ls, a, tw);
+  T* X;
+  if constexpr (NC > 0) X = fft_lines_ct<T, NC>(A, B, tl, ls, tw);
+  else X = fft_lines<T>(A, B, tl, ls, a, tw);
   if (a.kind == PASS_MID) {
     // z lines after the x and y transforms: point (l, e) holds wave numbers (i0 + l, j, e)
     const R* ex = (const R*)a.ex;
@@ -235,7 +256,8 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
     }
     __syncthreads();
     T* Y = (X == A) ? B : A;
-    X = fft_lines<T>(X, Y, tl, ls, a, tw);
+    if constexpr (NC > 0) X = fft_lines_ct<T, NC>(X, Y, tl, ls, tw);
+    else X = fft_lines<T>(X, Y, tl, ls, a, tw);
   }
   const bool conj_out = a.kind != PASS_FWD;
   const T* __restrict__ dg = (const T*)a.dg;
@@ -243,7 +265,7 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
   const bool comb = a.kind == PASS_LAST && a.combine;
   for (int t = threadIdx.x; t < tl * n; t += FT) {
     int l, e;
-    if (AXIS == 0) divmod(t, n, a.nsh, l, e);
+    if (AXIS == 0) divmod(t, n, nsh, l, e);
     else divmod(t, tl, a.tlsh, e, l);
     if (l >= nvalid) continue;
     T val = X[l * ls + e];
@@ -289,6 +311,13 @@ const void* e_of<double2>(const FftAxis& ax) { return ax.e64; }
 template <>
 const void* e_of<float2>(const FftAxis& ax) { return ax.e32; }
 
+template <typename T, int NC>
+cudaError_t launch_axis(int axis, dim3 grid, size_t smem, cudaStream_t st, const PassArgs& a) {
+  if (axis == 0) return launch_pdl(k_fft_pass<T, 0, NC>, grid, dim3(FT), smem, st, a);
+  if (axis == 1) return launch_pdl(k_fft_pass<T, 1, NC>, grid, dim3(FT), smem, st, a);
+  return launch_pdl(k_fft_pass<T, 2, NC>, grid, dim3(FT), smem, st, a);
+}
+
 template <typename T>
 cudaError_t run_pass(int axis, PassArgs a, const SpecPlan& sp, cudaStream_t st) {
   const FftAxis& ax = sp.ax[axis];
@@ -308,14 +337,20 @@ cudaError_t run_pass(int axis, PassArgs a, const SpecPlan& sp, cudaStream_t st) 
   a.tlsh = ilog2_exact(a.tl);
   const size_t smem = 2 * sizeof(T) * (size_t)a.tl * (size_t)(ax.n | 1);
   count_launch();
+  dim3 grid;
   if (axis == 0) {
     const long long lines = (long long)a.ny * a.nz * a.nvec;
-    const dim3 grid((unsigned)((lines + a.tl - 1) / a.tl));
-    return launch_pdl(k_fft_pass<T, 0>, grid, dim3(FT), smem, st, a);
+    grid = dim3((unsigned)((lines + a.tl - 1) / a.tl));
+  } else {
+    grid = dim3((a.nx + a.tl - 1) / a.tl, axis == 1 ? a.nz : a.ny, a.nvec);
   }
-  const dim3 grid((a.nx + a.tl - 1) / a.tl, axis == 1 ? a.nz : a.ny, a.nvec);
-  if (axis == 1) return launch_pdl(k_fft_pass<T, 1>, grid, dim3(FT), smem, st, a);
-  return launch_pdl(k_fft_pass<T, 2>, grid, dim3(FT), smem, st, a);
+  switch (ax.n) {
+    case 32: return launch_axis<T, 32>(axis, grid, smem, st, a);
+    case 64: return launch_axis<T, 64>(axis, grid, smem, st, a);
+    case 128: return launch_axis<T, 128>(axis, grid, smem, st, a);
+    case 256: return launch_axis<T, 256>(axis, grid, smem, st, a);
+    default: return launch_axis<T, 0>(axis, grid, smem, st, a);
+  }
 }
 
 // ------------------------------------------------------------------ polynomial stage

@@ -174,9 +174,10 @@ def _training_pairs(P, wl, k, seed):
 
 def test_learned_preconditioner_in_fgmres():
     """Train on (residual, error) pairs of the 32^3 point-source problem, then solve with the
-    network as the correction after FCI (mode 3) and alone (mode 1): the float64 true residual
-    still reaches 1e-8 (it alone decides convergence), the solution matches the oracle's
-    matvec residual, and the step counts against FCI alone are reported."""
+    network as the correction after FCI (mode 3), before FCI with its least-squares step
+    (mode 2) and alone (mode 1): the float64 true residual still reaches 1e-8 (it alone decides
+    convergence), the solution matches the oracle's matvec residual, mode 2 needs no more
+    outer steps than FCI alone, and the step counts are reported."""
     wl = W.point_source_32()
     op = O.make_operator(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max)
     P = hzpkg.Problem(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, wl.J, wl.t, wl.eps,
@@ -199,6 +200,16 @@ def test_learned_preconditioner_in_fgmres():
         sf = op.s * wl.f[0]
         assert np.linalg.norm(sf - op.apply(un)) / np.linalg.norm(sf) <= 1e-8 + 1e-12
         its[3] = st[0].its
+        # the network first with its least-squares step, FCI on the rest (mode 2): the step
+        # keeps a weak network from raising the residual, so FGMRES needs no more outer steps
+        # than with FCI alone (two steps of slack for the variable preconditioner)
+        P.set_preconditioner(net, 2)
+        u2, st2 = P.solve(f, **kw)
+        assert st2[0].converged and st2[0].rel_res_true <= 1e-8
+        un2 = u2.cpu().numpy().reshape(op.shape)
+        assert np.linalg.norm(sf - op.apply(un2)) / np.linalg.norm(sf) <= 1e-8 + 1e-12
+        its[2] = st2[0].its
+        assert its[2] <= its[0] + 2
         # the network alone: a weak preconditioner after this little training; the solve runs a
         # bounded number of cycles and must report its true residual honestly
         P.set_preconditioner(net, 1)
@@ -208,8 +219,8 @@ def test_learned_preconditioner_in_fgmres():
                    - st1[0].rel_res_true) <= 1e-9 + 1e-6 * st1[0].rel_res_true
         its[1] = (st1[0].its, st1[0].rel_res_true)
         P.set_preconditioner(None, 0)
-        print(f"outer steps to 1e-8: FCI {its[0]}, FCI + network {its[3]}; network alone "
-              f"{its[1][0]} steps reach {its[1][1]:.2e}")
+        print(f"outer steps to 1e-8: FCI {its[0]}, network + FCI {its[2]}, FCI + network "
+              f"{its[3]}; network alone {its[1][0]} steps reach {its[1][1]:.2e}")
     finally:
         net.close()
         P.close()
