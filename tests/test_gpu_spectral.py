@@ -164,6 +164,33 @@ def test_spectral_solve_error_vs_oracle(invlap):
             assert abs(st8[0].its - ref8.its) <= 2
 
 
+def test_spectral_multi_rhs_and_batched_solves():
+    """Two right-hand sides in one spectral solve equal two single solves (HZ_MIXED_C64, bit for
+    bit: the batched kernels keep every field's arithmetic), and hz_solve_batched runs a
+    spectral and a 7-point problem together with the results of separate solves."""
+    wl = W.spectral_bumps(24, 5)
+    op, nodes = spectral_oracle(wl)
+    f2 = np.stack([wl.f[0], W.random_field(3, 1, wl.nx, wl.ny, wl.nz)[0]]).reshape(2, -1)
+    kw = dict(restart=20, inner_k=4, rtol=1e-8, max_cycles=40, precision=hzpkg.HZ_MIXED_C64)
+    with spectral_problem(wl, nodes, nrhs_max=2, inner_k_max=4) as P:
+        u2, st2 = P.solve(to_dev(f2), **kw)
+        u2 = to_np(u2)
+        for v in range(2):
+            u1, st1 = P.solve(to_dev(f2[v:v + 1]), **kw)
+            assert st1[0].its == st2[v].its and st2[v].converged
+            assert np.array_equal(to_np(u1)[0], u2[v])
+        wf = W.small_case(4, 20, 16, 12, layer=2, J=4)
+        with hzpkg.Problem(wf.c, wf.h, wf.omega, wf.layer_cells, wf.sigma_max, wf.J, wf.t,
+                           wf.eps, nrhs_max=1, restart_max=20, inner_k_max=4) as Q:
+            fq = to_dev(wf.f[:1].reshape(1, -1))
+            us, sts = hzpkg.solve_batched([P, Q], [to_dev(f2[:1]), fq], **kw)
+            uq, stq = Q.solve(fq, **kw)
+            assert np.array_equal(to_np(us[0])[0], u2[0]) and sts[0][0].its == st2[0].its
+            assert np.array_equal(to_np(us[1]), to_np(uq)) and sts[1][0].its == stq[0].its
+    sf = op.s * f2[0].reshape(op.shape)
+    assert np.linalg.norm(sf - op.apply(u2[0].reshape(op.shape))) / np.linalg.norm(sf) <= 1.01e-8
+
+
 def test_spectral_argument_checks():
     """Sizes outside 2^a 3^b 5^c, Case Two, the complex64-Krylov forms, ILU(0) and the network
     are refused on a spectral problem; the inverse Laplacian on a 7-point one."""
