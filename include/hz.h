@@ -290,7 +290,10 @@ hz_status hz_profile_enable(hz_problem* p, int on);
 hz_status hz_problem_set_inner_ilu(hz_problem* p, int on);
 
 /* z = M^{-1} t with the ILU(0) factors above, for nvec double-complex fields of n points
- * (device; t and z must not overlap).  Needs hz_problem_set_inner_ilu(p, 1).  Asynchronous. */
+ * (device; t and z must not overlap).  Needs hz_problem_set_inner_ilu(p, 1).  The sweeps run as
+ * a wavefront over z-slabs, one block per slab, where all blocks fit on the device at once
+ * (then the call synchronises the stream and returns HZ_ERR_TIMEOUT if a bounded wait between
+ * blocks gave up), else in one block per field (asynchronous). */
 hz_status hz_ilu0_apply(hz_problem* p, const void* t, void* z, int nvec, void* stream);
 
 /* Spectral problems (HZ_DISC_SPECTRAL): right-precondition the inner GMRES of FCI (step 4 of

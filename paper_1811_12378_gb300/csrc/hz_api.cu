@@ -98,6 +98,8 @@ struct hz_problem {
   float* invd32 = nullptr;   // [n] the same in float32 (the sweeps of HZ_MIXED_C64)
   float2* ilu_u32 = nullptr; // [nrhs][n] complex64 scratch of those sweeps
   double2* ilu_t = nullptr;  // [nrhs][n] scratch field of the preconditioned inner GMRES
+  int* ilu_prog = nullptr;   // progress words of the multi-block wavefront sweeps
+  bool ilu_chain64 = false, ilu_chain32 = false;  // those sweeps fit (all blocks resident)
   long long nf = 0;          // points of a solver field: n, or 2n for Case Two
   bool z32 = false;          // HZ_LIMIT_Z_C64
   bool sweeps32 = false;     // HZ_LIMIT_SWEEPS_C64
@@ -703,6 +705,13 @@ hz_status run_fci(hz_problem* p, Buf<const double2> r, Buf<double2> out, int nve
   const bool ilu = p->ilu_on || p->invlap_on;
   const bool ilu32 = p->ilu_on && precision == HZ_MIXED_C64 && hz::ilu0_fits32(p->g);
   auto ilu_apply = [&](Buf<const double2> t, Buf<double2> z) -> cudaError_t {
+    if (p->ilu_on && (ilu32 ? p->ilu_chain32 : p->ilu_chain64) && nvec <= p->lim.nrhs_max) {
+      p->tail_used = true;  // its bounded waits report through the barrier words
+      if (ilu32)
+        return hz::launch_ilu0_chain32(p->g, p->invd32, t, Buf<float2>{p->ilu_u32, p->g.n}, z,
+                                       nvec, p->ilu_prog, p->tail_bar, st);
+      return hz::launch_ilu0_chain(p->g, p->invd, t, z, nvec, p->ilu_prog, p->tail_bar, st);
+    }
     if (p->invlap_on)
       return hz::launch_spectral<double2>(p->spec, p->g, hz::SPEC_INVLAP, hz::vec_map(t.p, t.rs),
                                           hz::vec_map(z.p, z.rs), nvec, p->d64, 0.0, 0.0,
@@ -1523,6 +1532,10 @@ hz_status hz_problem_set_inner_ilu(hz_problem* p, int on) {
     HZ_TRY(dalloc(p, (void**)&p->ilu_u32, sizeof(float2) * (size_t)p->g.n * p->lim.nrhs_max));
     HZ_CUDA(cudaMemcpy(p->invd32, invd32.data(), sizeof(float) * invd32.size(),
                        cudaMemcpyHostToDevice));
+    HZ_TRY(dalloc(p, (void**)&p->ilu_prog,
+                  sizeof(int) * (size_t)hz::ilu0_chain_prog_ints(p->g, p->lim.nrhs_max)));
+    p->ilu_chain64 = hz::ilu0_chain_fits(p->g, p->lim.nrhs_max, false);
+    p->ilu_chain32 = hz::ilu0_chain_fits(p->g, p->lim.nrhs_max, true);
   }
   if ((on != 0) != p->ilu_on) p->drop_graphs();
   p->ilu_on = on != 0;
@@ -1563,6 +1576,15 @@ hz_status hz_ilu0_apply(hz_problem* p, const void* t, void* z, int nvec, void* s
   if (!t || !z || t == z) return fail(HZ_ERR_INVALID, "null or overlapping fields");
   HZ_TRY(set_device(p));
   const long long n = p->g.n;
+  if (p->ilu_chain64 && nvec <= p->lim.nrhs_max) {
+    // the multi-block sweeps; a bounded wait that gave up is reported here (after a sync)
+    HZ_CUDA(hz::launch_ilu0_chain(p->g, p->invd, Buf<const double2>{(const double2*)t, n},
+                                  Buf<double2>{(double2*)z, n}, nvec, p->ilu_prog, p->tail_bar,
+                                  (cudaStream_t)stream));
+    p->tail_used = true;
+    HZ_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return check_tail_fault(p);
+  }
   HZ_CUDA(hz::launch_ilu0(p->g, p->invd, Buf<const double2>{(const double2*)t, n},
                           Buf<double2>{(double2*)z, n}, nvec, (cudaStream_t)stream));
   return HZ_OK;

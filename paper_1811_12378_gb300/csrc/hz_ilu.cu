@@ -14,6 +14,7 @@
 // its threads take the (j, k) lines, each holding the one point of its line on the plane.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "hz_device.cuh"
@@ -196,6 +197,267 @@ __global__ void __launch_bounds__(IT) k_ilu0_apply_smem32(Geom g, const float* _
 
 constexpr size_t kIluSmemMax = 200 * 1024;
 
+// ---------------------------------------------------------------- multi-block wavefront
+// The same sweeps spread over the SMs: block K owns the TK z-planes k0 = K TK .. k0 + TK - 1
+// (all their (j, k) lines) and walks the global hyperplanes w = i + j + k that cross them.  A
+// point's lower neighbour in z across the slab boundary, (i, j, k0 - 1), lies on hyperplane
+// w - 1 of block K - 1, so block K takes plane w once block K - 1 has published that it finished
+// plane w - 1 (a release store of w after each plane, an acquire load before); the backward
+// sweep mirrors this with block K + 1.  Within a block the lines' latest values live in shared
+// memory as in the one-block kernels, and a neighbour block's boundary values are read from the
+// global field past L1.  The blocks wait on one another, so the grid is launched cooperatively
+// (all blocks resident); each wait is bounded by the problem's poll limit, after which the
+// block records the error, stops waiting and runs on (its results are then wrong and the solve
+// reports HZ_ERR_TIMEOUT), so no block waits forever.
+constexpr int CHAIN_Q = 4;  // planes between two published progress values
+constexpr int CHAIN_D = 4;  // planes a line's loads run ahead of its computation
+
+template <typename R> struct CplxOf;
+template <> struct CplxOf<float> { using type = float2; };
+template <> struct CplxOf<double> { using type = double2; };
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+template <typename V>
+__device__ __forceinline__ V ld_cg(const V* p);
+template <>
+__device__ __forceinline__ float2 ld_cg<float2>(const float2* p) { return __ldcg(p); }
+template <>
+__device__ __forceinline__ double2 ld_cg<double2>(const double2* p) { return __ldcg(p); }
+
+// Bounded wait of thread 0 until ready(*flag); false (error recorded) if the limit ran out.
+template <typename Ready>
+__device__ bool chain_wait(const int* flag, Ready ready, unsigned* bar) {
+  const unsigned lim = *(volatile unsigned*)(bar + 3);
+  for (unsigned it = 0;; ++it) {
+    if (ready(ld_acquire(flag))) return true;
+    if (it >= lim) {
+      atomicExch(bar + 2, 1u);
+      return false;
+    }
+    if (it > 64) __nanosleep(32);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ typename CplxOf<R>::type to_r(double2 v);
+template <>
+__device__ __forceinline__ float2 to_r<float>(double2 v) {
+  return make_float2(float(v.x), float(v.y));
+}
+template <>
+__device__ __forceinline__ double2 to_r<double>(double2 v) { return v; }
+
+// Forward sweep (D + L) u = t: u into uo (complex of R).  One thread per (j, k) line of the
+// slab (blockDim >= lines), software-pipelined: a line's t and 1/d run CHAIN_D planes ahead of
+// its computation in registers, and the neighbour block's boundary value for plane w + 1 is
+// loaded during plane w when its published progress already covers plane w.  The neighbour's progress
+// is polled only when the last value seen is not far enough, and this block's is published
+// every CHAIN_Q planes, after the block barrier that closes the planes before, by one release
+// store (cumulative over the block's writes it has observed through that barrier).
+template <typename R>
+__global__ void k_ilu0_chain_fwd(Geom g, const R* __restrict__ invd, R cs,
+                                 const double2* __restrict__ t, long long trs,
+                                 typename CplxOf<R>::type* uo, long long urs, int TK, int* prog,
+                                 unsigned* bar) {
+  using V = typename CplxOf<R>::type;
+  extern __shared__ unsigned char ch_smem[];
+  __shared__ int s_seen;
+  const int K = blockIdx.x, r = blockIdx.y, nK = gridDim.x;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const long long sy = nx, sz = (long long)nx * ny;
+  const int k0 = K * TK, tkc = min(TK, nz - k0);
+  const int lines = ny * tkc;
+  V* buf0 = reinterpret_cast<V*>(ch_smem);
+  V* buf1 = buf0 + (size_t)ny * TK;
+  const double2* tr = t + r * trs;
+  V* ur = uo + r * urs;
+  int* mine = prog + (long long)r * nK + K;
+  const int* prev = K > 0 ? mine - 1 : nullptr;
+  bool waiting = prev != nullptr;
+  int seen = 0;
+  const int l = threadIdx.x;
+  const bool has = l < lines;
+  const int j = has ? l % ny : 0, kl = has ? l / ny : 0, k = k0 + kl;
+  const bool edge = has && kl == 0 && K > 0;  // the lower z neighbour lies in block K - 1
+  const long long pl = sy * j + sz * k;       // the line's first point
+  const int wlo = k0, whi = k0 + tkc - 1 + nx - 1 + ny - 1;
+  V tq[CHAIN_D], nb_n{};
+  R iq[CHAIN_D];
+  bool nb_ok = false;
+#pragma unroll
+  for (int d = 0; d < CHAIN_D; ++d) {  // the loads of planes wlo .. wlo + CHAIN_D - 1
+    const int id = wlo + d - j - k;
+    tq[d] = V{};
+    iq[d] = 0;
+    if (has && id >= 0 && id < nx) {
+      tq[d] = to_r<R>(tr[pl + id]);
+      iq[d] = invd[pl + id];
+    }
+  }
+  for (int w0 = wlo; w0 <= whi; w0 += CHAIN_D) {
+#pragma unroll
+  for (int d = 0; d < CHAIN_D; ++d) {  // slot d of the register ring holds plane w0 + d
+    const int w = w0 + d;
+    if (w > whi) break;
+    const int i = w - j - k;
+    const bool act = has && i >= 0 && i < nx;
+    const long long p = pl + i;
+    const V tv = tq[d], nbp = nb_n;
+    const R iv = iq[d];
+    const bool have_nb = nb_ok;
+    {
+      const int ia = i + CHAIN_D;  // the slot's next plane, w + CHAIN_D
+      if (has && ia >= 0 && ia < nx) {
+        tq[d] = to_r<R>(tr[pl + ia]);
+        iq[d] = invd[pl + ia];
+      }
+    }
+    if (threadIdx.x == 0) {
+      if (waiting && seen < w &&
+          !chain_wait(prev, [&seen, w](int v) { seen = v; return v >= w; }, bar))
+        waiting = false;
+      s_seen = waiting ? seen : 0x7fffffff;
+    }
+    __syncthreads();  // planes < w of this block are complete
+    if (threadIdx.x == 0 && w > wlo && (w - wlo) % CHAIN_Q == 0) st_release(mine, w);
+    // the next plane's boundary value where block K - 1 has finished plane w
+    nb_ok = false;
+    if (edge && i + 1 >= 0 && i + 1 < nx && s_seen >= w + 1) {
+      nb_n = ld_cg(ur + p + 1 - sz);
+      nb_ok = true;
+    }
+    const V* old = (w & 1) ? buf0 : buf1;
+    V* cur = (w & 1) ? buf1 : buf0;
+    if (act) {
+      R ax = 0, ay = 0;
+      if (i > 0) { ax += old[l].x; ay += old[l].y; }
+      if (j > 0) { ax += old[l - 1].x; ay += old[l - 1].y; }
+      if (kl > 0) {
+        ax += old[l - ny].x;
+        ay += old[l - ny].y;
+      } else if (K > 0) {
+        const V nb = have_nb ? nbp : ld_cg(ur + p - sz);
+        ax += nb.x;
+        ay += nb.y;
+      }
+      V u;
+      u.x = (tv.x + cs * ax) * iv;
+      u.y = (tv.y + cs * ay) * iv;
+      cur[l] = u;
+      ur[p] = u;
+    }
+  }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) st_release(mine, 0x7fffffff);  // finished: nothing more to wait for
+}
+
+// Backward sweep (D + U) z = D u: reads u (complex of R), writes z (double2); z may be the
+// field u lives in (float64 form: each point's u is read before this block overwrites it).
+// Pipelined and published like the forward sweep, towards decreasing planes.
+template <typename R>
+__global__ void k_ilu0_chain_bwd(Geom g, const R* __restrict__ invd, R cs,
+                                 const typename CplxOf<R>::type* ui, long long urs, double2* z,
+                                 long long zrs, int TK, int* prog, unsigned* bar) {
+  using V = typename CplxOf<R>::type;
+  extern __shared__ unsigned char ch_smem[];
+  __shared__ int s_seen;
+  const int K = blockIdx.x, r = blockIdx.y, nK = gridDim.x;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const long long sy = nx, sz = (long long)nx * ny;
+  const int k0 = K * TK, tkc = min(TK, nz - k0);
+  const int lines = ny * tkc;
+  V* buf0 = reinterpret_cast<V*>(ch_smem);
+  V* buf1 = buf0 + (size_t)ny * TK;
+  const V* ur = ui + r * urs;
+  double2* zr = z + r * zrs;
+  int* mine = prog + (long long)r * nK + K;
+  const int* next = K + 1 < nK ? mine + 1 : nullptr;
+  bool waiting = next != nullptr;
+  int seen = 0x7fffffff;
+  const int l = threadIdx.x;
+  const bool has = l < lines;
+  const int j = has ? l % ny : 0, kl = has ? l / ny : 0, k = k0 + kl;
+  const bool edge = has && kl == tkc - 1 && K + 1 < nK;  // upper z neighbour in block K + 1
+  const long long pl = sy * j + sz * k;
+  const int wlo = k0, whi = k0 + tkc - 1 + nx - 1 + ny - 1;
+  V uq[CHAIN_D], nb_n{};
+  R fq[CHAIN_D];
+  bool nb_ok = false;
+#pragma unroll
+  for (int d = 0; d < CHAIN_D; ++d) {  // the loads of planes whi .. whi - CHAIN_D + 1
+    const int id = whi - d - j - k;
+    uq[d] = V{};
+    fq[d] = 0;
+    if (has && id >= 0 && id < nx) {
+      uq[d] = ur[pl + id];
+      fq[d] = cs * invd[pl + id];
+    }
+  }
+  for (int w0 = whi; w0 >= wlo; w0 -= CHAIN_D) {
+#pragma unroll
+  for (int d = 0; d < CHAIN_D; ++d) {  // slot d holds plane w0 - d
+    const int w = w0 - d;
+    if (w < wlo) break;
+    const int i = w - j - k;
+    const bool act = has && i >= 0 && i < nx;
+    const long long p = pl + i;
+    const V u = uq[d], nbp = nb_n;
+    const R f = fq[d];
+    const bool have_nb = nb_ok;
+    {
+      const int ia = i - CHAIN_D;  // the slot's next plane, w - CHAIN_D
+      if (has && ia >= 0 && ia < nx) {
+        uq[d] = ur[pl + ia];
+        fq[d] = cs * invd[pl + ia];
+      }
+    }
+    if (threadIdx.x == 0) {
+      if (waiting && seen > w + 1 &&
+          !chain_wait(next, [&seen, w](int v) { seen = v; return v <= w + 1; }, bar))
+        waiting = false;
+      s_seen = waiting ? seen : (int)0x80000000;
+    }
+    __syncthreads();  // planes > w of this block are complete
+    if (threadIdx.x == 0 && w < whi && (whi - w) % CHAIN_Q == 0) st_release(mine, w + 1);
+    nb_ok = false;
+    if (edge && i - 1 >= 0 && i - 1 < nx && s_seen <= w) {  // block K + 1 finished plane w
+      nb_n = to_r<R>(__ldcg(zr + p - 1 + sz));
+      nb_ok = true;
+    }
+    const V* old = (w & 1) ? buf0 : buf1;
+    V* cur = (w & 1) ? buf1 : buf0;
+    if (act) {
+      R ax = 0, ay = 0;
+      if (i < nx - 1) { ax += old[l].x; ay += old[l].y; }
+      if (j < ny - 1) { ax += old[l + 1].x; ay += old[l + 1].y; }
+      if (kl < tkc - 1) {
+        ax += old[l + ny].x;
+        ay += old[l + ny].y;
+      } else if (K + 1 < nK) {
+        const V nb = have_nb ? nbp : to_r<R>(__ldcg(zr + p + sz));
+        ax += nb.x;
+        ay += nb.y;
+      }
+      V zv;
+      zv.x = u.x + f * ax;
+      zv.y = u.y + f * ay;
+      cur[l] = zv;
+      zr[p] = make_double2(double(zv.x), double(zv.y));
+    }
+  }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) st_release(mine, (int)0x80000000);  // finished
+}
+
 // out[r] += d[r] w[r], d the FCI step size in the inner GMRES state
 __global__ void k_add_dw(double2* __restrict__ out, long long ors, const double2* __restrict__ w,
                          long long wrs, long long n, GmresDev gs) {
@@ -263,6 +525,91 @@ cudaError_t launch_ilu0(const Geom& g, const double* invd, Buf<const double2> t,
   }
   return launch_pdl(k_ilu0_apply, dim3(nvec), dim3(IT), 0, st, g, invd, g.cs, t.p, t.rs, z.p,
                     z.rs);
+}
+
+// ---- multi-block wavefront sweeps
+namespace {
+int chain_tk(int ny) { return std::max(1, 512 / std::max(1, ny)); }
+int chain_threads(int ny, int tk) { return (ny * tk + 31) / 32 * 32; }  // one per line
+
+template <typename R>
+bool chain_fits_r(const Geom& g, int nvec) {
+  using V = typename CplxOf<R>::type;
+  const int tk = chain_tk(g.ny), nk = (g.nz + tk - 1) / tk, nt = chain_threads(g.ny, tk);
+  const size_t smem = 2 * sizeof(V) * (size_t)g.ny * tk;
+  if (smem > 48 * 1024 || nk < 2 || nt > 1024) return false;
+  int dev = 0, sms = 0, bf = 0, bb = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_ilu0_chain_fwd<R>, nt, smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_ilu0_chain_bwd<R>, nt, smem) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (long long)std::min(bf, bb) * sms >= (long long)nk * nvec;
+}
+
+template <typename K, typename... Args>
+cudaError_t launch_coop(K kern, dim3 grid, int nt, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(nt);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <typename R>
+cudaError_t launch_chain_r(const Geom& g, const R* invd, Buf<const double2> t,
+                           typename CplxOf<R>::type* u, long long urs, Buf<double2> z, int nvec,
+                           int* prog, unsigned* bar, cudaStream_t st) {
+  using V = typename CplxOf<R>::type;
+  const int tk = chain_tk(g.ny), nk = (g.nz + tk - 1) / tk, nt = chain_threads(g.ny, tk);
+  const size_t smem = 2 * sizeof(V) * (size_t)g.ny * tk;
+  const size_t np = (size_t)nk * nvec;
+  int* pf = prog;
+  int* pb = prog + np;
+  cudaError_t e = cudaMemsetAsync(pf, 0, sizeof(int) * np, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pb, 0x7f, sizeof(int) * np, st);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(nk, nvec);
+  count_launch();
+  e = launch_coop(k_ilu0_chain_fwd<R>, grid, nt, smem, st, g, invd, R(g.cs), t.p, t.rs, u, urs,
+                  tk, pf, bar);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  return launch_coop(k_ilu0_chain_bwd<R>, grid, nt, smem, st, g, invd, R(g.cs),
+                     (const V*)u, urs, z.p, z.rs, tk, pb, bar);
+}
+}  // namespace
+
+bool ilu0_chain_fits(const Geom& g, int nvec, bool f32) {
+  return f32 ? chain_fits_r<float>(g, nvec) : chain_fits_r<double>(g, nvec);
+}
+
+long long ilu0_chain_prog_ints(const Geom& g, int nvec) {
+  const int tk = chain_tk(g.ny);
+  return 2LL * ((g.nz + tk - 1) / tk) * nvec;
+}
+
+cudaError_t launch_ilu0_chain(const Geom& g, const double* invd, Buf<const double2> t,
+                              Buf<double2> z, int nvec, int* prog, unsigned* bar,
+                              cudaStream_t st) {
+  // the forward result lives in z itself, which the backward sweep overwrites point by point
+  return launch_chain_r<double>(g, invd, t, z.p, z.rs, z, nvec, prog, bar, st);
+}
+
+cudaError_t launch_ilu0_chain32(const Geom& g, const float* invd32, Buf<const double2> t,
+                                Buf<float2> u32, Buf<double2> z, int nvec, int* prog,
+                                unsigned* bar, cudaStream_t st) {
+  return launch_chain_r<float>(g, invd32, t, u32.p, u32.rs, z, nvec, prog, bar, st);
 }
 
 cudaError_t launch_add_dw(Buf<double2> out, Buf<const double2> w, long long n, const GmresDev& gs,

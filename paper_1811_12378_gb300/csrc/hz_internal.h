@@ -329,6 +329,17 @@ cudaError_t ilu0_prepare();
 cudaError_t launch_ilu0_32(const Geom& g, const float* invd32, Buf<const double2> t,
                            Buf<float2> u32, Buf<double2> z, int nvec, cudaStream_t st);
 bool ilu0_fits32(const Geom& g);
+// The same sweeps as a multi-block wavefront over z-slabs (cooperative launches; every wait on
+// a neighbouring block bounded by bar[3] polls, giving up sets bar[2]).  prog: scratch of
+// ilu0_chain_prog_ints ints.  ilu0_chain_fits: the grid can be co-resident.
+bool ilu0_chain_fits(const Geom& g, int nvec, bool f32);
+long long ilu0_chain_prog_ints(const Geom& g, int nvec);
+cudaError_t launch_ilu0_chain(const Geom& g, const double* invd, Buf<const double2> t,
+                              Buf<double2> z, int nvec, int* prog, unsigned* bar,
+                              cudaStream_t st);
+cudaError_t launch_ilu0_chain32(const Geom& g, const float* invd32, Buf<const double2> t,
+                                Buf<float2> u32, Buf<double2> z, int nvec, int* prog,
+                                unsigned* bar, cudaStream_t st);
 // z = M^{-1} t for nvec fields (t and z must not overlap).
 cudaError_t launch_ilu0(const Geom& g, const double* invd, Buf<const double2> t, Buf<double2> z,
                         int nvec, cudaStream_t st);

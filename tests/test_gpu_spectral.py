@@ -183,6 +183,10 @@ def test_spectral_multi_rhs_and_batched_solves():
         with hzpkg.Problem(wf.c, wf.h, wf.omega, wf.layer_cells, wf.sigma_max, wf.J, wf.t,
                            wf.eps, nrhs_max=1, restart_max=20, inner_k_max=4) as Q:
             fq = to_dev(wf.f[:1].reshape(1, -1))
+            # a batch runs the per-piece Krylov kernels; the lone solve of one right-hand side
+            # would otherwise take the cooperative ones (other rounding)
+            Q.fused_tail(0)
+            Q.fused_arnoldi(0)
             us, sts = hzpkg.solve_batched([P, Q], [to_dev(f2[:1]), fq], **kw)
             uq, stq = Q.solve(fq, **kw)
             assert np.array_equal(to_np(us[0])[0], u2[0]) and sts[0][0].its == st2[0].its
