@@ -767,6 +767,7 @@ def run_ours(args):
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"replicas x{world}"},
         "its": st_head.its, "matvecs": st_head.matvecs,
+        "matvecs_per_s": st_head.matvecs * value,
         "rel_res_true": st_head.rel_res_true, "rel_res_check": res,
         "roofline": roof,
         "kernel_classes": {k: {"launches": v[0], "ms": v[1], "GB": v[2] / 1e9,

@@ -263,7 +263,7 @@ __device__ __forceinline__ double2 to_r<double>(double2 v) { return v; }
 // store (cumulative over the block's writes it has observed through that barrier).
 template <typename R>
 __global__ void k_ilu0_chain_fwd(Geom g, const R* __restrict__ invd, R cs,
-                                 const double2* __restrict__ t, long long trs,
+                                 const typename CplxOf<R>::type* t, long long trs,
                                  typename CplxOf<R>::type* uo, long long urs, int TK, int* prog,
                                  unsigned* bar) {
   using V = typename CplxOf<R>::type;
@@ -276,7 +276,7 @@ __global__ void k_ilu0_chain_fwd(Geom g, const R* __restrict__ invd, R cs,
   const int lines = ny * tkc;
   V* buf0 = reinterpret_cast<V*>(ch_smem);
   V* buf1 = buf0 + (size_t)ny * TK;
-  const double2* tr = t + r * trs;
+  const V* tr = t + r * trs;  // may be the field u is written to: each point is read first
   V* ur = uo + r * urs;
   int* mine = prog + (long long)r * nK + K;
   const int* prev = K > 0 ? mine - 1 : nullptr;
@@ -297,7 +297,7 @@ __global__ void k_ilu0_chain_fwd(Geom g, const R* __restrict__ invd, R cs,
     tq[d] = V{};
     iq[d] = 0;
     if (has && id >= 0 && id < nx) {
-      tq[d] = to_r<R>(tr[pl + id]);
+      tq[d] = tr[pl + id];
       iq[d] = invd[pl + id];
     }
   }
@@ -315,7 +315,7 @@ __global__ void k_ilu0_chain_fwd(Geom g, const R* __restrict__ invd, R cs,
     {
       const int ia = i + CHAIN_D;  // the slot's next plane, w + CHAIN_D
       if (has && ia >= 0 && ia < nx) {
-        tq[d] = to_r<R>(tr[pl + ia]);
+        tq[d] = tr[pl + ia];
         iq[d] = invd[pl + ia];
       }
     }
@@ -364,8 +364,9 @@ __global__ void k_ilu0_chain_fwd(Geom g, const R* __restrict__ invd, R cs,
 // Pipelined and published like the forward sweep, towards decreasing planes.
 template <typename R>
 __global__ void k_ilu0_chain_bwd(Geom g, const R* __restrict__ invd, R cs,
-                                 const typename CplxOf<R>::type* ui, long long urs, double2* z,
-                                 long long zrs, int TK, int* prog, unsigned* bar) {
+                                 const typename CplxOf<R>::type* ui, long long urs,
+                                 typename CplxOf<R>::type* z, long long zrs, int TK, int* prog,
+                                 unsigned* bar) {
   using V = typename CplxOf<R>::type;
   extern __shared__ unsigned char ch_smem[];
   __shared__ int s_seen;
@@ -377,7 +378,7 @@ __global__ void k_ilu0_chain_bwd(Geom g, const R* __restrict__ invd, R cs,
   V* buf0 = reinterpret_cast<V*>(ch_smem);
   V* buf1 = buf0 + (size_t)ny * TK;
   const V* ur = ui + r * urs;
-  double2* zr = z + r * zrs;
+  V* zr = z + r * zrs;
   int* mine = prog + (long long)r * nK + K;
   const int* next = K + 1 < nK ? mine + 1 : nullptr;
   bool waiting = next != nullptr;
@@ -429,7 +430,7 @@ __global__ void k_ilu0_chain_bwd(Geom g, const R* __restrict__ invd, R cs,
     if (threadIdx.x == 0 && w < whi && (whi - w) % CHAIN_Q == 0) st_release(mine, w + 1);
     nb_ok = false;
     if (edge && i - 1 >= 0 && i - 1 < nx && s_seen <= w) {  // block K + 1 finished plane w
-      nb_n = to_r<R>(__ldcg(zr + p - 1 + sz));
+      nb_n = ld_cg(zr + p - 1 + sz);
       nb_ok = true;
     }
     const V* old = (w & 1) ? buf0 : buf1;
@@ -442,7 +443,7 @@ __global__ void k_ilu0_chain_bwd(Geom g, const R* __restrict__ invd, R cs,
         ax += old[l + ny].x;
         ay += old[l + ny].y;
       } else if (K + 1 < nK) {
-        const V nb = have_nb ? nbp : to_r<R>(__ldcg(zr + p + sz));
+        const V nb = have_nb ? nbp : ld_cg(zr + p + sz);
         ax += nb.x;
         ay += nb.y;
       }
@@ -450,7 +451,7 @@ __global__ void k_ilu0_chain_bwd(Geom g, const R* __restrict__ invd, R cs,
       zv.x = u.x + f * ax;
       zv.y = u.y + f * ay;
       cur[l] = zv;
-      zr[p] = make_double2(double(zv.x), double(zv.y));
+      zr[p] = zv;
     }
   }
   }
@@ -566,10 +567,14 @@ cudaError_t launch_coop(K kern, dim3 grid, int nt, size_t smem, cudaStream_t st,
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// t, u and z in the arithmetic's own type (the float32 sweeps run on complex64 copies made by
+// the caller: a float64 <-> float32 conversion is a float64-pipe instruction, too slow for
+// the sequential planes).
 template <typename R>
-cudaError_t launch_chain_r(const Geom& g, const R* invd, Buf<const double2> t,
-                           typename CplxOf<R>::type* u, long long urs, Buf<double2> z, int nvec,
-                           int* prog, unsigned* bar, cudaStream_t st) {
+cudaError_t launch_chain_r(const Geom& g, const R* invd, const typename CplxOf<R>::type* t,
+                           long long trs, typename CplxOf<R>::type* u, long long urs,
+                           typename CplxOf<R>::type* z, long long zrs, int nvec, int* prog,
+                           unsigned* bar, cudaStream_t st) {
   using V = typename CplxOf<R>::type;
   const int tk = chain_tk(g.ny), nk = (g.nz + tk - 1) / tk, nt = chain_threads(g.ny, tk);
   const size_t smem = 2 * sizeof(V) * (size_t)g.ny * tk;
@@ -581,12 +586,12 @@ cudaError_t launch_chain_r(const Geom& g, const R* invd, Buf<const double2> t,
   if (e != cudaSuccess) return e;
   const dim3 grid(nk, nvec);
   count_launch();
-  e = launch_coop(k_ilu0_chain_fwd<R>, grid, nt, smem, st, g, invd, R(g.cs), t.p, t.rs, u, urs,
+  e = launch_coop(k_ilu0_chain_fwd<R>, grid, nt, smem, st, g, invd, R(g.cs), t, trs, u, urs,
                   tk, pf, bar);
   if (e != cudaSuccess) return e;
   count_launch();
   return launch_coop(k_ilu0_chain_bwd<R>, grid, nt, smem, st, g, invd, R(g.cs),
-                     (const V*)u, urs, z.p, z.rs, tk, pb, bar);
+                     (const V*)u, urs, z, zrs, tk, pb, bar);
 }
 }  // namespace
 
@@ -603,13 +608,20 @@ cudaError_t launch_ilu0_chain(const Geom& g, const double* invd, Buf<const doubl
                               Buf<double2> z, int nvec, int* prog, unsigned* bar,
                               cudaStream_t st) {
   // the forward result lives in z itself, which the backward sweep overwrites point by point
-  return launch_chain_r<double>(g, invd, t, z.p, z.rs, z, nvec, prog, bar, st);
+  return launch_chain_r<double>(g, invd, t.p, t.rs, z.p, z.rs, z.p, z.rs, nvec, prog, bar, st);
 }
 
 cudaError_t launch_ilu0_chain32(const Geom& g, const float* invd32, Buf<const double2> t,
                                 Buf<float2> u32, Buf<double2> z, int nvec, int* prog,
                                 unsigned* bar, cudaStream_t st) {
-  return launch_chain_r<float>(g, invd32, t, u32.p, u32.rs, z, nvec, prog, bar, st);
+  // t rounded to complex64 into u32, both sweeps in place there, then back to float64 in z
+  cudaError_t e = launch_convert_c128_c64(t, u32, g.n, nvec, st);
+  if (e == cudaSuccess)
+    e = launch_chain_r<float>(g, invd32, u32.p, u32.rs, u32.p, u32.rs, u32.p, u32.rs, nvec, prog,
+                              bar, st);
+  if (e == cudaSuccess)
+    e = launch_convert_c64_c128(Buf<const float2>{u32.p, u32.rs}, z, g.n, nvec, st);
+  return e;
 }
 
 cudaError_t launch_add_dw(Buf<double2> out, Buf<const double2> w, long long n, const GmresDev& gs,
