@@ -626,11 +626,14 @@ def test_case_two_solves_point_source_32():
 
 
 # ---------------------------------------------------------------------- ILU(0) (§6.3, §7.3)
-@pytest.mark.parametrize("shape,layer", [((37, 19, 11), 3), ((1, 1, 1), 0), ((32, 32, 32), 8)],
+@pytest.mark.parametrize("shape,layer", [((37, 19, 11), 3), ((1, 1, 1), 0), ((32, 32, 32), 8),
+                                         ((20, 24, 37), 2), ((40, 64, 50), 4)],
                          ids=lambda v: str(v))
 def test_ilu0_apply_matches_oracle(shape, layer):
     """z = M^{-1} t with the ILU(0) factors of the 7-point Laplacian: the GPU's hyperplane sweeps
-    against the oracle's (two right-hand sides, ragged and degenerate grids): 1e-13."""
+    against the oracle's (two right-hand sides, ragged and degenerate grids): 1e-13.  The last
+    three grids run the multi-block wavefront (z-slabs of 512 / ny planes: 2 slabs at 32^3, 2
+    ragged at 24 x 37, 7 ragged at 64 x 50), the first two the one-block sweeps."""
     wl = W.small_case(21, *shape, layer=layer, J=2)
     op = O.make_operator(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max)
     Minv = O.ilu0_preconditioner(op)
@@ -642,13 +645,15 @@ def test_ilu0_apply_matches_oracle(shape, layer):
         assert rel(z[v], Minv(t[v])) <= 1e-13
 
 
+@pytest.mark.parametrize("shape", [(13, 9, 7), (24, 32, 20)], ids=str)
 @pytest.mark.parametrize("prec,tol", [(hzpkg.HZ_C128, 1e-11), (hzpkg.HZ_MIXED_C64, 1e-5)])
-def test_fci_with_ilu0_inner_preconditioner_matches_oracle(prec, tol):
+def test_fci_with_ilu0_inner_preconditioner_matches_oracle(prec, tol, shape):
     """Algorithm 1 with the inner GMRES right-preconditioned by ILU(0) (one and two right-hand
     sides per call) against the oracle's fci(..., inner_precond).  The mixed form takes its
     complex64 polynomial sweeps and float32 ILU(0) sweeps (1e-5, as for its FCI without ILU);
-    the all-float64 form its float64 ones (1e-11)."""
-    wl = W.small_case(3, 13, 9, 7, layer=2, J=4)
+    the all-float64 form its float64 ones (1e-11).  13 x 9 x 7 runs the one-block sweeps,
+    24 x 32 x 20 the multi-block wavefront (two z-slabs, the second ragged)."""
+    wl = W.small_case(3, *shape, layer=2, J=4)
     op, nodes = oracle_of(wl)
     Minv = O.ilu0_preconditioner(op)
     r = W.random_field(5, 2, wl.nx, wl.ny, wl.nz)
