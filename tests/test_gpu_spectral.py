@@ -58,7 +58,8 @@ def spectral_problem(wl, nodes=None, nrhs_max=2, restart_max=30, inner_k_max=6, 
 
 
 GRIDS = [((16, 16, 16), 2), ((30, 12, 10), 2), ((1, 8, 6), 1), ((25, 9, 20), 3),
-         ((64, 64, 64), 8)]
+         ((64, 64, 64), 8), ((128, 32, 12), 2), ((256, 10, 32), 2)]  # lines of 32-256 points
+                                                                      # take the compiled sizes
 
 
 @pytest.mark.parametrize("shape,layer", GRIDS, ids=lambda v: str(v))
