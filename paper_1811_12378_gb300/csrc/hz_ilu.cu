@@ -202,8 +202,8 @@ constexpr size_t kIluSmemMax = 200 * 1024;
 // (all their (j, k) lines) and walks the global hyperplanes w = i + j + k that cross them.  A
 // point's lower neighbour in z across the slab boundary, (i, j, k0 - 1), lies on hyperplane
 // w - 1 of block K - 1, so block K takes plane w once block K - 1 has published that it finished
-// plane w - 1 (a release store of w after each plane, an acquire load before); the backward
-// sweep mirrors this with block K + 1.  Within a block the lines' latest values live in shared
+// plane w - 1 (release stores of its progress every CHAIN_Q planes, acquire loads before); the
+// backward sweep mirrors this with block K + 1.  Within a block the lines' latest values live in shared
 // memory as in the one-block kernels, and a neighbour block's boundary values are read from the
 // global field past L1.  The blocks wait on one another, so the grid is launched cooperatively
 // (all blocks resident); each wait is bounded by the problem's poll limit, after which the
