@@ -1369,6 +1369,11 @@ hz_status hz_problem_create(const hz_grid* grid, const double* c_host,
     return cuda_fail(e, "cooperative FCI tail set-up");
   }
   if (p->spectral) {
+    e = hz::fft_prepare();
+    if (e != cudaSuccess) {
+      delete p;
+      return cuda_fail(e, "line-FFT kernel attributes");
+    }
     // line-FFT tables of every axis: twiddles exp(-2 pi i k / n) and the eigenvalue shares
     // s (2 pi min(k, n - k) / (n h))^2, float64 on the host, rounded for the float32 kernels
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) {

@@ -159,18 +159,129 @@ __device__ T* fft_lines(T* A, T* B, int tl, int ls, const PassArgs& a, const T* 
 
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
 
-// The same for a line length N = 2^k known at compile time: radix 4 stages, then one of radix 2
-// where k is odd; every index computation is then shifts and masks of constants.
-template <typename T, int N, int L = 1>
-__device__ __forceinline__ T* fft_lines_ct(T* A, T* B, int tl, int ls, const T* __restrict__ tw) {
-  if constexpr (L >= N) {
-    return A;
-  } else {
-    constexpr int P = (N / L) % 4 == 0 ? 4 : 2;
-    fft_stage<T, P>(A, B, tl, N, ls, L, ilog2c(L), ilog2c(N / P), tw);
-    __syncthreads();
-    return fft_lines_ct<T, N, L * P>(B, A, tl, ls, tw);
+// ---- compiled line lengths N = 32 .. 256: two register-radix stages (8 x 4, 16 x 4, 16 x 8,
+// 16 x 16), so every element passes through shared memory twice per transform, and a padded
+// shared layout (one spare element after every 16) so that the radix-strided accesses of a
+// warp fall into different banks.
+__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+template <int N> __host__ __device__ constexpr int padded_stride() { return N + N / 16 + 1; }
+
+// w_16^m = cos(2 pi m / 16) - i sin(2 pi m / 16) for the m = n2 k1 of a 16 = 4 x 4 split
+template <typename R>
+__device__ __forceinline__ void w16(int m, R& c, R& s) {
+  const R c1 = R(0.92387953251128674), s1 = R(0.38268343236508977), h = R(0.70710678118654752);
+  switch (m) {
+    case 0: c = R(1); s = R(0); break;
+    case 1: c = c1; s = -s1; break;
+    case 2: c = h; s = -h; break;
+    case 3: c = s1; s = -c1; break;
+    case 4: c = R(0); s = R(-1); break;
+    case 6: c = -h; s = -h; break;
+    default: c = -c1; s = s1; break;  // m = 9
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void dft4(T& a0, T& a1, T& a2, T& a3) {
+  const T s02 = cadd(a0, a2), d02 = csub(a0, a2);
+  const T s13 = cadd(a1, a3), d13 = csub(a1, a3);
+  const T mi = mk(d13.y, -d13.x);  // -i (a1 - a3)
+  a0 = cadd(s02, s13);
+  a1 = cadd(d02, mi);
+  a2 = csub(s02, s13);
+  a3 = csub(d02, mi);
+}
+
+// In-register DFT of P = 4, 8 or 16 points, natural order in and out.
+template <typename T, int P>
+__device__ __forceinline__ void dft_reg(T (&a)[P]) {
+  using R = decltype(a[0].x);
+  if constexpr (P == 4) {
+    dft4(a[0], a[1], a[2], a[3]);
+  } else if constexpr (P == 8) {
+    // 8 = 4 x 2: DFT4 over n1 of a[2 n1 + n2], twiddle w8^{n2 k1}, DFT2 over n2
+    T b0[4] = {a[0], a[2], a[4], a[6]}, b1[4] = {a[1], a[3], a[5], a[7]};
+    dft4(b0[0], b0[1], b0[2], b0[3]);
+    dft4(b1[0], b1[1], b1[2], b1[3]);
+    const R h = R(0.70710678118654752);
+    b1[1] = mk(h * (b1[1].x + b1[1].y), h * (b1[1].y - b1[1].x));    // * (1 - i)/sqrt2
+    b1[2] = mk(b1[2].y, -b1[2].x);                                     // * -i
+    b1[3] = mk(h * (b1[3].y - b1[3].x), -h * (b1[3].x + b1[3].y));   // * (-1 - i)/sqrt2
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      a[k1] = cadd(b0[k1], b1[k1]);
+      a[k1 + 4] = csub(b0[k1], b1[k1]);
+    }
+  } else {
+    // 16 = 4 x 4: DFT4 over n1 of a[4 n1 + n2], twiddle w16^{n2 k1}, DFT4 over n2
+    T b[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      b[n2][0] = a[n2];
+      b[n2][1] = a[4 + n2];
+      b[n2][2] = a[8 + n2];
+      b[n2][3] = a[12 + n2];
+      dft4(b[n2][0], b[n2][1], b[n2][2], b[n2][3]);
+    }
+#pragma unroll
+    for (int n2 = 1; n2 < 4; ++n2)
+#pragma unroll
+      for (int k1 = 1; k1 < 4; ++k1) {
+        R c, sn;
+        w16<R>(n2 * k1, c, sn);
+        b[n2][k1] = cmul(b[n2][k1], mk(c, sn));
+      }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      T c0 = b[0][k1], c1 = b[1][k1], c2 = b[2][k1], c3 = b[3][k1];
+      dft4(c0, c1, c2, c3);
+      a[k1] = c0;
+      a[k1 + 4] = c1;
+      a[k1 + 8] = c2;
+      a[k1 + 12] = c3;
+    }
+  }
+}
+
+// One Stockham stage of radix P (4, 8, 16) with the combined length L before it, all constants,
+// on the padded layout: butterfly (m, j) takes a_q = w_{LP}^{jq} X[(m + r q) L + j] to
+// Y[m L P + j + L k].
+template <typename T, int N, int L, int P>
+__device__ __forceinline__ void fft_stage_ct(const T* X, T* Y, int tl, int ls,
+                                             const T* __restrict__ tw) {
+  constexpr int nb = N / P, r = N / (L * P);
+  for (int b = threadIdx.x; b < tl * nb; b += FT) {
+    const int l = b / nb, u = b % nb;
+    const int j = u % L, m = u / L;
+    const T* x = X + l * ls;
+    T a[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const T v = x[padi((m + r * q) * L + j)];
+      a[q] = (q == 0 || j == 0) ? v : cmul(v, tw[j * q * r]);
+    }
+    dft_reg<T, P>(a);
+    T* y = Y + l * ls;
+#pragma unroll
+    for (int k = 0; k < P; ++k) y[padi(m * L * P + j + L * k)] = a[k];
+  }
+}
+
+template <int N> struct Plan2;
+template <> struct Plan2<32> { static constexpr int P1 = 8, P2 = 4; };
+template <> struct Plan2<64> { static constexpr int P1 = 16, P2 = 4; };
+template <> struct Plan2<128> { static constexpr int P1 = 16, P2 = 8; };
+template <> struct Plan2<256> { static constexpr int P1 = 16, P2 = 16; };
+
+template <typename T, int N>
+__device__ __forceinline__ T* fft_lines_ct(T* A, T* B, int tl, int ls, const T* __restrict__ tw) {
+  constexpr int P1 = Plan2<N>::P1, P2 = Plan2<N>::P2;
+  static_assert(P1 * P2 == N, "two stages");
+  fft_stage_ct<T, N, 1, P1>(A, B, tl, ls, tw);
+  __syncthreads();
+  fft_stage_ct<T, N, P1, P2>(B, A, tl, ls, tw);
+  __syncthreads();
+  return A;
 }
 
 // NC: the line length when it is one of the compiled power-of-two sizes, else 0 (any length
@@ -186,7 +297,9 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
   __shared__ long long s_off[FT_XLINES];  // x pass: each line's first point within its field
   const int n = NC > 0 ? NC : a.n, tl = a.tl;
   const int nsh = NC > 0 ? ilog2c(NC) : a.nsh;
-  const int ls = n | 1;  // odd line stride in shared memory
+  // line stride in shared memory (odd); compiled lengths use the padded layout
+  const int ls = NC > 0 ? padded_stride<(NC > 0 ? NC : 16)>() : (n | 1);
+  auto sx = [&](int l, int e) { return l * ls + (NC > 0 ? padi(e) : e); };
   T* A = reinterpret_cast<T*>(fft_smem);
   T* B = A + (size_t)tl * ls;
   const long long sxy = (long long)a.nx * a.ny;
@@ -233,7 +346,7 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
       val = AXIS == 0 ? s_src[l][e] : srcb[l + (long long)e * stride];
       if (conj_in) val = cconj(val);
     }
-    A[l * ls + e] = val;
+    A[sx(l, e)] = val;
   }
   __syncthreads();
   T* X;
@@ -251,8 +364,8 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
       divmod(t, tl, a.tlsh, e, l);
       const R lam = (l < nvalid ? ex[i0 + l] : R(0)) + lj + ez[e];
       const R mlt = a.invlap ? sc / (lam > R(1) ? lam : R(1)) : sc * lam;
-      const T x = X[l * ls + e];
-      X[l * ls + e] = mk(mlt * x.x, -(mlt * x.y));  // conj: the inverse transform follows
+      const T x = X[sx(l, e)];
+      X[sx(l, e)] = mk(mlt * x.x, -(mlt * x.y));  // conj: the inverse transform follows
     }
     __syncthreads();
     T* Y = (X == A) ? B : A;
@@ -268,7 +381,7 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
     if (AXIS == 0) divmod(t, n, nsh, l, e);
     else divmod(t, tl, a.tlsh, e, l);
     if (l >= nvalid) continue;
-    T val = X[l * ls + e];
+    T val = X[sx(l, e)];
     if (conj_out) val = cconj(val);
     if (AXIS == 0 && comb) {  // the last pass runs along x: add (dg - z) x at the point
       const T x = s_xin[l][e];
@@ -290,11 +403,22 @@ inline int ilog2_exact(long long v) {  // log2(v) for a power of two, else -1
 
 // Lines per tile: x passes about 512 points (at most FT_XLINES lines), y and z passes about
 // 1024 points and at most 16 lines (16 adjacent x positions: 128-256 byte rows); powers of two.
-int tile_lines(int n, int axis) {
-  const int target = axis == 0 ? 512 : 1024;
-  const int cap = axis == 0 ? FT_XLINES : 16;
-  int tl = 1;
-  while (tl * 2 <= cap && tl * 2 * n <= target) tl *= 2;
+// Lines per tile: x passes about 512 points (the lines are contiguous); y and z passes 16
+// adjacent x positions (128-256 contiguous bytes per row, the DRAM-friendly width) as long as
+// both buffers stay within kFftSmemMax, else 8 or fewer.
+constexpr size_t kFftSmemMax = 96 * 1024;
+int line_stride(int n) {
+  const bool compiled = n == 32 || n == 64 || n == 128 || n == 256;
+  return compiled ? n + n / 16 + 1 : (n | 1);  // as the kernel's line stride
+}
+int tile_lines(int n, int axis, size_t elem) {
+  if (axis == 0) {
+    int tl = 1;
+    while (tl * 2 <= FT_XLINES && tl * 2 * n <= 512) tl *= 2;
+    return tl;
+  }
+  int tl = 16;
+  while (tl > 1 && 2 * elem * (size_t)tl * (size_t)line_stride(n) > kFftSmemMax) tl /= 2;
   return tl;
 }
 
@@ -333,9 +457,9 @@ cudaError_t run_pass(int axis, PassArgs a, const SpecPlan& sp, cudaStream_t st) 
     L *= p;
   }
   a.tw = tw_of<T>(ax);
-  a.tl = tile_lines(ax.n, axis);
+  a.tl = tile_lines(ax.n, axis, sizeof(T));
   a.tlsh = ilog2_exact(a.tl);
-  const size_t smem = 2 * sizeof(T) * (size_t)a.tl * (size_t)(ax.n | 1);
+  const size_t smem = 2 * sizeof(T) * (size_t)a.tl * (size_t)line_stride(ax.n);
   count_launch();
   dim3 grid;
   if (axis == 0) {
@@ -439,6 +563,36 @@ cudaError_t launch_scaled_sub(const double2* f, long long frs, double sc, const 
   count_launch();
   return launch_pdl(k_scaled_sub, dim3((unsigned)((n + 255) / 256), nvec), dim3(256), 0, st, f,
                     frs, sc, a, ars, t, trs, n);
+}
+
+namespace {
+template <typename T, int NC>
+cudaError_t fft_attr() {
+  cudaError_t e = cudaFuncSetAttribute(k_fft_pass<T, 0, NC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFftSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fft_pass<T, 1, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kFftSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fft_pass<T, 2, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kFftSmemMax);
+  return e;
+}
+template <typename T>
+cudaError_t fft_attrs() {
+  cudaError_t e = fft_attr<T, 0>();
+  if (e == cudaSuccess) e = fft_attr<T, 32>();
+  if (e == cudaSuccess) e = fft_attr<T, 64>();
+  if (e == cudaSuccess) e = fft_attr<T, 128>();
+  if (e == cudaSuccess) e = fft_attr<T, 256>();
+  return e;
+}
+}  // namespace
+
+cudaError_t fft_prepare() {
+  cudaError_t e = fft_attrs<float2>();
+  if (e == cudaSuccess) e = fft_attrs<double2>();
+  return e;
 }
 
 template <typename T>

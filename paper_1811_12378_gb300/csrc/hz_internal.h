@@ -124,6 +124,8 @@ inline VecMap vec_map(const void* p, long long rs) {
 
 enum SpecMode { SPEC_APPLY = 0, SPEC_LAP = 1, SPEC_INVLAP = 2 };
 
+// Shared-memory limits of the line-FFT kernels (once per process, before any capture).
+cudaError_t fft_prepare();
 // Radices of an FFT of length n (false unless n = 2^a 3^b 5^c <= FFT_MAXN).
 bool fft_factor(int n, int* rad, int* nst);
 // out = (s S - diag(m) - i diag(a) - zI) in (SPEC_APPLY, dg = -m - i a), s S in (SPEC_LAP) or the
