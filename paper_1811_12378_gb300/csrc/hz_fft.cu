@@ -401,8 +401,6 @@ inline int ilog2_exact(long long v) {  // log2(v) for a power of two, else -1
   return k;
 }
 
-// Lines per tile: x passes about 512 points (at most FT_XLINES lines), y and z passes about
-// 1024 points and at most 16 lines (16 adjacent x positions: 128-256 byte rows); powers of two.
 // Lines per tile: x passes about 512 points (the lines are contiguous); y and z passes 16
 // adjacent x positions (128-256 contiguous bytes per row, the DRAM-friendly width) as long as
 // both buffers stay within kFftSmemMax, else 8 or fewer.
