@@ -457,7 +457,8 @@ def learned_preconditioner(hz, torch, dev, n_media=4, batches=4, nb=8, epochs=40
             _, st = P.solve(f, **kw)
             e1.record()
             e1.synchronize()
-            row[f"mode{mode}"] = {"its": st[0].its, "converged": st[0].converged,
+            row[f"mode{mode}"] = {"its": st[0].its, "max_steps": cyc * 30,
+                                  "converged": st[0].converged,
                                   "rel_res_true": st[0].rel_res_true,
                                   "ms": e0.elapsed_time(e1)}
         out["solves"].append(row)

@@ -47,6 +47,7 @@ namespace {
 
 constexpr int FT = 128;       // threads of a line-transform block
 constexpr int FT_XLINES = 64;  // most lines of an x-pass tile (their pointers sit in shared memory)
+constexpr int FU = 4;          // global loads a thread keeps in flight filling or draining an x tile
 
 enum PassKind { PASS_FWD = 0, PASS_MID = 1, PASS_INV = 2, PASS_LAST = 3 };
 
@@ -336,17 +337,32 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
     dstb = field_ptr<T>(a.dst, v) + off;
   }
   const bool conj_in = a.kind == PASS_INV || a.kind == PASS_LAST;
-  // load (x pass: consecutive threads walk a line; y, z: consecutive threads the x positions)
-  for (int t = threadIdx.x; t < tl * n; t += FT) {
-    int l, e;
+  const int tot = tl * n;
+  // global loads a thread issues before storing any of them to shared memory: FU along x
+  // (contiguous lines); one along y and z, whose rows are far apart (measured slower batched)
+  constexpr int fu = AXIS == 0 ? FU : 1;
+  // point t of the tile: x pass, consecutive threads walk a line; y, z, consecutive threads the
+  // x positions
+  auto point = [&](int t, int& l, int& e) {
     if (AXIS == 0) divmod(t, n, nsh, l, e);
     else divmod(t, tl, a.tlsh, e, l);
-    T val = czero<T>();
-    if (l < nvalid) {
-      val = AXIS == 0 ? s_src[l][e] : srcb[l + (long long)e * stride];
-      if (conj_in) val = cconj(val);
+  };
+  for (int t0 = threadIdx.x; t0 < tot; t0 += fu * FT) {
+    T v[fu];
+#pragma unroll
+    for (int k = 0; k < fu; ++k) {
+      int l, e;
+      point(t0 + k * FT, l, e);
+      v[k] = czero<T>();
+      if (t0 + k * FT < tot && l < nvalid)
+        v[k] = AXIS == 0 ? s_src[l][e] : srcb[l + (long long)e * stride];
     }
-    A[sx(l, e)] = val;
+#pragma unroll
+    for (int k = 0; k < fu; ++k) {
+      int l, e;
+      point(t0 + k * FT, l, e);
+      if (t0 + k * FT < tot) A[sx(l, e)] = conj_in ? cconj(v[k]) : v[k];
+    }
   }
   __syncthreads();
   T* X;
@@ -359,9 +375,9 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
     const R sc = R(a.scale);
     const R lj = ((const R*)a.ey)[blockIdx.y];
     const int i0 = blockIdx.x * tl;
-    for (int t = threadIdx.x; t < tl * n; t += FT) {
+    for (int t = threadIdx.x; t < tot; t += FT) {
       int l, e;
-      divmod(t, tl, a.tlsh, e, l);
+      point(t, l, e);
       const R lam = (l < nvalid ? ex[i0 + l] : R(0)) + lj + ez[e];
       const R mlt = a.invlap ? sc / (lam > R(1) ? lam : R(1)) : sc * lam;
       const T x = X[sx(l, e)];
@@ -375,22 +391,36 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
   const bool conj_out = a.kind != PASS_FWD;
   const T* __restrict__ dg = (const T*)a.dg;
   const R zr = R(a.zr), zi = R(a.zi);
-  const bool comb = a.kind == PASS_LAST && a.combine;
-  for (int t = threadIdx.x; t < tl * n; t += FT) {
-    int l, e;
-    if (AXIS == 0) divmod(t, n, nsh, l, e);
-    else divmod(t, tl, a.tlsh, e, l);
-    if (l >= nvalid) continue;
-    T val = X[sx(l, e)];
-    if (conj_out) val = cconj(val);
-    if (AXIS == 0 && comb) {  // the last pass runs along x: add (dg - z) x at the point
-      const T x = s_xin[l][e];
-      const T d = dg[s_off[l] + e];
-      const R dr = d.x - zr, di = d.y - zi;
-      val = mk(val.x + dr * x.x - di * x.y, val.y + dr * x.y + di * x.x);
+  const bool comb = AXIS == 0 && a.kind == PASS_LAST && a.combine;
+  for (int t0 = threadIdx.x; t0 < tot; t0 += fu * FT) {
+    T xv[fu], dv[fu];
+    if (comb) {  // the last pass runs along x: its pointwise part's loads, all in flight at once
+#pragma unroll
+      for (int k = 0; k < fu; ++k) {
+        int l, e;
+        point(t0 + k * FT, l, e);
+        xv[k] = dv[k] = czero<T>();
+        if (t0 + k * FT < tot && l < nvalid) {
+          xv[k] = s_xin[l][e];
+          dv[k] = dg[s_off[l] + e];
+        }
+      }
     }
-    if (AXIS == 0) s_dst[l][e] = val;
-    else dstb[l + (long long)e * stride] = val;
+#pragma unroll
+    for (int k = 0; k < fu; ++k) {
+      int l, e;
+      point(t0 + k * FT, l, e);
+      if (t0 + k * FT >= tot || l >= nvalid) continue;
+      T val = X[sx(l, e)];
+      if (conj_out) val = cconj(val);
+      if (comb) {  // add (dg - z) x at the point
+        const T x = xv[k];
+        const R dr = dv[k].x - zr, di = dv[k].y - zi;
+        val = mk(val.x + dr * x.x - di * x.y, val.y + dr * x.y + di * x.x);
+      }
+      if (AXIS == 0) s_dst[l][e] = val;
+      else dstb[l + (long long)e * stride] = val;
+    }
   }
 }
 
@@ -401,7 +431,7 @@ inline int ilog2_exact(long long v) {  // log2(v) for a power of two, else -1
   return k;
 }
 
-// Lines per tile: x passes about 512 points (the lines are contiguous); y and z passes 16
+// Lines per tile: x passes 512-1024 points (the lines are contiguous); y and z passes 16
 // adjacent x positions (128-256 contiguous bytes per row, the DRAM-friendly width) as long as
 // both buffers stay within kFftSmemMax, else 8 or fewer.
 constexpr size_t kFftSmemMax = 96 * 1024;
@@ -413,6 +443,12 @@ int tile_lines(int n, int axis, size_t elem) {
   if (axis == 0) {
     int tl = 1;
     while (tl * 2 <= FT_XLINES && tl * 2 * n <= 512) tl *= 2;
+    // compiled lengths: up to 1024 points while the first radix-16 (32: radix-8) stage has
+    // fewer butterflies than the block has threads
+    if (n == 32 || n == 64 || n == 128 || n == 256) {
+      const int p1 = n == 32 ? 8 : 16;
+      while (tl * 2 <= FT_XLINES && tl * (n / p1) < FT && tl * n < 1024) tl *= 2;
+    }
     return tl;
   }
   int tl = 16;
