@@ -10,13 +10,14 @@
 namespace hz {
 
 // ---------------------------------------------------------------- programmatic dependent launch
-// Every kernel of the library starts with pdl_enter(): wait until the kernel before it on the
-// stream has completed and its writes are visible, then allow the next kernel to be launched.
-// Kernels are launched with programmatic stream serialization (launch_pdl), so a dependent
-// kernel's launch and block dispatch overlap the tail of the one before it instead of
-// starting after it (the solver is a chain of short dependent kernels; CUDA graphs keep the
-// programmatic edges).  Nothing is read or written before the wait, so the ordering of the
-// stream is unchanged.
+// Every kernel launched with launch_pdl starts with pdl_enter(): wait until the kernel before
+// it on the stream has completed and its writes are visible.  Programmatic stream
+// serialization lets a dependent kernel's launch overlap the end of the one before it (the
+// solver is a chain of short dependent kernels; CUDA graphs keep the programmatic edges).
+// Nothing is read or written before the wait, so the ordering of the stream is unchanged.  No
+// kernel triggers its dependents early (griddepcontrol.launch_dependents): measured on the
+// 64^3 solve, a trigger right after the wait made it 38% slower.  Kernels without
+// pdl_enter() are launched without the attribute.
 __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
