@@ -45,9 +45,17 @@ bool fft_factor(int n, int* rad, int* nst) {
 
 namespace {
 
-constexpr int FT = 128;       // threads of a line-transform block
+constexpr int FT = 128;       // threads of a line-transform block (but see fft_threads)
 constexpr int FT_XLINES = 64;  // most lines of an x-pass tile (their pointers sit in shared memory)
 constexpr int FU = 4;          // global loads a thread keeps in flight filling or draining an x tile
+
+// Threads of a k_fft_pass block: 256 for complex64 y and z tiles of 256-point lines (16 lines
+// of 16 radix-16 butterflies a stage, one a thread; their two 70 KB buffers allow three blocks
+// an SM, and 128 threads left the SM with 12 warps), else FT.
+template <typename T, int AXIS, int NC>
+__host__ __device__ constexpr int fft_threads() {
+  return (sizeof(T) == 8 && AXIS != 0 && NC == 256) ? 256 : FT;
+}
 
 enum PassKind { PASS_FWD = 0, PASS_MID = 1, PASS_INV = 2, PASS_LAST = 3 };
 
@@ -247,11 +255,11 @@ __device__ __forceinline__ void dft_reg(T (&a)[P]) {
 // One Stockham stage of radix P (4, 8, 16) with the combined length L before it, all constants,
 // on the padded layout: butterfly (m, j) takes a_q = w_{LP}^{jq} X[(m + r q) L + j] to
 // Y[m L P + j + L k].
-template <typename T, int N, int L, int P>
+template <typename T, int N, int L, int P, int NT>
 __device__ __forceinline__ void fft_stage_ct(const T* X, T* Y, int tl, int ls,
                                              const T* __restrict__ tw) {
   constexpr int nb = N / P, r = N / (L * P);
-  for (int b = threadIdx.x; b < tl * nb; b += FT) {
+  for (int b = threadIdx.x; b < tl * nb; b += NT) {
     const int l = b / nb, u = b % nb;
     const int j = u % L, m = u / L;
     const T* x = X + l * ls;
@@ -274,13 +282,13 @@ template <> struct Plan2<64> { static constexpr int P1 = 16, P2 = 4; };
 template <> struct Plan2<128> { static constexpr int P1 = 16, P2 = 8; };
 template <> struct Plan2<256> { static constexpr int P1 = 16, P2 = 16; };
 
-template <typename T, int N>
+template <typename T, int N, int NT>
 __device__ __forceinline__ T* fft_lines_ct(T* A, T* B, int tl, int ls, const T* __restrict__ tw) {
   constexpr int P1 = Plan2<N>::P1, P2 = Plan2<N>::P2;
   static_assert(P1 * P2 == N, "two stages");
-  fft_stage_ct<T, N, 1, P1>(A, B, tl, ls, tw);
+  fft_stage_ct<T, N, 1, P1, NT>(A, B, tl, ls, tw);
   __syncthreads();
-  fft_stage_ct<T, N, P1, P2>(B, A, tl, ls, tw);
+  fft_stage_ct<T, N, P1, P2, NT>(B, A, tl, ls, tw);
   __syncthreads();
   return A;
 }
@@ -288,8 +296,9 @@ __device__ __forceinline__ T* fft_lines_ct(T* A, T* B, int tl, int ls, const T* 
 // NC: the line length when it is one of the compiled power-of-two sizes, else 0 (any length
 // with the radix plan of the pass arguments).
 template <typename T, int AXIS, int NC>
-__global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
+__global__ void __launch_bounds__(fft_threads<T, AXIS, NC>()) k_fft_pass(const PassArgs a) {
   pdl_enter();
+  constexpr int NT = fft_threads<T, AXIS, NC>();
   using R = typename RealT<T>::type;
   extern __shared__ __align__(16) unsigned char fft_smem[];
   __shared__ const T* s_src[FT_XLINES];  // x pass: each line's first point, per buffer
@@ -316,7 +325,7 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
     const long long total = per * a.nvec;
     const long long l0 = (long long)blockIdx.x * tl;
     nvalid = (int)(total - l0 < tl ? total - l0 : (long long)tl);
-    for (int l = threadIdx.x; l < nvalid; l += FT) {
+    for (int l = threadIdx.x; l < nvalid; l += NT) {
       const long long lg = l0 + l;
       const int v = (int)(lg / per);
       const long long off = (lg - (long long)v * per) * a.nx;
@@ -347,26 +356,26 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
     if (AXIS == 0) divmod(t, n, nsh, l, e);
     else divmod(t, tl, a.tlsh, e, l);
   };
-  for (int t0 = threadIdx.x; t0 < tot; t0 += fu * FT) {
+  for (int t0 = threadIdx.x; t0 < tot; t0 += fu * NT) {
     T v[fu];
 #pragma unroll
     for (int k = 0; k < fu; ++k) {
       int l, e;
-      point(t0 + k * FT, l, e);
+      point(t0 + k * NT, l, e);
       v[k] = czero<T>();
-      if (t0 + k * FT < tot && l < nvalid)
+      if (t0 + k * NT < tot && l < nvalid)
         v[k] = AXIS == 0 ? s_src[l][e] : srcb[l + (long long)e * stride];
     }
 #pragma unroll
     for (int k = 0; k < fu; ++k) {
       int l, e;
-      point(t0 + k * FT, l, e);
-      if (t0 + k * FT < tot) A[sx(l, e)] = conj_in ? cconj(v[k]) : v[k];
+      point(t0 + k * NT, l, e);
+      if (t0 + k * NT < tot) A[sx(l, e)] = conj_in ? cconj(v[k]) : v[k];
     }
   }
   __syncthreads();
   T* X;
-  if constexpr (NC > 0) X = fft_lines_ct<T, NC>(A, B, tl, ls, tw);
+  if constexpr (NC > 0) X = fft_lines_ct<T, NC, NT>(A, B, tl, ls, tw);
   else X = fft_lines<T>(A, B, tl, ls, a, tw);
   if (a.kind == PASS_MID) {
     // z lines after the x and y transforms: point (l, e) holds wave numbers (i0 + l, j, e)
@@ -375,7 +384,7 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
     const R sc = R(a.scale);
     const R lj = ((const R*)a.ey)[blockIdx.y];
     const int i0 = blockIdx.x * tl;
-    for (int t = threadIdx.x; t < tot; t += FT) {
+    for (int t = threadIdx.x; t < tot; t += NT) {
       int l, e;
       point(t, l, e);
       const R lam = (l < nvalid ? ex[i0 + l] : R(0)) + lj + ez[e];
@@ -385,22 +394,22 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
     }
     __syncthreads();
     T* Y = (X == A) ? B : A;
-    if constexpr (NC > 0) X = fft_lines_ct<T, NC>(X, Y, tl, ls, tw);
+    if constexpr (NC > 0) X = fft_lines_ct<T, NC, NT>(X, Y, tl, ls, tw);
     else X = fft_lines<T>(X, Y, tl, ls, a, tw);
   }
   const bool conj_out = a.kind != PASS_FWD;
   const T* __restrict__ dg = (const T*)a.dg;
   const R zr = R(a.zr), zi = R(a.zi);
   const bool comb = AXIS == 0 && a.kind == PASS_LAST && a.combine;
-  for (int t0 = threadIdx.x; t0 < tot; t0 += fu * FT) {
+  for (int t0 = threadIdx.x; t0 < tot; t0 += fu * NT) {
     T xv[fu], dv[fu];
     if (comb) {  // the last pass runs along x: its pointwise part's loads, all in flight at once
 #pragma unroll
       for (int k = 0; k < fu; ++k) {
         int l, e;
-        point(t0 + k * FT, l, e);
+        point(t0 + k * NT, l, e);
         xv[k] = dv[k] = czero<T>();
-        if (t0 + k * FT < tot && l < nvalid) {
+        if (t0 + k * NT < tot && l < nvalid) {
           xv[k] = s_xin[l][e];
           dv[k] = dg[s_off[l] + e];
         }
@@ -409,8 +418,8 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
 #pragma unroll
     for (int k = 0; k < fu; ++k) {
       int l, e;
-      point(t0 + k * FT, l, e);
-      if (t0 + k * FT >= tot || l >= nvalid) continue;
+      point(t0 + k * NT, l, e);
+      if (t0 + k * NT >= tot || l >= nvalid) continue;
       T val = X[sx(l, e)];
       if (conj_out) val = cconj(val);
       if (comb) {  // add (dg - z) x at the point
@@ -471,9 +480,11 @@ const void* e_of<float2>(const FftAxis& ax) { return ax.e32; }
 
 template <typename T, int NC>
 cudaError_t launch_axis(int axis, dim3 grid, size_t smem, cudaStream_t st, const PassArgs& a) {
-  if (axis == 0) return launch_pdl(k_fft_pass<T, 0, NC>, grid, dim3(FT), smem, st, a);
-  if (axis == 1) return launch_pdl(k_fft_pass<T, 1, NC>, grid, dim3(FT), smem, st, a);
-  return launch_pdl(k_fft_pass<T, 2, NC>, grid, dim3(FT), smem, st, a);
+  if (axis == 0)
+    return launch_pdl(k_fft_pass<T, 0, NC>, grid, dim3(fft_threads<T, 0, NC>()), smem, st, a);
+  if (axis == 1)
+    return launch_pdl(k_fft_pass<T, 1, NC>, grid, dim3(fft_threads<T, 1, NC>()), smem, st, a);
+  return launch_pdl(k_fft_pass<T, 2, NC>, grid, dim3(fft_threads<T, 2, NC>()), smem, st, a);
 }
 
 template <typename T>
