@@ -47,7 +47,7 @@ namespace {
 
 constexpr int FT = 128;       // threads of a line-transform block (but see fft_threads)
 constexpr int FT_XLINES = 64;  // most lines of an x-pass tile (their pointers sit in shared memory)
-constexpr int FU = 4;          // global loads a thread keeps in flight filling or draining an x tile
+constexpr int FU = 8;          // global loads a thread keeps in flight filling or draining an x tile
 
 // Threads of a k_fft_pass block: 256 for complex64 y and z tiles of 256-point lines (16 lines
 // of 16 radix-16 butterflies a stage, one a thread; their two 70 KB buffers allow three blocks
