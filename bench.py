@@ -751,8 +751,10 @@ def run_ours(args):
                              "the 64^3 fields stay in L2, so HBM is not the roof here"}
     else:
         achieved = (fl / nl) / ((ms / nl) / 1e3) / 1e12
+        traffic = (traffic_from_profile("cgs_f64_gaussian_bumps_64.txt", kernel_hash())
+                   if dom == "krylov" else None)
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "kernel": f"{dom} class (float64 Krylov kernels: CGS2 passes, step d)"
                           if dom == "krylov" else "k_stencil_diag (float64 stencil)",
                 "peak_kind": "float64 FMA rate from unit counts (152 SMs x 2 FMA/clk x 2 flops "
