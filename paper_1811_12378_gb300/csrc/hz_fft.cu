@@ -22,6 +22,12 @@
 // out, 3 and 5 use the twiddle table.  Inverse transforms are conj(FFT(conj(x))), unnormalised;
 // the 1/(nx ny nz) is folded into the diagonal of pass 3.  Twiddles and the per-axis
 // eigenvalue shares are tables made on the host in float64 (rounded for the float32 kernels).
+//
+// Compiled lengths 32, 64, 128 and 256 run two register-resident stages (radix 8 x 4, 16 x 4,
+// 16 x 8, 16 x 16) on a padded shared layout.  Complex64 256-point lines, the large grids, go
+// further (k_fft_x256, k_fft_yz256): one thread a radix-16 butterfly, the first stage read
+// straight from global memory and the second written straight back, so each transform passes
+// through shared memory once.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -45,17 +51,9 @@ bool fft_factor(int n, int* rad, int* nst) {
 
 namespace {
 
-constexpr int FT = 128;       // threads of a line-transform block (but see fft_threads)
+constexpr int FT = 128;       // threads of a k_fft_pass block
 constexpr int FT_XLINES = 64;  // most lines of an x-pass tile (their pointers sit in shared memory)
 constexpr int FU = 8;          // global loads a thread keeps in flight filling or draining an x tile
-
-// Threads of a k_fft_pass block: 256 for complex64 y and z tiles of 256-point lines (16 lines
-// of 16 radix-16 butterflies a stage, one a thread; their two 70 KB buffers allow three blocks
-// an SM, and 128 threads left the SM with 12 warps), else FT.
-template <typename T, int AXIS, int NC>
-__host__ __device__ constexpr int fft_threads() {
-  return (sizeof(T) == 8 && AXIS != 0 && NC == 256) ? 256 : FT;
-}
 
 enum PassKind { PASS_FWD = 0, PASS_MID = 1, PASS_INV = 2, PASS_LAST = 3 };
 
@@ -296,9 +294,9 @@ __device__ __forceinline__ T* fft_lines_ct(T* A, T* B, int tl, int ls, const T* 
 // NC: the line length when it is one of the compiled power-of-two sizes, else 0 (any length
 // with the radix plan of the pass arguments).
 template <typename T, int AXIS, int NC>
-__global__ void __launch_bounds__(fft_threads<T, AXIS, NC>()) k_fft_pass(const PassArgs a) {
+__global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
   pdl_enter();
-  constexpr int NT = fft_threads<T, AXIS, NC>();
+  constexpr int NT = FT;
   using R = typename RealT<T>::type;
   extern __shared__ __align__(16) unsigned char fft_smem[];
   __shared__ const T* s_src[FT_XLINES];  // x pass: each line's first point, per buffer
@@ -433,6 +431,155 @@ __global__ void __launch_bounds__(fft_threads<T, AXIS, NC>()) k_fft_pass(const P
   }
 }
 
+// y and z passes of complex64 256-point lines, 16 lines a tile, one thread per radix-16
+// butterfly (256 threads).  The first stage reads its 16 inputs straight from global memory (16
+// loads in flight a thread; a warp load is two 128-byte rows) and the second writes its 16
+// outputs straight back, so a transform passes through shared memory once, in one 35 KB
+// buffer.  Pass 3 (z) runs the diagonal and the inverse transform in the same block.  Stages
+// as in fft_stage_ct: the first (L = 1) takes points u + 16 q of butterfly u to 16 u + k, the
+// second (L = 16) points 16 q + u, with twiddles w_256^{u q}, to u + 16 k.
+template <int AXIS>
+__global__ void __launch_bounds__(256) k_fft_yz256(const PassArgs a) {
+  pdl_enter();
+  using T = float2;
+  using R = float;
+  constexpr int TL = 16;
+  constexpr int ls = padded_stride<256>();
+  extern __shared__ __align__(16) unsigned char fft_smem[];
+  const int l = threadIdx.x & (TL - 1);  // line of the tile: x position i0 + l
+  const int u = threadIdx.x >> 4;        // butterfly of the line
+  const int i0 = blockIdx.x * TL;
+  const bool valid = l < a.nx - i0;
+  const long long sxy = (long long)a.nx * a.ny;
+  const long long stride = AXIS == 1 ? a.nx : sxy;
+  const long long off =
+      (AXIS == 1 ? (long long)blockIdx.y * sxy : (long long)blockIdx.y * a.nx) + i0 + l;
+  const T* __restrict__ src = field_ptr<const T>(a.src, blockIdx.z) + off;
+  T* __restrict__ dst = field_ptr<T>(a.dst, blockIdx.z) + off;
+  const T* __restrict__ tw = (const T*)a.tw;
+  T* Al = reinterpret_cast<T*>(fft_smem) + l * ls;
+  const bool conj_in = a.kind == PASS_INV || a.kind == PASS_LAST;
+  T x[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) x[q] = valid ? src[(long long)(u + 16 * q) * stride] : czero<T>();
+  if (conj_in) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) x[q] = cconj(x[q]);
+  }
+  auto stage1 = [&]() {  // x holds points u + 16 q; leaves the stage's output in the buffer
+    dft_reg<T, 16>(x);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) Al[padi(16 * u + k)] = x[k];
+    __syncthreads();
+  };
+  auto stage2 = [&]() {  // leaves points u + 16 k in x[k]
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const T val = Al[padi(16 * q + u)];
+      x[q] = (q == 0 || u == 0) ? val : cmul(val, tw[u * q]);
+    }
+    dft_reg<T, 16>(x);
+  };
+  stage1();
+  stage2();
+  if (a.kind == PASS_MID) {
+    // z lines after the x and y transforms: point (l, e) holds wave numbers (i0 + l, j, e)
+    const R* ez = (const R*)a.ez;
+    const R sc = R(a.scale);
+    const R lxy = (valid ? ((const R*)a.ex)[i0 + l] : R(0)) + ((const R*)a.ey)[blockIdx.y];
+    __syncthreads();  // every thread has read the buffer
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int e = u + 16 * k;
+      const R lam = lxy + ez[e];
+      const R mlt = a.invlap ? sc / (lam > R(1) ? lam : R(1)) : sc * lam;
+      Al[padi(e)] = mk(mlt * x[k].x, -(mlt * x[k].y));  // conj: the inverse transform follows
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) x[q] = Al[padi(u + 16 * q)];
+    __syncthreads();  // every thread has read the buffer
+    stage1();
+    stage2();
+  }
+  if (!valid) return;
+  const bool conj_out = a.kind != PASS_FWD;
+#pragma unroll
+  for (int k = 0; k < 16; ++k)
+    dst[(long long)(u + 16 * k) * stride] = conj_out ? cconj(x[k]) : x[k];
+}
+
+// x passes of complex64 256-point lines: the same two register stages as k_fft_yz256, 16 lines a
+// block with the 16 lanes of a half-warp along a line (a warp load is two 128-byte runs).  The
+// last pass adds the operator's pointwise part (dg - z) x, its loads issued eight points at a
+// time.
+__global__ void __launch_bounds__(256) k_fft_x256(const PassArgs a) {
+  pdl_enter();
+  using T = float2;
+  using R = float;
+  constexpr int ls = padded_stride<256>();
+  extern __shared__ __align__(16) unsigned char fft_smem[];
+  const int u = threadIdx.x & 15;  // butterfly of the line
+  const int l = threadIdx.x >> 4;  // line of the tile
+  const long long per = (long long)a.ny * a.nz;
+  const long long lg = (long long)blockIdx.x * 16 + l;
+  const bool valid = lg < per * a.nvec;
+  int v = 0;
+  long long off = 0;  // the line's first point within its field
+  if (valid) {
+    v = (int)(lg / per);
+    off = (lg - (long long)v * per) * 256;
+  }
+  const T* __restrict__ src = field_ptr<const T>(a.src, v) + off;
+  T* __restrict__ dst = field_ptr<T>(a.dst, v) + off;
+  const T* __restrict__ tw = (const T*)a.tw;
+  T* Al = reinterpret_cast<T*>(fft_smem) + l * ls;
+  const bool conj_in = a.kind == PASS_INV || a.kind == PASS_LAST;
+  T x[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) x[q] = valid ? src[u + 16 * q] : czero<T>();
+  if (conj_in) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) x[q] = cconj(x[q]);
+  }
+  dft_reg<T, 16>(x);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) Al[padi(16 * u + k)] = x[k];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const T val = Al[padi(16 * q + u)];
+    x[q] = (q == 0 || u == 0) ? val : cmul(val, tw[u * q]);
+  }
+  dft_reg<T, 16>(x);  // x[k] = point u + 16 k
+  if (!valid) return;
+  const bool conj_out = a.kind != PASS_FWD;
+  if (a.kind == PASS_LAST && a.combine) {  // add (dg - z) x at the point
+    const T* __restrict__ xin = field_ptr<const T>(a.xin, v) + off;
+    const T* __restrict__ dg = (const T*)a.dg + off;
+    const R zr = R(a.zr), zi = R(a.zi);
+#pragma unroll
+    for (int k0 = 0; k0 < 16; k0 += 8) {
+      T xv[8], dv[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        xv[k] = xin[u + 16 * (k0 + k)];
+        dv[k] = dg[u + 16 * (k0 + k)];
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const T val = conj_out ? cconj(x[k0 + k]) : x[k0 + k];
+        const R dr = dv[k].x - zr, di = dv[k].y - zi;
+        dst[u + 16 * (k0 + k)] = mk(val.x + dr * xv[k].x - di * xv[k].y,
+                                    val.y + dr * xv[k].y + di * xv[k].x);
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) dst[u + 16 * k] = conj_out ? cconj(x[k]) : x[k];
+}
+
 inline int ilog2_exact(long long v) {  // log2(v) for a power of two, else -1
   if (v <= 0 || (v & (v - 1)) != 0) return -1;
   int k = 0;
@@ -480,11 +627,9 @@ const void* e_of<float2>(const FftAxis& ax) { return ax.e32; }
 
 template <typename T, int NC>
 cudaError_t launch_axis(int axis, dim3 grid, size_t smem, cudaStream_t st, const PassArgs& a) {
-  if (axis == 0)
-    return launch_pdl(k_fft_pass<T, 0, NC>, grid, dim3(fft_threads<T, 0, NC>()), smem, st, a);
-  if (axis == 1)
-    return launch_pdl(k_fft_pass<T, 1, NC>, grid, dim3(fft_threads<T, 1, NC>()), smem, st, a);
-  return launch_pdl(k_fft_pass<T, 2, NC>, grid, dim3(fft_threads<T, 2, NC>()), smem, st, a);
+  if (axis == 0) return launch_pdl(k_fft_pass<T, 0, NC>, grid, dim3(FT), smem, st, a);
+  if (axis == 1) return launch_pdl(k_fft_pass<T, 1, NC>, grid, dim3(FT), smem, st, a);
+  return launch_pdl(k_fft_pass<T, 2, NC>, grid, dim3(FT), smem, st, a);
 }
 
 template <typename T>
@@ -504,8 +649,21 @@ cudaError_t run_pass(int axis, PassArgs a, const SpecPlan& sp, cudaStream_t st) 
   a.tw = tw_of<T>(ax);
   a.tl = tile_lines(ax.n, axis, sizeof(T));
   a.tlsh = ilog2_exact(a.tl);
-  const size_t smem = 2 * sizeof(T) * (size_t)a.tl * (size_t)line_stride(ax.n);
+  size_t smem = 2 * sizeof(T) * (size_t)a.tl * (size_t)line_stride(ax.n);
   count_launch();
+  if (sizeof(T) == 8 && axis == 0 && ax.n == 256) {
+    // complex64 256-point x lines: 16 lines a block, stages through registers
+    smem = sizeof(T) * 16 * (size_t)line_stride(256);
+    const long long lines = (long long)a.ny * a.nz * a.nvec;
+    return launch_pdl(k_fft_x256, dim3((unsigned)((lines + 15) / 16)), dim3(256), smem, st, a);
+  }
+  if (sizeof(T) == 8 && axis != 0 && ax.n == 256 && a.tl == 16) {
+    // complex64 256-point y / z lines: one shared buffer, stages through registers
+    smem = sizeof(T) * 16 * (size_t)line_stride(256);
+    const dim3 grid((a.nx + 15) / 16, axis == 1 ? a.nz : a.ny, a.nvec);
+    if (axis == 1) return launch_pdl(k_fft_yz256<1>, grid, dim3(256), smem, st, a);
+    return launch_pdl(k_fft_yz256<2>, grid, dim3(256), smem, st, a);
+  }
   dim3 grid;
   if (axis == 0) {
     const long long lines = (long long)a.ny * a.nz * a.nvec;
