@@ -487,17 +487,14 @@ __global__ void __launch_bounds__(256) k_fft_yz256(const PassArgs a) {
     const R* ez = (const R*)a.ez;
     const R sc = R(a.scale);
     const R lxy = (valid ? ((const R*)a.ex)[i0 + l] : R(0)) + ((const R*)a.ey)[blockIdx.y];
-    __syncthreads();  // every thread has read the buffer
+    // x[k] holds point u + 16 k: the inputs of butterfly u of the inverse transform's first
+    // stage, so the diagonal is applied in registers
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      const int e = u + 16 * k;
-      const R lam = lxy + ez[e];
+      const R lam = lxy + ez[u + 16 * k];
       const R mlt = a.invlap ? sc / (lam > R(1) ? lam : R(1)) : sc * lam;
-      Al[padi(e)] = mk(mlt * x[k].x, -(mlt * x[k].y));  // conj: the inverse transform follows
+      x[k] = mk(mlt * x[k].x, -(mlt * x[k].y));  // conj: the inverse transform follows
     }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 16; ++q) x[q] = Al[padi(u + 16 * q)];
     __syncthreads();  // every thread has read the buffer
     stage1();
     stage2();
