@@ -24,10 +24,10 @@
 // eigenvalue shares are tables made on the host in float64 (rounded for the float32 kernels).
 //
 // Compiled lengths 32, 64, 128 and 256 run two register-resident stages (radix 8 x 4, 16 x 4,
-// 16 x 8, 16 x 16) on a padded shared layout.  Complex64 256-point lines, the large grids, go
-// further (k_fft_x256, k_fft_yz256): one thread a radix-16 butterfly, the first stage read
-// straight from global memory and the second written straight back, so each transform passes
-// through shared memory once.
+// 16 x 8, 16 x 16) on a padded shared layout.  Complex64 lines of 64 and 256 points go further
+// (k_fft_x_sq, k_fft_yz_sq): one thread a butterfly, the first stage read straight from global
+// memory and the second written straight back, so each transform passes through shared memory
+// once.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -431,23 +431,47 @@ __global__ void __launch_bounds__(FT) k_fft_pass(const PassArgs a) {
   }
 }
 
-// y and z passes of complex64 256-point lines, 16 lines a tile, one thread per radix-16
-// butterfly (256 threads).  The first stage reads its 16 inputs straight from global memory (16
-// loads in flight a thread; a warp load is two 128-byte rows) and the second writes its 16
-// outputs straight back, so a transform passes through shared memory once, in one 35 KB
-// buffer.  Pass 3 (z) runs the diagonal and the inverse transform in the same block.  Stages
-// as in fft_stage_ct: the first (L = 1) takes points u + 16 q of butterfly u to 16 u + k, the
-// second (L = 16) points 16 q + u, with twiddles w_256^{u q}, to u + 16 k.
-template <int AXIS>
-__global__ void __launch_bounds__(256) k_fft_yz256(const PassArgs a) {
+// Complex64 lines of a square length N = P^2 (64 = 8 x 8, 256 = 16 x 16), the sizes of the
+// large grids: one thread a radix-P butterfly, TL = 256 / P lines a block of 256 threads.  The
+// first stage reads its P inputs straight from global memory (P loads in flight a thread) and
+// the second writes its P outputs straight back, so a transform passes through shared memory
+// once, in one buffer of TL padded lines.  Stages as in fft_stage_ct: the first (L = 1) takes
+// points u + P q of butterfly u to P u + k, the second (L = P) points P q + u, with twiddles
+// w_N^{u q}, to u + P k.
+template <int N> struct SqRadix;
+template <> struct SqRadix<64> { static constexpr int P = 8; };
+template <> struct SqRadix<256> { static constexpr int P = 16; };
+
+// The two stages on the thread's butterfly u of its line's buffer Al: stage 1 from x (points
+// u + P q) into the buffer, then stage 2 from the buffer into x (points u + P k).
+template <int N>
+__device__ __forceinline__ void sq_stages(float2 (&x)[SqRadix<N>::P], float2* Al, int u,
+                                          const float2* __restrict__ tw) {
+  constexpr int P = SqRadix<N>::P;
+  dft_reg<float2, P>(x);
+#pragma unroll
+  for (int k = 0; k < P; ++k) Al[padi(P * u + k)] = x[k];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const float2 val = Al[padi(P * q + u)];
+    x[q] = (q == 0 || u == 0) ? val : cmul(val, tw[u * q]);
+  }
+  dft_reg<float2, P>(x);
+}
+
+// y and z passes: a tile is TL adjacent x positions (a warp load covers 128-256 contiguous
+// bytes of a row).  Pass 3 (z) runs the diagonal and the inverse transform in the same block.
+template <int AXIS, int N>
+__global__ void __launch_bounds__(256) k_fft_yz_sq(const PassArgs a) {
   pdl_enter();
   using T = float2;
   using R = float;
-  constexpr int TL = 16;
-  constexpr int ls = padded_stride<256>();
+  constexpr int P = SqRadix<N>::P, TL = 256 / P;
+  constexpr int ls = padded_stride<N>();
   extern __shared__ __align__(16) unsigned char fft_smem[];
-  const int l = threadIdx.x & (TL - 1);  // line of the tile: x position i0 + l
-  const int u = threadIdx.x >> 4;        // butterfly of the line
+  const int l = threadIdx.x % TL;  // line of the tile: x position i0 + l
+  const int u = threadIdx.x / TL;  // butterfly of the line
   const int i0 = blockIdx.x * TL;
   const bool valid = l < a.nx - i0;
   const long long sxy = (long long)a.nx * a.ny;
@@ -459,96 +483,72 @@ __global__ void __launch_bounds__(256) k_fft_yz256(const PassArgs a) {
   const T* __restrict__ tw = (const T*)a.tw;
   T* Al = reinterpret_cast<T*>(fft_smem) + l * ls;
   const bool conj_in = a.kind == PASS_INV || a.kind == PASS_LAST;
-  T x[16];
+  T x[P];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) x[q] = valid ? src[(long long)(u + 16 * q) * stride] : czero<T>();
+  for (int q = 0; q < P; ++q) x[q] = valid ? src[(long long)(u + P * q) * stride] : czero<T>();
   if (conj_in) {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) x[q] = cconj(x[q]);
+    for (int q = 0; q < P; ++q) x[q] = cconj(x[q]);
   }
-  auto stage1 = [&]() {  // x holds points u + 16 q; leaves the stage's output in the buffer
-    dft_reg<T, 16>(x);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) Al[padi(16 * u + k)] = x[k];
-    __syncthreads();
-  };
-  auto stage2 = [&]() {  // leaves points u + 16 k in x[k]
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const T val = Al[padi(16 * q + u)];
-      x[q] = (q == 0 || u == 0) ? val : cmul(val, tw[u * q]);
-    }
-    dft_reg<T, 16>(x);
-  };
-  stage1();
-  stage2();
+  sq_stages<N>(x, Al, u, tw);
   if (a.kind == PASS_MID) {
     // z lines after the x and y transforms: point (l, e) holds wave numbers (i0 + l, j, e)
     const R* ez = (const R*)a.ez;
     const R sc = R(a.scale);
     const R lxy = (valid ? ((const R*)a.ex)[i0 + l] : R(0)) + ((const R*)a.ey)[blockIdx.y];
-    // x[k] holds point u + 16 k: the inputs of butterfly u of the inverse transform's first
+    // x[k] holds point u + P k: the inputs of butterfly u of the inverse transform's first
     // stage, so the diagonal is applied in registers
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const R lam = lxy + ez[u + 16 * k];
+    for (int k = 0; k < P; ++k) {
+      const R lam = lxy + ez[u + P * k];
       const R mlt = a.invlap ? sc / (lam > R(1) ? lam : R(1)) : sc * lam;
       x[k] = mk(mlt * x[k].x, -(mlt * x[k].y));  // conj: the inverse transform follows
     }
     __syncthreads();  // every thread has read the buffer
-    stage1();
-    stage2();
+    sq_stages<N>(x, Al, u, tw);
   }
   if (!valid) return;
   const bool conj_out = a.kind != PASS_FWD;
 #pragma unroll
-  for (int k = 0; k < 16; ++k)
-    dst[(long long)(u + 16 * k) * stride] = conj_out ? cconj(x[k]) : x[k];
+  for (int k = 0; k < P; ++k)
+    dst[(long long)(u + P * k) * stride] = conj_out ? cconj(x[k]) : x[k];
 }
 
-// x passes of complex64 256-point lines: the same two register stages as k_fft_yz256, 16 lines a
-// block with the 16 lanes of a half-warp along a line (a warp load is two 128-byte runs).  The
-// last pass adds the operator's pointwise part (dg - z) x, its loads issued eight points at a
-// time.
-__global__ void __launch_bounds__(256) k_fft_x256(const PassArgs a) {
+// x passes: TL whole lines a block, the P lanes of a line's butterflies consecutive (a warp load
+// covers 256 contiguous bytes).  The last pass adds the operator's pointwise part (dg - z) x,
+// its loads issued eight points at a time.
+template <int N>
+__global__ void __launch_bounds__(256) k_fft_x_sq(const PassArgs a) {
   pdl_enter();
   using T = float2;
   using R = float;
-  constexpr int ls = padded_stride<256>();
+  constexpr int P = SqRadix<N>::P, TL = 256 / P;
+  constexpr int ls = padded_stride<N>();
   extern __shared__ __align__(16) unsigned char fft_smem[];
-  const int u = threadIdx.x & 15;  // butterfly of the line
-  const int l = threadIdx.x >> 4;  // line of the tile
+  const int u = threadIdx.x % P;  // butterfly of the line
+  const int l = threadIdx.x / P;  // line of the tile
   const long long per = (long long)a.ny * a.nz;
-  const long long lg = (long long)blockIdx.x * 16 + l;
+  const long long lg = (long long)blockIdx.x * TL + l;
   const bool valid = lg < per * a.nvec;
   int v = 0;
   long long off = 0;  // the line's first point within its field
   if (valid) {
     v = (int)(lg / per);
-    off = (lg - (long long)v * per) * 256;
+    off = (lg - (long long)v * per) * N;
   }
   const T* __restrict__ src = field_ptr<const T>(a.src, v) + off;
   T* __restrict__ dst = field_ptr<T>(a.dst, v) + off;
   const T* __restrict__ tw = (const T*)a.tw;
   T* Al = reinterpret_cast<T*>(fft_smem) + l * ls;
   const bool conj_in = a.kind == PASS_INV || a.kind == PASS_LAST;
-  T x[16];
+  T x[P];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) x[q] = valid ? src[u + 16 * q] : czero<T>();
+  for (int q = 0; q < P; ++q) x[q] = valid ? src[u + P * q] : czero<T>();
   if (conj_in) {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) x[q] = cconj(x[q]);
+    for (int q = 0; q < P; ++q) x[q] = cconj(x[q]);
   }
-  dft_reg<T, 16>(x);
-#pragma unroll
-  for (int k = 0; k < 16; ++k) Al[padi(16 * u + k)] = x[k];
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const T val = Al[padi(16 * q + u)];
-    x[q] = (q == 0 || u == 0) ? val : cmul(val, tw[u * q]);
-  }
-  dft_reg<T, 16>(x);  // x[k] = point u + 16 k
+  sq_stages<N>(x, Al, u, tw);  // x[k] = point u + P k
   if (!valid) return;
   const bool conj_out = a.kind != PASS_FWD;
   if (a.kind == PASS_LAST && a.combine) {  // add (dg - z) x at the point
@@ -556,25 +556,25 @@ __global__ void __launch_bounds__(256) k_fft_x256(const PassArgs a) {
     const T* __restrict__ dg = (const T*)a.dg + off;
     const R zr = R(a.zr), zi = R(a.zi);
 #pragma unroll
-    for (int k0 = 0; k0 < 16; k0 += 8) {
+    for (int k0 = 0; k0 < P; k0 += 8) {
       T xv[8], dv[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        xv[k] = xin[u + 16 * (k0 + k)];
-        dv[k] = dg[u + 16 * (k0 + k)];
+        xv[k] = xin[u + P * (k0 + k)];
+        dv[k] = dg[u + P * (k0 + k)];
       }
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const T val = conj_out ? cconj(x[k0 + k]) : x[k0 + k];
         const R dr = dv[k].x - zr, di = dv[k].y - zi;
-        dst[u + 16 * (k0 + k)] = mk(val.x + dr * xv[k].x - di * xv[k].y,
-                                    val.y + dr * xv[k].y + di * xv[k].x);
+        dst[u + P * (k0 + k)] = mk(val.x + dr * xv[k].x - di * xv[k].y,
+                                   val.y + dr * xv[k].y + di * xv[k].x);
       }
     }
     return;
   }
 #pragma unroll
-  for (int k = 0; k < 16; ++k) dst[u + 16 * k] = conj_out ? cconj(x[k]) : x[k];
+  for (int k = 0; k < P; ++k) dst[u + P * k] = conj_out ? cconj(x[k]) : x[k];
 }
 
 inline int ilog2_exact(long long v) {  // log2(v) for a power of two, else -1
@@ -648,18 +648,22 @@ cudaError_t run_pass(int axis, PassArgs a, const SpecPlan& sp, cudaStream_t st) 
   a.tlsh = ilog2_exact(a.tl);
   size_t smem = 2 * sizeof(T) * (size_t)a.tl * (size_t)line_stride(ax.n);
   count_launch();
-  if (sizeof(T) == 8 && axis == 0 && ax.n == 256) {
-    // complex64 256-point x lines: 16 lines a block, stages through registers
-    smem = sizeof(T) * 16 * (size_t)line_stride(256);
-    const long long lines = (long long)a.ny * a.nz * a.nvec;
-    return launch_pdl(k_fft_x256, dim3((unsigned)((lines + 15) / 16)), dim3(256), smem, st, a);
-  }
-  if (sizeof(T) == 8 && axis != 0 && ax.n == 256 && a.tl == 16) {
-    // complex64 256-point y / z lines: one shared buffer, stages through registers
-    smem = sizeof(T) * 16 * (size_t)line_stride(256);
-    const dim3 grid((a.nx + 15) / 16, axis == 1 ? a.nz : a.ny, a.nvec);
-    if (axis == 1) return launch_pdl(k_fft_yz256<1>, grid, dim3(256), smem, st, a);
-    return launch_pdl(k_fft_yz256<2>, grid, dim3(256), smem, st, a);
+  if (sizeof(T) == 8 && (ax.n == 64 || ax.n == 256)) {
+    // complex64 lines of a square length: TL = 256 / sqrt(n) lines a block, stages through
+    // registers, one shared buffer
+    const int P = ax.n == 64 ? 8 : 16, TL = 256 / P;
+    smem = sizeof(T) * (size_t)TL * (size_t)line_stride(ax.n);
+    if (axis == 0) {
+      const dim3 grid((unsigned)(((long long)a.ny * a.nz * a.nvec + TL - 1) / TL));
+      return ax.n == 64 ? launch_pdl(k_fft_x_sq<64>, grid, dim3(256), smem, st, a)
+                        : launch_pdl(k_fft_x_sq<256>, grid, dim3(256), smem, st, a);
+    }
+    const dim3 grid((a.nx + TL - 1) / TL, axis == 1 ? a.nz : a.ny, a.nvec);
+    if (ax.n == 64)
+      return axis == 1 ? launch_pdl(k_fft_yz_sq<1, 64>, grid, dim3(256), smem, st, a)
+                       : launch_pdl(k_fft_yz_sq<2, 64>, grid, dim3(256), smem, st, a);
+    return axis == 1 ? launch_pdl(k_fft_yz_sq<1, 256>, grid, dim3(256), smem, st, a)
+                     : launch_pdl(k_fft_yz_sq<2, 256>, grid, dim3(256), smem, st, a);
   }
   dim3 grid;
   if (axis == 0) {

@@ -57,11 +57,12 @@ def spectral_problem(wl, nodes=None, nrhs_max=2, restart_max=30, inner_k_max=6, 
     return P
 
 
-# lines of 32-256 points take the compiled sizes; the last two have 256-point y and z lines
-# (the 256-thread complex64 tiles) under x extents that leave the tiles ragged
+# lines of 32-256 points take the compiled sizes; the last four have 64- and 256-point y and z
+# lines (the complex64 register-staged tiles of 32 and 16 x positions) under x extents that
+# leave the tiles ragged
 GRIDS = [((16, 16, 16), 2), ((30, 12, 10), 2), ((1, 8, 6), 1), ((25, 9, 20), 3),
          ((64, 64, 64), 8), ((128, 32, 12), 2), ((256, 10, 32), 2), ((12, 256, 10), 2),
-         ((20, 8, 256), 2)]
+         ((20, 8, 256), 2), ((20, 64, 12), 2), ((40, 12, 64), 2)]
 
 
 @pytest.mark.parametrize("shape,layer", GRIDS, ids=lambda v: str(v))
