@@ -467,6 +467,52 @@ def learned_preconditioner(hz, torch, dev, n_media=4, batches=4, nb=8, epochs=40
     return out
 
 
+def next_rows_block(hz, torch, dev):
+    """Case Two (Section 3 eq:mat-2x2, float64) against Case One on the 32^3 point source, and
+    FCI with the ILU(0) inner preconditioner (Section 6.3, k_in = 4 and 8) against FCI alone on
+    the headline 64^3 workload (HZ_MIXED_C64): one untimed and one event-timed solve each to
+    a true relative residual of 1e-8."""
+    import workloads as W
+
+    def timed_solve(P, f, **kw):
+        P.solve(f, **kw)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, st = P.solve(f, **kw)
+        e1.record()
+        e1.synchronize()
+        return {"its": st[0].its, "converged": st[0].converged,
+                "rel_res_true": st[0].rel_res_true, "ms": e0.elapsed_time(e1)}
+
+    def problem(wl, inner_k_max, flags=0):
+        return hz.Problem(wl.c, wl.h, wl.omega, wl.layer_cells, wl.sigma_max, wl.J, wl.t, wl.eps,
+                          nrhs_max=1, restart_max=wl.restart, inner_k_max=inner_k_max,
+                          flags=flags)
+
+    out = {}
+    wl = W.point_source_32()
+    f = torch.from_numpy(wl.f.reshape(1, -1).copy()).to(dev)
+    row = {"workload": "point_source_32: 32^3 (h=1/33), c = 1, 10 ppw, 8-cell sponge, centre "
+                       "point source, J=4, FGMRES(30) + FCI with 4 inner steps, float64"}
+    for name, flags in (("case_one", 0), ("case_two", hz.HZ_LIMIT_CASE_TWO)):
+        P = problem(wl, wl.k_in, flags)
+        row[name] = timed_solve(P, f, restart=wl.restart, inner_k=wl.k_in, rtol=1e-8,
+                                max_cycles=40)
+        P.close()
+    out["case_two"] = row
+    wl = W.gaussian_bumps_64()
+    f = torch.from_numpy(wl.f.reshape(1, -1).copy()).to(dev)
+    P = problem(wl, 8)
+    row = {"workload": "gaussian_bumps_64 (the headline workload), HZ_MIXED_C64, FGMRES(30)"}
+    for name, ilu, kin in (("fci_k4", False, 4), ("ilu0_k4", True, 4), ("ilu0_k8", True, 8)):
+        P.set_inner_ilu(ilu)
+        row[name] = timed_solve(P, f, restart=wl.restart, inner_k=kin, rtol=1e-8, max_cycles=20,
+                                precision=hz.HZ_MIXED_C64)
+    P.close()
+    out["ilu0"] = row
+    return out
+
+
 def spectral_block(hz, torch, dev, n=64, n_bw=256):
     """The Fourier spectral discretisation (Section 7.1) with the regularised inverse-Laplacian
     inner preconditioner (Section 7.3): one solve to 1e-8 of the n^3 periodic Gaussian-bump
@@ -733,6 +779,7 @@ def run_ours(args):
     learned = (learned_preconditioner(hz, torch, dev) if world == 1 and not args.no_learned
                else None)
     spectral = spectral_block(hz, torch, dev) if world == 1 else None
+    next_rows = next_rows_block(hz, torch, dev) if world == 1 else None
 
     rhs_total = args.steps * world
     value = rhs_total / t_head
@@ -783,6 +830,7 @@ def run_ours(args):
         "batched_uneven": uneven,
         "learned_preconditioner": learned,
         "spectral": spectral,
+        "next_rows": next_rows,
         "gpu_launches": launches,
         "clocks": clk,
     }
