@@ -23,11 +23,11 @@
 // the 1/(nx ny nz) is folded into the diagonal of pass 3.  Twiddles and the per-axis
 // eigenvalue shares are tables made on the host in float64 (rounded for the float32 kernels).
 //
-// Compiled lengths 32, 64, 128 and 256 run two register-resident stages (radix 8 x 4, 16 x 4,
-// 16 x 8, 16 x 16) on a padded shared layout.  Complex64 lines of 64 and 256 points go further
-// (k_fft_x_sq, k_fft_yz_sq): one thread a butterfly, the first stage read straight from global
-// memory and the second written straight back, so each transform passes through shared memory
-// once.
+// Compiled lengths 32, 128 and 256 run two register-resident stages (radix 8 x 4, 16 x 8,
+// 16 x 16) on a padded shared layout.  The square lengths go further (k_fft_x_sq, k_fft_yz_sq:
+// 64-point lines, and complex64 256-point lines): one thread a butterfly, the first stage read
+// straight from global memory and the second written straight back, so each transform passes
+// through shared memory once.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -276,7 +276,6 @@ __device__ __forceinline__ void fft_stage_ct(const T* X, T* Y, int tl, int ls,
 
 template <int N> struct Plan2;
 template <> struct Plan2<32> { static constexpr int P1 = 8, P2 = 4; };
-template <> struct Plan2<64> { static constexpr int P1 = 16, P2 = 4; };
 template <> struct Plan2<128> { static constexpr int P1 = 16, P2 = 8; };
 template <> struct Plan2<256> { static constexpr int P1 = 16, P2 = 16; };
 
@@ -444,29 +443,28 @@ template <> struct SqRadix<256> { static constexpr int P = 16; };
 
 // The two stages on the thread's butterfly u of its line's buffer Al: stage 1 from x (points
 // u + P q) into the buffer, then stage 2 from the buffer into x (points u + P k).
-template <int N>
-__device__ __forceinline__ void sq_stages(float2 (&x)[SqRadix<N>::P], float2* Al, int u,
-                                          const float2* __restrict__ tw) {
+template <typename T, int N>
+__device__ __forceinline__ void sq_stages(T (&x)[SqRadix<N>::P], T* Al, int u,
+                                          const T* __restrict__ tw) {
   constexpr int P = SqRadix<N>::P;
-  dft_reg<float2, P>(x);
+  dft_reg<T, P>(x);
 #pragma unroll
   for (int k = 0; k < P; ++k) Al[padi(P * u + k)] = x[k];
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < P; ++q) {
-    const float2 val = Al[padi(P * q + u)];
+    const T val = Al[padi(P * q + u)];
     x[q] = (q == 0 || u == 0) ? val : cmul(val, tw[u * q]);
   }
-  dft_reg<float2, P>(x);
+  dft_reg<T, P>(x);
 }
 
 // y and z passes: a tile is TL adjacent x positions (a warp load covers 128-256 contiguous
 // bytes of a row).  Pass 3 (z) runs the diagonal and the inverse transform in the same block.
-template <int AXIS, int N>
+template <typename T, int AXIS, int N>
 __global__ void __launch_bounds__(256) k_fft_yz_sq(const PassArgs a) {
   pdl_enter();
-  using T = float2;
-  using R = float;
+  using R = typename RealT<T>::type;
   constexpr int P = SqRadix<N>::P, TL = 256 / P;
   constexpr int ls = padded_stride<N>();
   extern __shared__ __align__(16) unsigned char fft_smem[];
@@ -490,7 +488,7 @@ __global__ void __launch_bounds__(256) k_fft_yz_sq(const PassArgs a) {
 #pragma unroll
     for (int q = 0; q < P; ++q) x[q] = cconj(x[q]);
   }
-  sq_stages<N>(x, Al, u, tw);
+  sq_stages<T, N>(x, Al, u, tw);
   if (a.kind == PASS_MID) {
     // z lines after the x and y transforms: point (l, e) holds wave numbers (i0 + l, j, e)
     const R* ez = (const R*)a.ez;
@@ -505,7 +503,7 @@ __global__ void __launch_bounds__(256) k_fft_yz_sq(const PassArgs a) {
       x[k] = mk(mlt * x[k].x, -(mlt * x[k].y));  // conj: the inverse transform follows
     }
     __syncthreads();  // every thread has read the buffer
-    sq_stages<N>(x, Al, u, tw);
+    sq_stages<T, N>(x, Al, u, tw);
   }
   if (!valid) return;
   const bool conj_out = a.kind != PASS_FWD;
@@ -517,11 +515,10 @@ __global__ void __launch_bounds__(256) k_fft_yz_sq(const PassArgs a) {
 // x passes: TL whole lines a block, the P lanes of a line's butterflies consecutive (a warp load
 // covers 256 contiguous bytes).  The last pass adds the operator's pointwise part (dg - z) x,
 // its loads issued eight points at a time.
-template <int N>
+template <typename T, int N>
 __global__ void __launch_bounds__(256) k_fft_x_sq(const PassArgs a) {
   pdl_enter();
-  using T = float2;
-  using R = float;
+  using R = typename RealT<T>::type;
   constexpr int P = SqRadix<N>::P, TL = 256 / P;
   constexpr int ls = padded_stride<N>();
   extern __shared__ __align__(16) unsigned char fft_smem[];
@@ -548,7 +545,7 @@ __global__ void __launch_bounds__(256) k_fft_x_sq(const PassArgs a) {
 #pragma unroll
     for (int q = 0; q < P; ++q) x[q] = cconj(x[q]);
   }
-  sq_stages<N>(x, Al, u, tw);  // x[k] = point u + P k
+  sq_stages<T, N>(x, Al, u, tw);  // x[k] = point u + P k
   if (!valid) return;
   const bool conj_out = a.kind != PASS_FWD;
   if (a.kind == PASS_LAST && a.combine) {  // add (dg - z) x at the point
@@ -629,6 +626,21 @@ cudaError_t launch_axis(int axis, dim3 grid, size_t smem, cudaStream_t st, const
   return launch_pdl(k_fft_pass<T, 2, NC>, grid, dim3(FT), smem, st, a);
 }
 
+// One pass of lines of the square length N through k_fft_x_sq / k_fft_yz_sq: TL = 256 / sqrt(N)
+// lines a block of 256 threads.
+template <typename T, int N>
+cudaError_t launch_sq(int axis, const PassArgs& a, cudaStream_t st) {
+  constexpr int TL = 256 / SqRadix<N>::P;
+  const size_t smem = sizeof(T) * (size_t)TL * (size_t)line_stride(N);
+  if (axis == 0) {
+    const dim3 grid((unsigned)(((long long)a.ny * a.nz * a.nvec + TL - 1) / TL));
+    return launch_pdl(k_fft_x_sq<T, N>, grid, dim3(256), smem, st, a);
+  }
+  const dim3 grid((a.nx + TL - 1) / TL, axis == 1 ? a.nz : a.ny, a.nvec);
+  if (axis == 1) return launch_pdl(k_fft_yz_sq<T, 1, N>, grid, dim3(256), smem, st, a);
+  return launch_pdl(k_fft_yz_sq<T, 2, N>, grid, dim3(256), smem, st, a);
+}
+
 template <typename T>
 cudaError_t run_pass(int axis, PassArgs a, const SpecPlan& sp, cudaStream_t st) {
   const FftAxis& ax = sp.ax[axis];
@@ -646,24 +658,13 @@ cudaError_t run_pass(int axis, PassArgs a, const SpecPlan& sp, cudaStream_t st) 
   a.tw = tw_of<T>(ax);
   a.tl = tile_lines(ax.n, axis, sizeof(T));
   a.tlsh = ilog2_exact(a.tl);
-  size_t smem = 2 * sizeof(T) * (size_t)a.tl * (size_t)line_stride(ax.n);
+  const size_t smem = 2 * sizeof(T) * (size_t)a.tl * (size_t)line_stride(ax.n);
   count_launch();
-  if (sizeof(T) == 8 && (ax.n == 64 || ax.n == 256)) {
-    // complex64 lines of a square length: TL = 256 / sqrt(n) lines a block, stages through
-    // registers, one shared buffer
-    const int P = ax.n == 64 ? 8 : 16, TL = 256 / P;
-    smem = sizeof(T) * (size_t)TL * (size_t)line_stride(ax.n);
-    if (axis == 0) {
-      const dim3 grid((unsigned)(((long long)a.ny * a.nz * a.nvec + TL - 1) / TL));
-      return ax.n == 64 ? launch_pdl(k_fft_x_sq<64>, grid, dim3(256), smem, st, a)
-                        : launch_pdl(k_fft_x_sq<256>, grid, dim3(256), smem, st, a);
-    }
-    const dim3 grid((a.nx + TL - 1) / TL, axis == 1 ? a.nz : a.ny, a.nvec);
-    if (ax.n == 64)
-      return axis == 1 ? launch_pdl(k_fft_yz_sq<1, 64>, grid, dim3(256), smem, st, a)
-                       : launch_pdl(k_fft_yz_sq<2, 64>, grid, dim3(256), smem, st, a);
-    return axis == 1 ? launch_pdl(k_fft_yz_sq<1, 256>, grid, dim3(256), smem, st, a)
-                     : launch_pdl(k_fft_yz_sq<2, 256>, grid, dim3(256), smem, st, a);
+  // lines of a square length run the register-staged kernels (their one shared buffer is at
+  // most 35 KB: complex64 256-point, complex128 64-point lines)
+  if (ax.n == 64) return launch_sq<T, 64>(axis, a, st);
+  if constexpr (sizeof(T) == 8) {
+    if (ax.n == 256) return launch_sq<T, 256>(axis, a, st);
   }
   dim3 grid;
   if (axis == 0) {
@@ -674,7 +675,6 @@ cudaError_t run_pass(int axis, PassArgs a, const SpecPlan& sp, cudaStream_t st) 
   }
   switch (ax.n) {
     case 32: return launch_axis<T, 32>(axis, grid, smem, st, a);
-    case 64: return launch_axis<T, 64>(axis, grid, smem, st, a);
     case 128: return launch_axis<T, 128>(axis, grid, smem, st, a);
     case 256: return launch_axis<T, 256>(axis, grid, smem, st, a);
     default: return launch_axis<T, 0>(axis, grid, smem, st, a);
@@ -786,7 +786,6 @@ template <typename T>
 cudaError_t fft_attrs() {
   cudaError_t e = fft_attr<T, 0>();
   if (e == cudaSuccess) e = fft_attr<T, 32>();
-  if (e == cudaSuccess) e = fft_attr<T, 64>();
   if (e == cudaSuccess) e = fft_attr<T, 128>();
   if (e == cudaSuccess) e = fft_attr<T, 256>();
   return e;
